@@ -1,0 +1,369 @@
+"""Benchmark: tokens per second of one full WarpLDA MH sweep (document phase +
+word phase) on a synthetic LDA corpus shaped like NYTimes (D=300K, V=100K,
+~99M tokens, K=1,000, M=2), with the HBM roofline of the dominant kernel and
+of the whole sweep, the CPU oracle as the reported baseline, and the
+end-to-end throughput through the C ABI from host buffers.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload nytimes|pubmed|tiny]
+  python bench.py --impl reference ...   (the CPU oracle on the same workload)
+
+One "step" is one sweep.  Prints one JSON line (rank 0).  With N > 1
+(torchrun) every rank samples an independent replica of the workload on its
+own GPU (the sampler has no cross-GPU exchange on this path); `value` is the
+total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "tokens/sec per MH sweep"
+UNIT = "tokens/s"
+FALLBACK_HBM_GBS = 6800.0
+
+# algorithmic HBM bytes per token of each kernel class (int32 values):
+# the document phase reads perm (4) and z + M proposals (4(M+1)) and writes
+# them back (4(M+1)); the word phase reads and writes z + M proposals; the
+# multi-pass tier splits the same traffic over its passes.
+def alg_bytes_per_token(kind: str, M: int) -> float:
+    return {
+        "doc_batch": 4 + 8 * (M + 1),
+        "word_batch": 8 * (M + 1),
+        "word_mega_hist": 4,
+        "word_mega_accept": 4 * (M + 1) + 4,
+        "word_mega_draw": 4 * M,
+        "doc_huge_hist": 8,
+        "doc_huge_accept": 4 + 4 * (M + 1) + 4,
+        "doc_huge_draw": 4 + 4 * M,
+    }.get(kind, 0.0)
+
+
+def sweep_alg_bytes(M: int) -> int:
+    return 20 + 16 * M
+
+
+def measured_peaks() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def csrc_fingerprint() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1510_08628_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu capture of the current
+    kernel sources, or None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    e = rec.get(workload, {}).get(kernel)
+    if not e or e.get("csrc") != csrc_fingerprint():
+        return None
+    return e.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not getattr(self, "out", ""):
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def reduce_max(x: float, ws: int) -> float:
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_rate(c, wl, seed: int, sweeps: int, warm: int = 0):
+    """Tokens/s of the CPU oracle over `sweeps` sweeps of corpus c."""
+    import oracle
+    o = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, seed)
+    if warm:
+        o.sweep(warm)
+    t = time.perf_counter()
+    o.sweep(sweeps)
+    dt = time.perf_counter() - t
+    return c.N * sweeps / dt, oracle.num_threads(), dt
+
+
+def sample_docs(name: str) -> int | None:
+    return {"nytimes": 60_000, "pubmed": 600_000, "tiny": None}.get(name)
+
+
+def run_reference(args, ws, rank):
+    from paper_1510_08628_gb300 import corpus
+    if rank != 0:
+        return
+    nd = sample_docs(args.workload)
+    c, wl = corpus.generate(args.workload, seed=args.corpus_seed, D=nd)
+    import oracle
+    o = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, args.seed)
+    o.sweep(args.warmup)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        o.sweep(1)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = c.N * args.steps / total
+    sample = (f"first {c.D} documents ({c.N} tokens) of the {args.workload} corpus, "
+              f"full sweeps" if nd else f"{args.workload} corpus, full sweeps")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "K": wl.K, "M": wl.M, "N": c.N, "D": c.D,
+                   "V": c.V, "sampler": "CPU oracle (plain C, OpenMP)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="nytimes")
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--corpus-seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        if args.impl == "reference":
+            dist.init_process_group("gloo")
+        else:
+            import torch
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import torch
+
+    from paper_1510_08628_gb300 import corpus
+    from paper_1510_08628_gb300.warplda import WarpLDA
+
+    assert torch.cuda.is_available(), "the native arm needs a GPU"
+    torch.cuda.set_device(local)
+
+    # CPU baseline first (before any GPU work): the oracle on a bounded sample
+    cpu_base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        nd = sample_docs(args.workload)
+        cs, wls = corpus.generate(args.workload, seed=args.corpus_seed, D=nd)
+        rate, cores, dt = oracle_rate(cs, wls, args.seed, sweeps=2)
+        cpu_base = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                    "sample": f"2 full sweeps of the first {cs.D} documents ({cs.N} tokens) of "
+                              f"the {args.workload} corpus ({dt:.1f} s)"}
+        del cs
+
+    c, wl = corpus.generate(args.workload, seed=args.corpus_seed)
+    seed = args.seed + 1000 * rank
+    stream = torch.cuda.current_stream()
+    gpu = WarpLDA(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, seed, stream=stream)
+    info = gpu.info()
+    gpu.sweep(args.warmup)
+    torch.cuda.synchronize()
+
+    # timed region: K sweeps on the library's stream
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        start.record(stream)
+        gpu.sweep(args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+    ms = start.elapsed_time(stop)
+    ms_max = reduce_max(ms, ws)
+    value = c.N * args.steps * ws / (ms_max / 1000.0)
+
+    # per-kernel CUDA-event timing (a second timed pass, events on the same stream)
+    gpu.profile(True)
+    gpu.sweep(args.steps)
+    kt = gpu.kernel_times()
+    gpu.profile(False)
+    peak, peak_kind = measured_peaks()
+    tier_tokens = {
+        "doc_batch": c.N - info["huge_doc_tokens"], "word_batch": c.N - info["mega_word_tokens"],
+        "word_mega_hist": info["mega_word_tokens"], "word_mega_accept": info["mega_word_tokens"],
+        "word_mega_draw": info["mega_word_tokens"], "doc_huge_hist": info["huge_doc_tokens"],
+        "doc_huge_accept": info["huge_doc_tokens"], "doc_huge_draw": info["huge_doc_tokens"],
+    }
+    kernels = {}
+    for k, (n, tot) in kt.items():
+        avg = tot / n
+        alg = alg_bytes_per_token(k, wl.M) * tier_tokens.get(k, 0)
+        kernels[k] = {"launches": n, "avg_ms": avg, "share": None,
+                      "alg_bytes": alg, "gbs": (alg / (avg / 1000) / 1e9) if alg else None}
+    total_k = sum(v["avg_ms"] * v["launches"] for v in kernels.values())
+    for v in kernels.values():
+        v["share"] = v["avg_ms"] * v["launches"] / total_k if total_k else None
+    dom = max((k for k in kernels if kernels[k]["alg_bytes"]), key=lambda k: kernels[k]["avg_ms"] *
+              kernels[k]["launches"])
+    d = kernels[dom]
+    sweep_s = ms / 1000.0 / args.steps
+    sweep_gbs = sweep_alg_bytes(wl.M) * c.N / sweep_s / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": d["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": d["gbs"] / peak, "peak_source": f"{peak_kind} hbm_gbs",
+            "traffic": recorded_traffic(dom, args.workload),
+            "alg_bytes_per_launch": d["alg_bytes"]}
+
+    # end to end through the C ABI from pinned host buffers: init (H2D of the
+    # corpus, token-order build) + K sweeps + D2H of z and c_k
+    e2e = None
+    if not args.no_e2e:
+        dp = torch.from_numpy(c.doc_ptr).pin_memory().numpy()
+        dw = torch.from_numpy(c.doc_word).pin_memory().numpy()
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        g2 = WarpLDA(dp, dw, c.V, wl.K, wl.alpha, wl.beta, wl.M, seed, stream=stream)
+        g2.sweep(args.steps)
+        z, ck = g2.counts()
+        t1 = time.perf_counter()
+        g2.close()
+        e2e_s = reduce_max(t1 - t0, ws)
+        e2e = {"value": c.N * args.steps * ws / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int((dp.nbytes + dw.nbytes) / args.steps),
+               "d2h_bytes_per_step": int((z.nbytes + ck.nbytes) / args.steps),
+               "seconds": e2e_s, "includes": "init (host token-order build + H2D) + sweeps + "
+                                             "D2H of z and c_k"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "D": c.D, "V": c.V, "N": c.N, "K": wl.K,
+                       "M": wl.M, "alpha": wl.alpha, "beta": wl.beta,
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "l2": f"inputs larger than L2 (state {info['device_bytes'] / 1e9:.2f} GB)",
+                       "accept_arith": "FP32 RN, no FMA"},
+            "roofline": roof,
+            "sweep_roofline": {"alg_bytes_per_token": sweep_alg_bytes(wl.M), "achieved": sweep_gbs,
+                               "peak": peak, "unit": "GB/s", "frac": sweep_gbs / peak},
+            "kernels": kernels,
+            "cpu_baseline": cpu_base,
+            "e2e": e2e,
+            "gpu_launches": info["launches_per_sweep"] * args.steps,
+            "clocks": clk.summary(),
+            "paper_context": {"value": 110e6, "unit": UNIT,
+                              "hardware": "2x Xeon E5-2692v2 (24 cores), NYTimes/PubMed, M=2"},
+        }
+        print(json.dumps(line), flush=True)
+    gpu.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

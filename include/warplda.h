@@ -1,0 +1,186 @@
+/*
+ * warplda.h -- C ABI of the GB300 WarpLDA sampler (libwarplda.so).
+ *
+ * The library implements the hot path of WarpLDA (Chen et al., arXiv
+ * 1510.08628): the O(1) Metropolis-Hastings sweep over all tokens, one
+ * document phase followed by one word phase (Sec. 4.4), sampling the MCEM
+ * E-step target of Eq. 5 with the proposals of Eq. 6 and the acceptance rates
+ * of Eq. 7, as in the appendix algorithm (Alg. 2).  All of it runs in CUDA
+ * kernels for sm_103a on one GPU; there is no CPU fallback.
+ *
+ * Conventions
+ *  - Every call returns WARPLDA_OK (0) or a negative WARPLDA_E* code; the
+ *    message of the last failure on the calling thread is warplda_last_error().
+ *  - Host pointers are plain host memory (pageable or pinned); "_dev" calls
+ *    take device pointers of the context's device.  Inputs are copied; the
+ *    caller keeps ownership of every buffer it passes.  Outputs are
+ *    caller-allocated.
+ *  - The context owns all device state.  Its work is issued on the stream
+ *    given to warplda_init (NULL = the legacy default stream).  Calls that
+ *    write host buffers synchronise that stream; warplda_sweep and the _dev
+ *    calls do not.
+ *  - Index types: document and word ids are int32; token counts int64 at the
+ *    boundary.  N must be below 2^31.
+ *  - Random numbers: Philox4x32-10 keyed by the 64-bit seed, counter
+ *    (token's word-major index, iteration, phase << 8 | MH step, stream), so
+ *    results do not depend on the launch configuration.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef WARPLDA_H
+#define WARPLDA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WARPLDA_OK 0
+#define WARPLDA_EINVAL (-1)    /* bad argument or corpus */
+#define WARPLDA_ENOMEM (-2)    /* device or host allocation failed */
+#define WARPLDA_ECUDA (-3)     /* a CUDA call or kernel failed */
+#define WARPLDA_ETIMEDOUT (-4) /* a bounded device wait gave up */
+#define WARPLDA_ESTATE (-5)    /* call not valid in the context's state */
+#define WARPLDA_EIO (-6)       /* checkpoint file could not be read or written */
+
+#define WARPLDA_PHASE_DOC 1
+#define WARPLDA_PHASE_WORD 2
+
+typedef struct warplda_ctx warplda_ctx;
+
+/*
+ * Launch tuning.  Any field left 0 takes its default.  Results are identical
+ * for every valid tuning (the random stream is keyed by token, not by
+ * schedule); the fields only move segments between kernel tiers.
+ *   batch_max_tokens  documents / words with at most this many tokens are
+ *                     processed on chip, several per thread block (<= 4095).
+ *   huge_chunk        tokens per thread-block chunk for longer segments.
+ *   region_budget     32-bit words of shared memory for the per-segment
+ *                     count tables of one block batch.
+ */
+typedef struct warplda_tuning {
+    int32_t batch_max_tokens;
+    int32_t huge_chunk;
+    int32_t region_budget;
+    int32_t reserved[5];
+} warplda_tuning;
+
+/*
+ * warplda_init -- build the device state for a corpus (Sec. 2.1 problem
+ * statement: W, K, alpha, beta; Sec. 4.3: M proposals per token).
+ *   out        receives the new context.
+ *   D, V, N    documents, vocabulary size, tokens (N == doc_ptr[D] < 2^31).
+ *   doc_ptr    host int64[D+1], doc_ptr[0] = 0, non-decreasing: token CSR by
+ *              document.  Empty documents are allowed.
+ *   doc_word   host int32[N], word id in [0, V) of each token, in document
+ *              order.  Empty words are allowed.
+ *   K          topics, 1 <= K <= 16384.
+ *   alpha      symmetric document Dirichlet parameter (> 0, FP32; the paper's
+ *              alpha after its alpha' - 1 shift, Sec. 4.2).
+ *   beta       symmetric word Dirichlet parameter (> 0, FP32).
+ *   M          MH steps (proposals) per token per phase, 1 <= M <= 4.
+ *   seed       Philox key.
+ *   cuda_stream  cudaStream_t for all work of this context, or NULL.
+ *   tuning     NULL for defaults.
+ * Initialises z = Dice(K) per token and every proposal to z (Alg. 2), and
+ * c_k = histogram of z.  Errors: EINVAL (bad sizes, CSR, word id, K, M,
+ * alpha, beta), ENOMEM, ECUDA.  On error *out is NULL.
+ */
+int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64_t* doc_ptr,
+                 const int32_t* doc_word, int32_t K, float alpha, float beta, int32_t M,
+                 uint64_t seed, void* cuda_stream, const warplda_tuning* tuning);
+
+/*
+ * warplda_sweep -- run n full sweeps (document phase then word phase each,
+ * Sec. 4.4; counts refreshed only at phase boundaries, c_k reduced once per
+ * phase).  Asynchronous on the context's stream; n >= 0.  Errors: EINVAL,
+ * ESTATE (a single phase is pending, see warplda_phase), ECUDA (launch error).
+ */
+int warplda_sweep(warplda_ctx* ctx, int32_t n);
+
+/*
+ * warplda_phase -- run one phase of the next sweep: WARPLDA_PHASE_DOC, then
+ * WARPLDA_PHASE_WORD (which completes the sweep).  For tests and tracing.
+ * Errors: EINVAL (unknown phase), ESTATE (phases out of order), ECUDA.
+ */
+int warplda_phase(warplda_ctx* ctx, int32_t phase);
+
+/*
+ * warplda_counts -- copy results to host buffers (each may be NULL):
+ *   z_docmajor  int32[N], topic of each token in the caller's doc_ptr order.
+ *   ck          int32[K], global topic counts c_k (Sec. 2.1).
+ * Synchronises the stream.  Errors: ECUDA.
+ */
+int warplda_counts(warplda_ctx* ctx, int32_t* z_docmajor, int32_t* ck);
+
+/* As warplda_counts with device pointers; asynchronous on the stream. */
+int warplda_counts_dev(warplda_ctx* ctx, int32_t* z_docmajor_dev, int32_t* ck_dev);
+
+/*
+ * warplda_get_state / warplda_set_state -- the complete sampler state, in
+ * word-major token order (tokens sorted by word, then by their doc_ptr
+ * position): z int32[N], proposals int32[N*M] (token-major, M per token),
+ * c_k int32[K], and the number of completed sweeps.  get_state may be called
+ * between the two phases of a sweep (the state after the document phase).
+ * set_state recomputes c_k from z and checks that every value lies in [0, K);
+ * on a bad value it re-initialises the context and returns EINVAL.  Host
+ * buffers; both synchronise.  Errors: EINVAL, ESTATE (set_state while a
+ * word phase is pending), ECUDA.
+ */
+int warplda_get_state(warplda_ctx* ctx, int32_t* z_wordmajor, int32_t* prop_wordmajor,
+                      int32_t* ck, uint32_t* sweeps_done);
+int warplda_set_state(warplda_ctx* ctx, const int32_t* z_wordmajor, const int32_t* prop_wordmajor,
+                      uint32_t sweeps_done);
+
+/* word_ptr int64[V+1] and perm int32[N] (doc_ptr position -> word-major
+ * index) of the context's token order (Sec. 5.2 layout).  Host buffers. */
+int warplda_token_order(warplda_ctx* ctx, int64_t* word_ptr, int32_t* perm);
+
+/*
+ * warplda_loglik -- joint log-likelihood log p(W, Z | alpha, beta) of Sec. 6.1
+ * in FP64 (zero counts contribute zero; alpha_bar = K alpha and
+ * beta_bar = V beta in double).  Synchronises.  Errors: ECUDA, ESTATE.
+ */
+int warplda_loglik(warplda_ctx* ctx, double* out);
+
+/*
+ * warplda_save / warplda_load -- checkpoint the state of warplda_get_state to
+ * a file and restore it into a context built from the same corpus and
+ * parameters.  Resume is bit-exact.  Errors: EIO, EINVAL (mismatch), ECUDA.
+ */
+int warplda_save(warplda_ctx* ctx, const char* path);
+int warplda_load(warplda_ctx* ctx, const char* path);
+
+/* Per-context statistics for benchmarks (host struct, filled on return). */
+typedef struct warplda_info {
+    int64_t D, V, N;
+    int32_t K, M;
+    int32_t launches_per_sweep;       /* kernels one warplda_sweep(1) launches */
+    int32_t batch_max_tokens;
+    int64_t doc_batches, word_batches;
+    int64_t huge_docs, huge_doc_tokens;
+    int64_t mega_words, mega_word_tokens;
+    int64_t device_bytes;             /* device memory held by the context */
+    int32_t reserved[8];
+} warplda_info;
+int warplda_get_info(warplda_ctx* ctx, warplda_info* out);
+
+/*
+ * Kernel timing for benchmarks.  While enabled, every kernel launch of the
+ * context is bracketed by CUDA events recorded on the context's stream.
+ * warplda_kernel_times synchronises and reports, for up to `cap` kernel
+ * classes, their names, launch counts and total device milliseconds since the
+ * last enable.  Returns the number of classes (>= 0) or an error code.
+ */
+int warplda_profile(warplda_ctx* ctx, int32_t enable);
+int warplda_kernel_times(warplda_ctx* ctx, int32_t cap, const char** names, int64_t* launches,
+                         double* total_ms);
+
+void warplda_destroy(warplda_ctx* ctx);
+const char* warplda_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WARPLDA_H */

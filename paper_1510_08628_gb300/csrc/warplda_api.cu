@@ -1,0 +1,652 @@
+// C ABI of libwarplda.so (include/warplda.h): device state, the host-side
+// token-order build at initialisation (Sec. 5.2 layout: word-major store plus
+// the doc-major pointer array perm), work lists, and the per-phase launch
+// sequence of the sweep (Sec. 4.4).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/warplda.h"
+#include "wl_kernels.h"
+
+using namespace wl;
+
+namespace {
+
+thread_local std::string g_err;
+
+int64_t r4(int64_t x) { return (x + 3) & ~(int64_t)3; }
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? WARPLDA_ENOMEM : WARPLDA_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define WL_CU(call, what)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
+    } while (0)
+
+enum KernelClass {
+    kcDocBatch, kcDocHugeHist, kcDocHugeAccept, kcDocHugeDraw,
+    kcWordBatch, kcWordMegaHist, kcWordMegaAccept, kcWordMegaDraw,
+    kcFinalize, kcZero, kcCount
+};
+const char* kClassNames[kcCount] = {
+    "doc_batch", "doc_huge_hist", "doc_huge_accept", "doc_huge_draw",
+    "word_batch", "word_mega_hist", "word_mega_accept", "word_mega_draw",
+    "finalize_ck", "zero_rows"};
+
+struct Rec {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+struct Tier {
+    std::vector<int2> batches;       // [first segment, end segment)
+    std::vector<int4> chunks;        // {row, segment, first position, count}
+    int64_t nrows = 0, row_tokens = 0;
+    int2* d_batches = nullptr;
+    int4* d_chunks = nullptr;
+};
+
+}  // namespace
+
+struct warplda_ctx {
+    int64_t D = 0, V = 0, N = 0;
+    int K = 0, M = 0;
+    float alpha = 0, beta = 0, abar = 0, bbar = 0, kbeta = 0;
+    uint64_t seed = 0;
+    uint32_t k0 = 0, k1 = 0;
+    uint32_t iter = 0;
+    int doc_done = 0;
+    cudaStream_t st = nullptr;
+    int dev = 0, sms = 0;
+    int tpt = 16, bmax = 0, region_words = 0, chunk = 0, stage_ck = 0, kbits = 0;
+    int32_t *z = nullptr, *prop = nullptr, *perm = nullptr, *doc_off = nullptr, *word_off = nullptr;
+    int32_t *ck = nullptr, *counters = nullptr, *rows = nullptr, *scratch = nullptr;
+    float* ckb = nullptr;
+    double* d_ll = nullptr;
+    int32_t* d_bad = nullptr;
+    int32_t *rows_doc = nullptr, *rows_pre = nullptr, *rows_post = nullptr;
+    int64_t rows_words = 0;
+    Tier docs, words;
+    std::vector<int64_t> word_ptr_h;
+    int grid_doc_batch = 1, grid_word_batch = 1, grid_hist = 1, grid_acc_doc = 1,
+        grid_acc_word = 1, grid_draw = 1;
+    bool prof = false;
+    std::vector<Rec> recs;
+    int64_t device_bytes = 0;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(warplda_ctx* c, T** p, int64_t n, const char* what) {
+    size_t bytes = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
+    bytes = (bytes + 255) & ~(size_t)255;
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    c->allocs.push_back(*p);
+    c->device_bytes += (int64_t)bytes;
+    e = cudaMemsetAsync(*p, 0, bytes, c->st);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return WARPLDA_OK;
+}
+
+void free_all(warplda_ctx* c) {
+    for (auto& r : c->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    c->recs.clear();
+    for (void* p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+}
+
+// Split segments [0, S) with offsets off[] into block batches (at most bmax
+// tokens, kSegsMax segments, region_words table words each) and long
+// segments, which get a count row and token chunks.
+void build_tier(const std::vector<int32_t>& off, int64_t S, int K, int bmax, int region_words,
+                int chunk, Tier* t) {
+    t->batches.clear();
+    t->chunks.clear();
+    t->nrows = 0;
+    t->row_tokens = 0;
+    int cur0 = -1, ntok = 0, nseg = 0, nw = 0;
+    auto close = [&](int end) {
+        if (cur0 >= 0 && end > cur0) t->batches.push_back(make_int2(cur0, end));
+        cur0 = -1;
+        ntok = nseg = nw = 0;
+    };
+    for (int64_t s = 0; s < S; ++s) {
+        const int L = off[s + 1] - off[s];
+        uint32_t w = 0, cap = 0;
+        table_shape((uint32_t)L, (uint32_t)K, &w, &cap);
+        if (L > bmax || (int)w > region_words) {
+            close((int)s);
+            const int row = (int)t->nrows++;
+            t->row_tokens += L;
+            for (int p = off[s]; p < off[s + 1]; p += chunk)
+                t->chunks.push_back(make_int4(row, (int)s, p, std::min(chunk, off[s + 1] - p)));
+            continue;
+        }
+        if (cur0 >= 0 && (ntok + L > bmax || nseg + 1 > kSegsMax || nw + (int)w > region_words))
+            close((int)s);
+        if (cur0 < 0) cur0 = (int)s;
+        ntok += L;
+        nseg += 1;
+        nw += (int)w;
+    }
+    close((int)S);
+}
+
+int launch_rec(warplda_ctx* c, int cls, cudaError_t (*fn)(warplda_ctx*, void*), void* arg) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->prof) {
+        WL_CU(cudaEventCreate(&a), "cudaEventCreate");
+        WL_CU(cudaEventCreate(&b), "cudaEventCreate");
+        WL_CU(cudaEventRecord(a, c->st), "cudaEventRecord");
+    }
+    cudaError_t e = fn(c, arg);
+    if (e != cudaSuccess) return cuda_fail(e, kClassNames[cls]);
+    if (c->prof) {
+        WL_CU(cudaEventRecord(b, c->st), "cudaEventRecord");
+        c->recs.push_back(Rec{cls, a, b});
+    }
+    return WARPLDA_OK;
+}
+
+PhaseArgs phase_args(warplda_ctx* c, bool doc, uint32_t iter) {
+    PhaseArgs a;
+    a.z = c->z;
+    a.prop = c->prop;
+    a.perm = c->perm;
+    a.seg_off = doc ? c->doc_off : c->word_off;
+    a.ckb = c->ckb;
+    a.ck = c->ck;
+    a.K = c->K;
+    a.M = c->M;
+    a.g = doc ? c->alpha : c->beta;
+    a.G = doc ? c->abar : c->kbeta;
+    a.iter = iter;
+    a.k0 = c->k0;
+    a.k1 = c->k1;
+    a.stage_ck = c->stage_ck;
+    return a;
+}
+
+struct PhaseCall {
+    PhaseArgs a;
+    bool doc;
+};
+
+int run_phase(warplda_ctx* c, bool doc) {
+    const uint32_t it = c->iter + 1;
+    PhaseCall pc{phase_args(c, doc, it), doc};
+    Tier& T = doc ? c->docs : c->words;
+    const int nch = (int)T.chunks.size();
+    const int nb = (int)T.batches.size();
+    int rc;
+    if (nch > 0) {
+        rc = launch_rec(c, kcZero, [](warplda_ctx* cc, void* p) {
+            const bool d = ((PhaseCall*)p)->doc;
+            return d ? launch_zero(cc->rows_doc, r4(cc->docs.nrows * (int64_t)cc->K), cc->st)
+                     : launch_zero(cc->rows_pre, 2 * r4(cc->words.nrows * (int64_t)cc->K), cc->st);
+        }, &pc);
+        if (rc) return rc;
+        rc = launch_rec(c, doc ? kcDocHugeHist : kcWordMegaHist, [](warplda_ctx* cc, void* p) {
+            PhaseCall* q = (PhaseCall*)p;
+            Tier& TT = q->doc ? cc->docs : cc->words;
+            return launch_huge_hist(q->doc, q->a, TT.d_chunks, (int)TT.chunks.size(),
+                                    q->doc ? cc->rows_doc : cc->rows_pre, cc->grid_hist, cc->st);
+        }, &pc);
+        if (rc) return rc;
+    }
+    if (nb > 0) {
+        rc = launch_rec(c, doc ? kcDocBatch : kcWordBatch, [](warplda_ctx* cc, void* p) {
+            PhaseCall* q = (PhaseCall*)p;
+            Tier& TT = q->doc ? cc->docs : cc->words;
+            return launch_batch_phase(q->doc, cc->tpt, q->a, TT.d_batches, (int)TT.batches.size(),
+                                      cc->counters + (q->doc ? 0 : 1), cc->region_words, cc->kbits,
+                                      q->doc ? cc->grid_doc_batch : cc->grid_word_batch, cc->st);
+        }, &pc);
+        if (rc) return rc;
+    }
+    if (nch > 0) {
+        rc = launch_rec(c, doc ? kcDocHugeAccept : kcWordMegaAccept, [](warplda_ctx* cc, void* p) {
+            PhaseCall* q = (PhaseCall*)p;
+            Tier& TT = q->doc ? cc->docs : cc->words;
+            return launch_huge_accept(q->doc, q->a, TT.d_chunks, (int)TT.chunks.size(),
+                                      q->doc ? cc->rows_doc : cc->rows_pre, cc->rows_post,
+                                      q->doc ? cc->grid_acc_doc : cc->grid_acc_word, cc->st);
+        }, &pc);
+        if (rc) return rc;
+        rc = launch_rec(c, doc ? kcDocHugeDraw : kcWordMegaDraw, [](warplda_ctx* cc, void* p) {
+            PhaseCall* q = (PhaseCall*)p;
+            Tier& TT = q->doc ? cc->docs : cc->words;
+            return launch_huge_draw(q->doc, q->a, TT.d_chunks, (int)TT.chunks.size(),
+                                    cc->rows_post, cc->grid_draw, cc->st);
+        }, &pc);
+        if (rc) return rc;
+    }
+    rc = launch_rec(c, kcFinalize, [](warplda_ctx* cc, void*) {
+        return launch_finalize_ck(cc->ck, cc->ckb, cc->K, cc->bbar, cc->counters, 2, cc->st);
+    }, nullptr);
+    if (rc) return rc;
+    if (doc) {
+        c->doc_done = 1;
+    } else {
+        c->doc_done = 0;
+        c->iter = it;
+    }
+    return WARPLDA_OK;
+}
+
+int launches_per_phase(const warplda_ctx* c, bool doc) {
+    const Tier& T = doc ? c->docs : c->words;
+    return (T.chunks.empty() ? 0 : 4) + (T.batches.empty() ? 0 : 1) + 1;
+}
+
+int recount(warplda_ctx* c) {
+    WL_CU(launch_topic_hist(c->z, c->N, c->ck, c->K, c->st), "topic histogram");
+    WL_CU(launch_finalize_ck(c->ck, c->ckb, c->K, c->bbar, c->counters, 2, c->st), "finalize c_k");
+    return WARPLDA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* warplda_last_error(void) { return g_err.c_str(); }
+
+int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64_t* doc_ptr,
+                 const int32_t* doc_word, int32_t K, float alpha, float beta, int32_t M,
+                 uint64_t seed, void* cuda_stream, const warplda_tuning* tuning) {
+    if (!out) return fail(WARPLDA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (D < 0 || V < 1) return fail(WARPLDA_EINVAL, "need D >= 0 and V >= 1");
+    if (N < 0 || N > (int64_t)0x7FFFFFF0) return fail(WARPLDA_EINVAL, "N must be in [0, 2^31 - 16]");
+    if (V > (int64_t)0x7FFFFFF0 || D > (int64_t)0x7FFFFFF0) return fail(WARPLDA_EINVAL, "D, V too large");
+    if (K < 1 || K > 16384) return fail(WARPLDA_EINVAL, "K must be in [1, 16384]");
+    if (M < 1 || M > 4) return fail(WARPLDA_EINVAL, "M must be in [1, 4]");
+    if (!(alpha > 0.0f) || !std::isfinite(alpha)) return fail(WARPLDA_EINVAL, "alpha must be > 0");
+    if (!(beta > 0.0f) || !std::isfinite(beta)) return fail(WARPLDA_EINVAL, "beta must be > 0");
+    if (!doc_ptr || (N > 0 && !doc_word)) return fail(WARPLDA_EINVAL, "null corpus pointer");
+    if (doc_ptr[0] != 0 || doc_ptr[D] != N) return fail(WARPLDA_EINVAL, "doc_ptr must run from 0 to N");
+    for (int64_t d = 0; d < D; ++d)
+        if (doc_ptr[d + 1] < doc_ptr[d]) return fail(WARPLDA_EINVAL, "doc_ptr decreases at %lld", (long long)d);
+    std::vector<int64_t> wcount(V + 1, 0);
+    for (int64_t p = 0; p < N; ++p) {
+        const int32_t w = doc_word[p];
+        if (w < 0 || (int64_t)w >= V) return fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", w, (long long)p);
+        wcount[w + 1] += 1;
+    }
+
+    warplda_ctx* c = new warplda_ctx();
+    c->D = D; c->V = V; c->N = N; c->K = K; c->M = M;
+    c->alpha = alpha; c->beta = beta;
+    c->abar = (float)K * alpha;   // one FP32 product each
+    c->bbar = (float)V * beta;
+    c->kbeta = (float)K * beta;
+    c->seed = seed;
+    c->k0 = (uint32_t)seed;
+    c->k1 = (uint32_t)(seed >> 32);
+    c->st = (cudaStream_t)cuda_stream;
+    c->stage_ck = K <= 4096 ? 1 : 0;
+    while ((1 << c->kbits) < K) ++c->kbits;
+    c->tpt = 16;
+    int bmax = (tuning && tuning->batch_max_tokens > 0) ? tuning->batch_max_tokens : kMaxBatchTokens;
+    c->chunk = (tuning && tuning->huge_chunk > 0) ? tuning->huge_chunk : 16384;
+    c->region_words = (tuning && tuning->region_budget > 0) ? tuning->region_budget : 8192;
+    c->region_words = (c->region_words + 3) & ~3;
+    if (bmax <= kThreads * 8 - 3) c->tpt = 8;
+    bmax = std::min(bmax, std::min(kMaxBatchTokens, kThreads * c->tpt - 3));
+    c->bmax = bmax;
+
+    auto bail = [&](int rc) {
+        free_all(c);
+        delete c;
+        return rc;
+    };
+    cudaError_t e = cudaGetDevice(&c->dev);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
+    e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
+
+    // word-major order: stable counting sort of the tokens by word (Sec. 5.2)
+    std::vector<int32_t> doc_off(D + 1), word_off(V + 1), perm((size_t)N + 4, 0);
+    for (int64_t d = 0; d <= D; ++d) doc_off[d] = (int32_t)doc_ptr[d];
+    c->word_ptr_h.assign(V + 1, 0);
+    for (int64_t w = 0; w < V; ++w) c->word_ptr_h[w + 1] = c->word_ptr_h[w] + wcount[w + 1];
+    for (int64_t w = 0; w <= V; ++w) word_off[w] = (int32_t)c->word_ptr_h[w];
+    {
+        std::vector<int64_t> fill(c->word_ptr_h.begin(), c->word_ptr_h.end() - 1);
+        for (int64_t p = 0; p < N; ++p) perm[p] = (int32_t)(fill[doc_word[p]]++);
+    }
+    build_tier(doc_off, D, K, bmax, c->region_words, c->chunk, &c->docs);
+    build_tier(word_off, V, K, bmax, c->region_words, c->chunk, &c->words);
+
+    int rc;
+    if ((rc = dalloc(c, &c->z, N + 4, "alloc z"))) return bail(rc);
+    if ((rc = dalloc(c, &c->prop, (N + 4) * M, "alloc proposals"))) return bail(rc);
+    if ((rc = dalloc(c, &c->perm, N + 4, "alloc perm"))) return bail(rc);
+    if ((rc = dalloc(c, &c->doc_off, D + 1, "alloc doc offsets"))) return bail(rc);
+    if ((rc = dalloc(c, &c->word_off, V + 1, "alloc word offsets"))) return bail(rc);
+    if ((rc = dalloc(c, &c->ck, K, "alloc c_k"))) return bail(rc);
+    if ((rc = dalloc(c, &c->ckb, K, "alloc c_k float"))) return bail(rc);
+    if ((rc = dalloc(c, &c->counters, 4, "alloc counters"))) return bail(rc);
+    if ((rc = dalloc(c, &c->d_ll, 1, "alloc loglik"))) return bail(rc);
+    if ((rc = dalloc(c, &c->d_bad, 1, "alloc flag"))) return bail(rc);
+    // count rows of the multi-pass tier; each row set starts 16-byte aligned
+    // and is zeroed in whole int4 units
+    const int64_t rd = r4(c->docs.nrows * (int64_t)K), rw = r4(c->words.nrows * (int64_t)K);
+    c->rows_words = rd + 2 * rw + 4;
+    if ((rc = dalloc(c, &c->rows, c->rows_words, "alloc count rows"))) return bail(rc);
+    c->rows_doc = c->rows;
+    c->rows_pre = c->rows + rd;
+    c->rows_post = c->rows_pre + rw;
+    for (Tier* t : {&c->docs, &c->words}) {
+        if ((rc = dalloc(c, &t->d_batches, (int64_t)t->batches.size(), "alloc batches"))) return bail(rc);
+        if ((rc = dalloc(c, &t->d_chunks, (int64_t)t->chunks.size(), "alloc chunks"))) return bail(rc);
+        if (!t->batches.empty())
+            if ((e = cudaMemcpyAsync(t->d_batches, t->batches.data(), t->batches.size() * sizeof(int2),
+                                     cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+                return bail(cuda_fail(e, "upload batches"));
+        if (!t->chunks.empty())
+            if ((e = cudaMemcpyAsync(t->d_chunks, t->chunks.data(), t->chunks.size() * sizeof(int4),
+                                     cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+                return bail(cuda_fail(e, "upload chunks"));
+    }
+    if ((e = cudaMemcpyAsync(c->perm, perm.data(), ((size_t)N + 4) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+        return bail(cuda_fail(e, "upload perm"));
+    if ((e = cudaMemcpyAsync(c->doc_off, doc_off.data(), (D + 1) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+        return bail(cuda_fail(e, "upload doc offsets"));
+    if ((e = cudaMemcpyAsync(c->word_off, word_off.data(), (V + 1) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+        return bail(cuda_fail(e, "upload word offsets"));
+
+    // grids: persistent blocks, as many as fit
+    auto fit = [&](int per_sm) { return std::max(1, per_sm) * c->sms; };
+    c->grid_doc_batch = std::min<int64_t>(fit(batch_blocks_per_sm(K, c->stage_ck, c->region_words, c->tpt, 0, M)),
+                                          std::max<int64_t>(1, (int64_t)c->docs.batches.size()));
+    c->grid_word_batch = std::min<int64_t>(fit(batch_blocks_per_sm(K, c->stage_ck, c->region_words, c->tpt, 1, M)),
+                                           std::max<int64_t>(1, (int64_t)c->words.batches.size()));
+    c->grid_hist = fit(huge_blocks_per_sm(K, c->stage_ck, 0, false, M));
+    c->grid_acc_doc = fit(huge_blocks_per_sm(K, c->stage_ck, 1, true, M));
+    c->grid_acc_word = fit(huge_blocks_per_sm(K, c->stage_ck, 1, false, M));
+    c->grid_draw = fit(huge_blocks_per_sm(K, c->stage_ck, 2, false, M));
+    if (batch_blocks_per_sm(K, c->stage_ck, c->region_words, c->tpt, 0, M) < 1 ||
+        batch_blocks_per_sm(K, c->stage_ck, c->region_words, c->tpt, 1, M) < 1)
+        return bail(fail(WARPLDA_EINVAL, "batch kernel does not fit (region_budget too large?)"));
+
+    // z = Dice(K), proposals = z (Alg. 2); c_k = histogram of z
+    if ((e = launch_init_z(c->z, c->prop, N, K, M, c->k0, c->k1, c->st)) != cudaSuccess)
+        return bail(cuda_fail(e, "init z"));
+    if ((rc = recount(c))) return bail(rc);
+    if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return bail(cuda_fail(e, "init"));
+    *out = c;
+    return WARPLDA_OK;
+}
+
+int warplda_sweep(warplda_ctx* c, int32_t n) {
+    if (!c || n < 0) return fail(WARPLDA_EINVAL, "bad context or n");
+    if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    for (int i = 0; i < n; ++i) {
+        int rc = run_phase(c, true);
+        if (rc) return rc;
+        rc = run_phase(c, false);
+        if (rc) return rc;
+    }
+    return WARPLDA_OK;
+}
+
+int warplda_phase(warplda_ctx* c, int32_t phase) {
+    if (!c) return fail(WARPLDA_EINVAL, "null context");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    if (phase == WARPLDA_PHASE_DOC) {
+        if (c->doc_done) return fail(WARPLDA_ESTATE, "document phase already run");
+        return run_phase(c, true);
+    }
+    if (phase == WARPLDA_PHASE_WORD) {
+        if (!c->doc_done) return fail(WARPLDA_ESTATE, "word phase before document phase");
+        return run_phase(c, false);
+    }
+    return fail(WARPLDA_EINVAL, "unknown phase %d", phase);
+}
+
+static int ensure_scratch(warplda_ctx* c) {
+    if (c->scratch) return WARPLDA_OK;
+    return dalloc(c, &c->scratch, c->N + 4, "alloc export scratch");
+}
+
+int warplda_counts_dev(warplda_ctx* c, int32_t* z_dev, int32_t* ck_dev) {
+    if (!c) return fail(WARPLDA_EINVAL, "null context");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    if (z_dev) WL_CU(launch_gather_docmajor(c->z, c->perm, c->N, z_dev, c->st), "gather z");
+    if (ck_dev) WL_CU(cudaMemcpyAsync(ck_dev, c->ck, (size_t)c->K * 4, cudaMemcpyDeviceToDevice, c->st), "copy c_k");
+    return WARPLDA_OK;
+}
+
+int warplda_counts(warplda_ctx* c, int32_t* z_docmajor, int32_t* ck) {
+    if (!c) return fail(WARPLDA_EINVAL, "null context");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    if (z_docmajor && c->N > 0) {
+        int rc = ensure_scratch(c);
+        if (rc) return rc;
+        WL_CU(launch_gather_docmajor(c->z, c->perm, c->N, c->scratch, c->st), "gather z");
+        WL_CU(cudaMemcpyAsync(z_docmajor, c->scratch, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->st), "copy z");
+    }
+    if (ck) WL_CU(cudaMemcpyAsync(ck, c->ck, (size_t)c->K * 4, cudaMemcpyDeviceToHost, c->st), "copy c_k");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    return WARPLDA_OK;
+}
+
+int warplda_get_state(warplda_ctx* c, int32_t* z, int32_t* prop, int32_t* ck, uint32_t* sweeps) {
+    if (!c) return fail(WARPLDA_EINVAL, "null context");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    if (z && c->N) WL_CU(cudaMemcpyAsync(z, c->z, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->st), "copy z");
+    if (prop && c->N) WL_CU(cudaMemcpyAsync(prop, c->prop, (size_t)c->N * c->M * 4, cudaMemcpyDeviceToHost, c->st), "copy proposals");
+    if (ck) WL_CU(cudaMemcpyAsync(ck, c->ck, (size_t)c->K * 4, cudaMemcpyDeviceToHost, c->st), "copy c_k");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    if (sweeps) *sweeps = c->iter;
+    return WARPLDA_OK;
+}
+
+int warplda_set_state(warplda_ctx* c, const int32_t* z, const int32_t* prop, uint32_t sweeps) {
+    if (!c || (c->N > 0 && (!z || !prop))) return fail(WARPLDA_EINVAL, "null argument");
+    if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    if (c->N) {
+        WL_CU(cudaMemcpyAsync(c->z, z, (size_t)c->N * 4, cudaMemcpyHostToDevice, c->st), "upload z");
+        WL_CU(cudaMemcpyAsync(c->prop, prop, (size_t)c->N * c->M * 4, cudaMemcpyHostToDevice, c->st), "upload proposals");
+    }
+    WL_CU(cudaMemsetAsync(c->d_bad, 0, 4, c->st), "memset");
+    WL_CU(launch_check_range(c->z, c->N, c->K, c->d_bad, c->st), "range check");
+    WL_CU(launch_check_range(c->prop, c->N * c->M, c->K, c->d_bad, c->st), "range check");
+    int32_t bad = 0;
+    WL_CU(cudaMemcpyAsync(&bad, c->d_bad, 4, cudaMemcpyDeviceToHost, c->st), "copy flag");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    if (bad) {
+        // leave a valid state behind: re-initialise
+        WL_CU(launch_init_z(c->z, c->prop, c->N, c->K, c->M, c->k0, c->k1, c->st), "init z");
+        int rc = recount(c);
+        if (rc) return rc;
+        c->iter = 0;
+        WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+        return fail(WARPLDA_EINVAL, "%d values outside [0, K); state re-initialised", bad);
+    }
+    int rc = recount(c);
+    if (rc) return rc;
+    c->iter = sweeps;
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    return WARPLDA_OK;
+}
+
+int warplda_token_order(warplda_ctx* c, int64_t* word_ptr, int32_t* perm) {
+    if (!c) return fail(WARPLDA_EINVAL, "null context");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    if (word_ptr) std::memcpy(word_ptr, c->word_ptr_h.data(), (size_t)(c->V + 1) * 8);
+    if (perm && c->N) {
+        WL_CU(cudaMemcpyAsync(perm, c->perm, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->st), "copy perm");
+        WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    }
+    return WARPLDA_OK;
+}
+
+int warplda_loglik(warplda_ctx* c, double* out) {
+    if (!c || !out) return fail(WARPLDA_EINVAL, "null argument");
+    if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    WL_CU(cudaMemsetAsync(c->d_ll, 0, sizeof(double), c->st), "memset");
+    const double a = c->alpha, b = c->beta;
+    const double abar = (double)c->K * a, bbar = (double)c->V * b;
+    for (int doc = 1; doc >= 0; --doc) {
+        Tier& T = doc ? c->docs : c->words;
+        PhaseArgs pa = phase_args(c, doc, c->iter);
+        int32_t* rows = doc ? c->rows_doc : c->rows_pre;
+        if (!T.chunks.empty()) {
+            WL_CU(launch_zero(rows, r4(T.nrows * (int64_t)c->K), c->st), "zero rows");
+            WL_CU(launch_huge_hist(doc, pa, T.d_chunks, (int)T.chunks.size(), rows, c->grid_hist, c->st), "loglik rows");
+            WL_CU(launch_loglik_rows(rows, T.nrows, c->K, doc ? a : b, c->d_ll, c->st), "loglik rows");
+        }
+        WL_CU(launch_loglik_batches(doc, c->z, c->perm, doc ? c->doc_off : c->word_off, T.d_batches,
+                                    (int)T.batches.size(), c->K, doc ? a : b, c->region_words, c->d_ll,
+                                    c->sms * 2, c->st), "loglik batches");
+    }
+    WL_CU(launch_loglik_lengths(c->doc_off, c->D, abar, c->d_ll, c->st), "loglik lengths");
+    WL_CU(launch_loglik_topics(c->ck, c->K, bbar, c->d_ll, c->st), "loglik topics");
+    WL_CU(cudaMemcpyAsync(out, c->d_ll, sizeof(double), cudaMemcpyDeviceToHost, c->st), "copy loglik");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    return WARPLDA_OK;
+}
+
+struct CkptHeader {
+    char magic[8];
+    int64_t D, V, N;
+    int32_t K, M;
+    float alpha, beta;
+    uint64_t seed;
+    uint32_t iter, pad;
+};
+
+int warplda_save(warplda_ctx* c, const char* path) {
+    if (!c || !path) return fail(WARPLDA_EINVAL, "null argument");
+    std::vector<int32_t> z((size_t)c->N), p((size_t)c->N * c->M);
+    uint32_t it = 0;
+    int rc = warplda_get_state(c, z.data(), p.data(), nullptr, &it);
+    if (rc) return rc;
+    CkptHeader h{};
+    std::memcpy(h.magic, "WARPLDA1", 8);
+    h.D = c->D; h.V = c->V; h.N = c->N; h.K = c->K; h.M = c->M;
+    h.alpha = c->alpha; h.beta = c->beta; h.seed = c->seed; h.iter = it;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(WARPLDA_EIO, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+              std::fwrite(z.data(), 4, z.size(), f) == z.size() &&
+              std::fwrite(p.data(), 4, p.size(), f) == p.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? WARPLDA_OK : fail(WARPLDA_EIO, "write to %s failed", path);
+}
+
+int warplda_load(warplda_ctx* c, const char* path) {
+    if (!c || !path) return fail(WARPLDA_EINVAL, "null argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(WARPLDA_EIO, "cannot open %s", path);
+    CkptHeader h{};
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "WARPLDA1", 8) != 0) {
+        std::fclose(f);
+        return fail(WARPLDA_EIO, "%s is not a checkpoint", path);
+    }
+    if (h.D != c->D || h.V != c->V || h.N != c->N || h.K != c->K || h.M != c->M ||
+        h.alpha != c->alpha || h.beta != c->beta || h.seed != c->seed) {
+        std::fclose(f);
+        return fail(WARPLDA_EINVAL, "checkpoint does not match this context");
+    }
+    std::vector<int32_t> z((size_t)c->N), p((size_t)c->N * c->M);
+    bool ok = std::fread(z.data(), 4, z.size(), f) == z.size() &&
+              std::fread(p.data(), 4, p.size(), f) == p.size();
+    std::fclose(f);
+    if (!ok) return fail(WARPLDA_EIO, "%s is truncated", path);
+    return warplda_set_state(c, z.data(), p.data(), h.iter);
+}
+
+int warplda_get_info(warplda_ctx* c, warplda_info* o) {
+    if (!c || !o) return fail(WARPLDA_EINVAL, "null argument");
+    std::memset(o, 0, sizeof(*o));
+    o->D = c->D; o->V = c->V; o->N = c->N; o->K = c->K; o->M = c->M;
+    o->launches_per_sweep = launches_per_phase(c, true) + launches_per_phase(c, false);
+    o->batch_max_tokens = c->bmax;
+    o->doc_batches = (int64_t)c->docs.batches.size();
+    o->word_batches = (int64_t)c->words.batches.size();
+    o->huge_docs = c->docs.nrows;
+    o->huge_doc_tokens = c->docs.row_tokens;
+    o->mega_words = c->words.nrows;
+    o->mega_word_tokens = c->words.row_tokens;
+    o->device_bytes = c->device_bytes;
+    return WARPLDA_OK;
+}
+
+int warplda_profile(warplda_ctx* c, int32_t enable) {
+    if (!c) return fail(WARPLDA_EINVAL, "null context");
+    for (auto& r : c->recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    c->recs.clear();
+    c->prof = enable != 0;
+    return WARPLDA_OK;
+}
+
+int warplda_kernel_times(warplda_ctx* c, int32_t cap, const char** names, int64_t* launches,
+                         double* total_ms) {
+    if (!c) return fail(WARPLDA_EINVAL, "null context");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    double ms[kcCount] = {0};
+    int64_t n[kcCount] = {0};
+    for (auto& r : c->recs) {
+        float t = 0;
+        WL_CU(cudaEventElapsedTime(&t, r.a, r.b), "cudaEventElapsedTime");
+        ms[r.cls] += t;
+        n[r.cls] += 1;
+    }
+    int k = 0;
+    for (int i = 0; i < kcCount; ++i) {
+        if (n[i] == 0) continue;
+        if (k < cap) {
+            if (names) names[k] = kClassNames[i];
+            if (launches) launches[k] = n[i];
+            if (total_ms) total_ms[k] = ms[i];
+        }
+        ++k;
+    }
+    return k;
+}
+
+void warplda_destroy(warplda_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    cudaStreamSynchronize(c->st);
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,52 @@
+// Host-side launchers of the sampler kernels (internal to libwarplda.so).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "wl_common.cuh"
+
+namespace wl {
+
+// On-chip batch tier (wl_batch.cu).
+int batch_smem_bytes(int K, int stage_ck, int region_words, int tpt, int word_phase);
+int batch_blocks_per_sm(int K, int stage_ck, int region_words, int tpt, int word_phase, int M);
+cudaError_t launch_batch_phase(bool doc, int tpt, const PhaseArgs& a, const int2* batches,
+                               int nbatch, int* counter, int region_words, int kbits, int grid,
+                               cudaStream_t st);
+
+// Multi-pass tier for segments too long for one block (wl_huge.cu).
+// chunk = {row, segment id, first token position, token count}
+int huge_smem_bytes(int K, int stage_ck, int pass, bool doc);
+int huge_blocks_per_sm(int K, int stage_ck, int pass, bool doc, int M);
+cudaError_t launch_huge_hist(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
+                             int32_t* rows, int grid, cudaStream_t st);
+cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
+                               const int32_t* rows_pre, int32_t* rows_post, int grid,
+                               cudaStream_t st);
+cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
+                             const int32_t* rows_post, int grid, cudaStream_t st);
+
+// Initialisation, c_k, export, log-likelihood (wl_misc.cu).
+cudaError_t launch_init_z(int32_t* z, int32_t* prop, int64_t N, int K, int M, uint32_t k0,
+                          uint32_t k1, cudaStream_t st);
+cudaError_t launch_topic_hist(const int32_t* z, int64_t N, int32_t* ck, int K, cudaStream_t st);
+cudaError_t launch_finalize_ck(const int32_t* ck, float* ckb, int K, float beta_bar,
+                               int32_t* counters, int ncounters, cudaStream_t st);
+cudaError_t launch_zero(int32_t* p, int64_t n, cudaStream_t st);
+cudaError_t launch_gather_docmajor(const int32_t* z, const int32_t* perm, int64_t N, int32_t* out,
+                                   cudaStream_t st);
+cudaError_t launch_check_range(const int32_t* v, int64_t n, int K, int32_t* bad, cudaStream_t st);
+cudaError_t launch_loglik_batches(bool doc, const int32_t* z, const int32_t* perm,
+                                  const int32_t* seg_off, const int2* batches, int nbatch, int K,
+                                  double g, int region_words, double* out, int grid,
+                                  cudaStream_t st);
+cudaError_t launch_loglik_rows(const int32_t* rows, int64_t nrows, int K, double g, double* out,
+                               cudaStream_t st);
+cudaError_t launch_loglik_lengths(const int32_t* seg_off, int64_t nseg, double abar, double* out,
+                                  cudaStream_t st);
+cudaError_t launch_loglik_topics(const int32_t* ck, int K, double bbar, double* out,
+                                 cudaStream_t st);
+int loglik_smem_bytes(int region_words);
+
+}  // namespace wl

@@ -1,0 +1,220 @@
+"""Python binding of libwarplda.so (include/warplda.h): argument marshalling only.
+
+Every step of the sampler runs in the library's CUDA kernels; this module
+converts numpy arrays / torch tensors to pointers and return codes to
+exceptions.  There is no CPU fallback: if the library or a GPU is missing the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, ESTATE, EIO = 0, -1, -2, -3, -4, -5, -6
+PHASE_DOC, PHASE_WORD = 1, 2
+
+_LOCK = threading.Lock()
+_LIB = None
+
+
+class WarpLDAError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"warplda error {code}: {msg}")
+        self.code = code
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("batch_max_tokens", ctypes.c_int32), ("huge_chunk", ctypes.c_int32),
+                ("region_budget", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("D", ctypes.c_int64), ("V", ctypes.c_int64), ("N", ctypes.c_int64),
+                ("K", ctypes.c_int32), ("M", ctypes.c_int32),
+                ("launches_per_sweep", ctypes.c_int32), ("batch_max_tokens", ctypes.c_int32),
+                ("doc_batches", ctypes.c_int64), ("word_batches", ctypes.c_int64),
+                ("huge_docs", ctypes.c_int64), ("huge_doc_tokens", ctypes.c_int64),
+                ("mega_words", ctypes.c_int64), ("mega_word_tokens", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+# Symbols declared in include/warplda.h, with their ctypes signatures.
+_P = ctypes.c_void_p
+_SIGS = {
+    "warplda_init": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int64, _P, _P, ctypes.c_int32, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_int32, ctypes.c_uint64, _P, _P]),
+    "warplda_sweep": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "warplda_phase": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "warplda_counts": (ctypes.c_int, [_P, _P, _P]),
+    "warplda_counts_dev": (ctypes.c_int, [_P, _P, _P]),
+    "warplda_get_state": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "warplda_set_state": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32]),
+    "warplda_token_order": (ctypes.c_int, [_P, _P, _P]),
+    "warplda_loglik": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "warplda_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "warplda_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
+    "warplda_get_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    "warplda_profile": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "warplda_kernel_times": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
+                                            ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_double)]),
+    "warplda_destroy": (None, [_P]),
+    "warplda_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libwarplda.so (building it with nvcc if it is missing)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise WarpLDAError(ECUDA, f"{path} not built")
+            path = _build.build()
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = lib
+        return lib
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        msg = load().warplda_last_error()
+        raise WarpLDAError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev_ptr(t) -> int | None:
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+class WarpLDA:
+    """One sampler context (warplda_ctx) on the current CUDA device."""
+
+    def __init__(self, doc_ptr, doc_word, V: int, K: int, alpha: float, beta: float, M: int,
+                 seed: int, stream=None, tuning: dict | None = None):
+        lib = load()
+        self.doc_ptr = np.ascontiguousarray(doc_ptr, dtype=np.int64)
+        doc_word = np.ascontiguousarray(doc_word, dtype=np.int32)
+        self.D = len(self.doc_ptr) - 1
+        self.N = int(self.doc_ptr[-1])
+        self.V, self.K, self.M = int(V), int(K), int(M)
+        tun = None
+        if tuning:
+            tun = Tuning()
+            for k, v in tuning.items():
+                setattr(tun, k, int(v))
+        st = None
+        if stream is not None:
+            st = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        h = ctypes.c_void_p()
+        _check(lib.warplda_init(ctypes.byref(h), self.D, self.V, self.N, _ptr(self.doc_ptr),
+                                _ptr(doc_word), self.K, ctypes.c_float(alpha),
+                                ctypes.c_float(beta), self.M, ctypes.c_uint64(seed & (2**64 - 1)),
+                                st, ctypes.byref(tun) if tun is not None else None))
+        self._h = h
+
+    # -- sampler --------------------------------------------------------------
+    def sweep(self, n: int = 1) -> None:
+        _check(load().warplda_sweep(self._h, int(n)))
+
+    def phase(self, which: int) -> None:
+        _check(load().warplda_phase(self._h, int(which)))
+
+    # -- results --------------------------------------------------------------
+    def counts(self, want_z: bool = True, want_ck: bool = True):
+        z = np.empty(max(self.N, 1), dtype=np.int32) if want_z else None
+        ck = np.empty(self.K, dtype=np.int32) if want_ck else None
+        _check(load().warplda_counts(self._h, _ptr(z), _ptr(ck)))
+        return (z[: self.N] if z is not None else None), ck
+
+    def counts_dev(self, z_dev=None, ck_dev=None) -> None:
+        _check(load().warplda_counts_dev(self._h, _dev_ptr(z_dev), _dev_ptr(ck_dev)))
+
+    def get_state(self):
+        z = np.empty(max(self.N, 1), dtype=np.int32)
+        p = np.empty(max(self.N * self.M, 1), dtype=np.int32)
+        ck = np.empty(self.K, dtype=np.int32)
+        it = ctypes.c_uint32()
+        _check(load().warplda_get_state(self._h, _ptr(z), _ptr(p), _ptr(ck), ctypes.byref(it)))
+        return z[: self.N], p[: self.N * self.M], ck, int(it.value)
+
+    def set_state(self, z, prop, sweeps_done: int) -> None:
+        z = np.ascontiguousarray(z, dtype=np.int32)
+        prop = np.ascontiguousarray(prop, dtype=np.int32)
+        _check(load().warplda_set_state(self._h, _ptr(z), _ptr(prop), int(sweeps_done)))
+
+    def token_order(self):
+        wp = np.empty(self.V + 1, dtype=np.int64)
+        perm = np.empty(max(self.N, 1), dtype=np.int32)
+        _check(load().warplda_token_order(self._h, _ptr(wp), _ptr(perm)))
+        return wp, perm[: self.N]
+
+    def loglik(self) -> float:
+        out = ctypes.c_double()
+        _check(load().warplda_loglik(self._h, ctypes.byref(out)))
+        return float(out.value)
+
+    def save(self, path: str) -> None:
+        _check(load().warplda_save(self._h, path.encode()))
+
+    def load_state(self, path: str) -> None:
+        _check(load().warplda_load(self._h, path.encode()))
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(load().warplda_get_info(self._h, ctypes.byref(inf)))
+        return inf.as_dict()
+
+    def profile(self, enable: bool) -> None:
+        _check(load().warplda_profile(self._h, 1 if enable else 0))
+
+    def kernel_times(self) -> dict:
+        cap = 32
+        names = (ctypes.c_char_p * cap)()
+        launches = (ctypes.c_int64 * cap)()
+        ms = (ctypes.c_double * cap)()
+        n = _check(load().warplda_kernel_times(self._h, cap, names, launches, ms))
+        return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(n, cap))}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().warplda_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,196 @@
+"""GPU sampler against the CPU oracle, through the C ABI.
+
+Bit-exact parity of z, the proposals and c_k (all integer state) after whole
+sweeps and after single phases, on the ``tiny`` workload and on small
+adversarial corpora that reach every kernel tier: empty documents and words,
+K = 1 and 2, hash and dense count tables, documents and words longer than a
+block batch (multi-pass tier), M = 1..4, and launch tunings that move segments
+between tiers.  The log-likelihood (FP64, different summation order) is
+compared at 1e-9 relative.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_08628_gb300 import corpus
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    torch.cuda.set_device(0)
+    from paper_1510_08628_gb300 import warplda
+    warplda.load()
+
+
+def _gpu(c, V, K, alpha, beta, M, seed, tuning=None):
+    from paper_1510_08628_gb300.warplda import WarpLDA
+    return WarpLDA(c.doc_ptr, c.doc_word, V, K, alpha, beta, M, seed, tuning=tuning)
+
+
+def _same_state(gpu, ref, tag=""):
+    z, p, ck, _ = gpu.get_state()
+    N, M = ref.N, ref.M
+    assert np.array_equal(z, ref.z[:N]), f"{tag}: z differs at {np.flatnonzero(z != ref.z[:N])[:10]}"
+    assert np.array_equal(p, ref.prop[: N * M]), f"{tag}: proposals differ"
+    assert np.array_equal(ck, ref.ck), f"{tag}: c_k differs"
+
+
+def test_init_matches_oracle(tiny_corpus):
+    c, wl = tiny_corpus
+    gpu = _gpu(c, c.V, wl.K, wl.alpha, wl.beta, wl.M, 7)
+    ref = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, 7)
+    wp, perm = gpu.token_order()
+    assert np.array_equal(wp, ref.word_ptr) and np.array_equal(perm, ref.perm[: ref.N])
+    _same_state(gpu, ref, "init")
+
+
+def test_tiny_workload_20_sweeps_bit_exact(tiny_corpus):
+    c, wl = tiny_corpus
+    gpu = _gpu(c, c.V, wl.K, wl.alpha, wl.beta, wl.M, 7)
+    ref = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, 7)
+    done = 0
+    for cp in (1, 2, 5, 10, 20):
+        gpu.sweep(cp - done)
+        ref.sweep(cp - done)
+        done = cp
+        _same_state(gpu, ref, f"sweep {cp}")
+        z, ck = gpu.counts()
+        assert np.array_equal(z, ref.z_docmajor())
+    ll, want = gpu.loglik(), ref.loglik()
+    assert abs(ll - want) <= 1e-9 * abs(want)
+
+
+@pytest.mark.parametrize("K,M", [(40, 2), (5, 3), (3000, 1)])
+def test_phase_by_phase(K, M):
+    c, wl = corpus.generate("tiny", seed=3, D=300)
+    gpu = _gpu(c, c.V, K, 0.2, 0.01, M, 21)
+    ref = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, K, 0.2, 0.01, M, 21)
+    for it in range(1, 4):
+        gpu.phase(1)
+        ref.doc_phase(it)
+        ref.recount()
+        z, ck = gpu.counts()
+        assert np.array_equal(z, ref.z_docmajor()), f"doc phase {it}"
+        assert np.array_equal(ck, ref.ck)
+        gpu.phase(2)
+        ref.word_phase(it)
+        ref.recount()
+        ref.iteration = it
+        _same_state(gpu, ref, f"word phase {it}")
+
+
+def _edge_corpus(kind, seed=5):
+    rng = np.random.default_rng(seed)
+    if kind == "empty_segments":
+        lens = [0, 3, 0, 0, 7, 1, 0, 12, 0]
+        c = corpus.from_lengths(lens, V=40, seed=seed)
+        return c
+    if kind == "giant_doc":
+        lens = [5, 9000, 3, 14, 4100, 2]
+        return corpus.from_lengths(lens, V=300, seed=seed)
+    if kind == "giant_word":
+        lens = rng.integers(1, 60, size=600)
+        c = corpus.from_lengths(lens, V=200, seed=seed)
+        w = c.doc_word.copy()
+        w[rng.random(len(w)) < 0.5] = 17          # one word with ~half the tokens
+        return corpus.Corpus(c.doc_ptr, w, 200)
+    if kind == "mixed":
+        lens = np.concatenate([rng.integers(0, 30, size=400), [5000, 4093, 4094, 1]])
+        return corpus.from_lengths(lens, V=500, seed=seed, zipf_s=1.2)
+    raise ValueError(kind)
+
+
+EDGE_CASES = [
+    ("empty_segments", 3, 1), ("empty_segments", 1, 2), ("giant_doc", 2, 2), ("giant_doc", 16, 4),
+    ("giant_word", 30, 2), ("giant_word", 1, 1), ("mixed", 7, 3), ("mixed", 5000, 2),
+    ("mixed", 4097, 1), ("giant_word", 200, 4),
+]
+
+
+@pytest.mark.parametrize("kind,K,M", EDGE_CASES)
+def test_edge_corpora_bit_exact(kind, K, M):
+    c = _edge_corpus(kind)
+    gpu = _gpu(c, c.V, K, 0.3, 0.02, M, 99)
+    ref = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, K, 0.3, 0.02, M, 99)
+    for s in (1, 2, 4):
+        gpu.sweep(1 if s != 4 else 2)
+        ref.sweep(1 if s != 4 else 2)
+        _same_state(gpu, ref, f"{kind} K={K} M={M} sweep {s}")
+    ll, want = gpu.loglik(), ref.loglik()
+    assert abs(ll - want) <= 1e-9 * abs(want)
+
+
+TUNINGS = [None, {"batch_max_tokens": 64}, {"batch_max_tokens": 2000, "region_budget": 1024},
+           {"huge_chunk": 300, "batch_max_tokens": 500}, {"batch_max_tokens": 4095}]
+
+
+def test_schedule_independence():
+    c = _edge_corpus("mixed")
+    states = []
+    for t in TUNINGS:
+        gpu = _gpu(c, c.V, 50, 0.1, 0.01, 2, 5, tuning=t)
+        gpu.sweep(3)
+        states.append(gpu.get_state())
+        gpu.close()
+    for s in states[1:]:
+        for a, b in zip(states[0], s):
+            assert np.array_equal(np.asarray(a), np.asarray(b))
+
+
+def test_save_load_resume_bit_exact(tiny_corpus):
+    c, wl = tiny_corpus
+    a = _gpu(c, c.V, wl.K, wl.alpha, wl.beta, 2, 13)
+    a.sweep(10)
+    b = _gpu(c, c.V, wl.K, wl.alpha, wl.beta, 2, 13)
+    b.sweep(5)
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "ck.bin")
+        b.save(path)
+        b2 = _gpu(c, c.V, wl.K, wl.alpha, wl.beta, 2, 13)
+        b2.load_state(path)
+    b2.sweep(5)
+    for x, y in zip(a.get_state(), b2.get_state()):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_counts_dev_and_bad_state(tiny_corpus):
+    import torch
+    from paper_1510_08628_gb300.warplda import WarpLDAError
+    c, wl = tiny_corpus
+    g = _gpu(c, c.V, wl.K, wl.alpha, wl.beta, wl.M, 3)
+    g.sweep(2)
+    zt = torch.empty(c.N, dtype=torch.int32, device="cuda")
+    ckt = torch.empty(wl.K, dtype=torch.int32, device="cuda")
+    g.counts_dev(zt, ckt)
+    torch.cuda.synchronize()
+    z, ck = g.counts()
+    assert np.array_equal(zt.cpu().numpy(), z) and np.array_equal(ckt.cpu().numpy(), ck)
+    zs, ps, _, it = g.get_state()
+    bad = zs.copy()
+    bad[5] = wl.K
+    with pytest.raises(WarpLDAError):
+        g.set_state(bad, ps, it)
+    g.set_state(zs, ps, it)
+    assert np.array_equal(g.get_state()[0], zs)
+
+
+def test_invalid_arguments_rejected():
+    from paper_1510_08628_gb300.warplda import WarpLDA, WarpLDAError
+    c = corpus.from_lengths([3, 4], V=10, seed=1)
+    for kw in ({"K": 0}, {"K": 20000}, {"M": 0}, {"M": 5}, {"alpha": 0.0}, {"beta": -1.0}):
+        args = dict(K=4, alpha=0.1, beta=0.1, M=1)
+        args.update(kw)
+        with pytest.raises(WarpLDAError):
+            WarpLDA(c.doc_ptr, c.doc_word, 10, args["K"], args["alpha"], args["beta"], args["M"], 1)
+    bad = c.doc_word.copy()
+    bad[0] = 10
+    with pytest.raises(WarpLDAError):
+        WarpLDA(c.doc_ptr, bad, 10, 4, 0.1, 0.1, 1, 1)
