@@ -179,6 +179,37 @@ int warplda_kernel_times(warplda_ctx* ctx, int32_t cap, const char** names, int6
 void warplda_destroy(warplda_ctx* ctx);
 const char* warplda_last_error(void);
 
+/*
+ * warplda_loglik_noalloc -- the joint log-likelihood of warplda_loglik
+ * (same definition and FP64 arithmetic) for callers that cannot allocate
+ * device memory: code inside a host framework that owns every device
+ * allocation (a caching allocator or a fixed arena that forbids raw
+ * cudaMalloc), or a serving process with a fixed device-memory budget.  It
+ * takes no context, because creating one allocates.  The paper has no
+ * counterpart; this is an interface convenience.
+ *   D, V, N     documents, vocabulary size, tokens (N < 2^31).
+ *   K, alpha, beta   as for warplda_init; K must be at most 16384, else
+ *               EINVAL (the scratch below holds that many topic counts).
+ *   doc_ptr_dev     device int64[D+1], token offsets of the documents.
+ *   z_docmajor_dev  device int32[N], topics in document order.
+ *   word_ptr_dev    device int64[V+1], token offsets of the words.
+ *   z_wordmajor_dev device int32[N], the same topics grouped by word.
+ *   out_dev     device double, receives the log-likelihood.
+ *   cuda_stream cudaStream_t or NULL; the call is asynchronous on it.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its
+ * scratch is a static device array of about 66 KB that every GPU loading
+ * this library holds until the process exits; the first call on a device
+ * looks up that array's device address (make that first call before any
+ * stream capture).  All calls share the array and each call clears it
+ * first, so calls whose kernels overlap on a GPU (different streams,
+ * threads) race and must be serialised by the caller.  Errors: EINVAL
+ * (sizes, K above 16384, null pointer), ECUDA.
+ */
+int warplda_loglik_noalloc(int64_t D, int64_t V, int64_t N, int32_t K, float alpha, float beta,
+                           const int64_t* doc_ptr_dev, const int32_t* z_docmajor_dev,
+                           const int64_t* word_ptr_dev, const int32_t* z_wordmajor_dev,
+                           double* out_dev, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -274,6 +274,8 @@ int recount(warplda_ctx* c) {
 
 }  // namespace
 
+int wl::record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 extern "C" {
 
 const char* warplda_last_error(void) { return g_err.c_str(); }

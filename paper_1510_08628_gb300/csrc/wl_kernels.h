@@ -49,4 +49,7 @@ cudaError_t launch_loglik_topics(const int32_t* ck, int K, double bbar, double* 
                                  cudaStream_t st);
 int loglik_smem_bytes(int region_words);
 
+// Sets the message warplda_last_error() returns on this thread; returns code.
+int record_error(int code, const char* msg);
+
 }  // namespace wl

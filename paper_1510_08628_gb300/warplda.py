@@ -68,6 +68,9 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double)]),
     "warplda_destroy": (None, [_P]),
+    "warplda_loglik_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                              ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                              _P, _P, _P, _P, _P, _P]),
     "warplda_last_error": (ctypes.c_char_p, []),
 }
 
@@ -111,6 +114,16 @@ def _dev_ptr(t) -> int | None:
     if t is None:
         return None
     return int(t.data_ptr())
+
+
+def loglik_noalloc(D: int, V: int, N: int, K: int, alpha: float, beta: float, doc_ptr_dev,
+                   z_docmajor_dev, word_ptr_dev, z_wordmajor_dev, out_dev, stream=None) -> None:
+    """warplda_loglik_noalloc on device tensors (no allocation; asynchronous)."""
+    st = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+    _check(load().warplda_loglik_noalloc(int(D), int(V), int(N), int(K), ctypes.c_float(alpha),
+                                         ctypes.c_float(beta), _dev_ptr(doc_ptr_dev),
+                                         _dev_ptr(z_docmajor_dev), _dev_ptr(word_ptr_dev),
+                                         _dev_ptr(z_wordmajor_dev), _dev_ptr(out_dev), st))
 
 
 class WarpLDA:
