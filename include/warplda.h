@@ -57,12 +57,16 @@ typedef struct warplda_ctx warplda_ctx;
  *   huge_chunk        tokens per thread-block chunk for longer segments.
  *   region_budget     32-bit words of shared memory for the per-segment
  *                     count tables of one block batch.
+ *   doc_warp_max      documents with at most this many tokens (capped at 512
+ *                     with dense count tables, 256 with hash tables) are
+ *                     sampled one warp per document; 0 (default) or -1: off.
  */
 typedef struct warplda_tuning {
     int32_t batch_max_tokens;
     int32_t huge_chunk;
     int32_t region_budget;
-    int32_t reserved[5];
+    int32_t doc_warp_max;
+    int32_t reserved[4];
 } warplda_tuning;
 
 /*

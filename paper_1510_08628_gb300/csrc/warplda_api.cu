@@ -45,14 +45,15 @@ int cuda_fail(cudaError_t e, const char* what) {
     } while (0)
 
 enum KernelClass {
-    kcDocBatch, kcDocHugeHist, kcDocHugeAccept, kcDocHugeDraw,
+    kcDocWarp, kcDocBatch, kcDocHugeHist, kcDocHugeAccept, kcDocHugeDraw,
     kcWordBatch, kcWordMegaHist, kcWordMegaAccept, kcWordMegaDraw,
     kcFinalize, kcZero, kcCount
 };
 const char* kClassNames[kcCount] = {
-    "doc_batch", "doc_huge_hist", "doc_huge_accept", "doc_huge_draw",
+    "doc_warp", "doc_batch", "doc_huge_hist", "doc_huge_accept", "doc_huge_draw",
     "word_batch", "word_mega_hist", "word_mega_accept", "word_mega_draw",
     "finalize_ck", "zero_rows"};
+constexpr int kCounters = 8;   // work counters: batches [class][phase], doc warp tier
 
 struct Rec {
     int cls;
@@ -60,11 +61,17 @@ struct Rec {
 };
 
 struct Tier {
-    std::vector<int2> batches;       // [first segment, end segment)
+    std::vector<int4> batches[2];    // {first segment, end segment, table words, 0}: small, large
+    std::vector<int32_t> warp_list;  // segments of the warp tier (documents only)
     std::vector<int4> chunks;        // {row, segment, first position, count}
-    int64_t nrows = 0, row_tokens = 0;
-    int2* d_batches = nullptr;
+    std::vector<int32_t> region;     // table offset of each batched segment in its batch
+    std::vector<int4> ll_batches;    // log-likelihood batches over all non-chunked segments
+    int64_t nrows = 0, row_tokens = 0, large_tokens = 0, warp_tokens = 0;
+    int4* d_batches[2] = {nullptr, nullptr};
+    int32_t* d_warp_list = nullptr;
     int4* d_chunks = nullptr;
+    int32_t* d_region = nullptr;
+    int4* d_ll_batches = nullptr;
 };
 
 }  // namespace
@@ -79,8 +86,13 @@ struct warplda_ctx {
     int doc_done = 0;
     cudaStream_t st = nullptr;
     int dev = 0, sms = 0;
-    int tpt = 16, bmax = 0, region_words = 0, chunk = 0, stage_ck = 0, kbits = 0;
+    int bmax[2] = {0, 0}, region[2] = {0, 0}, chunk = 0, stage_ck = 0, kbits = 0;
+    bool dense = true;   // 16-bit dense count tables (K <= kDenseMaxK), else hash tables
+    int warp_tpl = 16;   // tokens per lane of the document warp tier
+    int grid_doc_warp = 1;
     int32_t *z = nullptr, *prop = nullptr, *perm = nullptr, *doc_off = nullptr, *word_off = nullptr;
+    int32_t* sperm = nullptr;     // document batches' tokens in word-major order
+    uint32_t* sinfo = nullptr;    // their (slot << 16 | position in batch)
     int32_t *ck = nullptr, *counters = nullptr, *rows = nullptr, *scratch = nullptr;
     float* ckb = nullptr;
     double* d_ll = nullptr;
@@ -89,8 +101,8 @@ struct warplda_ctx {
     int64_t rows_words = 0;
     Tier docs, words;
     std::vector<int64_t> word_ptr_h;
-    int grid_doc_batch = 1, grid_word_batch = 1, grid_hist = 1, grid_acc_doc = 1,
-        grid_acc_word = 1, grid_draw = 1;
+    int grid_batch[2][2] = {{1, 1}, {1, 1}};   // [doc 0 / word 1][class]
+    int grid_hist = 1, grid_acc_doc = 1, grid_acc_word = 1, grid_draw = 1;
     bool prof = false;
     std::vector<Rec> recs;
     int64_t device_bytes = 0;
@@ -122,41 +134,102 @@ void free_all(warplda_ctx* c) {
     c->allocs.clear();
 }
 
-// Split segments [0, S) with offsets off[] into block batches (at most bmax
-// tokens, kSegsMax segments, region_words table words each) and long
-// segments, which get a count row and token chunks.
-void build_tier(const std::vector<int32_t>& off, int64_t S, int K, int bmax, int region_words,
-                int chunk, Tier* t) {
-    t->batches.clear();
+// Table words of a segment of L tokens: dense ceil(K/2) words (two 16-bit
+// counts each), or a hash of the smallest power of two above min(2L, K)
+// (Sec. 5.4); empty segments need none.
+int table_words(int L, int K, bool dense) {
+    if (L <= 0) return 0;
+    if (dense) return (K + 1) / 2;
+    return (int)pow2_above((uint32_t)std::min(2 * L, K));
+}
+
+// Split segments [0, S) with offsets off[] into the kernel tiers: segments
+// with 1..warp_max tokens go to the warp tier (warp_max = 0: none); small
+// segments to block batches of the 8-tokens-per-thread kernel (at most
+// bmax[0] tokens, kSegsMax segments, region[0] table words per batch), large
+// ones to batches of the 16-tokens-per-thread kernel (bmax[1], region[1]);
+// longer segments get a count row and token chunks.  A batch is a run of
+// consecutive segments of one class (empty segments join the open batch);
+// each batched segment records its table offset within the batch.  The
+// log-likelihood batches cover every segment that is not chunked, with the
+// paper's table rule.
+void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, int warp_max,
+                const int bmax[2], const int region[2], int chunk, Tier* t) {
+    for (auto& b : t->batches) b.clear();
+    t->warp_list.clear();
     t->chunks.clear();
-    t->nrows = 0;
-    t->row_tokens = 0;
-    int cur0 = -1, ntok = 0, nseg = 0, nw = 0;
+    t->ll_batches.clear();
+    t->region.assign((size_t)std::max<int64_t>(S, 1), 0);
+    t->nrows = t->row_tokens = t->large_tokens = t->warp_tokens = 0;
+    int cur0 = -1, cls = -1, ntok = 0, nseg = 0, nw = 0;
     auto close = [&](int end) {
-        if (cur0 >= 0 && end > cur0) t->batches.push_back(make_int2(cur0, end));
+        if (cur0 >= 0 && end > cur0) t->batches[cls].push_back(make_int4(cur0, end, nw, 0));
         cur0 = -1;
         ntok = nseg = nw = 0;
     };
+    int l0 = -1, lt = 0, ls = 0, lw = 0;   // open log-likelihood batch
+    auto lclose = [&](int end) {
+        if (l0 >= 0 && end > l0) t->ll_batches.push_back(make_int4(l0, end, lw, 0));
+        l0 = -1;
+        lt = ls = lw = 0;
+    };
     for (int64_t s = 0; s < S; ++s) {
         const int L = off[s + 1] - off[s];
-        uint32_t w = 0, cap = 0;
-        table_shape((uint32_t)L, (uint32_t)K, &w, &cap);
-        if (L > bmax || (int)w > region_words) {
+        if (L == 0) {
+            if (cur0 >= 0 && nseg + 1 <= kSegsMax) {
+                t->region[s] = nw;
+                nseg += 1;
+            } else {
+                close((int)s);
+            }
+            if (l0 >= 0 && ls + 1 <= kSegsMax) ls += 1; else lclose((int)s);
+            continue;
+        }
+        const int w = table_words(L, K, dense);
+        int c = -1;
+        if (L <= warp_max) c = 2;
+        else if (L <= bmax[0] && w <= region[0]) c = 0;
+        else if (L <= bmax[1] && w <= region[1]) c = 1;
+        if (c < 0) {
             close((int)s);
+            lclose((int)s);
             const int row = (int)t->nrows++;
             t->row_tokens += L;
             for (int p = off[s]; p < off[s + 1]; p += chunk)
                 t->chunks.push_back(make_int4(row, (int)s, p, std::min(chunk, off[s + 1] - p)));
             continue;
         }
-        if (cur0 >= 0 && (ntok + L > bmax || nseg + 1 > kSegsMax || nw + (int)w > region_words))
+        // log-likelihood batches (paper's table rule)
+        {
+            uint32_t w2 = 0, cap2 = 0;
+            table_shape((uint32_t)L, (uint32_t)K, &w2, &cap2);
+            if (l0 >= 0 && (lt + L > kMaxBatchTokens || ls + 1 > kSegsMax || lw + (int)w2 > 8192))
+                lclose((int)s);
+            if (l0 < 0) l0 = (int)s;
+            lt += L;
+            ls += 1;
+            lw += (int)w2;
+        }
+        if (c == 2) {
             close((int)s);
-        if (cur0 < 0) cur0 = (int)s;
+            t->warp_list.push_back((int32_t)s);
+            t->warp_tokens += L;
+            continue;
+        }
+        if (c == 1) t->large_tokens += L;
+        if (cur0 >= 0 && (c != cls || ntok + L > bmax[c] || nseg + 1 > kSegsMax || nw + w > region[c]))
+            close((int)s);
+        if (cur0 < 0) {
+            cur0 = (int)s;
+            cls = c;
+        }
+        t->region[s] = nw;
         ntok += L;
         nseg += 1;
-        nw += (int)w;
+        nw += w;
     }
     close((int)S);
+    lclose((int)S);
 }
 
 int launch_rec(warplda_ctx* c, int cls, cudaError_t (*fn)(warplda_ctx*, void*), void* arg) {
@@ -180,6 +253,8 @@ PhaseArgs phase_args(warplda_ctx* c, bool doc, uint32_t iter) {
     a.z = c->z;
     a.prop = c->prop;
     a.perm = c->perm;
+    a.sperm = c->sperm;
+    a.sinfo = c->sinfo;
     a.seg_off = doc ? c->doc_off : c->word_off;
     a.ckb = c->ckb;
     a.ck = c->ck;
@@ -188,8 +263,7 @@ PhaseArgs phase_args(warplda_ctx* c, bool doc, uint32_t iter) {
     a.g = doc ? c->alpha : c->beta;
     a.G = doc ? c->abar : c->kbeta;
     a.iter = iter;
-    a.k0 = c->k0;
-    a.k1 = c->k1;
+    a.rk = round_keys(c->seed);
     a.stage_ck = c->stage_ck;
     return a;
 }
@@ -197,14 +271,14 @@ PhaseArgs phase_args(warplda_ctx* c, bool doc, uint32_t iter) {
 struct PhaseCall {
     PhaseArgs a;
     bool doc;
+    int cls;
 };
 
 int run_phase(warplda_ctx* c, bool doc) {
     const uint32_t it = c->iter + 1;
-    PhaseCall pc{phase_args(c, doc, it), doc};
+    PhaseCall pc{phase_args(c, doc, it), doc, 0};
     Tier& T = doc ? c->docs : c->words;
     const int nch = (int)T.chunks.size();
-    const int nb = (int)T.batches.size();
     int rc;
     if (nch > 0) {
         rc = launch_rec(c, kcZero, [](warplda_ctx* cc, void* p) {
@@ -221,13 +295,27 @@ int run_phase(warplda_ctx* c, bool doc) {
         }, &pc);
         if (rc) return rc;
     }
-    if (nb > 0) {
+    if (doc && !T.warp_list.empty()) {
+        rc = launch_rec(c, kcDocWarp, [](warplda_ctx* cc, void* p) {
+            PhaseCall* q = (PhaseCall*)p;
+            return launch_doc_warp(cc->warp_tpl, cc->dense, q->a, cc->docs.d_warp_list,
+                                   (int)cc->docs.warp_list.size(), cc->counters + 4,
+                                   cc->grid_doc_warp, cc->st);
+        }, &pc);
+        if (rc) return rc;
+    }
+    for (int cls = 1; cls >= 0; --cls) {
+        if (T.batches[cls].empty()) continue;
+        pc.cls = cls;
         rc = launch_rec(c, doc ? kcDocBatch : kcWordBatch, [](warplda_ctx* cc, void* p) {
             PhaseCall* q = (PhaseCall*)p;
             Tier& TT = q->doc ? cc->docs : cc->words;
-            return launch_batch_phase(q->doc, cc->tpt, q->a, TT.d_batches, (int)TT.batches.size(),
-                                      cc->counters + (q->doc ? 0 : 1), cc->region_words, cc->kbits,
-                                      q->doc ? cc->grid_doc_batch : cc->grid_word_batch, cc->st);
+            const int k = q->cls;
+            return launch_batch_phase(q->doc, cc->dense, k ? 16 : 8, q->a, TT.d_batches[k],
+                                      (int)TT.batches[k].size(),
+                                      cc->counters + 2 * k + (q->doc ? 0 : 1), TT.d_region,
+                                      cc->region[k], cc->kbits, cc->grid_batch[q->doc ? 0 : 1][k],
+                                      cc->st);
         }, &pc);
         if (rc) return rc;
     }
@@ -249,7 +337,7 @@ int run_phase(warplda_ctx* c, bool doc) {
         if (rc) return rc;
     }
     rc = launch_rec(c, kcFinalize, [](warplda_ctx* cc, void*) {
-        return launch_finalize_ck(cc->ck, cc->ckb, cc->K, cc->bbar, cc->counters, 2, cc->st);
+        return launch_finalize_ck(cc->ck, cc->ckb, cc->K, cc->bbar, cc->counters, kCounters, cc->st);
     }, nullptr);
     if (rc) return rc;
     if (doc) {
@@ -263,12 +351,13 @@ int run_phase(warplda_ctx* c, bool doc) {
 
 int launches_per_phase(const warplda_ctx* c, bool doc) {
     const Tier& T = doc ? c->docs : c->words;
-    return (T.chunks.empty() ? 0 : 4) + (T.batches.empty() ? 0 : 1) + 1;
+    return (T.chunks.empty() ? 0 : 4) + (T.batches[0].empty() ? 0 : 1) +
+           (T.batches[1].empty() ? 0 : 1) + (T.warp_list.empty() ? 0 : 1) + 1;
 }
 
 int recount(warplda_ctx* c) {
     WL_CU(launch_topic_hist(c->z, c->N, c->ck, c->K, c->st), "topic histogram");
-    WL_CU(launch_finalize_ck(c->ck, c->ckb, c->K, c->bbar, c->counters, 2, c->st), "finalize c_k");
+    WL_CU(launch_finalize_ck(c->ck, c->ckb, c->K, c->bbar, c->counters, kCounters, c->st), "finalize c_k");
     return WARPLDA_OK;
 }
 
@@ -315,14 +404,26 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     c->st = (cudaStream_t)cuda_stream;
     c->stage_ck = K <= 4096 ? 1 : 0;
     while ((1 << c->kbits) < K) ++c->kbits;
-    c->tpt = 16;
-    int bmax = (tuning && tuning->batch_max_tokens > 0) ? tuning->batch_max_tokens : kMaxBatchTokens;
+    // block batches: up to 2045 tokens with 8 tokens per thread, up to 4093
+    // with 16; the table budget of a batch is region_budget words (defaults
+    // 4096 and 8192)
+    const int bmax = (tuning && tuning->batch_max_tokens > 0) ? tuning->batch_max_tokens : kMaxBatchTokens;
     c->chunk = (tuning && tuning->huge_chunk > 0) ? tuning->huge_chunk : 16384;
-    c->region_words = (tuning && tuning->region_budget > 0) ? tuning->region_budget : 8192;
-    c->region_words = (c->region_words + 3) & ~3;
-    if (bmax <= kThreads * 8 - 3) c->tpt = 8;
-    bmax = std::min(bmax, std::min(kMaxBatchTokens, kThreads * c->tpt - 3));
-    c->bmax = bmax;
+    const int rb = (tuning && tuning->region_budget > 0) ? ((tuning->region_budget + 3) & ~3) : 0;
+    c->bmax[0] = std::min(bmax, kThreads * 8 - 3);
+    c->bmax[1] = std::min(bmax, std::min(kMaxBatchTokens, kThreads * 16 - 3));
+    c->region[0] = rb ? rb : 8192;
+    c->region[1] = rb ? rb : 8192;
+    c->dense = K <= kDenseMaxK;
+    // documents of up to 32 * warp_tpl tokens go to the warp tier; the
+    // block tier takes the rest (its small class is not used for documents)
+    c->warp_tpl = c->dense ? 16 : 8;
+    // the warp tier is off unless asked for: all documents in one kernel keep
+    // the doc-order sweep over the word columns that makes the perm gather
+    // hit L2 (Sec. 5.2)
+    int warp_max = 0;
+    if (tuning && tuning->doc_warp_max > 0)
+        warp_max = std::min(std::min(32 * c->warp_tpl, bmax), (int)tuning->doc_warp_max);
 
     auto bail = [&](int rc) {
         free_all(c);
@@ -344,18 +445,47 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         std::vector<int64_t> fill(c->word_ptr_h.begin(), c->word_ptr_h.end() - 1);
         for (int64_t p = 0; p < N; ++p) perm[p] = (int32_t)(fill[doc_word[p]]++);
     }
-    build_tier(doc_off, D, K, bmax, c->region_words, c->chunk, &c->docs);
-    build_tier(word_off, V, K, bmax, c->region_words, c->chunk, &c->words);
+    build_tier(doc_off, D, K, c->dense, warp_max, c->bmax, c->region, c->chunk, &c->docs);
+    build_tier(word_off, V, K, c->dense, 0, c->bmax, c->region, c->chunk, &c->words);
+
+    // document batches list their tokens in word-major order, with each
+    // token's segment slot and position (document order) in the batch: a
+    // counting pass over the word-major order grouped by batch
+    std::vector<int32_t> sperm((size_t)N + 4, 0);
+    std::vector<uint32_t> sinfo((size_t)N + 4, 0u);
+    {
+        std::vector<int32_t> bod((size_t)std::max<int64_t>(D, 1), -1);
+        std::vector<int32_t> bfirst, bfill;
+        for (int k = 0; k < 2; ++k)
+            for (const int4& br : c->docs.batches[k]) {
+                for (int d = br.x; d < br.y; ++d) bod[d] = (int32_t)bfirst.size();
+                bfirst.push_back(br.x);
+                bfill.push_back(doc_off[br.x]);
+            }
+        std::vector<int32_t> inv((size_t)std::max<int64_t>(N, 1)), dop((size_t)std::max<int64_t>(N, 1));
+        for (int64_t p = 0; p < N; ++p) inv[perm[p]] = (int32_t)p;
+        for (int64_t d = 0; d < D; ++d)
+            for (int32_t p = doc_off[d]; p < doc_off[d + 1]; ++p) dop[p] = (int32_t)d;
+        for (int64_t t = 0; t < N; ++t) {
+            const int32_t p = inv[t], d = dop[p], b = bod[d];
+            if (b < 0) continue;
+            const int32_t q = bfill[b]++;
+            sperm[q] = (int32_t)t;
+            sinfo[q] = ((uint32_t)(d - bfirst[b]) << 16) | (uint32_t)(p - doc_off[bfirst[b]]);
+        }
+    }
 
     int rc;
     if ((rc = dalloc(c, &c->z, N + 4, "alloc z"))) return bail(rc);
+    if ((rc = dalloc(c, &c->sperm, N + 4, "alloc sorted perm"))) return bail(rc);
+    if ((rc = dalloc(c, &c->sinfo, N + 4, "alloc sorted info"))) return bail(rc);
     if ((rc = dalloc(c, &c->prop, (N + 4) * M, "alloc proposals"))) return bail(rc);
     if ((rc = dalloc(c, &c->perm, N + 4, "alloc perm"))) return bail(rc);
     if ((rc = dalloc(c, &c->doc_off, D + 1, "alloc doc offsets"))) return bail(rc);
     if ((rc = dalloc(c, &c->word_off, V + 1, "alloc word offsets"))) return bail(rc);
     if ((rc = dalloc(c, &c->ck, K, "alloc c_k"))) return bail(rc);
     if ((rc = dalloc(c, &c->ckb, K, "alloc c_k float"))) return bail(rc);
-    if ((rc = dalloc(c, &c->counters, 4, "alloc counters"))) return bail(rc);
+    if ((rc = dalloc(c, &c->counters, kCounters, "alloc counters"))) return bail(rc);
     if ((rc = dalloc(c, &c->d_ll, 1, "alloc loglik"))) return bail(rc);
     if ((rc = dalloc(c, &c->d_bad, 1, "alloc flag"))) return bail(rc);
     // count rows of the multi-pass tier; each row set starts 16-byte aligned
@@ -367,12 +497,28 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     c->rows_pre = c->rows + rd;
     c->rows_post = c->rows_pre + rw;
     for (Tier* t : {&c->docs, &c->words}) {
-        if ((rc = dalloc(c, &t->d_batches, (int64_t)t->batches.size(), "alloc batches"))) return bail(rc);
-        if ((rc = dalloc(c, &t->d_chunks, (int64_t)t->chunks.size(), "alloc chunks"))) return bail(rc);
-        if (!t->batches.empty())
-            if ((e = cudaMemcpyAsync(t->d_batches, t->batches.data(), t->batches.size() * sizeof(int2),
+        for (int k = 0; k < 2; ++k) {
+            if ((rc = dalloc(c, &t->d_batches[k], (int64_t)t->batches[k].size(), "alloc batches"))) return bail(rc);
+            if (!t->batches[k].empty())
+                if ((e = cudaMemcpyAsync(t->d_batches[k], t->batches[k].data(), t->batches[k].size() * sizeof(int4),
+                                         cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+                    return bail(cuda_fail(e, "upload batches"));
+        }
+        if ((rc = dalloc(c, &t->d_warp_list, (int64_t)t->warp_list.size(), "alloc warp list"))) return bail(rc);
+        if (!t->warp_list.empty())
+            if ((e = cudaMemcpyAsync(t->d_warp_list, t->warp_list.data(), t->warp_list.size() * sizeof(int32_t),
                                      cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
-                return bail(cuda_fail(e, "upload batches"));
+                return bail(cuda_fail(e, "upload warp list"));
+        if ((rc = dalloc(c, &t->d_ll_batches, (int64_t)t->ll_batches.size(), "alloc ll batches"))) return bail(rc);
+        if (!t->ll_batches.empty())
+            if ((e = cudaMemcpyAsync(t->d_ll_batches, t->ll_batches.data(), t->ll_batches.size() * sizeof(int4),
+                                     cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+                return bail(cuda_fail(e, "upload ll batches"));
+        if ((rc = dalloc(c, &t->d_region, (int64_t)t->region.size(), "alloc table offsets"))) return bail(rc);
+        if ((e = cudaMemcpyAsync(t->d_region, t->region.data(), t->region.size() * sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+            return bail(cuda_fail(e, "upload table offsets"));
+        if ((rc = dalloc(c, &t->d_chunks, (int64_t)t->chunks.size(), "alloc chunks"))) return bail(rc);
         if (!t->chunks.empty())
             if ((e = cudaMemcpyAsync(t->d_chunks, t->chunks.data(), t->chunks.size() * sizeof(int4),
                                      cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
@@ -380,6 +526,10 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     }
     if ((e = cudaMemcpyAsync(c->perm, perm.data(), ((size_t)N + 4) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
         return bail(cuda_fail(e, "upload perm"));
+    if ((e = cudaMemcpyAsync(c->sperm, sperm.data(), ((size_t)N + 4) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+        return bail(cuda_fail(e, "upload sorted perm"));
+    if ((e = cudaMemcpyAsync(c->sinfo, sinfo.data(), ((size_t)N + 4) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+        return bail(cuda_fail(e, "upload sorted info"));
     if ((e = cudaMemcpyAsync(c->doc_off, doc_off.data(), (D + 1) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
         return bail(cuda_fail(e, "upload doc offsets"));
     if ((e = cudaMemcpyAsync(c->word_off, word_off.data(), (V + 1) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
@@ -387,20 +537,27 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
 
     // grids: persistent blocks, as many as fit
     auto fit = [&](int per_sm) { return std::max(1, per_sm) * c->sms; };
-    c->grid_doc_batch = std::min<int64_t>(fit(batch_blocks_per_sm(K, c->stage_ck, c->region_words, c->tpt, 0, M)),
-                                          std::max<int64_t>(1, (int64_t)c->docs.batches.size()));
-    c->grid_word_batch = std::min<int64_t>(fit(batch_blocks_per_sm(K, c->stage_ck, c->region_words, c->tpt, 1, M)),
-                                           std::max<int64_t>(1, (int64_t)c->words.batches.size()));
+    for (int w = 0; w < 2; ++w)
+        for (int k = 0; k < 2; ++k) {
+            const int per_sm = batch_blocks_per_sm(K, c->stage_ck, c->region[k], k ? 16 : 8, w, M, c->dense);
+            if (per_sm < 1)
+                return bail(fail(WARPLDA_EINVAL, "batch kernel does not fit (region_budget too large?)"));
+            const int64_t nb = (int64_t)(w ? c->words : c->docs).batches[k].size();
+            c->grid_batch[w][k] = (int)std::min<int64_t>(fit(per_sm), std::max<int64_t>(1, nb));
+        }
+    {
+        const int per_sm = docwarp_blocks_per_sm(K, c->stage_ck, c->warp_tpl, M, c->dense);
+        if (per_sm < 1) return bail(fail(WARPLDA_EINVAL, "document warp kernel does not fit"));
+        const int64_t need = ((int64_t)c->docs.warp_list.size() + kWarps - 1) / kWarps;
+        c->grid_doc_warp = (int)std::min<int64_t>(fit(per_sm), std::max<int64_t>(1, need));
+    }
     c->grid_hist = fit(huge_blocks_per_sm(K, c->stage_ck, 0, false, M));
     c->grid_acc_doc = fit(huge_blocks_per_sm(K, c->stage_ck, 1, true, M));
     c->grid_acc_word = fit(huge_blocks_per_sm(K, c->stage_ck, 1, false, M));
     c->grid_draw = fit(huge_blocks_per_sm(K, c->stage_ck, 2, false, M));
-    if (batch_blocks_per_sm(K, c->stage_ck, c->region_words, c->tpt, 0, M) < 1 ||
-        batch_blocks_per_sm(K, c->stage_ck, c->region_words, c->tpt, 1, M) < 1)
-        return bail(fail(WARPLDA_EINVAL, "batch kernel does not fit (region_budget too large?)"));
 
     // z = Dice(K), proposals = z (Alg. 2); c_k = histogram of z
-    if ((e = launch_init_z(c->z, c->prop, N, K, M, c->k0, c->k1, c->st)) != cudaSuccess)
+    if ((e = launch_init_z(c->z, c->prop, N, K, M, c->seed, c->st)) != cudaSuccess)
         return bail(cuda_fail(e, "init z"));
     if ((rc = recount(c))) return bail(rc);
     if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return bail(cuda_fail(e, "init"));
@@ -489,7 +646,7 @@ int warplda_set_state(warplda_ctx* c, const int32_t* z, const int32_t* prop, uin
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     if (bad) {
         // leave a valid state behind: re-initialise
-        WL_CU(launch_init_z(c->z, c->prop, c->N, c->K, c->M, c->k0, c->k1, c->st), "init z");
+        WL_CU(launch_init_z(c->z, c->prop, c->N, c->K, c->M, c->seed, c->st), "init z");
         int rc = recount(c);
         if (rc) return rc;
         c->iter = 0;
@@ -530,9 +687,9 @@ int warplda_loglik(warplda_ctx* c, double* out) {
             WL_CU(launch_huge_hist(doc, pa, T.d_chunks, (int)T.chunks.size(), rows, c->grid_hist, c->st), "loglik rows");
             WL_CU(launch_loglik_rows(rows, T.nrows, c->K, doc ? a : b, c->d_ll, c->st), "loglik rows");
         }
-        WL_CU(launch_loglik_batches(doc, c->z, c->perm, doc ? c->doc_off : c->word_off, T.d_batches,
-                                    (int)T.batches.size(), c->K, doc ? a : b, c->region_words, c->d_ll,
-                                    c->sms * 2, c->st), "loglik batches");
+        WL_CU(launch_loglik_batches(doc, c->z, c->perm, doc ? c->doc_off : c->word_off,
+                                    T.d_ll_batches, (int)T.ll_batches.size(), c->K, doc ? a : b,
+                                    8192, c->d_ll, c->sms * 2, c->st), "loglik batches");
     }
     WL_CU(launch_loglik_lengths(c->doc_off, c->D, abar, c->d_ll, c->st), "loglik lengths");
     WL_CU(launch_loglik_topics(c->ck, c->K, bbar, c->d_ll, c->st), "loglik topics");
@@ -596,9 +753,10 @@ int warplda_get_info(warplda_ctx* c, warplda_info* o) {
     std::memset(o, 0, sizeof(*o));
     o->D = c->D; o->V = c->V; o->N = c->N; o->K = c->K; o->M = c->M;
     o->launches_per_sweep = launches_per_phase(c, true) + launches_per_phase(c, false);
-    o->batch_max_tokens = c->bmax;
-    o->doc_batches = (int64_t)c->docs.batches.size();
-    o->word_batches = (int64_t)c->words.batches.size();
+    o->batch_max_tokens = std::max(c->bmax[0], c->bmax[1]);
+    o->doc_batches = (int64_t)(c->docs.batches[0].size() + c->docs.batches[1].size() +
+                               c->docs.warp_list.size());
+    o->word_batches = (int64_t)(c->words.batches[0].size() + c->words.batches[1].size());
     o->huge_docs = c->docs.nrows;
     o->huge_doc_tokens = c->docs.row_tokens;
     o->mega_words = c->words.nrows;

@@ -1,10 +1,14 @@
 // On-chip tier of the document and word phases (Sec. 4.4): one thread block
-// takes a batch of consecutive documents (or words) with at most 4095 tokens
+// takes a batch of consecutive documents (or words) with at most 4093 tokens
 // in all, builds every segment's count table in shared memory (Sec. 5.4),
 // runs the M chained MH steps of each token against it (Alg. 1, Eq. 7), and
 // draws the M new proposals of Eq. 6 from the post-acceptance assignments:
 //   document phase: random positioning (Sec. 4.3) in the caller's token order;
 //   word phase:     the j-th smallest post-acceptance topic of the word.
+// Count tables are dense (two 16-bit counts per word) when K <= 2048, else
+// the paper's open-addressing hash; the choice is uniform per context.  The
+// word phase orders each word's post-acceptance topics by a counting sort
+// through its dense table, or by a block radix sort with hash tables.
 // Word-major arrays are read and written with 128-bit accesses in the word
 // phase and through perm (the doc-major -> word-major pointer array of
 // Sec. 5.2) in the document phase.
@@ -19,7 +23,7 @@ struct BatchSmem {
 };
 
 __host__ __device__ inline BatchSmem batch_smem_layout(int K, int stage_ck, int region_words,
-                                                       int tpt, int word_phase) {
+                                                       int tpt, int radix) {
     BatchSmem s;
     int o = 0;
     s.ck_off = o;
@@ -29,14 +33,13 @@ __host__ __device__ inline BatchSmem batch_smem_layout(int K, int stage_ck, int 
     o += (3 * kSegsMax + 4) * 4;
     o = (o + 15) & ~15;
     s.region_off = o;
-    o += region_words * 4;
-    o = (o + 15) & ~15;
+    o += ((region_words + 3) & ~3) * 4;
     s.stage_off = o;
     const int n = kThreads * tpt;
     o += (n + (n >> 5) + 4) * 4;
     o = (o + 15) & ~15;
     s.cnt_off = o;
-    if (word_phase) o += 16 * kThreads * 2;
+    if (radix) o += 16 * kThreads * 2;
     s.total = (o + 15) & ~15;
     return s;
 }
@@ -44,19 +47,71 @@ __host__ __device__ inline BatchSmem batch_smem_layout(int K, int stage_ck, int 
 template <int M>
 struct Props { int v[M]; };
 
-template <bool kDoc, int TPT, int M>
-__global__ void __launch_bounds__(kThreads) batch_phase_kernel(PhaseArgs a,
-                                                               const int2* __restrict__ batches,
-                                                               int nbatch, int* __restrict__ counter,
-                                                               int region_words, int kbits) {
+// The M proposals of token t: one 8- or 16-byte load when M is 2 or 4.
+template <int M>
+__device__ __forceinline__ void load_props(const int32_t* prop, int t, int* v) {
+    if (M == 2) {
+        const int2 x = *reinterpret_cast<const int2*>(prop + (int64_t)t * 2);
+        v[0] = x.x;
+        v[1 % M] = x.y;
+    } else if (M == 4) {
+        const int4 x = *reinterpret_cast<const int4*>(prop + (int64_t)t * 4);
+        v[0] = x.x;
+        v[1 % M] = x.y;
+        v[2 % M] = x.z;
+        v[3 % M] = x.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < M; ++i) v[i] = prop[(int64_t)t * M + i];
+    }
+}
+
+template <int M>
+__device__ __forceinline__ void store_props(int32_t* prop, int t, const int* v) {
+    if (M == 2) {
+        *reinterpret_cast<int2*>(prop + (int64_t)t * 2) = make_int2(v[0], v[1 % M]);
+    } else if (M == 4) {
+        *reinterpret_cast<int4*>(prop + (int64_t)t * 4) = make_int4(v[0], v[1 % M], v[2 % M], v[3 % M]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < M; ++i) prop[(int64_t)t * M + i] = v[i];
+    }
+}
+
+// Dense table: topic k's 16-bit count lives in word k >> 1.
+__device__ __forceinline__ uint32_t dense_unit(uint32_t k) { return (k & 1) ? 65536u : 1u; }
+__device__ __forceinline__ int dense_get(const uint32_t* tab, uint32_t k) {
+    return (int)((tab[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu);
+}
+
+template <bool kDense>
+__device__ __forceinline__ void tab_add(uint32_t* tab, uint32_t cap, uint32_t k) {
+    if (kDense) atomicAdd(&tab[k >> 1], dense_unit(k));
+    else table_add(tab, cap, k);
+}
+
+template <bool kDense>
+__device__ __forceinline__ int tab_get(const uint32_t* tab, uint32_t cap, uint32_t k) {
+    return kDense ? dense_get(tab, k) : table_get(tab, cap, k);
+}
+
+// Resident blocks per SM the register allocation is held to.
+template <bool kDoc, int TPT>
+constexpr int batch_min_blocks() { return TPT == 8 ? 2 : 1; }
+
+template <bool kDoc, bool kDense, int TPT, int M>
+__global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) batch_phase_kernel(
+    PhaseArgs a, const int4* __restrict__ batches, int nbatch, int* __restrict__ counter,
+    const int32_t* __restrict__ seg_region, int region_words, int kbits) {
     static_assert(TPT % 4 == 0, "tokens per thread come in chunks of four");
+    constexpr bool kRadix = !kDoc && !kDense;
     extern __shared__ __align__(16) unsigned char smem[];
-    const BatchSmem L = batch_smem_layout(a.K, a.stage_ck, region_words, TPT, kDoc ? 0 : 1);
+    const BatchSmem L = batch_smem_layout(a.K, kDense ? 1 : 0, region_words, TPT, kRadix ? 1 : 0);
     float* ckb_s = reinterpret_cast<float*>(smem + L.ck_off);
     int* dck_s = reinterpret_cast<int*>(smem + L.ck_off) + a.K;
-    int* seg_tok = reinterpret_cast<int*>(smem + L.seg_off);        // [kSegsMax + 1]
-    int* seg_reg = seg_tok + kSegsMax + 1;                          // [kSegsMax]
-    int* seg_cap = seg_reg + kSegsMax;                              // [kSegsMax]
+    int* seg_tok = reinterpret_cast<int*>(smem + L.seg_off);   // [kSegsMax + 1] token offsets
+    int* seg_reg = seg_tok + kSegsMax + 1;                     // [kSegsMax + 1] table offsets
+    int* seg_aux = seg_reg + kSegsMax + 1;                     // [kSegsMax] hash cap / prefix base
     uint32_t* region = reinterpret_cast<uint32_t*>(smem + L.region_off);
     uint32_t* stage = reinterpret_cast<uint32_t*>(smem + L.stage_off);
     uint16_t* cnt = reinterpret_cast<uint16_t*>(smem + L.cnt_off);
@@ -65,7 +120,8 @@ __global__ void __launch_bounds__(kThreads) batch_phase_kernel(PhaseArgs a,
 
     const int tid = threadIdx.x;
     const int K = a.K;
-    if (a.stage_ck) {
+    if (tid == 0) s_batch = atomicAdd(counter, 1);
+    if (kDense) {
         for (int k = tid; k < K; k += kThreads) {
             ckb_s[k] = a.ckb[k];
             dck_s[k] = 0;
@@ -74,35 +130,39 @@ __global__ void __launch_bounds__(kThreads) batch_phase_kernel(PhaseArgs a,
     __syncthreads();
 
     for (;;) {
-        if (tid == 0) s_batch = atomicAdd(counter, 1);
-        __syncthreads();
         const int b = s_batch;
         if (b >= nbatch) break;
-        const int2 br = batches[b];
+        const int4 br = batches[b];      // {first segment, end segment, table words, 0}
         const int nseg = br.y - br.x;
+        const int used = br.z;
         const int base = a.seg_off[br.x];
         const int end = a.seg_off[br.y];
 
-        // segment table: token offsets and count-table shapes
+        // segment table (layout precomputed at init) and cleared count tables
         for (int s = tid; s < nseg; s += kThreads) {
-            const int o0 = a.seg_off[br.x + s], o1 = a.seg_off[br.x + s + 1];
-            uint32_t w, cap;
-            table_shape((uint32_t)(o1 - o0), (uint32_t)K, &w, &cap);
+            const int o0 = a.seg_off[br.x + s];
             seg_tok[s] = o0 - base;
-            seg_reg[s] = (int)w;
-            seg_cap[s] = (int)cap;
+            seg_reg[s] = seg_region[br.x + s];
+            if (!kDense) {
+                uint32_t w, cap;
+                table_shape((uint32_t)(a.seg_off[br.x + s + 1] - o0), (uint32_t)K, &w, &cap);
+                seg_aux[s] = (int)cap;
+            }
         }
-        if (tid == 0) seg_tok[nseg] = end - base;
+        if (tid == 0) {
+            seg_tok[nseg] = end - base;
+            seg_reg[nseg] = used;
+        }
+        for (int i = tid; i < ((used + 3) >> 2); i += kThreads)
+            reinterpret_cast<uint4*>(region)[i] = make_uint4(0u, 0u, 0u, 0u);
         __syncthreads();
-        block_scan_array(seg_reg, nseg, warp_tot, &s_total);
-        const int region_used = s_total;
-        for (int i = tid; i < region_used; i += kThreads) region[i] = 0u;
-        __syncthreads();
+        if (tid == 0) s_batch = atomicAdd(counter, 1);   // every thread has read b
 
         // load the tokens this thread owns: chunks of 4 consecutive positions
         const int abase = base & ~3;
         int tk[TPT];          // word-major token index (-1: not ours)
         int zz[TPT];          // topic: phase-start, then post-acceptance
+        int zo[TPT];          // phase-start topic (word phase with dense tables)
         int sl[TPT];          // segment slot in the batch
         Props<M> pp[TPT];     // pending proposals, then picks
 #pragma unroll
@@ -110,12 +170,32 @@ __global__ void __launch_bounds__(kThreads) batch_phase_kernel(PhaseArgs a,
             const int q0 = abase + 4 * (c * kThreads + tid);
             int4 pv = make_int4(0, 0, 0, 0);
             int4 zv = make_int4(0, 0, 0, 0);
+            int pw[4 * M];
+#pragma unroll
+            for (int i = 0; i < 4 * M; ++i) pw[i] = 0;
+            uint4 iv = make_uint4(0u, 0u, 0u, 0u);
             if (q0 < end) {
-                if (kDoc) pv = *reinterpret_cast<const int4*>(a.perm + q0);
-                else zv = *reinterpret_cast<const int4*>(a.z + q0);
+                if (kDoc) {
+                    // a document batch's tokens in word-major order: lanes
+                    // reading neighbouring tokens of one word share sectors
+                    pv = *reinterpret_cast<const int4*>(a.sperm + q0);
+                    iv = *reinterpret_cast<const uint4*>(a.sinfo + q0);
+                } else {
+                    zv = *reinterpret_cast<const int4*>(a.z + q0);
+                    // the chunk's 4M proposals are M aligned 16-byte words
+#pragma unroll
+                    for (int u = 0; u < M; ++u) {
+                        const int4 x = reinterpret_cast<const int4*>(a.prop + (int64_t)q0 * M)[u];
+                        pw[4 * u] = x.x;
+                        pw[4 * u + 1] = x.y;
+                        pw[4 * u + 2] = x.z;
+                        pw[4 * u + 3] = x.w;
+                    }
+                }
             }
             const int pa[4] = {pv.x, pv.y, pv.z, pv.w};
             const int za[4] = {zv.x, zv.y, zv.z, zv.w};
+            const uint32_t ia[4] = {iv.x, iv.y, iv.z, iv.w};
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 const int j = 4 * c + v;
@@ -123,75 +203,174 @@ __global__ void __launch_bounds__(kThreads) batch_phase_kernel(PhaseArgs a,
                 const bool mine = (q >= base) && (q < end);
                 tk[j] = mine ? (kDoc ? pa[v] : q) : -1;
                 if (kDoc) {
+                    sl[j] = mine ? (int)ia[v] : 0;     // slot << 16 | position, split below
                     zz[j] = mine ? a.z[tk[j]] : 0;
+                    if (mine) load_props<M>(a.prop, tk[j], pp[j].v);
                 } else {
                     zz[j] = za[v];
-                }
-                if (mine) {
-                    const int64_t pb = (int64_t)tk[j] * M;
 #pragma unroll
-                    for (int i = 0; i < M; ++i) pp[j].v[i] = a.prop[pb + i];
+                    for (int i = 0; i < M; ++i) pp[j].v[i] = pw[v * M + i];
                 }
             }
         }
-        // segment slots and count tables
+        // segment slots and count tables: documents carry their slot and
+        // position; words find the slot by one binary search per chunk of four
+        int lp[TPT];          // document phase: position within the batch (document order)
 #pragma unroll
-        for (int j = 0; j < TPT; ++j) {
-            if (tk[j] < 0) { sl[j] = 0; continue; }
-            const int p = (kDoc ? (abase + 4 * ((j / 4) * kThreads + tid) + (j % 4))
-                                : tk[j]) - base;
-            int lo = 0, hi = nseg - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (seg_tok[mid] <= p) lo = mid; else hi = mid - 1;
+        for (int c = 0; c < TPT / 4; ++c) {
+            const int q0 = abase + 4 * (c * kThreads + tid);
+            int slot = 0;
+            if (!kDoc && q0 < end) {
+                const int pf = (q0 > base ? q0 : base) - base;
+                int lo = 0, hi = nseg - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (seg_tok[mid] <= pf) lo = mid; else hi = mid - 1;
+                }
+                slot = lo;
             }
-            sl[j] = lo;
-            table_add(region + seg_reg[lo], (uint32_t)seg_cap[lo], (uint32_t)zz[j]);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int j = 4 * c + v;
+                if (kDoc) {
+                    lp[j] = sl[j] & 0xFFFF;
+                    sl[j] = sl[j] >> 16;
+                } else {
+                    lp[j] = 0;
+                    sl[j] = 0;
+                    if (tk[j] < 0) continue;
+                    const int p = q0 + v - base;
+                    while (slot + 1 < nseg && seg_tok[slot + 1] <= p) ++slot;
+                    sl[j] = slot;
+                }
+                if (tk[j] < 0) continue;
+                tab_add<kDense>(region + seg_reg[sl[j]], kDense ? 0u : (uint32_t)seg_aux[sl[j]],
+                                (uint32_t)zz[j]);
+            }
         }
         __syncthreads();
 
-        // M chained MH steps per token (Alg. 1, Eq. 7), then the picks of Eq. 6
+        // M chained MH steps per token (Alg. 1, Eq. 7), then the picks of Eq. 6:
+        // a topic, or -(index + 1) into the post-acceptance segment.  Every
+        // operand a token's chain can need -- the counts and c_k entries of
+        // its phase-start topic and of each proposal -- is loaded up front
+        // for a group of tokens, so the group waits on shared memory twice;
+        // the chain itself is branch-free (a token that is not ours runs on
+        // topic 0 of slot 0 and has its side effects masked).
         const uint32_t phase = kDoc ? kPhaseDoc : kPhaseWord;
+        constexpr int kGroup = 4;
 #pragma unroll
-        for (int j = 0; j < TPT; ++j) {
-            if (tk[j] < 0) continue;
-            const int slot = sl[j];
-            const uint32_t* tab = region + seg_reg[slot];
-            const uint32_t cap = (uint32_t)seg_cap[slot];
-            const int Ls = seg_tok[slot + 1] - seg_tok[slot];
-            const float Lf = __int2float_rn(Ls);
-            const float LG = __fadd_rn(Lf, a.G);
-            const int z0 = zz[j];
-            int s = z0;
+        for (int g0 = 0; g0 < TPT; g0 += kGroup) {
+            int toff[kGroup], tlen[kGroup];
 #pragma unroll
-            for (int i = 0; i < M; ++i) {
-                const uint4 r = draw((uint32_t)tk[j], a.iter, phase, (uint32_t)(i + 1), 0u, a.k0, a.k1);
-                const int t = pp[j].v[i];
-                if (t != s) {
-                    const float cs = a.stage_ck ? ckb_s[s] : __ldg(a.ckb + s);
-                    const float ct = a.stage_ck ? ckb_s[t] : __ldg(a.ckb + t);
-                    if (accept(r.x, table_get(tab, cap, (uint32_t)s), table_get(tab, cap, (uint32_t)t),
-                               a.g, cs, ct))
-                        s = t;
-                }
-                pp[j].v[i] = coin(r.y, Lf, LG) ? -(int)(dice(r.z, (uint32_t)Ls) + 1)
-                                               : (int)dice(r.z, (uint32_t)K);
+            for (int u = 0; u < kGroup; ++u) {
+                const int slot = sl[g0 + u];
+                toff[u] = seg_reg[slot];
+                tlen[u] = max(seg_tok[slot + 1] - seg_tok[slot], 1);
             }
-            if (s != z0) {
-                if (a.stage_ck) {
-                    atomicSub(&dck_s[z0], 1);
-                    atomicAdd(&dck_s[s], 1);
-                } else {
-                    atomicSub(&a.ck[z0], 1);
-                    atomicAdd(&a.ck[s], 1);
+            int cnt_v[kGroup][M + 1];
+            float ck_v[kGroup][M + 1];
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+                const int j = g0 + u;
+                const bool mine = tk[j] >= 0;
+                const uint32_t* tab = region + toff[u];
+                const uint32_t cap = kDense ? 0u : (uint32_t)seg_aux[sl[j]];
+#pragma unroll
+                for (int i = 0; i <= M; ++i) {
+                    const int k = mine ? (i == 0 ? zz[j] : pp[j].v[i - 1]) : 0;
+                    cnt_v[u][i] = tab_get<kDense>(tab, cap, (uint32_t)k);
+                    ck_v[u][i] = kDense ? ckb_s[k] : __ldg(a.ckb + k);
                 }
             }
-            zz[j] = s;
-            const int p = (kDoc ? (abase + 4 * ((j / 4) * kThreads + tid) + (j % 4)) : tk[j]) - base;
-            stage[pad(p)] = kDoc ? (uint32_t)s : (((uint32_t)slot << kbits) | (uint32_t)s);
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+                const int j = g0 + u;
+                const bool mine = tk[j] >= 0;
+                zo[j] = zz[j];
+                const int Ls = tlen[u];
+                const float Lf = __int2float_rn(Ls);
+                const float LG = __fadd_rn(Lf, a.G);
+                const int z0 = mine ? zz[j] : 0;
+                int s = z0;
+                int cs = cnt_v[u][0];
+                float ks = ck_v[u][0];
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    const uint4 r = draw((uint32_t)(mine ? tk[j] : 0), a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
+                    const int t = mine ? pp[j].v[i] : s;
+                    const int ct = cnt_v[u][i + 1];
+                    const float kt = ck_v[u][i + 1];
+                    const bool acc = (t != s) && accept(r.x, cs, ct, a.g, ks, kt);
+                    s = acc ? t : s;
+                    cs = acc ? ct : cs;
+                    ks = acc ? kt : ks;
+                    const int head = -(int)(dice(r.z, (uint32_t)Ls) + 1);
+                    const int tail = (int)dice(r.z, (uint32_t)K);
+                    pp[j].v[i] = coin(r.y, Lf, LG) ? head : tail;
+                }
+                if (mine && s != z0) {
+                    if (kDense) {
+                        atomicSub(&dck_s[z0], 1);
+                        atomicAdd(&dck_s[s], 1);
+                    } else {
+                        atomicSub(&a.ck[z0], 1);
+                        atomicAdd(&a.ck[s], 1);
+                    }
+                }
+                zz[j] = mine ? s : zz[j];
+                if ((kDoc || kRadix) && mine) {
+                    const int p = kDoc ? lp[j] : tk[j] - base;
+                    stage[pad(p)] = kDoc ? (uint32_t)s : (((uint32_t)sl[j] << kbits) | (uint32_t)s);
+                }
+            }
+        }
+        __syncthreads();
+
+        if (!kDoc && kDense) {
+            // counting sort of each word's post-acceptance topics through its
+            // dense table: post-acceptance counts, a block-wide exclusive scan
+            // of the tables in place (16-bit prefixes), then each token takes
+            // the next slot of its topic's range
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+                if (tk[j] < 0 || zz[j] == zo[j]) continue;
+                uint32_t* tab = region + seg_reg[sl[j]];
+                atomicSub(&tab[(uint32_t)zo[j] >> 1], dense_unit((uint32_t)zo[j]));
+                atomicAdd(&tab[(uint32_t)zz[j] >> 1], dense_unit((uint32_t)zz[j]));
+            }
+            __syncthreads();
+            const int per = (used + kThreads - 1) / kThreads;
+            const int w0 = tid * per, w1 = min(used, w0 + per);
+            int sum = 0;
+            for (int w = w0; w < w1; ++w) {
+                const uint32_t x = region[w];
+                sum += (int)(x & 0xFFFFu) + (int)(x >> 16);
+            }
+            int run = block_excl_scan(sum, warp_tot, &s_total);
+            for (int w = w0; w < w1; ++w) {
+                const uint32_t x = region[w];
+                const int lo = (int)(x & 0xFFFFu);
+                region[w] = (uint32_t)run | ((uint32_t)(run + lo) << 16);
+                run += lo + (int)(x >> 16);
+            }
+            __syncthreads();
+            for (int s = tid; s < nseg; s += kThreads)
+                if (seg_tok[s + 1] > seg_tok[s]) seg_aux[s] = (int)(region[seg_reg[s]] & 0xFFFFu);
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < TPT; ++j) {
+                if (tk[j] < 0) continue;
+                const int slot = sl[j];
+                const uint32_t k = (uint32_t)zz[j];
+                const uint32_t old = atomicAdd(&region[seg_reg[slot] + (k >> 1)], dense_unit(k));
+                const int g = (int)((old >> ((k & 1) * 16)) & 0xFFFFu);
+                stage[pad(seg_tok[slot] + g - seg_aux[slot])] = k;
+            }
+            __syncthreads();
         }
         const int ntok = end - base;
-        if (!kDoc) {
+        if (kRadix) {
             // padding keys sort last; then the word's post-acceptance topics
             // are contiguous and ascending at [seg_tok[slot], seg_tok[slot+1])
             for (int p = ntok + tid; p < kThreads * TPT; p += kThreads) stage[pad(p)] = 0xFFFFFFFFu;
@@ -199,24 +378,25 @@ __global__ void __launch_bounds__(kThreads) batch_phase_kernel(PhaseArgs a,
             int sbits = 0;
             while ((1 << sbits) < nseg) ++sbits;
             block_radix_sort<TPT>(stage, cnt, sbits + kbits, warp_tot, &s_total);
+            __syncthreads();
         }
-        __syncthreads();
 
         // resolve picks and write back
-        const uint32_t kmask = (1u << kbits) - 1u;
+        const uint32_t kmask = kRadix ? ((1u << kbits) - 1u) : 0xFFFFFFFFu;
         if (kDoc) {
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {
-                if (tk[j] < 0) continue;
                 const int sb = seg_tok[sl[j]];
-                const int64_t pb = (int64_t)tk[j] * M;
 #pragma unroll
                 for (int i = 0; i < M; ++i) {
-                    int pk = pp[j].v[i];
-                    if (pk < 0) pk = (int)stage[pad(sb + (-pk - 1))];
-                    a.prop[pb + i] = pk;
+                    const int pk = pp[j].v[i];
+                    const int v = (int)stage[pad(sb + (pk < 0 ? -pk - 1 : 0))];
+                    pp[j].v[i] = pk < 0 ? v : pk;
                 }
-                a.z[tk[j]] = zz[j];
+                if (tk[j] >= 0) {
+                    store_props<M>(a.prop, tk[j], pp[j].v);
+                    a.z[tk[j]] = zz[j];
+                }
             }
         } else {
 #pragma unroll
@@ -262,7 +442,7 @@ __global__ void __launch_bounds__(kThreads) batch_phase_kernel(PhaseArgs a,
         __syncthreads();
     }
 
-    if (a.stage_ck) {
+    if (kDense) {
         for (int k = tid; k < K; k += kThreads) {
             const int d = dck_s[k];
             if (d != 0) atomicAdd(&a.ck[k], d);
@@ -270,64 +450,59 @@ __global__ void __launch_bounds__(kThreads) batch_phase_kernel(PhaseArgs a,
     }
 }
 
-int batch_smem_bytes(int K, int stage_ck, int region_words, int tpt, int word_phase) {
-    return batch_smem_layout(K, stage_ck, region_words, tpt, word_phase).total;
+int batch_smem_bytes(int K, int stage_ck, int region_words, int tpt, int word_phase, int dense) {
+    (void)stage_ck;   // c_k is staged in shared memory exactly with dense tables
+    return batch_smem_layout(K, dense, region_words, tpt, (word_phase && !dense) ? 1 : 0).total;
 }
 
-template <bool kDoc, int TPT>
-static cudaError_t launch_t(const PhaseArgs& a, const int2* batches, int nbatch, int* counter,
-                            int region_words, int kbits, int grid, cudaStream_t st) {
-    const int smem = batch_smem_bytes(a.K, a.stage_ck, region_words, TPT, kDoc ? 0 : 1);
-    cudaError_t e = cudaSuccess;
-    switch (a.M) {
-#define WL_CASE(MM)                                                                            \
-    case MM: {                                                                                 \
-        auto kern = batch_phase_kernel<kDoc, TPT, MM>;                                         \
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
-        if (e != cudaSuccess) return e;                                                        \
-        kern<<<grid, kThreads, smem, st>>>(a, batches, nbatch, counter, region_words, kbits);  \
-        return cudaGetLastError();                                                             \
-    }
-        WL_CASE(1)
-        WL_CASE(2)
-        WL_CASE(3)
-        WL_CASE(4)
-#undef WL_CASE
-        default:
-            return cudaErrorInvalidValue;
-    }
-    return e;
+template <bool kDoc, bool kDense, int TPT, int M>
+static const void* kernel_ptr() {
+    return (const void*)batch_phase_kernel<kDoc, kDense, TPT, M>;
 }
 
-int batch_blocks_per_sm(int K, int stage_ck, int region_words, int tpt, int word_phase, int M) {
-    const int smem = batch_smem_bytes(K, stage_ck, region_words, tpt, word_phase);
-    int n = 0;
-    const void* f = nullptr;
-#define WL_PICK(D, T, MM) \
-    if (word_phase == !D && tpt == T && M == MM) f = (const void*)batch_phase_kernel<D, T, MM>;
-    WL_PICK(true, 16, 1) WL_PICK(true, 16, 2) WL_PICK(true, 16, 3) WL_PICK(true, 16, 4)
-    WL_PICK(false, 16, 1) WL_PICK(false, 16, 2) WL_PICK(false, 16, 3) WL_PICK(false, 16, 4)
-    WL_PICK(true, 8, 1) WL_PICK(true, 8, 2) WL_PICK(true, 8, 3) WL_PICK(true, 8, 4)
-    WL_PICK(false, 8, 1) WL_PICK(false, 8, 2) WL_PICK(false, 8, 3) WL_PICK(false, 8, 4)
-#undef WL_PICK
+static const void* pick_kernel(bool doc, bool dense, int tpt, int M) {
+#define WL_K(D, DN, T)                                                     \
+    if (doc == D && dense == DN && tpt == T) {                             \
+        switch (M) {                                                       \
+            case 1: return kernel_ptr<D, DN, T, 1>();                      \
+            case 2: return kernel_ptr<D, DN, T, 2>();                      \
+            case 3: return kernel_ptr<D, DN, T, 3>();                      \
+            case 4: return kernel_ptr<D, DN, T, 4>();                      \
+            default: return nullptr;                                       \
+        }                                                                  \
+    }
+    WL_K(true, true, 8) WL_K(true, true, 16) WL_K(true, false, 8) WL_K(true, false, 16)
+    WL_K(false, true, 8) WL_K(false, true, 16) WL_K(false, false, 8) WL_K(false, false, 16)
+#undef WL_K
+    return nullptr;
+}
+
+int batch_blocks_per_sm(int K, int stage_ck, int region_words, int tpt, int word_phase, int M,
+                        int dense) {
+    const int smem = batch_smem_bytes(K, stage_ck, region_words, tpt, word_phase, dense);
+    const void* f = pick_kernel(!word_phase, dense != 0, tpt, M);
     if (!f) return 0;
     if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return 0;
+    int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kThreads, smem) != cudaSuccess) return 0;
     return n;
 }
 
-cudaError_t launch_batch_phase(bool doc, int tpt, const PhaseArgs& a, const int2* batches,
-                               int nbatch, int* counter, int region_words, int kbits, int grid,
+cudaError_t launch_batch_phase(bool doc, bool dense, int tpt, const PhaseArgs& a,
+                               const int4* batches, int nbatch, int* counter,
+                               const int32_t* seg_region, int region_words, int kbits, int grid,
                                cudaStream_t st) {
     if (nbatch <= 0) return cudaSuccess;
-    if (tpt == 16)
-        return doc ? launch_t<true, 16>(a, batches, nbatch, counter, region_words, kbits, grid, st)
-                   : launch_t<false, 16>(a, batches, nbatch, counter, region_words, kbits, grid, st);
-    if (tpt == 8)
-        return doc ? launch_t<true, 8>(a, batches, nbatch, counter, region_words, kbits, grid, st)
-                   : launch_t<false, 8>(a, batches, nbatch, counter, region_words, kbits, grid, st);
-    return cudaErrorInvalidValue;
+    const int smem = batch_smem_bytes(a.K, a.stage_ck, region_words, tpt, doc ? 0 : 1, dense ? 1 : 0);
+    const void* f = pick_kernel(doc, dense, tpt, a.M);
+    if (!f) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    PhaseArgs args = a;
+    void* params[] = {&args, (void*)&batches, &nbatch, &counter, (void*)&seg_region, &region_words,
+                      &kbits};
+    return cudaLaunchKernel(f, dim3(grid), dim3(kThreads), params, (size_t)smem, st);
 }
 
 }  // namespace wl

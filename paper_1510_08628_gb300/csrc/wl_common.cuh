@@ -11,30 +11,46 @@ constexpr int kThreads = 256;          // threads of every sampler block
 constexpr int kWarps = kThreads / 32;
 constexpr int kSegsMax = 512;          // segments (documents / words) per block batch
 constexpr int kHashCountBits = 12;     // packed hash entry: (topic + 1) << 12 | count
-constexpr int kMaxBatchTokens = 4095;  // count of a packed entry stays below 2^12
+constexpr int kMaxBatchTokens = 4093;  // count of a packed entry stays below 2^12
+constexpr int kDenseMaxK = 2048;       // dense 16-bit count tables up to this K, hash above
 
 enum Phase : uint32_t { kPhaseInit = 0, kPhaseDoc = 1, kPhaseWord = 2 };
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
-// multiply-xor bijection with the Weyl key schedule.
+// multiply-xor bijection.  The Weyl key schedule is precomputed on the host
+// (round_keys) and passed in the kernel parameters, so a round costs two
+// 32x32->64 multiplies and two 3-input xors.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+struct RoundKeys { uint32_t k[20]; };   // (k0, k1) of rounds 0..9
+
+__host__ __device__ inline RoundKeys round_keys(uint64_t seed) {
+    RoundKeys r;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        r.k[2 * i] = k0;
+        r.k[2 * i + 1] = k1;
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
+    }
+    return r;
+}
+
+__device__ __forceinline__ uint4 philox(uint4 c, const RoundKeys& rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k[2 * r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ rk.k[2 * r + 1], (uint32_t)p0);
     }
     return c;
 }
 
 // The sampler's block for (token t, iteration, phase, MH step i, stream).
 __device__ __forceinline__ uint4 draw(uint32_t t, uint32_t iter, uint32_t phase, uint32_t step,
-                                      uint32_t stream, uint32_t k0, uint32_t k1) {
-    return philox(make_uint4(t, iter, (phase << 8) | step, stream), k0, k1);
+                                      uint32_t stream, const RoundKeys& rk) {
+    return philox(make_uint4(t, iter, (phase << 8) | step, stream), rk);
 }
 
 // u = (r >> 8) * 2^-24, exact in FP32.
@@ -124,13 +140,17 @@ struct PhaseArgs {
     int32_t* z;              // [N] word-major topics
     int32_t* prop;           // [N*M] word-major proposals
     const int32_t* perm;     // [N] doc-major position -> word-major index
+    const int32_t* sperm;    // document batches: word-major indices of each batch's tokens,
+                             // ascending within the batch (same position range as the batch)
+    const uint32_t* sinfo;   // (segment slot << 16) | position within the batch, per sperm entry
     const int32_t* seg_off;  // [S+1] token offsets of documents (doc-major) or words
     const float* ckb;        // [K] (float)c_k + beta_bar, frozen for the phase
     int32_t* ck;             // [K] c_k, receives this phase's deltas
     int32_t K, M;
     float g;                 // alpha (document phase) or beta (word phase)
     float G;                 // alpha_bar or K*beta: mixture weight L / (L + G)
-    uint32_t iter, k0, k1;   // iteration and Philox key
+    uint32_t iter;           // iteration
+    RoundKeys rk;            // Philox key schedule
     int32_t stage_ck;        // 1: c_k table and deltas in shared memory
 };
 

@@ -9,26 +9,35 @@
 //   draw   : M proposals per token from Eq. 6 -- positioning through perm
 //            over the post-acceptance document, or the j-th smallest
 //            post-acceptance topic of the word (inverse CDF of row_post).
-// The draw pass recomputes the Philox blocks of the accept pass.
+// Word chunks are contiguous in the word-major arrays and are streamed with
+// 128-bit loads and stores, several in flight per thread.  For words, the
+// accept pass draws each token's Philox blocks once and stores its picks in
+// the consumed proposal slots; the draw pass only resolves ranks.  For long
+// documents the draw pass recomputes the blocks.
 #include "wl_block.cuh"
 #include "wl_kernels.h"
 
 namespace wl {
 
-// Warp-aggregated increment of h[k]: lanes holding the same k add once.
+constexpr int kVecUnroll = 2;   // 16-byte vectors in flight per thread per array
+constexpr int kGuideBits = 12;  // guide table of 4096 buckets over a word's ranks
+
+// Increment of a shared-memory histogram bin.
 __device__ __forceinline__ void agg_add(int* h, int k) {
-    const unsigned act = __activemask();
-    const unsigned m = __match_any_sync(act, k);
-    const int lane = threadIdx.x & 31;
-    if (lane == __ffs(m) - 1) atomicAdd(&h[k], __popc(m));
+    atomicAdd(&h[k], 1);
+}
+
+__device__ __forceinline__ int elem(const int4& v, int e) {
+    return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
 }
 
 int huge_smem_bytes(int K, int stage_ck, int pass, bool doc) {
-    // pass 0 hist: K; pass 1 accept: row + (word) hist + staged ck; pass 2 draw: K+1 prefix
+    // pass 0 hist: K; pass 1 accept: row + (word) hist + staged ck;
+    // pass 2 draw: K+1 prefix + guide table
     int words = 0;
     if (pass == 0) words = K;
     else if (pass == 1) words = K + (doc ? 0 : K) + (stage_ck ? 2 * K : 0);
-    else words = doc ? 0 : K + 1;
+    else words = doc ? 0 : K + 1 + (1 << kGuideBits);
     return ((words * 4) + 15) & ~15;
 }
 
@@ -39,11 +48,32 @@ __global__ void __launch_bounds__(kThreads) huge_hist_kernel(PhaseArgs a, const 
     const int K = a.K, tid = threadIdx.x;
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const int4 ch = chunks[c];
+        const int p0 = ch.z, p1 = ch.z + ch.w;
         for (int k = tid; k < K; k += kThreads) hist[k] = 0;
         __syncthreads();
-        for (int p = ch.z + tid; p < ch.z + ch.w; p += kThreads) {
-            const int t = kDoc ? a.perm[p] : p;
-            agg_add(hist, a.z[t]);
+        if (kDoc) {
+            for (int p = p0 + tid; p < p1; p += kThreads) agg_add(hist, a.z[a.perm[p]]);
+        } else {
+            const int v0 = p0 >> 2, v1 = (p1 + 3) >> 2;
+            const int4* zv = reinterpret_cast<const int4*>(a.z);
+            for (int vb = v0 + tid; vb < v1; vb += kThreads * kVecUnroll) {
+                int4 x[kVecUnroll];
+#pragma unroll
+                for (int u = 0; u < kVecUnroll; ++u) {
+                    const int v = vb + u * kThreads;
+                    if (v < v1) x[u] = zv[v];
+                }
+#pragma unroll
+                for (int u = 0; u < kVecUnroll; ++u) {
+                    const int v = vb + u * kThreads;
+                    if (v >= v1) continue;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int q = 4 * v + e;
+                        if (q >= p0 && q < p1) agg_add(hist, elem(x[u], e));
+                    }
+                }
+            }
         }
         __syncthreads();
         int32_t* row = rows + (int64_t)ch.x * K;
@@ -51,6 +81,24 @@ __global__ void __launch_bounds__(kThreads) huge_hist_kernel(PhaseArgs a, const 
             if (hist[k] != 0) atomicAdd(&row[k], hist[k]);
         __syncthreads();
     }
+}
+
+// M chained MH steps of one token from z0 against the count row (Eq. 7).
+template <int M>
+__device__ __forceinline__ int mh_chain(const PhaseArgs& a, uint32_t t, uint32_t phase, int z0,
+                                        const int* pr, const int* row, const float* ckb_s) {
+    int s = z0;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const int tp = pr[i];
+        if (tp != s) {
+            const uint4 r = draw(t, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
+            const float cs = a.stage_ck ? ckb_s[s] : __ldg(a.ckb + s);
+            const float ct = a.stage_ck ? ckb_s[tp] : __ldg(a.ckb + tp);
+            if (accept(r.x, row[s], row[tp], a.g, cs, ct)) s = tp;
+        }
+    }
+    return s;
 }
 
 template <bool kDoc, int M>
@@ -70,42 +118,107 @@ __global__ void __launch_bounds__(kThreads) huge_accept_kernel(PhaseArgs a, cons
         }
     }
     const uint32_t phase = kDoc ? kPhaseDoc : kPhaseWord;
+    auto delta = [&](int z0, int s) {
+        if (a.stage_ck) {
+            atomicSub(&dck_s[z0], 1);
+            atomicAdd(&dck_s[s], 1);
+        } else {
+            atomicSub(&a.ck[z0], 1);
+            atomicAdd(&a.ck[s], 1);
+        }
+    };
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const int4 ch = chunks[c];
+        const int p0 = ch.z, p1 = ch.z + ch.w;
         const int32_t* rp = rows_pre + (int64_t)ch.x * K;
         for (int k = tid; k < K; k += kThreads) {
             row[k] = rp[k];
             if (!kDoc) hist[k] = 0;
         }
         __syncthreads();
-        for (int p = ch.z + tid; p < ch.z + ch.w; p += kThreads) {
-            const int t = kDoc ? a.perm[p] : p;
-            const int z0 = a.z[t];
-            int pr[M];
+        if (kDoc) {
+            for (int p = p0 + tid; p < p1; p += kThreads) {
+                const int t = a.perm[p];
+                const int z0 = a.z[t];
+                int pr[M];
 #pragma unroll
-            for (int i = 0; i < M; ++i) pr[i] = a.prop[(int64_t)t * M + i];
-            int s = z0;
-#pragma unroll
-            for (int i = 0; i < M; ++i) {
-                const int tp = pr[i];
-                if (tp != s) {
-                    const uint4 r = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.k0, a.k1);
-                    const float cs = a.stage_ck ? ckb_s[s] : __ldg(a.ckb + s);
-                    const float ct = a.stage_ck ? ckb_s[tp] : __ldg(a.ckb + tp);
-                    if (accept(r.x, row[s], row[tp], a.g, cs, ct)) s = tp;
+                for (int i = 0; i < M; ++i) pr[i] = a.prop[(int64_t)t * M + i];
+                const int s = mh_chain<M>(a, (uint32_t)t, phase, z0, pr, row, ckb_s);
+                if (s != z0) {
+                    a.z[t] = s;
+                    delta(z0, s);
                 }
             }
-            if (s != z0) {
-                a.z[t] = s;
-                if (a.stage_ck) {
-                    atomicSub(&dck_s[z0], 1);
-                    atomicAdd(&dck_s[s], 1);
-                } else {
-                    atomicSub(&a.ck[z0], 1);
-                    atomicAdd(&a.ck[s], 1);
+        } else {
+            // word chunk: 128-bit loads of z and of the proposals; the M blocks
+            // of each token are drawn here once, the accept uses r0 and the
+            // pick of Eq. 6 (a topic, or -(rank + 1) resolved by the draw pass)
+            // is written over the consumed proposal
+            const int Ls = a.seg_off[ch.y + 1] - a.seg_off[ch.y];
+            const float Lf = __int2float_rn(Ls);
+            const float LG = __fadd_rn(Lf, a.G);
+            const int v0 = p0 >> 2, v1 = (p1 + 3) >> 2;
+            int4* zv = reinterpret_cast<int4*>(a.z);
+            int4* pv = reinterpret_cast<int4*>(a.prop);
+            for (int vb = v0 + tid; vb < v1; vb += kThreads * kVecUnroll) {
+                int4 x[kVecUnroll], y[kVecUnroll][M];
+#pragma unroll
+                for (int u = 0; u < kVecUnroll; ++u) {
+                    const int v = vb + u * kThreads;
+                    if (v < v1) {
+                        x[u] = zv[v];
+#pragma unroll
+                        for (int i = 0; i < M; ++i) y[u][i] = pv[(int64_t)v * M + i];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kVecUnroll; ++u) {
+                    const int v = vb + u * kThreads;
+                    if (v >= v1) continue;
+                    int out[4], pk[4 * M];
+                    bool full = true;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int q = 4 * v + e;
+                        out[e] = elem(x[u], e);
+#pragma unroll
+                        for (int i = 0; i < M; ++i) pk[e * M + i] = 0;
+                        if (q < p0 || q >= p1) { full = false; continue; }
+                        const int z0 = out[e];
+                        int s = z0;
+#pragma unroll
+                        for (int i = 0; i < M; ++i) {
+                            const uint4 r = draw((uint32_t)q, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
+                            const int tp = elem(y[u][(e * M + i) / 4], (e * M + i) % 4);
+                            if (tp != s) {
+                                const float cs = a.stage_ck ? ckb_s[s] : __ldg(a.ckb + s);
+                                const float ct = a.stage_ck ? ckb_s[tp] : __ldg(a.ckb + tp);
+                                if (accept(r.x, row[s], row[tp], a.g, cs, ct)) s = tp;
+                            }
+                            pk[e * M + i] = coin(r.y, Lf, LG) ? -(int)(dice(r.z, (uint32_t)Ls) + 1)
+                                                              : (int)dice(r.z, (uint32_t)K);
+                        }
+                        if (s != z0) delta(z0, s);
+                        agg_add(hist, s);
+                        out[e] = s;
+                    }
+                    if (full) {
+                        zv[v] = make_int4(out[0], out[1], out[2], out[3]);
+#pragma unroll
+                        for (int i = 0; i < M; ++i)
+                            pv[(int64_t)v * M + i] = make_int4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int q = 4 * v + e;
+                            if (q < p0 || q >= p1) continue;
+                            a.z[q] = out[e];
+#pragma unroll
+                            for (int i = 0; i < M; ++i) a.prop[(int64_t)q * M + i] = pk[e * M + i];
+                        }
+                    }
                 }
             }
-            if (!kDoc) agg_add(hist, s);
         }
         __syncthreads();
         if (!kDoc) {
@@ -134,6 +247,7 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const 
         const int4 ch = chunks[c];
         const int sb = a.seg_off[ch.y];
         const int Ls = a.seg_off[ch.y + 1] - sb;
+        const int p0 = ch.z, p1 = ch.z + ch.w;
         if (!kDoc) {
             const int32_t* rq = rows_post + (int64_t)ch.x * K;
             int carry = 0;
@@ -145,33 +259,86 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const 
                 carry += s_total;
             }
             if (tid == 0) P[K] = carry;
+            __syncthreads();
+            // guide[b] = the answer for the smallest rank of bucket b,
+            // ceil(b L / 2^kGuideBits); a rank j's bucket is at least
+            // (j * floor(2^(32+kGuideBits) / L)) >> 32
+            int* guide = P + K + 1;
+            for (int b = tid; b < (1 << kGuideBits); b += kThreads) {
+                const int j = (int)((((int64_t)b * Ls) + (1 << kGuideBits) - 1) >> kGuideBits);
+                int lo = 0, hi = K - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (P[mid] <= j) lo = mid; else hi = mid - 1;
+                }
+                guide[b] = lo;
+            }
         }
         __syncthreads();
         const float Lf = __int2float_rn(Ls);
         const float LG = __fadd_rn(Lf, a.G);
-        for (int p = ch.z + tid; p < ch.z + ch.w; p += kThreads) {
-            const int t = kDoc ? a.perm[p] : p;
+        if (kDoc) {
+            for (int p = p0 + tid; p < p1; p += kThreads) {
+                const int t = a.perm[p];
 #pragma unroll
-            for (int i = 0; i < M; ++i) {
-                const uint4 r = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.k0, a.k1);
-                int k;
-                if (coin(r.y, Lf, LG)) {
-                    const int j = (int)dice(r.z, (uint32_t)Ls);
-                    if (kDoc) {
-                        k = a.z[a.perm[sb + j]];
-                    } else {
-                        // largest k with P[k] <= j: the j-th smallest topic
-                        int lo = 0, hi = K - 1;
-                        while (lo < hi) {
-                            const int mid = (lo + hi + 1) >> 1;
-                            if (P[mid] <= j) lo = mid; else hi = mid - 1;
-                        }
-                        k = lo;
-                    }
-                } else {
-                    k = (int)dice(r.z, (uint32_t)a.K);
+                for (int i = 0; i < M; ++i) {
+                    const uint4 r = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
+                    const int k = coin(r.y, Lf, LG) ? a.z[a.perm[sb + (int)dice(r.z, (uint32_t)Ls)]]
+                                                    : (int)dice(r.z, (uint32_t)K);
+                    a.prop[(int64_t)t * M + i] = k;
                 }
-                a.prop[(int64_t)t * M + i] = k;
+            }
+        } else {
+            // resolve the picks the accept pass stored: a rank j < L_w becomes
+            // the j-th smallest post-acceptance topic of the word
+            const uint64_t mult = (1ull << (32 + kGuideBits)) / (uint64_t)Ls;
+            const int* guide = P + K + 1;
+            const int v0 = p0 >> 2, v1 = (p1 + 3) >> 2;
+            int4* pv = reinterpret_cast<int4*>(a.prop);
+            for (int vb = v0 + tid; vb < v1; vb += kThreads * kVecUnroll) {
+                int4 y[kVecUnroll][M];
+#pragma unroll
+                for (int u = 0; u < kVecUnroll; ++u) {
+                    const int v = vb + u * kThreads;
+                    if (v < v1)
+#pragma unroll
+                        for (int i = 0; i < M; ++i) y[u][i] = pv[(int64_t)v * M + i];
+                }
+#pragma unroll
+                for (int u = 0; u < kVecUnroll; ++u) {
+                    const int v = vb + u * kThreads;
+                    if (v >= v1) continue;
+                    int out[4 * M];
+#pragma unroll
+                    for (int n = 0; n < 4 * M; ++n) {
+                        // only this chunk's tokens: an edge vector's other
+                        // entries belong to a neighbouring chunk or word
+                        const int q = 4 * v + n / M;
+                        int pk = elem(y[u][n / 4], n % 4);
+                        if (q < p0 || q >= p1) pk = 0;
+                        if (pk < 0) {
+                            const int j = -pk - 1;
+                            int k = guide[(int)(((uint64_t)j * mult) >> 32)];
+                            while (P[k + 1] <= j) ++k;
+                            pk = k;
+                        }
+                        out[n] = pk;
+                    }
+                    const bool full = (4 * v >= p0) && (4 * v + 3 < p1);
+                    if (full) {
+#pragma unroll
+                        for (int i = 0; i < M; ++i)
+                            pv[(int64_t)v * M + i] = make_int4(out[4 * i], out[4 * i + 1], out[4 * i + 2], out[4 * i + 3]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int q = 4 * v + e;
+                            if (q < p0 || q >= p1) continue;
+#pragma unroll
+                            for (int i = 0; i < M; ++i) a.prop[(int64_t)q * M + i] = out[e * M + i];
+                        }
+                    }
+                }
             }
         }
         __syncthreads();

@@ -8,12 +8,24 @@
 
 namespace wl {
 
-// On-chip batch tier (wl_batch.cu).
-int batch_smem_bytes(int K, int stage_ck, int region_words, int tpt, int word_phase);
-int batch_blocks_per_sm(int K, int stage_ck, int region_words, int tpt, int word_phase, int M);
-cudaError_t launch_batch_phase(bool doc, int tpt, const PhaseArgs& a, const int2* batches,
-                               int nbatch, int* counter, int region_words, int kbits, int grid,
+// On-chip batch tier (wl_batch.cu).  A batch is {first segment, end
+// segment, table words, 0}; seg_region[s] is segment s's table offset in its
+// batch; dense selects 16-bit dense tables (else hash tables).
+int batch_smem_bytes(int K, int stage_ck, int region_words, int tpt, int word_phase, int dense);
+int batch_blocks_per_sm(int K, int stage_ck, int region_words, int tpt, int word_phase, int M,
+                        int dense);
+cudaError_t launch_batch_phase(bool doc, bool dense, int tpt, const PhaseArgs& a,
+                               const int4* batches, int nbatch, int* counter,
+                               const int32_t* seg_region, int region_words, int kbits, int grid,
                                cudaStream_t st);
+
+// Warp tier of the document phase (wl_docwarp.cu): docs = ids of documents
+// with 1..32*tpl tokens.
+int docwarp_table_words(int K, int tpl, int dense);
+int docwarp_smem_bytes(int K, int stage_ck, int tpl, int dense);
+int docwarp_blocks_per_sm(int K, int stage_ck, int tpl, int M, int dense);
+cudaError_t launch_doc_warp(int tpl, bool dense, const PhaseArgs& a, const int32_t* docs, int ndocs,
+                            int* counter, int grid, cudaStream_t st);
 
 // Multi-pass tier for segments too long for one block (wl_huge.cu).
 // chunk = {row, segment id, first token position, token count}
@@ -28,8 +40,8 @@ cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const int4* chunks, i
                              const int32_t* rows_post, int grid, cudaStream_t st);
 
 // Initialisation, c_k, export, log-likelihood (wl_misc.cu).
-cudaError_t launch_init_z(int32_t* z, int32_t* prop, int64_t N, int K, int M, uint32_t k0,
-                          uint32_t k1, cudaStream_t st);
+cudaError_t launch_init_z(int32_t* z, int32_t* prop, int64_t N, int K, int M, uint64_t seed,
+                          cudaStream_t st);
 cudaError_t launch_topic_hist(const int32_t* z, int64_t N, int32_t* ck, int K, cudaStream_t st);
 cudaError_t launch_finalize_ck(const int32_t* ck, float* ckb, int K, float beta_bar,
                                int32_t* counters, int ncounters, cudaStream_t st);
@@ -38,7 +50,7 @@ cudaError_t launch_gather_docmajor(const int32_t* z, const int32_t* perm, int64_
                                    cudaStream_t st);
 cudaError_t launch_check_range(const int32_t* v, int64_t n, int K, int32_t* bad, cudaStream_t st);
 cudaError_t launch_loglik_batches(bool doc, const int32_t* z, const int32_t* perm,
-                                  const int32_t* seg_off, const int2* batches, int nbatch, int K,
+                                  const int32_t* seg_off, const int4* batches, int nbatch, int K,
                                   double g, int region_words, double* out, int grid,
                                   cudaStream_t st);
 cudaError_t launch_loglik_rows(const int32_t* rows, int64_t nrows, int K, double g, double* out,

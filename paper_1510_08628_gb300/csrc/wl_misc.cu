@@ -13,21 +13,20 @@ static int grid_for(int64_t n, int per_block = kThreads, int cap = 152 * 16) {
     return (int)g;
 }
 
-__global__ void init_z_kernel(int32_t* z, int32_t* prop, int64_t N, int K, int M, uint32_t k0,
-                              uint32_t k1) {
+__global__ void init_z_kernel(int32_t* z, int32_t* prop, int64_t N, int K, int M, RoundKeys rk) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const uint4 r = draw((uint32_t)t, 0u, kPhaseInit, 0u, 0u, k0, k1);
+        const uint4 r = draw((uint32_t)t, 0u, kPhaseInit, 0u, 0u, rk);
         const int k = (int)dice(r.x, (uint32_t)K);
         z[t] = k;
         for (int i = 0; i < M; ++i) prop[t * M + i] = k;
     }
 }
 
-cudaError_t launch_init_z(int32_t* z, int32_t* prop, int64_t N, int K, int M, uint32_t k0,
-                          uint32_t k1, cudaStream_t st) {
+cudaError_t launch_init_z(int32_t* z, int32_t* prop, int64_t N, int K, int M, uint64_t seed,
+                          cudaStream_t st) {
     if (N <= 0) return cudaSuccess;
-    init_z_kernel<<<grid_for(N), kThreads, 0, st>>>(z, prop, N, K, M, k0, k1);
+    init_z_kernel<<<grid_for(N), kThreads, 0, st>>>(z, prop, N, K, M, round_keys(seed));
     return cudaGetLastError();
 }
 
@@ -130,7 +129,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 int loglik_smem_bytes(int region_words) { return (3 * kSegsMax + 4 + region_words) * 4; }
 
 __global__ void __launch_bounds__(kThreads) loglik_batch_kernel(bool doc, const int32_t* z, const int32_t* perm,
-                                                                const int32_t* seg_off, const int2* batches,
+                                                                const int32_t* seg_off, const int4* batches,
                                                                 int nbatch, int K, double g, double* out) {
     extern __shared__ __align__(16) int lsm[];
     int* seg_tok = lsm;
@@ -144,7 +143,7 @@ __global__ void __launch_bounds__(kThreads) loglik_batch_kernel(bool doc, const 
     const double lg0 = lgamma(g);
     double acc = 0.0;
     for (int b = blockIdx.x; b < nbatch; b += gridDim.x) {
-        const int2 br = batches[b];
+        const int4 br = batches[b];
         const int nseg = br.y - br.x;
         const int base = seg_off[br.x], end = seg_off[br.y];
         for (int s = tid; s < nseg; s += kThreads) {
@@ -194,7 +193,7 @@ __global__ void __launch_bounds__(kThreads) loglik_batch_kernel(bool doc, const 
 }
 
 cudaError_t launch_loglik_batches(bool doc, const int32_t* z, const int32_t* perm,
-                                  const int32_t* seg_off, const int2* batches, int nbatch, int K,
+                                  const int32_t* seg_off, const int4* batches, int nbatch, int K,
                                   double g, int region_words, double* out, int grid,
                                   cudaStream_t st) {
     if (nbatch <= 0) return cudaSuccess;

@@ -129,7 +129,8 @@ def test_edge_corpora_bit_exact(kind, K, M):
 
 
 TUNINGS = [None, {"batch_max_tokens": 64}, {"batch_max_tokens": 2000, "region_budget": 1024},
-           {"huge_chunk": 300, "batch_max_tokens": 500}, {"batch_max_tokens": 4095}]
+           {"huge_chunk": 300, "batch_max_tokens": 500}, {"batch_max_tokens": 4095},
+           {"doc_warp_max": 512}, {"doc_warp_max": 20, "batch_max_tokens": 3000}]
 
 
 def test_schedule_independence():
