@@ -270,6 +270,7 @@ def main():
     info = gpu.info()
     gpu.sweep(args.warmup)
     torch.cuda.synchronize()
+    gpu.sync()   # raises if a kernel's index check failed
 
     # timed region: K sweeps on the library's stream
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -281,6 +282,7 @@ def main():
         stop.record(stream)
         torch.cuda.synchronize()
         barrier(ws)
+    gpu.sync()
     ms = start.elapsed_time(stop)
     ms_max = reduce_max(ms, ws)
     value = c.N * args.steps * ws / (ms_max / 1000.0)

@@ -180,6 +180,19 @@ int warplda_profile(warplda_ctx* ctx, int32_t enable);
 int warplda_kernel_times(warplda_ctx* ctx, int32_t cap, const char** names, int64_t* launches,
                          double* total_ms);
 
+/*
+ * warplda_sync -- wait for the work queued on the context's stream and report
+ * the kernels' index checks.  Every sampler kernel validates the indices it
+ * takes from stored state (topics, proposals, token pointers, work lists)
+ * before it uses them; a failed check skips the access and is recorded.
+ * Returns OK, or ECUDA with the kernel site and value of the first failed
+ * check since the last report (the record is then cleared).  warplda_counts,
+ * warplda_get_state and warplda_loglik report the record the same way.
+ * Setting WARPLDA_SYNC_CHECK=1 in the environment before warplda_init makes
+ * the context read the record after every launch (debugging; slow).
+ */
+int warplda_sync(warplda_ctx* ctx);
+
 void warplda_destroy(warplda_ctx* ctx);
 const char* warplda_last_error(void);
 
@@ -198,6 +211,8 @@ const char* warplda_last_error(void);
  *   z_docmajor_dev  device int32[N], topics in document order.
  *   word_ptr_dev    device int64[V+1], token offsets of the words.
  *   z_wordmajor_dev device int32[N], the same topics grouped by word.
+ *               A value outside [0, K) is not counted and makes the
+ *               result NaN; the offsets must be valid (not checked).
  *   out_dev     device double, receives the log-likelihood.
  *   cuda_stream cudaStream_t or NULL; the call is asynchronous on it.
  * It calls no cudaMalloc, cudaFree or allocating library routine.  Its

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -97,6 +98,8 @@ struct warplda_ctx {
     float* ckb = nullptr;
     double* d_ll = nullptr;
     int32_t* d_bad = nullptr;
+    int32_t* d_fault = nullptr;   // index-check record of the kernels
+    bool sync_check = false;      // WARPLDA_SYNC_CHECK=1: read the record after every launch
     int32_t *rows_doc = nullptr, *rows_pre = nullptr, *rows_post = nullptr;
     int64_t rows_words = 0;
     Tier docs, words;
@@ -232,6 +235,17 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
     lclose((int)S);
 }
 
+// Reads the index-check record of the kernels (synchronises); a non-zero
+// record means a kernel met a bad index and skipped the access.
+int check_record(warplda_ctx* c, const char* where) {
+    int32_t f[4] = {0, 0, 0, 0};
+    WL_CU(cudaMemcpyAsync(f, c->d_fault, sizeof(f), cudaMemcpyDeviceToHost, c->st), "read check record");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    if (f[0] == 0) return WARPLDA_OK;
+    WL_CU(cudaMemsetAsync(c->d_fault, 0, sizeof(f), c->st), "clear check record");
+    return fail(WARPLDA_ECUDA, "index check failed (%s): site %d value %d", where, f[0], f[1]);
+}
+
 int launch_rec(warplda_ctx* c, int cls, cudaError_t (*fn)(warplda_ctx*, void*), void* arg) {
     cudaEvent_t a = nullptr, b = nullptr;
     if (c->prof) {
@@ -244,6 +258,12 @@ int launch_rec(warplda_ctx* c, int cls, cudaError_t (*fn)(warplda_ctx*, void*), 
     if (c->prof) {
         WL_CU(cudaEventRecord(b, c->st), "cudaEventRecord");
         c->recs.push_back(Rec{cls, a, b});
+    }
+    if (c->sync_check) {
+        // debugging mode (WARPLDA_SYNC_CHECK=1): every launch is followed by a
+        // look at the index-check record
+        const int rc = check_record(c, kClassNames[cls]);
+        if (rc) return rc;
     }
     return WARPLDA_OK;
 }
@@ -265,6 +285,9 @@ PhaseArgs phase_args(warplda_ctx* c, bool doc, uint32_t iter) {
     a.iter = iter;
     a.rk = round_keys(c->seed);
     a.stage_ck = c->stage_ck;
+    a.N = c->N;
+    a.nseg_total = doc ? c->D : c->V;
+    a.fault = c->d_fault;
     return a;
 }
 
@@ -290,7 +313,7 @@ int run_phase(warplda_ctx* c, bool doc) {
         rc = launch_rec(c, doc ? kcDocHugeHist : kcWordMegaHist, [](warplda_ctx* cc, void* p) {
             PhaseCall* q = (PhaseCall*)p;
             Tier& TT = q->doc ? cc->docs : cc->words;
-            return launch_huge_hist(q->doc, q->a, TT.d_chunks, (int)TT.chunks.size(),
+            return launch_huge_hist(q->doc, q->a, TT.d_chunks, (int)TT.chunks.size(), (int)TT.nrows,
                                     q->doc ? cc->rows_doc : cc->rows_pre, cc->grid_hist, cc->st);
         }, &pc);
         if (rc) return rc;
@@ -323,7 +346,7 @@ int run_phase(warplda_ctx* c, bool doc) {
         rc = launch_rec(c, doc ? kcDocHugeAccept : kcWordMegaAccept, [](warplda_ctx* cc, void* p) {
             PhaseCall* q = (PhaseCall*)p;
             Tier& TT = q->doc ? cc->docs : cc->words;
-            return launch_huge_accept(q->doc, q->a, TT.d_chunks, (int)TT.chunks.size(),
+            return launch_huge_accept(q->doc, q->a, TT.d_chunks, (int)TT.chunks.size(), (int)TT.nrows,
                                       q->doc ? cc->rows_doc : cc->rows_pre, cc->rows_post,
                                       q->doc ? cc->grid_acc_doc : cc->grid_acc_word, cc->st);
         }, &pc);
@@ -331,8 +354,8 @@ int run_phase(warplda_ctx* c, bool doc) {
         rc = launch_rec(c, doc ? kcDocHugeDraw : kcWordMegaDraw, [](warplda_ctx* cc, void* p) {
             PhaseCall* q = (PhaseCall*)p;
             Tier& TT = q->doc ? cc->docs : cc->words;
-            return launch_huge_draw(q->doc, q->a, TT.d_chunks, (int)TT.chunks.size(),
-                                    cc->rows_post, cc->grid_draw, cc->st);
+            return launch_huge_draw(q->doc, q->a, TT.d_chunks, (int)TT.chunks.size(), (int)TT.nrows,
+                                    q->doc ? cc->rows_doc : cc->rows_post, cc->grid_draw, cc->st);
         }, &pc);
         if (rc) return rc;
     }
@@ -402,6 +425,10 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     c->k0 = (uint32_t)seed;
     c->k1 = (uint32_t)(seed >> 32);
     c->st = (cudaStream_t)cuda_stream;
+    {
+        const char* sc = std::getenv("WARPLDA_SYNC_CHECK");
+        c->sync_check = sc && sc[0] == '1';
+    }
     c->stage_ck = K <= 4096 ? 1 : 0;
     while ((1 << c->kbits) < K) ++c->kbits;
     // block batches: up to 2045 tokens with 8 tokens per thread, up to 4093
@@ -488,6 +515,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     if ((rc = dalloc(c, &c->counters, kCounters, "alloc counters"))) return bail(rc);
     if ((rc = dalloc(c, &c->d_ll, 1, "alloc loglik"))) return bail(rc);
     if ((rc = dalloc(c, &c->d_bad, 1, "alloc flag"))) return bail(rc);
+    if ((rc = dalloc(c, &c->d_fault, 4, "alloc check record"))) return bail(rc);
     // count rows of the multi-pass tier; each row set starts 16-byte aligned
     // and is zeroed in whole int4 units
     const int64_t rd = r4(c->docs.nrows * (int64_t)K), rw = r4(c->words.nrows * (int64_t)K);
@@ -616,7 +644,7 @@ int warplda_counts(warplda_ctx* c, int32_t* z_docmajor, int32_t* ck) {
     }
     if (ck) WL_CU(cudaMemcpyAsync(ck, c->ck, (size_t)c->K * 4, cudaMemcpyDeviceToHost, c->st), "copy c_k");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
-    return WARPLDA_OK;
+    return check_record(c, "counts");
 }
 
 int warplda_get_state(warplda_ctx* c, int32_t* z, int32_t* prop, int32_t* ck, uint32_t* sweeps) {
@@ -627,7 +655,7 @@ int warplda_get_state(warplda_ctx* c, int32_t* z, int32_t* prop, int32_t* ck, ui
     if (ck) WL_CU(cudaMemcpyAsync(ck, c->ck, (size_t)c->K * 4, cudaMemcpyDeviceToHost, c->st), "copy c_k");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     if (sweeps) *sweeps = c->iter;
-    return WARPLDA_OK;
+    return check_record(c, "state");
 }
 
 int warplda_set_state(warplda_ctx* c, const int32_t* z, const int32_t* prop, uint32_t sweeps) {
@@ -684,18 +712,20 @@ int warplda_loglik(warplda_ctx* c, double* out) {
         int32_t* rows = doc ? c->rows_doc : c->rows_pre;
         if (!T.chunks.empty()) {
             WL_CU(launch_zero(rows, r4(T.nrows * (int64_t)c->K), c->st), "zero rows");
-            WL_CU(launch_huge_hist(doc, pa, T.d_chunks, (int)T.chunks.size(), rows, c->grid_hist, c->st), "loglik rows");
+            WL_CU(launch_huge_hist(doc, pa, T.d_chunks, (int)T.chunks.size(), (int)T.nrows, rows, c->grid_hist,
+                                   c->st), "loglik rows");
             WL_CU(launch_loglik_rows(rows, T.nrows, c->K, doc ? a : b, c->d_ll, c->st), "loglik rows");
         }
         WL_CU(launch_loglik_batches(doc, c->z, c->perm, doc ? c->doc_off : c->word_off,
                                     T.d_ll_batches, (int)T.ll_batches.size(), c->K, doc ? a : b,
-                                    8192, c->d_ll, c->sms * 2, c->st), "loglik batches");
+                                    8192, c->N, doc ? c->D : c->V, c->d_fault, c->d_ll, c->sms * 2,
+                                    c->st), "loglik batches");
     }
     WL_CU(launch_loglik_lengths(c->doc_off, c->D, abar, c->d_ll, c->st), "loglik lengths");
     WL_CU(launch_loglik_topics(c->ck, c->K, bbar, c->d_ll, c->st), "loglik topics");
     WL_CU(cudaMemcpyAsync(out, c->d_ll, sizeof(double), cudaMemcpyDeviceToHost, c->st), "copy loglik");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
-    return WARPLDA_OK;
+    return check_record(c, "loglik");
 }
 
 struct CkptHeader {
@@ -799,6 +829,12 @@ int warplda_kernel_times(warplda_ctx* c, int32_t cap, const char** names, int64_
         ++k;
     }
     return k;
+}
+
+int warplda_sync(warplda_ctx* c) {
+    if (!c) return fail(WARPLDA_EINVAL, "null context");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    return check_record(c, "sync");
 }
 
 void warplda_destroy(warplda_ctx* c) {

@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
 
     const int tid = threadIdx.x;
     const int K = a.K;
+    Checks chk;
     if (tid == 0) s_batch = atomicAdd(counter, 1);
     if (kDense) {
         for (int k = tid; k < K; k += kThreads) {
@@ -133,21 +134,39 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
         const int b = s_batch;
         if (b >= nbatch) break;
         const int4 br = batches[b];      // {first segment, end segment, table words, 0}
-        const int nseg = br.y - br.x;
-        const int used = br.z;
+        int nseg = br.y - br.x;
+        int used = br.z;
         const int base = a.seg_off[br.x];
-        const int end = a.seg_off[br.y];
+        int end = a.seg_off[br.y];
+        if (!(chk(br.x >= 0 && nseg >= 1 && nseg <= kSegsMax && br.y <= a.nseg_total, 1, nseg) &
+              chk(used >= 0 && used <= region_words, 2, used) &
+              chk(end >= base && end - (base & ~3) <= kThreads * TPT && end <= a.N, 3, end - base))) {
+            nseg = 1;            // a malformed batch is skipped
+            used = 0;
+            end = base;
+        }
 
-        // segment table (layout precomputed at init) and cleared count tables
+        // segment table (layout precomputed at init) and cleared count tables;
+        // a segment whose table would leave the region gets a one-entry hash
+        // at offset 0 (wrong counts, reported, but no access out of bounds)
         for (int s = tid; s < nseg; s += kThreads) {
             const int o0 = a.seg_off[br.x + s];
-            seg_tok[s] = o0 - base;
-            seg_reg[s] = seg_region[br.x + s];
-            if (!kDense) {
-                uint32_t w, cap;
-                table_shape((uint32_t)(a.seg_off[br.x + s + 1] - o0), (uint32_t)K, &w, &cap);
-                seg_aux[s] = (int)cap;
+            const uint32_t Ls = (uint32_t)(a.seg_off[br.x + s + 1] - o0);
+            uint32_t w, cap;
+            if (kDense) {
+                w = Ls ? (uint32_t)(K + 1) / 2 : 0u;
+                cap = 0u;
+            } else {
+                table_shape(Ls, (uint32_t)K, &w, &cap);
             }
+            int off = seg_region[br.x + s];
+            if (!chk(off >= 0 && (int64_t)off + w <= used, 4, s)) {
+                off = 0;
+                cap = 1u;
+            }
+            seg_tok[s] = o0 - base;
+            seg_reg[s] = off;
+            if (!kDense) seg_aux[s] = (int)cap;
         }
         if (tid == 0) {
             seg_tok[nseg] = end - base;
@@ -201,15 +220,24 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
                 const int j = 4 * c + v;
                 const int q = q0 + v;
                 const bool mine = (q >= base) && (q < end);
-                tk[j] = mine ? (kDoc ? pa[v] : q) : -1;
+                bool ok = mine;
+                if (kDoc && mine)
+                    ok = chk(pa[v] >= 0 && pa[v] < a.N, 10, pa[v]) &
+                         chk((int)(ia[v] >> 16) < nseg && (int)(ia[v] & 0xFFFFu) < end - base, 11, (int)ia[v]);
+                tk[j] = ok ? (kDoc ? pa[v] : q) : -1;
                 if (kDoc) {
-                    sl[j] = mine ? (int)ia[v] : 0;     // slot << 16 | position, split below
-                    zz[j] = mine ? a.z[tk[j]] : 0;
-                    if (mine) load_props<M>(a.prop, tk[j], pp[j].v);
+                    sl[j] = ok ? (int)ia[v] : 0;     // slot << 16 | position, split below
+                    zz[j] = ok ? a.z[tk[j]] : 0;
+                    if (ok) load_props<M>(a.prop, tk[j], pp[j].v);
                 } else {
                     zz[j] = za[v];
 #pragma unroll
                     for (int i = 0; i < M; ++i) pp[j].v[i] = pw[v * M + i];
+                }
+                if (ok) {
+                    zz[j] = chk.topic(zz[j], K, 13);
+#pragma unroll
+                    for (int i = 0; i < M; ++i) pp[j].v[i] = chk.topic(pp[j].v[i], K, 14);
                 }
             }
         }
@@ -265,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
 #pragma unroll
             for (int u = 0; u < kGroup; ++u) {
                 const int slot = sl[g0 + u];
-                toff[u] = seg_reg[slot];
+                toff[u] = tk[g0 + u] >= 0 ? seg_reg[slot] : 0;
                 tlen[u] = max(seg_tok[slot + 1] - seg_tok[slot], 1);
             }
             int cnt_v[kGroup][M + 1];
@@ -275,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
                 const int j = g0 + u;
                 const bool mine = tk[j] >= 0;
                 const uint32_t* tab = region + toff[u];
-                const uint32_t cap = kDense ? 0u : (uint32_t)seg_aux[sl[j]];
+                const uint32_t cap = (kDense || !mine) ? 0u : (uint32_t)seg_aux[sl[j]];
 #pragma unroll
                 for (int i = 0; i <= M; ++i) {
                     const int k = mine ? (i == 0 ? zz[j] : pp[j].v[i - 1]) : 0;
@@ -365,7 +393,8 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
                 const uint32_t k = (uint32_t)zz[j];
                 const uint32_t old = atomicAdd(&region[seg_reg[slot] + (k >> 1)], dense_unit(k));
                 const int g = (int)((old >> ((k & 1) * 16)) & 0xFFFFu);
-                stage[pad(seg_tok[slot] + g - seg_aux[slot])] = k;
+                const int pos = seg_tok[slot] + g - seg_aux[slot];
+                if (chk(pos >= seg_tok[slot] && pos < seg_tok[slot + 1], 31, pos)) stage[pad(pos)] = k;
             }
             __syncthreads();
         }
@@ -412,7 +441,7 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
 #pragma unroll
                     for (int i = 0; i < M; ++i) {
                         const int pk = pp[j].v[i];
-                        if (pk < 0) pp[j].v[i] = (int)(stage[pad(sb + (-pk - 1))] & kmask);
+                        if (pk < 0) pp[j].v[i] = (int)(stage[pad(sb - pk - 1)] & kmask);
                     }
                 }
                 if (full) {
@@ -448,6 +477,7 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
             if (d != 0) atomicAdd(&a.ck[k], d);
         }
     }
+    chk.publish(a.fault);
 }
 
 int batch_smem_bytes(int K, int stage_ck, int region_words, int tpt, int word_phase, int dense) {

@@ -152,6 +152,35 @@ struct PhaseArgs {
     uint32_t iter;           // iteration
     RoundKeys rk;            // Philox key schedule
     int32_t stage_ck;        // 1: c_k table and deltas in shared memory
+    int64_t N;               // tokens
+    int64_t nseg_total;      // documents (document phase) or words (word phase)
+    int32_t* fault;          // {site, value} of the first failed index check
+};
+
+// Index checks.  Every index a kernel takes from stored state (a work list,
+// a token pointer, a topic) is validated before use; a failed check replaces
+// the index by a safe one and is remembered by the thread (first site and
+// value, kept in registers, no branch).  Each thread publishes its first
+// failure to a.fault {site, value} once, when it finishes; the host reads the
+// record at the next synchronising call and reports it as an error.  So a
+// corrupt input never makes a kernel access memory out of bounds.
+struct Checks {
+    int site = 0, value = 0;
+    __device__ __forceinline__ bool operator()(bool ok, int s, int v) {
+        const bool first = !ok && site == 0;
+        site = first ? s : site;
+        value = first ? v : value;
+        return ok;
+    }
+    // k if it is a topic in [0, K), else 0 (and the failure is remembered)
+    __device__ __forceinline__ int topic(int k, int K, int s) {
+        const bool ok = (uint32_t)k < (uint32_t)K;
+        (*this)(ok, s, k);
+        return ok ? k : 0;
+    }
+    __device__ __forceinline__ void publish(int32_t* fault) const {
+        if (site != 0 && atomicCAS(fault, 0, site) == 0) fault[1] = value;
+    }
 };
 
 }  // namespace wl

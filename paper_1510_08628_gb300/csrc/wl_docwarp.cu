@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
     int tab_words) {
     extern __shared__ __align__(16) uint32_t dsm[];
     const int K = a.K, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    Checks chk;
     float* ckb_s = reinterpret_cast<float*>(dsm);
     int* dck_s = reinterpret_cast<int*>(dsm) + K;
     uint32_t* wbase = dsm + docwarp_ck_words(K, a.stage_ck) + warp * (tab_words + 32 * TPL);
@@ -62,9 +63,11 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
         if (d0 >= ndocs) break;
         const int d1 = min(d0 + kDocsPerGrab, ndocs);
         for (int di = d0; di < d1; ++di) {
-            const int d = docs[di];
+            int d = docs[di];
+            if (!chk(d >= 0 && (int64_t)d < a.nseg_total, 70, d)) d = 0;
             const int base = a.seg_off[d];
-            const int L = a.seg_off[d + 1] - base;
+            int L = a.seg_off[d + 1] - base;
+            if (!chk(L >= 0 && L <= 32 * TPL, 71, L)) L = 0;
             const uint32_t cap = kDense ? 0u : pow2_above((uint32_t)min(2 * L, K));
             const int words = kDense ? tab_words : (int)cap;
             for (int i = lane; i < (words >> 2); i += 32)
@@ -80,9 +83,10 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
                 const int j = 32 * m + lane;
                 tk[m] = -1;
                 if (j < L) {
-                    const int t = a.perm[base + j];
+                    int t = a.perm[base + j];
+                    if (!chk(t >= 0 && t < a.N, 72, t)) t = 0;
                     tk[m] = t;
-                    zz[m] = a.z[t];
+                    zz[m] = chk.topic(a.z[t], K, 73);
                     if (M == 2) {
                         const int2 x = *reinterpret_cast<const int2*>(a.prop + (int64_t)t * 2);
                         pp[m][0] = x.x;
@@ -91,6 +95,8 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
 #pragma unroll
                         for (int i = 0; i < M; ++i) pp[m][i] = a.prop[(int64_t)t * M + i];
                     }
+#pragma unroll
+                    for (int i = 0; i < M; ++i) pp[m][i] = chk.topic(pp[m][i], K, 74);
                 }
             }
 #pragma unroll
@@ -176,6 +182,7 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
             if (dv != 0) atomicAdd(&a.ck[k], dv);
         }
     }
+    chk.publish(a.fault);
 }
 
 template <int TPL, int M, bool kDense>

@@ -31,6 +31,14 @@ __device__ __forceinline__ int elem(const int4& v, int e) {
     return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
 }
 
+// A work chunk {row, segment, first position, length}: valid when it lies in
+// its segment and names an existing count row.
+__device__ __forceinline__ bool chunk_ok(const PhaseArgs& a, const int4& ch, int nrows) {
+    if (ch.x < 0 || ch.x >= nrows || ch.y < 0 || (int64_t)ch.y >= a.nseg_total || ch.w < 0) return false;
+    const int s0 = a.seg_off[ch.y], s1 = a.seg_off[ch.y + 1];
+    return ch.z >= s0 && (int64_t)ch.z + ch.w <= s1;
+}
+
 int huge_smem_bytes(int K, int stage_ck, int pass, bool doc) {
     // pass 0 hist: K; pass 1 accept: row + (word) hist + staged ck;
     // pass 2 draw: K+1 prefix + guide table
@@ -43,16 +51,22 @@ int huge_smem_bytes(int K, int stage_ck, int pass, bool doc) {
 
 template <bool kDoc>
 __global__ void __launch_bounds__(kThreads) huge_hist_kernel(PhaseArgs a, const int4* __restrict__ chunks,
-                                                             int nchunks, int32_t* __restrict__ rows) {
+                                                             int nchunks, int nrows, int32_t* __restrict__ rows) {
     extern __shared__ __align__(16) int hist[];
     const int K = a.K, tid = threadIdx.x;
+    Checks chk;
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const int4 ch = chunks[c];
+        int4 ch = chunks[c];
+        if (!chk(chunk_ok(a, ch, nrows), 43, c)) ch = make_int4(0, 0, 0, 0);
         const int p0 = ch.z, p1 = ch.z + ch.w;
         for (int k = tid; k < K; k += kThreads) hist[k] = 0;
         __syncthreads();
         if (kDoc) {
-            for (int p = p0 + tid; p < p1; p += kThreads) agg_add(hist, a.z[a.perm[p]]);
+            for (int p = p0 + tid; p < p1; p += kThreads) {
+                const int t = a.perm[p];
+                if (!chk(t >= 0 && t < a.N, 40, t)) continue;
+                agg_add(hist, chk.topic(a.z[t], K, 41));
+            }
         } else {
             const int v0 = p0 >> 2, v1 = (p1 + 3) >> 2;
             const int4* zv = reinterpret_cast<const int4*>(a.z);
@@ -70,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) huge_hist_kernel(PhaseArgs a, const 
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int q = 4 * v + e;
-                        if (q >= p0 && q < p1) agg_add(hist, elem(x[u], e));
+                        if (q >= p0 && q < p1) agg_add(hist, chk.topic(elem(x[u], e), K, 42));
                     }
                 }
             }
@@ -81,6 +95,7 @@ __global__ void __launch_bounds__(kThreads) huge_hist_kernel(PhaseArgs a, const 
             if (hist[k] != 0) atomicAdd(&row[k], hist[k]);
         __syncthreads();
     }
+    chk.publish(a.fault);
 }
 
 // M chained MH steps of one token from z0 against the count row (Eq. 7).
@@ -103,10 +118,12 @@ __device__ __forceinline__ int mh_chain(const PhaseArgs& a, uint32_t t, uint32_t
 
 template <bool kDoc, int M>
 __global__ void __launch_bounds__(kThreads) huge_accept_kernel(PhaseArgs a, const int4* __restrict__ chunks,
-                                                               int nchunks, const int32_t* __restrict__ rows_pre,
+                                                               int nchunks, int nrows,
+                                                               const int32_t* __restrict__ rows_pre,
                                                                int32_t* __restrict__ rows_post) {
     extern __shared__ __align__(16) int sm[];
     const int K = a.K, tid = threadIdx.x;
+    Checks chk;
     int* row = sm;
     int* hist = sm + K;                                    // word phase only
     float* ckb_s = reinterpret_cast<float*>(sm + (kDoc ? K : 2 * K));
@@ -128,7 +145,8 @@ __global__ void __launch_bounds__(kThreads) huge_accept_kernel(PhaseArgs a, cons
         }
     };
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const int4 ch = chunks[c];
+        int4 ch = chunks[c];
+        if (!chk(chunk_ok(a, ch, nrows), 47, c)) ch = make_int4(0, 0, 0, 0);
         const int p0 = ch.z, p1 = ch.z + ch.w;
         const int32_t* rp = rows_pre + (int64_t)ch.x * K;
         for (int k = tid; k < K; k += kThreads) {
@@ -139,10 +157,11 @@ __global__ void __launch_bounds__(kThreads) huge_accept_kernel(PhaseArgs a, cons
         if (kDoc) {
             for (int p = p0 + tid; p < p1; p += kThreads) {
                 const int t = a.perm[p];
-                const int z0 = a.z[t];
+                if (!chk(t >= 0 && t < a.N, 44, t)) continue;
+                const int z0 = chk.topic(a.z[t], K, 45);
                 int pr[M];
 #pragma unroll
-                for (int i = 0; i < M; ++i) pr[i] = a.prop[(int64_t)t * M + i];
+                for (int i = 0; i < M; ++i) pr[i] = chk.topic(a.prop[(int64_t)t * M + i], K, 46);
                 const int s = mh_chain<M>(a, (uint32_t)t, phase, z0, pr, row, ckb_s);
                 if (s != z0) {
                     a.z[t] = s;
@@ -184,12 +203,12 @@ __global__ void __launch_bounds__(kThreads) huge_accept_kernel(PhaseArgs a, cons
 #pragma unroll
                         for (int i = 0; i < M; ++i) pk[e * M + i] = 0;
                         if (q < p0 || q >= p1) { full = false; continue; }
-                        const int z0 = out[e];
+                        const int z0 = chk.topic(out[e], K, 50);
                         int s = z0;
 #pragma unroll
                         for (int i = 0; i < M; ++i) {
                             const uint4 r = draw((uint32_t)q, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
-                            const int tp = elem(y[u][(e * M + i) / 4], (e * M + i) % 4);
+                            const int tp = chk.topic(elem(y[u][(e * M + i) / 4], (e * M + i) % 4), K, 51);
                             if (tp != s) {
                                 const float cs = a.stage_ck ? ckb_s[s] : __ldg(a.ckb + s);
                                 const float ct = a.stage_ck ? ckb_s[tp] : __ldg(a.ckb + tp);
@@ -232,21 +251,25 @@ __global__ void __launch_bounds__(kThreads) huge_accept_kernel(PhaseArgs a, cons
         for (int k = tid; k < K; k += kThreads)
             if (dck_s[k] != 0) atomicAdd(&a.ck[k], dck_s[k]);
     }
+    chk.publish(a.fault);
 }
 
 template <bool kDoc, int M>
 __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const int4* __restrict__ chunks,
-                                                             int nchunks, const int32_t* __restrict__ rows_post) {
+                                                             int nchunks, int nrows,
+                                                             const int32_t* __restrict__ rows_post) {
     extern __shared__ __align__(16) int sm[];
     __shared__ int warp_tot[kWarps];
     __shared__ int s_total;
     const int K = a.K, tid = threadIdx.x;
     int* P = sm;   // word phase: exclusive prefix of row_post, P[K] = L_w
     const uint32_t phase = kDoc ? kPhaseDoc : kPhaseWord;
+    Checks chk;
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const int4 ch = chunks[c];
+        int4 ch = chunks[c];
+        if (!chk(chunk_ok(a, ch, nrows), 48, c)) ch = make_int4(0, 0, 0, 0);
         const int sb = a.seg_off[ch.y];
-        const int Ls = a.seg_off[ch.y + 1] - sb;
+        const int Ls = max(a.seg_off[ch.y + 1] - sb, 1);
         const int p0 = ch.z, p1 = ch.z + ch.w;
         if (!kDoc) {
             const int32_t* rq = rows_post + (int64_t)ch.x * K;
@@ -283,8 +306,11 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const 
 #pragma unroll
                 for (int i = 0; i < M; ++i) {
                     const uint4 r = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
-                    const int k = coin(r.y, Lf, LG) ? a.z[a.perm[sb + (int)dice(r.z, (uint32_t)Ls)]]
-                                                    : (int)dice(r.z, (uint32_t)K);
+                    int k = (int)dice(r.z, (uint32_t)K);
+                    if (coin(r.y, Lf, LG)) {
+                        const int tq = a.perm[sb + (int)dice(r.z, (uint32_t)Ls)];
+                        if (chk(tq >= 0 && tq < a.N, 63, tq)) k = a.z[tq];
+                    }
                     a.prop[(int64_t)t * M + i] = k;
                 }
             }
@@ -317,10 +343,11 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const 
                         int pk = elem(y[u][n / 4], n % 4);
                         if (q < p0 || q >= p1) pk = 0;
                         if (pk < 0) {
-                            const int j = -pk - 1;
+                            int j = -pk - 1;
+                            if (!chk((uint32_t)j < (uint32_t)Ls, 60, j)) j = 0;
                             int k = guide[(int)(((uint64_t)j * mult) >> 32)];
-                            while (P[k + 1] <= j) ++k;
-                            pk = k;
+                            while (k + 1 < K && P[k + 1] <= j) ++k;
+                            pk = chk(P[k + 1] > j, 62, j) ? k : 0;
                         }
                         out[n] = pk;
                     }
@@ -343,6 +370,7 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const 
         }
         __syncthreads();
     }
+    chk.publish(a.fault);
 }
 
 template <typename F>
@@ -351,17 +379,17 @@ static cudaError_t set_smem(F f, int smem) {
 }
 
 cudaError_t launch_huge_hist(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
-                             int32_t* rows, int grid, cudaStream_t st) {
+                             int nrows, int32_t* rows, int grid, cudaStream_t st) {
     if (nchunks <= 0) return cudaSuccess;
     const int smem = huge_smem_bytes(a.K, a.stage_ck, 0, doc);
     if (doc) {
         cudaError_t e = set_smem(huge_hist_kernel<true>, smem);
         if (e != cudaSuccess) return e;
-        huge_hist_kernel<true><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, rows);
+        huge_hist_kernel<true><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, nrows, rows);
     } else {
         cudaError_t e = set_smem(huge_hist_kernel<false>, smem);
         if (e != cudaSuccess) return e;
-        huge_hist_kernel<false><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, rows);
+        huge_hist_kernel<false><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, nrows, rows);
     }
     return cudaGetLastError();
 }
@@ -376,7 +404,7 @@ cudaError_t launch_huge_hist(bool doc, const PhaseArgs& a, const int4* chunks, i
     }
 
 cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
-                               const int32_t* rows_pre, int32_t* rows_post, int grid,
+                               int nrows, const int32_t* rows_pre, int32_t* rows_post, int grid,
                                cudaStream_t st) {
     if (nchunks <= 0) return cudaSuccess;
     const int smem = huge_smem_bytes(a.K, a.stage_ck, 1, doc);
@@ -385,20 +413,20 @@ cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const int4* chunks,
         WL_M_SWITCH({
             e = set_smem(huge_accept_kernel<true, MM>, smem);
             if (e != cudaSuccess) return e;
-            huge_accept_kernel<true, MM><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, rows_pre, rows_post);
+            huge_accept_kernel<true, MM><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, nrows, rows_pre, rows_post);
         })
     } else {
         WL_M_SWITCH({
             e = set_smem(huge_accept_kernel<false, MM>, smem);
             if (e != cudaSuccess) return e;
-            huge_accept_kernel<false, MM><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, rows_pre, rows_post);
+            huge_accept_kernel<false, MM><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, nrows, rows_pre, rows_post);
         })
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
-                             const int32_t* rows_post, int grid, cudaStream_t st) {
+                             int nrows, const int32_t* rows_post, int grid, cudaStream_t st) {
     if (nchunks <= 0) return cudaSuccess;
     const int smem = huge_smem_bytes(a.K, a.stage_ck, 2, doc);
     cudaError_t e = cudaSuccess;
@@ -406,13 +434,13 @@ cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const int4* chunks, i
         WL_M_SWITCH({
             e = set_smem(huge_draw_kernel<true, MM>, smem);
             if (e != cudaSuccess) return e;
-            huge_draw_kernel<true, MM><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, rows_post);
+            huge_draw_kernel<true, MM><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, nrows, rows_post);
         })
     } else {
         WL_M_SWITCH({
             e = set_smem(huge_draw_kernel<false, MM>, smem);
             if (e != cudaSuccess) return e;
-            huge_draw_kernel<false, MM><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, rows_post);
+            huge_draw_kernel<false, MM><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, nrows, rows_post);
         })
     }
     return cudaGetLastError();

@@ -31,13 +31,14 @@ cudaError_t launch_doc_warp(int tpl, bool dense, const PhaseArgs& a, const int32
 // chunk = {row, segment id, first token position, token count}
 int huge_smem_bytes(int K, int stage_ck, int pass, bool doc);
 int huge_blocks_per_sm(int K, int stage_ck, int pass, bool doc, int M);
+// chunks: {count row, segment, first position, length}; nrows rows of K ints.
 cudaError_t launch_huge_hist(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
-                             int32_t* rows, int grid, cudaStream_t st);
+                             int nrows, int32_t* rows, int grid, cudaStream_t st);
 cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
-                               const int32_t* rows_pre, int32_t* rows_post, int grid,
+                               int nrows, const int32_t* rows_pre, int32_t* rows_post, int grid,
                                cudaStream_t st);
 cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
-                             const int32_t* rows_post, int grid, cudaStream_t st);
+                             int nrows, const int32_t* rows_post, int grid, cudaStream_t st);
 
 // Initialisation, c_k, export, log-likelihood (wl_misc.cu).
 cudaError_t launch_init_z(int32_t* z, int32_t* prop, int64_t N, int K, int M, uint64_t seed,
@@ -51,8 +52,8 @@ cudaError_t launch_gather_docmajor(const int32_t* z, const int32_t* perm, int64_
 cudaError_t launch_check_range(const int32_t* v, int64_t n, int K, int32_t* bad, cudaStream_t st);
 cudaError_t launch_loglik_batches(bool doc, const int32_t* z, const int32_t* perm,
                                   const int32_t* seg_off, const int4* batches, int nbatch, int K,
-                                  double g, int region_words, double* out, int grid,
-                                  cudaStream_t st);
+                                  double g, int region_words, int64_t N, int64_t nseg_total,
+                                  int32_t* fault, double* out, int grid, cudaStream_t st);
 cudaError_t launch_loglik_rows(const int32_t* rows, int64_t nrows, int K, double g, double* out,
                                cudaStream_t st);
 cudaError_t launch_loglik_lengths(const int32_t* seg_off, int64_t nseg, double abar, double* out,

@@ -130,7 +130,9 @@ int loglik_smem_bytes(int region_words) { return (3 * kSegsMax + 4 + region_word
 
 __global__ void __launch_bounds__(kThreads) loglik_batch_kernel(bool doc, const int32_t* z, const int32_t* perm,
                                                                 const int32_t* seg_off, const int4* batches,
-                                                                int nbatch, int K, double g, double* out) {
+                                                                int nbatch, int K, double g, int region_words,
+                                                                int64_t N, int64_t nseg_total, int32_t* fault,
+                                                                double* out) {
     extern __shared__ __align__(16) int lsm[];
     int* seg_tok = lsm;
     int* seg_reg = seg_tok + kSegsMax + 1;
@@ -142,10 +144,14 @@ __global__ void __launch_bounds__(kThreads) loglik_batch_kernel(bool doc, const 
     const int tid = threadIdx.x;
     const double lg0 = lgamma(g);
     double acc = 0.0;
+    Checks chk;
     for (int b = blockIdx.x; b < nbatch; b += gridDim.x) {
-        const int4 br = batches[b];
+        int4 br = batches[b];
+        if (!chk(br.x >= 0 && br.y > br.x && br.y - br.x <= kSegsMax && br.y <= nseg_total, 80, b))
+            br = make_int4(0, 0, 0, 0);
         const int nseg = br.y - br.x;
-        const int base = seg_off[br.x], end = seg_off[br.y];
+        const int base = seg_off[br.x];
+        int end = seg_off[br.y];
         for (int s = tid; s < nseg; s += kThreads) {
             const int o0 = seg_off[br.x + s], o1 = seg_off[br.x + s + 1];
             uint32_t w, cap;
@@ -157,17 +163,22 @@ __global__ void __launch_bounds__(kThreads) loglik_batch_kernel(bool doc, const 
         if (tid == 0) seg_tok[nseg] = end - base;
         __syncthreads();
         block_scan_array(seg_reg, nseg, warp_tot, &s_total);
-        const int used = s_total;
+        int used = s_total;
+        if (!chk(used <= region_words, 81, used)) {
+            used = 0;   // the batch's tables do not fit: skip it
+            end = base;
+        }
         for (int i = tid; i < used; i += kThreads) region[i] = 0u;
         __syncthreads();
         for (int p = base + tid; p < end; p += kThreads) {
             const int t = doc ? perm[p] : p;
+            if (!chk(t >= 0 && t < N, 82, t)) continue;
             int lo = 0, hi = nseg - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (seg_tok[mid] <= p - base) lo = mid; else hi = mid - 1;
             }
-            table_add(region + seg_reg[lo], (uint32_t)seg_cap[lo], (uint32_t)z[t]);
+            table_add(region + seg_reg[lo], (uint32_t)seg_cap[lo], (uint32_t)chk.topic(z[t], K, 83));
         }
         __syncthreads();
         // every table word: dense halves or packed hash entries
@@ -190,19 +201,20 @@ __global__ void __launch_bounds__(kThreads) loglik_batch_kernel(bool doc, const 
     }
     const double s = block_sum(acc, red);
     if (tid == 0) atomicAdd(out, s);
+    chk.publish(fault);
 }
 
 cudaError_t launch_loglik_batches(bool doc, const int32_t* z, const int32_t* perm,
                                   const int32_t* seg_off, const int4* batches, int nbatch, int K,
-                                  double g, int region_words, double* out, int grid,
-                                  cudaStream_t st) {
+                                  double g, int region_words, int64_t N, int64_t nseg_total,
+                                  int32_t* fault, double* out, int grid, cudaStream_t st) {
     if (nbatch <= 0) return cudaSuccess;
     const int smem = loglik_smem_bytes(region_words);
     cudaError_t e = cudaFuncSetAttribute(loglik_batch_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     loglik_batch_kernel<<<grid, kThreads, smem, st>>>(doc, z, perm, seg_off, batches, nbatch, K, g,
-                                                      out);
+                                                      region_words, N, nseg_total, fault, out);
     return cudaGetLastError();
 }
 

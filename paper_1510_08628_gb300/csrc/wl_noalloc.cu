@@ -97,6 +97,10 @@ __global__ void __launch_bounds__(wl::kThreads) na_segments_kernel(
         __syncthreads();
         for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
             const int k = z[p];
+            if ((uint32_t)k >= (uint32_t)K) {   // not a topic: the result becomes NaN
+                acc = __longlong_as_double(0x7FF8000000000000ll);
+                continue;
+            }
             atomicAdd(&hist[k], 1);
             if (doc) atomicAdd(&ck[k], 1);
         }

@@ -68,6 +68,7 @@ _SIGS = {
     "warplda_kernel_times": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_char_p),
                                             ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double)]),
+    "warplda_sync": (ctypes.c_int, [_P]),
     "warplda_destroy": (None, [_P]),
     "warplda_loglik_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                               ctypes.c_int32, ctypes.c_float, ctypes.c_float,
@@ -199,6 +200,10 @@ class WarpLDA:
 
     def load_state(self, path: str) -> None:
         _check(load().warplda_load(self._h, path.encode()))
+
+    def sync(self) -> None:
+        """Wait for queued work; raise if a kernel's index check failed."""
+        _check(load().warplda_sync(self._h))
 
     def info(self) -> dict:
         inf = Info()

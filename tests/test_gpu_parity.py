@@ -195,3 +195,14 @@ def test_invalid_arguments_rejected():
     bad[0] = 10
     with pytest.raises(WarpLDAError):
         WarpLDA(c.doc_ptr, bad, 10, 4, 0.1, 0.1, 1, 1)
+
+
+def test_sync_reports_clean_checks(tiny_corpus):
+    c, wl = tiny_corpus
+    g = _gpu(c, c.V, wl.K, wl.alpha, wl.beta, wl.M, 17)
+    g.sweep(3)
+    g.sync()
+    g.phase(1)
+    g.sync()
+    g.phase(2)
+    g.sync()

@@ -38,3 +38,10 @@ def test_loglik_noalloc_matches_loglik_twice():
     with pytest.raises(warplda.WarpLDAError, match="16384"):
         warplda.loglik_noalloc(c.D, c.V, c.N, 20000, 0.2, 0.01, dev(c.doc_ptr), dev(z_doc),
                                dev(wp), dev(z_word), out)
+    # a value outside [0, K) is not counted and turns the result into NaN
+    bad = z_doc.copy()
+    bad[3] = 40
+    warplda.loglik_noalloc(c.D, c.V, c.N, 40, 0.2, 0.01, dev(c.doc_ptr), dev(bad), dev(wp),
+                           dev(z_word), out)
+    torch.cuda.synchronize()
+    assert np.isnan(float(out.item()))
