@@ -45,6 +45,9 @@ def _fingerprint(extra: list[str]) -> str:
 
 def build(force: bool = False, extra_flags: list[str] | None = None, verbose: bool = False) -> str:
     extra = list(extra_flags or [])
+    if os.environ.get("WARPLDA_CHECKED") == "1":
+        # checked build: every per-token index is validated as well
+        extra.append("-DWL_CHECKED")
     os.makedirs(OUT_DIR, exist_ok=True)
     stamp = os.path.join(OUT_DIR, "libwarplda.stamp")
     fp = _fingerprint(extra)

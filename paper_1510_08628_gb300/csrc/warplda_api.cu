@@ -243,7 +243,11 @@ int check_record(warplda_ctx* c, const char* where) {
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     if (f[0] == 0) return WARPLDA_OK;
     WL_CU(cudaMemsetAsync(c->d_fault, 0, sizeof(f), c->st), "clear check record");
-    return fail(WARPLDA_ECUDA, "index check failed (%s): site %d value %d", where, f[0], f[1]);
+    static const char* kSites[] = {"?", "doc batch", "word batch", "multi-pass hist",
+                                   "multi-pass accept", "multi-pass draw", "doc warp", "loglik"};
+    const char* site = (f[0] >= 1 && f[0] <= 7) ? kSites[f[0]] : "?";
+    return fail(WARPLDA_ECUDA, "index check failed (reported at %s): first in the %s kernel, checks 0x%x",
+                where, site, (unsigned)f[2]);
 }
 
 int launch_rec(warplda_ctx* c, int cls, cudaError_t (*fn)(warplda_ctx*, void*), void* arg) {

@@ -138,9 +138,9 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
         int used = br.z;
         const int base = a.seg_off[br.x];
         int end = a.seg_off[br.y];
-        if (!(chk(br.x >= 0 && nseg >= 1 && nseg <= kSegsMax && br.y <= a.nseg_total, 1, nseg) &
-              chk(used >= 0 && used <= region_words, 2, used) &
-              chk(end >= base && end - (base & ~3) <= kThreads * TPT && end <= a.N, 3, end - base))) {
+        if (!(chk(br.x >= 0 && nseg >= 1 && nseg <= kSegsMax && br.y <= a.nseg_total, 0) &
+              chk(used >= 0 && used <= region_words, 1) &
+              chk(end >= base && end - (base & ~3) <= kThreads * TPT && end <= a.N, 2))) {
             nseg = 1;            // a malformed batch is skipped
             used = 0;
             end = base;
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
                 table_shape(Ls, (uint32_t)K, &w, &cap);
             }
             int off = seg_region[br.x + s];
-            if (!chk(off >= 0 && (int64_t)off + w <= used, 4, s)) {
+            if (!chk(off >= 0 && (int64_t)off + w <= used, 3)) {
                 off = 0;
                 cap = 1u;
             }
@@ -222,8 +222,8 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
                 const bool mine = (q >= base) && (q < end);
                 bool ok = mine;
                 if (kDoc && mine)
-                    ok = chk(pa[v] >= 0 && pa[v] < a.N, 10, pa[v]) &
-                         chk((int)(ia[v] >> 16) < nseg && (int)(ia[v] & 0xFFFFu) < end - base, 11, (int)ia[v]);
+                    ok = chk.tok((uint32_t)pa[v] < (uint32_t)a.N, 4) &
+                         chk.tok((int)(ia[v] >> 16) < nseg && (int)(ia[v] & 0xFFFFu) < end - base, 5);
                 tk[j] = ok ? (kDoc ? pa[v] : q) : -1;
                 if (kDoc) {
                     sl[j] = ok ? (int)ia[v] : 0;     // slot << 16 | position, split below
@@ -235,9 +235,9 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
                     for (int i = 0; i < M; ++i) pp[j].v[i] = pw[v * M + i];
                 }
                 if (ok) {
-                    zz[j] = chk.topic(zz[j], K, 13);
+                    zz[j] = chk.topic(zz[j], K, 6);
 #pragma unroll
-                    for (int i = 0; i < M; ++i) pp[j].v[i] = chk.topic(pp[j].v[i], K, 14);
+                    for (int i = 0; i < M; ++i) pp[j].v[i] = chk.topic(pp[j].v[i], K, 7);
                 }
             }
         }
@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
                 const uint32_t old = atomicAdd(&region[seg_reg[slot] + (k >> 1)], dense_unit(k));
                 const int g = (int)((old >> ((k & 1) * 16)) & 0xFFFFu);
                 const int pos = seg_tok[slot] + g - seg_aux[slot];
-                if (chk(pos >= seg_tok[slot] && pos < seg_tok[slot + 1], 31, pos)) stage[pad(pos)] = k;
+                if (chk.tok(pos >= seg_tok[slot] && pos < seg_tok[slot + 1], 8)) stage[pad(pos)] = k;
             }
             __syncthreads();
         }
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
             if (d != 0) atomicAdd(&a.ck[k], d);
         }
     }
-    chk.publish(a.fault);
+    chk.publish(a.fault, kDoc ? kSiteDocBatch : kSiteWordBatch);
 }
 
 int batch_smem_bytes(int K, int stage_ck, int region_words, int tpt, int word_phase, int dense) {

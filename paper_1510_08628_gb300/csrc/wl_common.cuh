@@ -154,33 +154,54 @@ struct PhaseArgs {
     int32_t stage_ck;        // 1: c_k table and deltas in shared memory
     int64_t N;               // tokens
     int64_t nseg_total;      // documents (document phase) or words (word phase)
-    int32_t* fault;          // {site, value} of the first failed index check
+    int32_t* fault;          // index-check record {kernel site, 0, check bits, 0}
 };
 
-// Index checks.  Every index a kernel takes from stored state (a work list,
-// a token pointer, a topic) is validated before use; a failed check replaces
-// the index by a safe one and is remembered by the thread (first site and
-// value, kept in registers, no branch).  Each thread publishes its first
-// failure to a.fault {site, value} once, when it finishes; the host reads the
-// record at the next synchronising call and reports it as an error.  So a
-// corrupt input never makes a kernel access memory out of bounds.
+// Index checks.  Indices a kernel takes from its work lists (batches, chunks,
+// segment table layouts) are validated once per work item; a failed check
+// replaces the item by a safe empty one and sets the check's bit in a
+// per-thread mask.  Per-token indices (token pointers, topics read back from
+// z and the proposals) are in range by construction -- every topic a kernel
+// stores is a phase-start topic, a proposal, or a draw in [0, K) -- and are
+// validated the same way only in checked builds (-DWL_CHECKED), where a bad
+// one is replaced by 0.  Each thread publishes its mask once, when it
+// finishes: a.fault = {first kernel site, 0, OR of the masks}; the host reads
+// the record at the next synchronising call and reports it as an error.
+#ifdef WL_CHECKED
+constexpr bool kTokenChecks = true;
+#else
+constexpr bool kTokenChecks = false;
+#endif
+
 struct Checks {
-    int site = 0, value = 0;
-    __device__ __forceinline__ bool operator()(bool ok, int s, int v) {
-        const bool first = !ok && site == 0;
-        site = first ? s : site;
-        value = first ? v : value;
+    uint32_t bad = 0;
+    __device__ __forceinline__ bool operator()(bool ok, int bit) {
+        bad |= ok ? 0u : (1u << bit);
         return ok;
     }
-    // k if it is a topic in [0, K), else 0 (and the failure is remembered)
-    __device__ __forceinline__ int topic(int k, int K, int s) {
+    // per-token check (checked builds)
+    __device__ __forceinline__ bool tok(bool ok, int bit) {
+        return kTokenChecks ? (*this)(ok, bit) : true;
+    }
+    // per-token topic: k, or 0 if a checked build finds it outside [0, K)
+    __device__ __forceinline__ int topic(int k, int K, int bit) {
+        if (!kTokenChecks) return k;
         const bool ok = (uint32_t)k < (uint32_t)K;
-        (*this)(ok, s, k);
+        bad |= ok ? 0u : (1u << bit);
         return ok ? k : 0;
     }
-    __device__ __forceinline__ void publish(int32_t* fault) const {
-        if (site != 0 && atomicCAS(fault, 0, site) == 0) fault[1] = value;
+    __device__ __forceinline__ void publish(int32_t* fault, int kernel_site) const {
+        if (bad != 0) {
+            atomicCAS(fault, 0, kernel_site);
+            atomicOr(reinterpret_cast<unsigned int*>(fault + 2), bad);
+        }
     }
+};
+
+// Kernel sites of the check record.
+enum : int {
+    kSiteDocBatch = 1, kSiteWordBatch = 2, kSiteHugeHist = 3, kSiteHugeAccept = 4,
+    kSiteHugeDraw = 5, kSiteDocWarp = 6, kSiteLoglik = 7
 };
 
 }  // namespace wl

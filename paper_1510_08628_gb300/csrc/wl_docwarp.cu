@@ -64,10 +64,10 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
         const int d1 = min(d0 + kDocsPerGrab, ndocs);
         for (int di = d0; di < d1; ++di) {
             int d = docs[di];
-            if (!chk(d >= 0 && (int64_t)d < a.nseg_total, 70, d)) d = 0;
+            if (!chk(d >= 0 && (int64_t)d < a.nseg_total, 0)) d = 0;
             const int base = a.seg_off[d];
             int L = a.seg_off[d + 1] - base;
-            if (!chk(L >= 0 && L <= 32 * TPL, 71, L)) L = 0;
+            if (!chk(L >= 0 && L <= 32 * TPL, 1)) L = 0;
             const uint32_t cap = kDense ? 0u : pow2_above((uint32_t)min(2 * L, K));
             const int words = kDense ? tab_words : (int)cap;
             for (int i = lane; i < (words >> 2); i += 32)
@@ -84,9 +84,9 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
                 tk[m] = -1;
                 if (j < L) {
                     int t = a.perm[base + j];
-                    if (!chk(t >= 0 && t < a.N, 72, t)) t = 0;
+                    if (!chk.tok((uint32_t)t < (uint32_t)a.N, 2)) t = 0;
                     tk[m] = t;
-                    zz[m] = chk.topic(a.z[t], K, 73);
+                    zz[m] = chk.topic(a.z[t], K, 3);
                     if (M == 2) {
                         const int2 x = *reinterpret_cast<const int2*>(a.prop + (int64_t)t * 2);
                         pp[m][0] = x.x;
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
                         for (int i = 0; i < M; ++i) pp[m][i] = a.prop[(int64_t)t * M + i];
                     }
 #pragma unroll
-                    for (int i = 0; i < M; ++i) pp[m][i] = chk.topic(pp[m][i], K, 74);
+                    for (int i = 0; i < M; ++i) pp[m][i] = chk.topic(pp[m][i], K, 4);
                 }
             }
 #pragma unroll
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
             if (dv != 0) atomicAdd(&a.ck[k], dv);
         }
     }
-    chk.publish(a.fault);
+    chk.publish(a.fault, kSiteDocWarp);
 }
 
 template <int TPL, int M, bool kDense>

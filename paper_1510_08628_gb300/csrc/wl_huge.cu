@@ -57,15 +57,15 @@ __global__ void __launch_bounds__(kThreads) huge_hist_kernel(PhaseArgs a, const 
     Checks chk;
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         int4 ch = chunks[c];
-        if (!chk(chunk_ok(a, ch, nrows), 43, c)) ch = make_int4(0, 0, 0, 0);
+        if (!chk(chunk_ok(a, ch, nrows), 0)) ch = make_int4(0, 0, 0, 0);
         const int p0 = ch.z, p1 = ch.z + ch.w;
         for (int k = tid; k < K; k += kThreads) hist[k] = 0;
         __syncthreads();
         if (kDoc) {
             for (int p = p0 + tid; p < p1; p += kThreads) {
                 const int t = a.perm[p];
-                if (!chk(t >= 0 && t < a.N, 40, t)) continue;
-                agg_add(hist, chk.topic(a.z[t], K, 41));
+                if (!chk.tok((uint32_t)t < (uint32_t)a.N, 1)) continue;
+                agg_add(hist, chk.topic(a.z[t], K, 2));
             }
         } else {
             const int v0 = p0 >> 2, v1 = (p1 + 3) >> 2;
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) huge_hist_kernel(PhaseArgs a, const 
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const int q = 4 * v + e;
-                        if (q >= p0 && q < p1) agg_add(hist, chk.topic(elem(x[u], e), K, 42));
+                        if (q >= p0 && q < p1) agg_add(hist, chk.topic(elem(x[u], e), K, 2));
                     }
                 }
             }
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(kThreads) huge_hist_kernel(PhaseArgs a, const 
             if (hist[k] != 0) atomicAdd(&row[k], hist[k]);
         __syncthreads();
     }
-    chk.publish(a.fault);
+    chk.publish(a.fault, kSiteHugeHist);
 }
 
 // M chained MH steps of one token from z0 against the count row (Eq. 7).
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(kThreads) huge_accept_kernel(PhaseArgs a, cons
     };
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         int4 ch = chunks[c];
-        if (!chk(chunk_ok(a, ch, nrows), 47, c)) ch = make_int4(0, 0, 0, 0);
+        if (!chk(chunk_ok(a, ch, nrows), 0)) ch = make_int4(0, 0, 0, 0);
         const int p0 = ch.z, p1 = ch.z + ch.w;
         const int32_t* rp = rows_pre + (int64_t)ch.x * K;
         for (int k = tid; k < K; k += kThreads) {
@@ -157,11 +157,11 @@ __global__ void __launch_bounds__(kThreads) huge_accept_kernel(PhaseArgs a, cons
         if (kDoc) {
             for (int p = p0 + tid; p < p1; p += kThreads) {
                 const int t = a.perm[p];
-                if (!chk(t >= 0 && t < a.N, 44, t)) continue;
-                const int z0 = chk.topic(a.z[t], K, 45);
+                if (!chk.tok((uint32_t)t < (uint32_t)a.N, 1)) continue;
+                const int z0 = chk.topic(a.z[t], K, 2);
                 int pr[M];
 #pragma unroll
-                for (int i = 0; i < M; ++i) pr[i] = chk.topic(a.prop[(int64_t)t * M + i], K, 46);
+                for (int i = 0; i < M; ++i) pr[i] = chk.topic(a.prop[(int64_t)t * M + i], K, 3);
                 const int s = mh_chain<M>(a, (uint32_t)t, phase, z0, pr, row, ckb_s);
                 if (s != z0) {
                     a.z[t] = s;
@@ -203,12 +203,12 @@ __global__ void __launch_bounds__(kThreads) huge_accept_kernel(PhaseArgs a, cons
 #pragma unroll
                         for (int i = 0; i < M; ++i) pk[e * M + i] = 0;
                         if (q < p0 || q >= p1) { full = false; continue; }
-                        const int z0 = chk.topic(out[e], K, 50);
+                        const int z0 = chk.topic(out[e], K, 2);
                         int s = z0;
 #pragma unroll
                         for (int i = 0; i < M; ++i) {
                             const uint4 r = draw((uint32_t)q, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
-                            const int tp = chk.topic(elem(y[u][(e * M + i) / 4], (e * M + i) % 4), K, 51);
+                            const int tp = chk.topic(elem(y[u][(e * M + i) / 4], (e * M + i) % 4), K, 3);
                             if (tp != s) {
                                 const float cs = a.stage_ck ? ckb_s[s] : __ldg(a.ckb + s);
                                 const float ct = a.stage_ck ? ckb_s[tp] : __ldg(a.ckb + tp);
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kThreads) huge_accept_kernel(PhaseArgs a, cons
         for (int k = tid; k < K; k += kThreads)
             if (dck_s[k] != 0) atomicAdd(&a.ck[k], dck_s[k]);
     }
-    chk.publish(a.fault);
+    chk.publish(a.fault, kSiteHugeAccept);
 }
 
 template <bool kDoc, int M>
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const 
     Checks chk;
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         int4 ch = chunks[c];
-        if (!chk(chunk_ok(a, ch, nrows), 48, c)) ch = make_int4(0, 0, 0, 0);
+        if (!chk(chunk_ok(a, ch, nrows), 0)) ch = make_int4(0, 0, 0, 0);
         const int sb = a.seg_off[ch.y];
         const int Ls = max(a.seg_off[ch.y + 1] - sb, 1);
         const int p0 = ch.z, p1 = ch.z + ch.w;
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const 
                     int k = (int)dice(r.z, (uint32_t)K);
                     if (coin(r.y, Lf, LG)) {
                         const int tq = a.perm[sb + (int)dice(r.z, (uint32_t)Ls)];
-                        if (chk(tq >= 0 && tq < a.N, 63, tq)) k = a.z[tq];
+                        if (chk.tok((uint32_t)tq < (uint32_t)a.N, 1)) k = a.z[tq];
                     }
                     a.prop[(int64_t)t * M + i] = k;
                 }
@@ -344,10 +344,10 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const 
                         if (q < p0 || q >= p1) pk = 0;
                         if (pk < 0) {
                             int j = -pk - 1;
-                            if (!chk((uint32_t)j < (uint32_t)Ls, 60, j)) j = 0;
+                            if (!chk.tok((uint32_t)j < (uint32_t)Ls, 4)) j = 0;
                             int k = guide[(int)(((uint64_t)j * mult) >> 32)];
                             while (k + 1 < K && P[k + 1] <= j) ++k;
-                            pk = chk(P[k + 1] > j, 62, j) ? k : 0;
+                            pk = chk.tok(P[k + 1] > j, 5) ? k : 0;
                         }
                         out[n] = pk;
                     }
@@ -370,7 +370,7 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const 
         }
         __syncthreads();
     }
-    chk.publish(a.fault);
+    chk.publish(a.fault, kSiteHugeDraw);
 }
 
 template <typename F>

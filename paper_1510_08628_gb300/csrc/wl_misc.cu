@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) loglik_batch_kernel(bool doc, const 
     Checks chk;
     for (int b = blockIdx.x; b < nbatch; b += gridDim.x) {
         int4 br = batches[b];
-        if (!chk(br.x >= 0 && br.y > br.x && br.y - br.x <= kSegsMax && br.y <= nseg_total, 80, b))
+        if (!chk(br.x >= 0 && br.y > br.x && br.y - br.x <= kSegsMax && br.y <= nseg_total, 0))
             br = make_int4(0, 0, 0, 0);
         const int nseg = br.y - br.x;
         const int base = seg_off[br.x];
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) loglik_batch_kernel(bool doc, const 
         __syncthreads();
         block_scan_array(seg_reg, nseg, warp_tot, &s_total);
         int used = s_total;
-        if (!chk(used <= region_words, 81, used)) {
+        if (!chk(used <= region_words, 1)) {
             used = 0;   // the batch's tables do not fit: skip it
             end = base;
         }
@@ -172,13 +172,13 @@ __global__ void __launch_bounds__(kThreads) loglik_batch_kernel(bool doc, const 
         __syncthreads();
         for (int p = base + tid; p < end; p += kThreads) {
             const int t = doc ? perm[p] : p;
-            if (!chk(t >= 0 && t < N, 82, t)) continue;
+            if (!chk.tok(t >= 0 && t < N, 2)) continue;
             int lo = 0, hi = nseg - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
                 if (seg_tok[mid] <= p - base) lo = mid; else hi = mid - 1;
             }
-            table_add(region + seg_reg[lo], (uint32_t)seg_cap[lo], (uint32_t)chk.topic(z[t], K, 83));
+            table_add(region + seg_reg[lo], (uint32_t)seg_cap[lo], (uint32_t)chk.topic(z[t], K, 3));
         }
         __syncthreads();
         // every table word: dense halves or packed hash entries
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) loglik_batch_kernel(bool doc, const 
     }
     const double s = block_sum(acc, red);
     if (tid == 0) atomicAdd(out, s);
-    chk.publish(fault);
+    chk.publish(fault, kSiteLoglik);
 }
 
 cudaError_t launch_loglik_batches(bool doc, const int32_t* z, const int32_t* perm,
