@@ -224,6 +224,8 @@ def main():
     ap.add_argument("--corpus-seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--docs", type=int, default=0,
+                    help="use only the first DOCS documents of the workload (small profiling cases)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -263,7 +265,7 @@ def main():
                               f"the {args.workload} corpus ({dt:.1f} s)"}
         del cs
 
-    c, wl = corpus.generate(args.workload, seed=args.corpus_seed)
+    c, wl = corpus.generate(args.workload, seed=args.corpus_seed, D=args.docs or None)
     seed = args.seed + 1000 * rank
     stream = torch.cuda.current_stream()
     gpu = WarpLDA(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, seed, stream=stream)

@@ -54,7 +54,9 @@ typedef struct warplda_ctx warplda_ctx;
  * schedule); the fields only move segments between kernel tiers.
  *   batch_max_tokens  documents / words with at most this many tokens are
  *                     processed on chip, several per thread block (<= 4095).
- *   huge_chunk        tokens per thread-block chunk for longer segments.
+ *   huge_chunk        most tokens in one piece of a longer segment (the
+ *                     multi-pass tier cuts such segments into ranges of
+ *                     about equal size; 0: no further limit).
  *   region_budget     32-bit words of shared memory for the per-segment
  *                     count tables of one block batch.
  *   doc_warp_max      documents with at most this many tokens (capped at 512

@@ -47,14 +47,17 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 enum KernelClass {
     kcDocWarp, kcDocBatch, kcDocHugeHist, kcDocHugeAccept, kcDocHugeDraw,
-    kcWordBatch, kcWordMegaHist, kcWordMegaAccept, kcWordMegaDraw,
-    kcFinalize, kcZero, kcCount
+    kcWordBatch, kcWordMegaHist, kcWordMegaAccept, kcWordMegaHistPost, kcWordMegaDraw,
+    kcCountCk, kcFinalize, kcZero, kcCount
 };
 const char* kClassNames[kcCount] = {
     "doc_warp", "doc_batch", "doc_huge_hist", "doc_huge_accept", "doc_huge_draw",
-    "word_batch", "word_mega_hist", "word_mega_accept", "word_mega_draw",
-    "finalize_ck", "zero_rows"};
-constexpr int kCounters = 8;   // work counters: batches [class][phase], doc warp tier
+    "word_batch", "word_mega_hist", "word_mega_accept", "word_mega_hist_post", "word_mega_draw",
+    "count_ck", "finalize_ck", "zero_rows"};
+// work counters: 0-3 batches [class][phase], 4 doc warp tier, 5-8 the
+// multi-pass passes (hist, accept, post hist, draw), 9 log-likelihood hist
+constexpr int kCounters = 12;
+constexpr int kCtrHist = 5, kCtrAccept = 6, kCtrHistPost = 7, kCtrDraw = 8, kCtrLoglik = 9;
 
 struct Rec {
     int cls;
@@ -64,13 +67,15 @@ struct Rec {
 struct Tier {
     std::vector<int4> batches[2];    // {first segment, end segment, table words, 0}: small, large
     std::vector<int32_t> warp_list;  // segments of the warp tier (documents only)
-    std::vector<int4> chunks;        // {row, segment, first position, count}
+    std::vector<int4> chunks;        // pieces {row, segment, first position, count}
+    std::vector<int32_t> range_off;  // range r = pieces [range_off[r], range_off[r+1])
     std::vector<int32_t> region;     // table offset of each batched segment in its batch
     std::vector<int4> ll_batches;    // log-likelihood batches over all non-chunked segments
     int64_t nrows = 0, row_tokens = 0, large_tokens = 0, warp_tokens = 0;
     int4* d_batches[2] = {nullptr, nullptr};
     int32_t* d_warp_list = nullptr;
     int4* d_chunks = nullptr;
+    int32_t* d_range_off = nullptr;
     int32_t* d_region = nullptr;
     int4* d_ll_batches = nullptr;
 };
@@ -105,7 +110,7 @@ struct warplda_ctx {
     Tier docs, words;
     std::vector<int64_t> word_ptr_h;
     int grid_batch[2][2] = {{1, 1}, {1, 1}};   // [doc 0 / word 1][class]
-    int grid_hist = 1, grid_acc_doc = 1, grid_acc_word = 1, grid_draw = 1;
+    int grid_hist = 1, grid_acc_doc = 1, grid_acc_word = 1, grid_draw = 1, grid_topic = 1;
     bool prof = false;
     std::vector<Rec> recs;
     int64_t device_bytes = 0;
@@ -151,17 +156,21 @@ int table_words(int L, int K, bool dense) {
 // segments to block batches of the 8-tokens-per-thread kernel (at most
 // bmax[0] tokens, kSegsMax segments, region[0] table words per batch), large
 // ones to batches of the 16-tokens-per-thread kernel (bmax[1], region[1]);
-// longer segments get a count row and token chunks.  A batch is a run of
+// longer segments get a count row, and their tokens are cut into ranges of
+// about equal size (ranges_target of them), each a list of pieces of at
+// most `chunk` tokens of one segment.  A batch is a run of
 // consecutive segments of one class (empty segments join the open batch);
 // each batched segment records its table offset within the batch.  The
 // log-likelihood batches cover every segment that is not chunked, with the
 // paper's table rule.
 void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, int warp_max,
-                const int bmax[2], const int region[2], int chunk, Tier* t) {
+                const int bmax[2], const int region[2], int chunk, int ranges_target, Tier* t) {
     for (auto& b : t->batches) b.clear();
     t->warp_list.clear();
     t->chunks.clear();
+    t->range_off.clear();
     t->ll_batches.clear();
+    std::vector<int4> longs;   // {row, segment, first position, length}
     t->region.assign((size_t)std::max<int64_t>(S, 1), 0);
     t->nrows = t->row_tokens = t->large_tokens = t->warp_tokens = 0;
     int cur0 = -1, cls = -1, ntok = 0, nseg = 0, nw = 0;
@@ -198,8 +207,7 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
             lclose((int)s);
             const int row = (int)t->nrows++;
             t->row_tokens += L;
-            for (int p = off[s]; p < off[s + 1]; p += chunk)
-                t->chunks.push_back(make_int4(row, (int)s, p, std::min(chunk, off[s + 1] - p)));
+            longs.push_back(make_int4(row, (int)s, off[s], L));
             continue;
         }
         // log-likelihood batches (paper's table rule)
@@ -233,6 +241,27 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
     }
     close((int)S);
     lclose((int)S);
+    if (t->row_tokens > 0) {
+        const int64_t R = std::max<int64_t>(1, std::min<int64_t>(ranges_target, (t->row_tokens + 4095) / 4096));
+        const int64_t per = (t->row_tokens + R - 1) / R;
+        int64_t fill = 0;
+        t->range_off.push_back(0);
+        for (const int4& h : longs) {
+            int p = h.z, left = h.w;
+            while (left > 0) {
+                const int take = (int)std::min<int64_t>(std::min<int64_t>(left, per - fill), chunk);
+                t->chunks.push_back(make_int4(h.x, h.y, p, take));
+                p += take;
+                left -= take;
+                fill += take;
+                if (fill == per) {
+                    t->range_off.push_back((int32_t)t->chunks.size());
+                    fill = 0;
+                }
+            }
+        }
+        if (fill > 0) t->range_off.push_back((int32_t)t->chunks.size());
+    }
 }
 
 // Reads the index-check record of the kernels (synchronises); a non-zero
@@ -281,13 +310,13 @@ PhaseArgs phase_args(warplda_ctx* c, bool doc, uint32_t iter) {
     a.sinfo = c->sinfo;
     a.seg_off = doc ? c->doc_off : c->word_off;
     a.ckb = c->ckb;
-    a.ck = c->ck;
     a.K = c->K;
     a.M = c->M;
     a.g = doc ? c->alpha : c->beta;
     a.G = doc ? c->abar : c->kbeta;
     a.iter = iter;
     a.rk = round_keys(c->seed);
+    a.ck = c->ck;
     a.stage_ck = c->stage_ck;
     a.N = c->N;
     a.nseg_total = doc ? c->D : c->V;
@@ -300,6 +329,18 @@ struct PhaseCall {
     bool doc;
     int cls;
 };
+
+HugeWork huge_work(warplda_ctx* c, const Tier& T, int counter) {
+    HugeWork w;
+    w.pieces = T.d_chunks;
+    w.range_off = T.d_range_off;
+    w.nranges = (int)T.range_off.size() - 1;
+    w.npieces = (int)T.chunks.size();
+    w.nrows = (int)T.nrows;
+    w.guide_bits = huge_guide_bits(c->K);
+    w.counter = c->counters + counter;
+    return w;
+}
 
 int run_phase(warplda_ctx* c, bool doc) {
     const uint32_t it = c->iter + 1;
@@ -316,8 +357,7 @@ int run_phase(warplda_ctx* c, bool doc) {
         if (rc) return rc;
         rc = launch_rec(c, doc ? kcDocHugeHist : kcWordMegaHist, [](warplda_ctx* cc, void* p) {
             PhaseCall* q = (PhaseCall*)p;
-            Tier& TT = q->doc ? cc->docs : cc->words;
-            return launch_huge_hist(q->doc, q->a, TT.d_chunks, (int)TT.chunks.size(), (int)TT.nrows,
+            return launch_huge_hist(q->doc, q->a, huge_work(cc, q->doc ? cc->docs : cc->words, kCtrHist),
                                     q->doc ? cc->rows_doc : cc->rows_pre, cc->grid_hist, cc->st);
         }, &pc);
         if (rc) return rc;
@@ -349,18 +389,33 @@ int run_phase(warplda_ctx* c, bool doc) {
     if (nch > 0) {
         rc = launch_rec(c, doc ? kcDocHugeAccept : kcWordMegaAccept, [](warplda_ctx* cc, void* p) {
             PhaseCall* q = (PhaseCall*)p;
-            Tier& TT = q->doc ? cc->docs : cc->words;
-            return launch_huge_accept(q->doc, q->a, TT.d_chunks, (int)TT.chunks.size(), (int)TT.nrows,
-                                      q->doc ? cc->rows_doc : cc->rows_pre, cc->rows_post,
+            return launch_huge_accept(q->doc, q->a, huge_work(cc, q->doc ? cc->docs : cc->words, kCtrAccept),
+                                      q->doc ? cc->rows_doc : cc->rows_pre,
                                       q->doc ? cc->grid_acc_doc : cc->grid_acc_word, cc->st);
         }, &pc);
         if (rc) return rc;
+        if (!doc) {
+            // the word draw takes its ranks from the post-acceptance counts
+            rc = launch_rec(c, kcWordMegaHistPost, [](warplda_ctx* cc, void* p) {
+                PhaseCall* q = (PhaseCall*)p;
+                return launch_huge_hist(false, q->a, huge_work(cc, cc->words, kCtrHistPost),
+                                        cc->rows_post, cc->grid_hist, cc->st);
+            }, &pc);
+            if (rc) return rc;
+        }
         rc = launch_rec(c, doc ? kcDocHugeDraw : kcWordMegaDraw, [](warplda_ctx* cc, void* p) {
             PhaseCall* q = (PhaseCall*)p;
-            Tier& TT = q->doc ? cc->docs : cc->words;
-            return launch_huge_draw(q->doc, q->a, TT.d_chunks, (int)TT.chunks.size(), (int)TT.nrows,
+            return launch_huge_draw(q->doc, q->a, huge_work(cc, q->doc ? cc->docs : cc->words, kCtrDraw),
                                     q->doc ? cc->rows_doc : cc->rows_post, cc->grid_draw, cc->st);
         }, &pc);
+        if (rc) return rc;
+    }
+    // c_k of the new assignments (per-block partials, one global pass;
+    // Sec. 5.4), then the FP32 operands of the next phase
+    if (!c->stage_ck) {
+        rc = launch_rec(c, kcCountCk, [](warplda_ctx* cc, void*) {
+            return launch_topic_hist(cc->z, cc->N, cc->ck, cc->K, cc->grid_topic, cc->st);
+        }, nullptr);
         if (rc) return rc;
     }
     rc = launch_rec(c, kcFinalize, [](warplda_ctx* cc, void*) {
@@ -378,12 +433,12 @@ int run_phase(warplda_ctx* c, bool doc) {
 
 int launches_per_phase(const warplda_ctx* c, bool doc) {
     const Tier& T = doc ? c->docs : c->words;
-    return (T.chunks.empty() ? 0 : 4) + (T.batches[0].empty() ? 0 : 1) +
-           (T.batches[1].empty() ? 0 : 1) + (T.warp_list.empty() ? 0 : 1) + 1;
+    return (T.chunks.empty() ? 0 : (doc ? 4 : 5)) + (T.batches[0].empty() ? 0 : 1) +
+           (T.batches[1].empty() ? 0 : 1) + (T.warp_list.empty() ? 0 : 1) + (c->stage_ck ? 1 : 2);
 }
 
 int recount(warplda_ctx* c) {
-    WL_CU(launch_topic_hist(c->z, c->N, c->ck, c->K, c->st), "topic histogram");
+    WL_CU(launch_topic_hist(c->z, c->N, c->ck, c->K, c->grid_topic, c->st), "topic histogram");
     WL_CU(launch_finalize_ck(c->ck, c->ckb, c->K, c->bbar, c->counters, kCounters, c->st), "finalize c_k");
     return WARPLDA_OK;
 }
@@ -433,19 +488,21 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         const char* sc = std::getenv("WARPLDA_SYNC_CHECK");
         c->sync_check = sc && sc[0] == '1';
     }
-    c->stage_ck = K <= 4096 ? 1 : 0;
+    c->dense = K <= kDenseMaxK;
+    // dense tables: c_k is staged in shared memory and kept by per-block
+    // deltas; larger K: a histogram pass after each phase rebuilds c_k
+    c->stage_ck = c->dense ? 1 : 0;
     while ((1 << c->kbits) < K) ++c->kbits;
     // block batches: up to 2045 tokens with 8 tokens per thread, up to 4093
     // with 16; the table budget of a batch is region_budget words (defaults
     // 4096 and 8192)
     const int bmax = (tuning && tuning->batch_max_tokens > 0) ? tuning->batch_max_tokens : kMaxBatchTokens;
-    c->chunk = (tuning && tuning->huge_chunk > 0) ? tuning->huge_chunk : 16384;
+    c->chunk = (tuning && tuning->huge_chunk > 0) ? tuning->huge_chunk : (1 << 30);
     const int rb = (tuning && tuning->region_budget > 0) ? ((tuning->region_budget + 3) & ~3) : 0;
     c->bmax[0] = std::min(bmax, kThreads * 8 - 3);
     c->bmax[1] = std::min(bmax, std::min(kMaxBatchTokens, kThreads * 16 - 3));
     c->region[0] = rb ? rb : 8192;
     c->region[1] = rb ? rb : 8192;
-    c->dense = K <= kDenseMaxK;
     // documents of up to 32 * warp_tpl tokens go to the warp tier; the
     // block tier takes the rest (its small class is not used for documents)
     c->warp_tpl = c->dense ? 16 : 8;
@@ -476,8 +533,9 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         std::vector<int64_t> fill(c->word_ptr_h.begin(), c->word_ptr_h.end() - 1);
         for (int64_t p = 0; p < N; ++p) perm[p] = (int32_t)(fill[doc_word[p]]++);
     }
-    build_tier(doc_off, D, K, c->dense, warp_max, c->bmax, c->region, c->chunk, &c->docs);
-    build_tier(word_off, V, K, c->dense, 0, c->bmax, c->region, c->chunk, &c->words);
+    // multi-pass ranges: four per SM, so that blocks that finish early take more
+    build_tier(doc_off, D, K, c->dense, warp_max, c->bmax, c->region, c->chunk, 4 * c->sms, &c->docs);
+    build_tier(word_off, V, K, c->dense, 0, c->bmax, c->region, c->chunk, 4 * c->sms, &c->words);
 
     // document batches list their tokens in word-major order, with each
     // token's segment slot and position (document order) in the batch: a
@@ -555,6 +613,11 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
             if ((e = cudaMemcpyAsync(t->d_chunks, t->chunks.data(), t->chunks.size() * sizeof(int4),
                                      cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
                 return bail(cuda_fail(e, "upload chunks"));
+        if ((rc = dalloc(c, &t->d_range_off, (int64_t)t->range_off.size(), "alloc ranges"))) return bail(rc);
+        if (!t->range_off.empty())
+            if ((e = cudaMemcpyAsync(t->d_range_off, t->range_off.data(), t->range_off.size() * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+                return bail(cuda_fail(e, "upload ranges"));
     }
     if ((e = cudaMemcpyAsync(c->perm, perm.data(), ((size_t)N + 4) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
         return bail(cuda_fail(e, "upload perm"));
@@ -587,6 +650,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     c->grid_acc_doc = fit(huge_blocks_per_sm(K, c->stage_ck, 1, true, M));
     c->grid_acc_word = fit(huge_blocks_per_sm(K, c->stage_ck, 1, false, M));
     c->grid_draw = fit(huge_blocks_per_sm(K, c->stage_ck, 2, false, M));
+    c->grid_topic = (int)std::min<int64_t>(fit(topic_hist_blocks_per_sm(K)), std::max<int64_t>(1, (N + 8191) / 8192));
 
     // z = Dice(K), proposals = z (Alg. 2); c_k = histogram of z
     if ((e = launch_init_z(c->z, c->prop, N, K, M, c->seed, c->st)) != cudaSuccess)
@@ -716,8 +780,9 @@ int warplda_loglik(warplda_ctx* c, double* out) {
         int32_t* rows = doc ? c->rows_doc : c->rows_pre;
         if (!T.chunks.empty()) {
             WL_CU(launch_zero(rows, r4(T.nrows * (int64_t)c->K), c->st), "zero rows");
-            WL_CU(launch_huge_hist(doc, pa, T.d_chunks, (int)T.chunks.size(), (int)T.nrows, rows, c->grid_hist,
-                                   c->st), "loglik rows");
+            WL_CU(cudaMemsetAsync(c->counters + kCtrLoglik, 0, sizeof(int32_t), c->st), "reset counter");
+            WL_CU(launch_huge_hist(doc, pa, huge_work(c, T, kCtrLoglik), rows, c->grid_hist, c->st),
+                  "loglik rows");
             WL_CU(launch_loglik_rows(rows, T.nrows, c->K, doc ? a : b, c->d_ll, c->st), "loglik rows");
         }
         WL_CU(launch_loglik_batches(doc, c->z, c->perm, doc ? c->doc_off : c->word_off,

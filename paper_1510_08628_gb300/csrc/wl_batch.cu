@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
     extern __shared__ __align__(16) unsigned char smem[];
     const BatchSmem L = batch_smem_layout(a.K, kDense ? 1 : 0, region_words, TPT, kRadix ? 1 : 0);
     float* ckb_s = reinterpret_cast<float*>(smem + L.ck_off);
-    int* dck_s = reinterpret_cast<int*>(smem + L.ck_off) + a.K;
+    int* dck_s = reinterpret_cast<int*>(smem + L.ck_off) + a.K;   // c_k deltas (dense tables)
     int* seg_tok = reinterpret_cast<int*>(smem + L.seg_off);   // [kSegsMax + 1] token offsets
     int* seg_reg = seg_tok + kSegsMax + 1;                     // [kSegsMax + 1] table offsets
     int* seg_aux = seg_reg + kSegsMax + 1;                     // [kSegsMax] hash cap / prefix base
@@ -337,14 +337,9 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
                     const int tail = (int)dice(r.z, (uint32_t)K);
                     pp[j].v[i] = coin(r.y, Lf, LG) ? head : tail;
                 }
-                if (mine && s != z0) {
-                    if (kDense) {
-                        atomicSub(&dck_s[z0], 1);
-                        atomicAdd(&dck_s[s], 1);
-                    } else {
-                        atomicSub(&a.ck[z0], 1);
-                        atomicAdd(&a.ck[s], 1);
-                    }
+                if (kDense && mine && s != z0) {
+                    atomicSub(&dck_s[z0], 1);
+                    atomicAdd(&dck_s[s], 1);
                 }
                 zz[j] = mine ? s : zz[j];
                 if ((kDoc || kRadix) && mine) {

@@ -145,16 +145,28 @@ struct PhaseArgs {
     const uint32_t* sinfo;   // (segment slot << 16) | position within the batch, per sperm entry
     const int32_t* seg_off;  // [S+1] token offsets of documents (doc-major) or words
     const float* ckb;        // [K] (float)c_k + beta_bar, frozen for the phase
-    int32_t* ck;             // [K] c_k, receives this phase's deltas
     int32_t K, M;
     float g;                 // alpha (document phase) or beta (word phase)
     float G;                 // alpha_bar or K*beta: mixture weight L / (L + G)
     uint32_t iter;           // iteration
     RoundKeys rk;            // Philox key schedule
-    int32_t stage_ck;        // 1: c_k table and deltas in shared memory
+    int32_t* ck;             // [K] c_k; with stage_ck it receives the phase's deltas
+    int32_t stage_ck;        // 1 (dense tables): c_k table and deltas in shared memory;
+                             // 0: kernels leave c_k alone, a histogram pass rebuilds it
     int64_t N;               // tokens
     int64_t nseg_total;      // documents (document phase) or words (word phase)
     int32_t* fault;          // index-check record {kernel site, 0, check bits, 0}
+};
+
+// Work of the multi-pass tier: pieces {count row, segment, first position,
+// length} grouped into ranges of consecutive tokens (range r = pieces
+// [range_off[r], range_off[r+1])), handed to blocks by a work counter.
+struct HugeWork {
+    const int4* pieces;
+    const int32_t* range_off;
+    int nranges, npieces, nrows;
+    int guide_bits;          // word draw: log2 of the rank guide table size
+    int* counter;
 };
 
 // Index checks.  Indices a kernel takes from its work lists (batches, chunks,

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
     const int K = a.K, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Checks chk;
     float* ckb_s = reinterpret_cast<float*>(dsm);
-    int* dck_s = reinterpret_cast<int*>(dsm) + K;
+    int* dck_s = reinterpret_cast<int*>(dsm) + K;   // c_k deltas (with stage_ck)
     uint32_t* wbase = dsm + docwarp_ck_words(K, a.stage_ck) + warp * (tab_words + 32 * TPL);
     uint32_t* tab = wbase;                  // the document's count table
     uint32_t* zst = wbase + tab_words;      // post-acceptance topics, document order
@@ -138,14 +138,9 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
                     pp[m][i] = coin(r.y, Lf, LG) ? -(int)(dice(r.z, (uint32_t)L) + 1)
                                                  : (int)dice(r.z, (uint32_t)K);
                 }
-                if (s != z0) {
-                    if (a.stage_ck) {
-                        atomicSub(&dck_s[z0], 1);
-                        atomicAdd(&dck_s[s], 1);
-                    } else {
-                        atomicSub(&a.ck[z0], 1);
-                        atomicAdd(&a.ck[s], 1);
-                    }
+                if (a.stage_ck && s != z0) {
+                    atomicSub(&dck_s[z0], 1);
+                    atomicAdd(&dck_s[s], 1);
                 }
                 zz[m] = s;
                 zst[j] = (uint32_t)s;
@@ -175,8 +170,8 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
         }
     }
 
-    __syncthreads();
     if (a.stage_ck) {
+        __syncthreads();
         for (int k = tid; k < K; k += kThreads) {
             const int dv = dck_s[k];
             if (dv != 0) atomicAdd(&a.ck[k], dv);

@@ -1,99 +1,129 @@
 // Multi-pass tier of the document and word phases for segments with more
 // tokens than one block batch holds (the paper's intra-word parallelism for
-// frequent words, Sec. 5.4).  The segment's tokens are split into chunks that
-// many blocks process concurrently; the per-segment count row (K ints) lives
-// in global memory (L2-resident) and is completed between passes:
-//   hist   : row_pre  = histogram of the phase-start z of the segment
-//   accept : M chained MH steps per token against row_pre (Eq. 7), z written;
-//            word phase also builds row_post = histogram of the new z
+// frequent words, Sec. 5.4).  The tier's tokens are cut into equal ranges of
+// consecutive tokens; a range is a list of pieces, each piece a run of one
+// segment's tokens.  Blocks take ranges from a work counter, so a block
+// walks long runs of one segment and loads that segment's count row (K ints,
+// global memory) once per piece.  Per phase:
+//   hist   : row = histogram of the segment's z (before acceptance; for
+//            words, once more after acceptance)
+//   accept : M chained MH steps per token against the phase-start row
+//            (Eq. 7), z written
 //   draw   : M proposals per token from Eq. 6 -- positioning through perm
 //            over the post-acceptance document, or the j-th smallest
-//            post-acceptance topic of the word (inverse CDF of row_post).
-// Word chunks are contiguous in the word-major arrays and are streamed with
-// 128-bit loads and stores, several in flight per thread.  For words, the
-// accept pass draws each token's Philox blocks once and stores its picks in
-// the consumed proposal slots; the draw pass only resolves ranks.  For long
-// documents the draw pass recomputes the blocks.
+//            post-acceptance topic of the word (inverse CDF of its row).
+// Word pieces are contiguous in the word-major arrays and are streamed with
+// 128-bit loads and stores, the next vectors loaded while the current ones
+// are processed.  For words, the accept pass draws each token's Philox
+// blocks once and stores its picks in the consumed proposal slots; the draw
+// pass only resolves ranks.  For long documents the draw pass recomputes the
+// blocks.
 #include "wl_block.cuh"
 #include "wl_kernels.h"
 
 namespace wl {
 
-constexpr int kVecUnroll = 2;   // 16-byte vectors in flight per thread per array
-constexpr int kGuideBits = 12;  // guide table of 4096 buckets over a word's ranks
-
-// Increment of a shared-memory histogram bin.
-__device__ __forceinline__ void agg_add(int* h, int k) {
-    atomicAdd(&h[k], 1);
-}
+constexpr int kVecUnroll = 2;   // 16-byte vectors per thread per array per step
 
 __device__ __forceinline__ int elem(const int4& v, int e) {
     return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
 }
 
-// A work chunk {row, segment, first position, length}: valid when it lies in
-// its segment and names an existing count row.
-__device__ __forceinline__ bool chunk_ok(const PhaseArgs& a, const int4& ch, int nrows) {
+// A piece {row, segment, first position, length}: valid when it lies in its
+// segment and names an existing count row.
+__device__ __forceinline__ bool piece_ok(const PhaseArgs& a, const int4& ch, int nrows) {
     if (ch.x < 0 || ch.x >= nrows || ch.y < 0 || (int64_t)ch.y >= a.nseg_total || ch.w < 0) return false;
     const int s0 = a.seg_off[ch.y], s1 = a.seg_off[ch.y + 1];
     return ch.z >= s0 && (int64_t)ch.z + ch.w <= s1;
 }
 
+// The next range of the block (uniform over the block): its pieces
+// [*pc0, *pc1), or false when the ranges are exhausted.
+__device__ __forceinline__ bool next_range(const HugeWork& w, int* s_r, Checks& chk, int* pc0,
+                                           int* pc1) {
+    if (threadIdx.x == 0) *s_r = atomicAdd(w.counter, 1);
+    __syncthreads();
+    const int r = *s_r;
+    __syncthreads();
+    if (r >= w.nranges) return false;
+    *pc0 = w.range_off[r];
+    *pc1 = w.range_off[r + 1];
+    if (!chk(0 <= *pc0 && *pc0 <= *pc1 && *pc1 <= w.npieces, 0)) *pc1 = *pc0;
+    return true;
+}
+
+__device__ __forceinline__ int4 get_piece(const PhaseArgs& a, const HugeWork& w, int pc, Checks& chk) {
+    int4 ch = w.pieces[pc];
+    if (!chk(piece_ok(a, ch, w.nrows), 1)) ch = make_int4(0, 0, 0, 0);
+    return ch;
+}
+
+// Buckets of the rank guide table of the word draw: a power of two of at
+// least 2K (so that a bucket spans about half a topic or less), 4096 to 16384.
+int huge_guide_bits(int K) {
+    int b = 12;
+    while (b < 14 && (1 << b) < 2 * K) ++b;
+    return b;
+}
+
 int huge_smem_bytes(int K, int stage_ck, int pass, bool doc) {
-    // pass 0 hist: K; pass 1 accept: row + (word) hist + staged ck;
-    // pass 2 draw: K+1 prefix + guide table
+    // pass 0 hist: K; pass 1 accept: row + staged c_k and deltas; pass 2
+    // draw: (words) K+1 prefix + guide table
     int words = 0;
     if (pass == 0) words = K;
-    else if (pass == 1) words = K + (doc ? 0 : K) + (stage_ck ? 2 * K : 0);
-    else words = doc ? 0 : K + 1 + (1 << kGuideBits);
+    else if (pass == 1) words = K + (stage_ck ? 2 * K : 0);
+    else words = doc ? 0 : K + 1 + (1 << huge_guide_bits(K));
     return ((words * 4) + 15) & ~15;
 }
 
 template <bool kDoc>
-__global__ void __launch_bounds__(kThreads) huge_hist_kernel(PhaseArgs a, const int4* __restrict__ chunks,
-                                                             int nchunks, int nrows, int32_t* __restrict__ rows) {
+__global__ void __launch_bounds__(kThreads) huge_hist_kernel(PhaseArgs a, HugeWork w,
+                                                             int32_t* __restrict__ rows) {
     extern __shared__ __align__(16) int hist[];
+    __shared__ int s_r;
     const int K = a.K, tid = threadIdx.x;
     Checks chk;
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        int4 ch = chunks[c];
-        if (!chk(chunk_ok(a, ch, nrows), 0)) ch = make_int4(0, 0, 0, 0);
-        const int p0 = ch.z, p1 = ch.z + ch.w;
-        for (int k = tid; k < K; k += kThreads) hist[k] = 0;
-        __syncthreads();
-        if (kDoc) {
-            for (int p = p0 + tid; p < p1; p += kThreads) {
-                const int t = a.perm[p];
-                if (!chk.tok((uint32_t)t < (uint32_t)a.N, 1)) continue;
-                agg_add(hist, chk.topic(a.z[t], K, 2));
-            }
-        } else {
-            const int v0 = p0 >> 2, v1 = (p1 + 3) >> 2;
-            const int4* zv = reinterpret_cast<const int4*>(a.z);
-            for (int vb = v0 + tid; vb < v1; vb += kThreads * kVecUnroll) {
-                int4 x[kVecUnroll];
-#pragma unroll
-                for (int u = 0; u < kVecUnroll; ++u) {
-                    const int v = vb + u * kThreads;
-                    if (v < v1) x[u] = zv[v];
+    int pc0, pc1;
+    while (next_range(w, &s_r, chk, &pc0, &pc1)) {
+        for (int pc = pc0; pc < pc1; ++pc) {
+            const int4 ch = get_piece(a, w, pc, chk);
+            const int p0 = ch.z, p1 = ch.z + ch.w;
+            for (int k = tid; k < K; k += kThreads) hist[k] = 0;
+            __syncthreads();
+            if (kDoc) {
+                for (int p = p0 + tid; p < p1; p += kThreads) {
+                    const int t = a.perm[p];
+                    if (!chk.tok((uint32_t)t < (uint32_t)a.N, 2)) continue;
+                    atomicAdd(&hist[chk.topic(a.z[t], K, 3)], 1);
                 }
+            } else {
+                const int v0 = p0 >> 2, v1 = (p1 + 3) >> 2;
+                const int4* zv = reinterpret_cast<const int4*>(a.z);
+                for (int vb = v0 + tid; vb < v1; vb += kThreads * kVecUnroll) {
+                    int4 x[kVecUnroll];
 #pragma unroll
-                for (int u = 0; u < kVecUnroll; ++u) {
-                    const int v = vb + u * kThreads;
-                    if (v >= v1) continue;
+                    for (int u = 0; u < kVecUnroll; ++u) {
+                        const int v = vb + u * kThreads;
+                        if (v < v1) x[u] = zv[v];
+                    }
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int q = 4 * v + e;
-                        if (q >= p0 && q < p1) agg_add(hist, chk.topic(elem(x[u], e), K, 2));
+                    for (int u = 0; u < kVecUnroll; ++u) {
+                        const int v = vb + u * kThreads;
+                        if (v >= v1) continue;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int q = 4 * v + e;
+                            if (q >= p0 && q < p1) atomicAdd(&hist[chk.topic(elem(x[u], e), K, 3)], 1);
+                        }
                     }
                 }
             }
+            __syncthreads();
+            int32_t* row = rows + (int64_t)ch.x * K;
+            for (int k = tid; k < K; k += kThreads)
+                if (hist[k] != 0) atomicAdd(&row[k], hist[k]);
+            __syncthreads();
         }
-        __syncthreads();
-        int32_t* row = rows + (int64_t)ch.x * K;
-        for (int k = tid; k < K; k += kThreads)
-            if (hist[k] != 0) atomicAdd(&row[k], hist[k]);
-        __syncthreads();
     }
     chk.publish(a.fault, kSiteHugeHist);
 }
@@ -117,137 +147,140 @@ __device__ __forceinline__ int mh_chain(const PhaseArgs& a, uint32_t t, uint32_t
 }
 
 template <bool kDoc, int M>
-__global__ void __launch_bounds__(kThreads) huge_accept_kernel(PhaseArgs a, const int4* __restrict__ chunks,
-                                                               int nchunks, int nrows,
-                                                               const int32_t* __restrict__ rows_pre,
-                                                               int32_t* __restrict__ rows_post) {
+__global__ void __launch_bounds__(kThreads, (M <= 2 ? 3 : 2)) huge_accept_kernel(PhaseArgs a, HugeWork w,
+                                                               const int32_t* __restrict__ rows_pre) {
     extern __shared__ __align__(16) int sm[];
+    __shared__ int s_r;
     const int K = a.K, tid = threadIdx.x;
-    Checks chk;
     int* row = sm;
-    int* hist = sm + K;                                    // word phase only
-    float* ckb_s = reinterpret_cast<float*>(sm + (kDoc ? K : 2 * K));
-    int* dck_s = sm + (kDoc ? 2 * K : 3 * K);
+    float* ckb_s = reinterpret_cast<float*>(sm + K);
+    int* dck_s = sm + 2 * K;   // c_k deltas (with stage_ck)
+    Checks chk;
     if (a.stage_ck) {
         for (int k = tid; k < K; k += kThreads) {
             ckb_s[k] = a.ckb[k];
             dck_s[k] = 0;
         }
     }
-    const uint32_t phase = kDoc ? kPhaseDoc : kPhaseWord;
     auto delta = [&](int z0, int s) {
-        if (a.stage_ck) {
+        if (a.stage_ck && s != z0) {
             atomicSub(&dck_s[z0], 1);
             atomicAdd(&dck_s[s], 1);
-        } else {
-            atomicSub(&a.ck[z0], 1);
-            atomicAdd(&a.ck[s], 1);
         }
     };
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        int4 ch = chunks[c];
-        if (!chk(chunk_ok(a, ch, nrows), 0)) ch = make_int4(0, 0, 0, 0);
-        const int p0 = ch.z, p1 = ch.z + ch.w;
-        const int32_t* rp = rows_pre + (int64_t)ch.x * K;
-        for (int k = tid; k < K; k += kThreads) {
-            row[k] = rp[k];
-            if (!kDoc) hist[k] = 0;
-        }
-        __syncthreads();
-        if (kDoc) {
-            for (int p = p0 + tid; p < p1; p += kThreads) {
-                const int t = a.perm[p];
-                if (!chk.tok((uint32_t)t < (uint32_t)a.N, 1)) continue;
-                const int z0 = chk.topic(a.z[t], K, 2);
-                int pr[M];
+    const uint32_t phase = kDoc ? kPhaseDoc : kPhaseWord;
+    int pc0, pc1;
+    while (next_range(w, &s_r, chk, &pc0, &pc1)) {
+        for (int pc = pc0; pc < pc1; ++pc) {
+            const int4 ch = get_piece(a, w, pc, chk);
+            const int p0 = ch.z, p1 = ch.z + ch.w;
+            const int4* rp = reinterpret_cast<const int4*>(rows_pre + (int64_t)ch.x * K);
+            if ((K & 3) == 0) {
+                for (int k = tid; k < (K >> 2); k += kThreads) reinterpret_cast<int4*>(row)[k] = rp[k];
+            } else {
+                for (int k = tid; k < K; k += kThreads) row[k] = rows_pre[(int64_t)ch.x * K + k];
+            }
+            __syncthreads();
+            if (kDoc) {
+                for (int p = p0 + tid; p < p1; p += kThreads) {
+                    const int t = a.perm[p];
+                    if (!chk.tok((uint32_t)t < (uint32_t)a.N, 2)) continue;
+                    const int z0 = chk.topic(a.z[t], K, 3);
+                    int pr[M];
 #pragma unroll
-                for (int i = 0; i < M; ++i) pr[i] = chk.topic(a.prop[(int64_t)t * M + i], K, 3);
-                const int s = mh_chain<M>(a, (uint32_t)t, phase, z0, pr, row, ckb_s);
-                if (s != z0) {
-                    a.z[t] = s;
+                    for (int i = 0; i < M; ++i) pr[i] = chk.topic(a.prop[(int64_t)t * M + i], K, 4);
+                    const int s = mh_chain<M>(a, (uint32_t)t, phase, z0, pr, row, ckb_s);
+                    if (s != z0) a.z[t] = s;
                     delta(z0, s);
                 }
-            }
-        } else {
-            // word chunk: 128-bit loads of z and of the proposals; the M blocks
-            // of each token are drawn here once, the accept uses r0 and the
-            // pick of Eq. 6 (a topic, or -(rank + 1) resolved by the draw pass)
-            // is written over the consumed proposal
-            const int Ls = a.seg_off[ch.y + 1] - a.seg_off[ch.y];
-            const float Lf = __int2float_rn(Ls);
-            const float LG = __fadd_rn(Lf, a.G);
-            const int v0 = p0 >> 2, v1 = (p1 + 3) >> 2;
-            int4* zv = reinterpret_cast<int4*>(a.z);
-            int4* pv = reinterpret_cast<int4*>(a.prop);
-            for (int vb = v0 + tid; vb < v1; vb += kThreads * kVecUnroll) {
-                int4 x[kVecUnroll], y[kVecUnroll][M];
+            } else {
+                // word piece: 128-bit loads of z and of the proposals, the next
+                // step's vectors in flight while this step's are processed; the
+                // M blocks of each token are drawn here once, the accept uses r0
+                // and the pick of Eq. 6 (a topic, or -(rank + 1) resolved by the
+                // draw pass) is written over the consumed proposal
+                const int Ls = a.seg_off[ch.y + 1] - a.seg_off[ch.y];
+                const float Lf = __int2float_rn(Ls);
+                const float LG = __fadd_rn(Lf, a.G);
+                const int v0 = p0 >> 2, v1 = (p1 + 3) >> 2;
+                int4* zv = reinterpret_cast<int4*>(a.z);
+                int4* pv = reinterpret_cast<int4*>(a.prop);
+                constexpr int kStep = kThreads * kVecUnroll;
+                int4 xn[kVecUnroll], yn[kVecUnroll][M];
+                auto load = [&](int vb) {
 #pragma unroll
-                for (int u = 0; u < kVecUnroll; ++u) {
-                    const int v = vb + u * kThreads;
-                    if (v < v1) {
-                        x[u] = zv[v];
+                    for (int u = 0; u < kVecUnroll; ++u) {
+                        const int v = vb + u * kThreads;
+                        if (v < v1) {
+                            xn[u] = zv[v];
 #pragma unroll
-                        for (int i = 0; i < M; ++i) y[u][i] = pv[(int64_t)v * M + i];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < kVecUnroll; ++u) {
-                    const int v = vb + u * kThreads;
-                    if (v >= v1) continue;
-                    int out[4], pk[4 * M];
-                    bool full = true;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int q = 4 * v + e;
-                        out[e] = elem(x[u], e);
-#pragma unroll
-                        for (int i = 0; i < M; ++i) pk[e * M + i] = 0;
-                        if (q < p0 || q >= p1) { full = false; continue; }
-                        const int z0 = chk.topic(out[e], K, 2);
-                        int s = z0;
-#pragma unroll
-                        for (int i = 0; i < M; ++i) {
-                            const uint4 r = draw((uint32_t)q, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
-                            const int tp = chk.topic(elem(y[u][(e * M + i) / 4], (e * M + i) % 4), K, 3);
-                            if (tp != s) {
-                                const float cs = a.stage_ck ? ckb_s[s] : __ldg(a.ckb + s);
-                                const float ct = a.stage_ck ? ckb_s[tp] : __ldg(a.ckb + tp);
-                                if (accept(r.x, row[s], row[tp], a.g, cs, ct)) s = tp;
-                            }
-                            pk[e * M + i] = coin(r.y, Lf, LG) ? -(int)(dice(r.z, (uint32_t)Ls) + 1)
-                                                              : (int)dice(r.z, (uint32_t)K);
+                            for (int i = 0; i < M; ++i) yn[u][i] = pv[(int64_t)v * M + i];
                         }
-                        if (s != z0) delta(z0, s);
-                        agg_add(hist, s);
-                        out[e] = s;
                     }
-                    if (full) {
-                        zv[v] = make_int4(out[0], out[1], out[2], out[3]);
+                };
+                load(v0 + tid);
+                for (int vb = v0 + tid; vb < v1; vb += kStep) {
+                    int4 x[kVecUnroll], y[kVecUnroll][M];
 #pragma unroll
-                        for (int i = 0; i < M; ++i)
-                            pv[(int64_t)v * M + i] = make_int4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
-                    } else {
+                    for (int u = 0; u < kVecUnroll; ++u) {
+                        x[u] = xn[u];
+#pragma unroll
+                        for (int i = 0; i < M; ++i) y[u][i] = yn[u][i];
+                    }
+                    if (vb + kStep < v1) load(vb + kStep);
+#pragma unroll
+                    for (int u = 0; u < kVecUnroll; ++u) {
+                        const int v = vb + u * kThreads;
+                        if (v >= v1) continue;
+                        int out[4], pk[4 * M];
+                        bool full = true;
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
                             const int q = 4 * v + e;
-                            if (q < p0 || q >= p1) continue;
-                            a.z[q] = out[e];
+                            out[e] = elem(x[u], e);
 #pragma unroll
-                            for (int i = 0; i < M; ++i) a.prop[(int64_t)q * M + i] = pk[e * M + i];
+                            for (int i = 0; i < M; ++i) pk[e * M + i] = 0;
+                            if (q < p0 || q >= p1) { full = false; continue; }
+                            const int z0 = chk.topic(out[e], K, 3);
+                            int s = z0;
+#pragma unroll
+                            for (int i = 0; i < M; ++i) {
+                                const uint4 r = draw((uint32_t)q, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
+                                const int tp = chk.topic(elem(y[u][(e * M + i) / 4], (e * M + i) % 4), K, 4);
+                                if (tp != s) {
+                                    const float cs = a.stage_ck ? ckb_s[s] : __ldg(a.ckb + s);
+                                    const float ct = a.stage_ck ? ckb_s[tp] : __ldg(a.ckb + tp);
+                                    if (accept(r.x, row[s], row[tp], a.g, cs, ct)) s = tp;
+                                }
+                                pk[e * M + i] = coin(r.y, Lf, LG) ? -(int)(dice(r.z, (uint32_t)Ls) + 1)
+                                                                  : (int)dice(r.z, (uint32_t)K);
+                            }
+                            delta(z0, s);
+                            out[e] = s;
+                        }
+                        if (full) {
+                            zv[v] = make_int4(out[0], out[1], out[2], out[3]);
+#pragma unroll
+                            for (int i = 0; i < M; ++i)
+                                pv[(int64_t)v * M + i] = make_int4(pk[4 * i], pk[4 * i + 1], pk[4 * i + 2], pk[4 * i + 3]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int q = 4 * v + e;
+                                if (q < p0 || q >= p1) continue;
+                                a.z[q] = out[e];
+#pragma unroll
+                                for (int i = 0; i < M; ++i) a.prop[(int64_t)q * M + i] = pk[e * M + i];
+                            }
                         }
                     }
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
-        if (!kDoc) {
-            int32_t* rq = rows_post + (int64_t)ch.x * K;
-            for (int k = tid; k < K; k += kThreads)
-                if (hist[k] != 0) atomicAdd(&rq[k], hist[k]);
-        }
-        __syncthreads();
     }
     if (a.stage_ck) {
+        __syncthreads();
         for (int k = tid; k < K; k += kThreads)
             if (dck_s[k] != 0) atomicAdd(&a.ck[k], dck_s[k]);
     }
@@ -255,81 +288,96 @@ __global__ void __launch_bounds__(kThreads) huge_accept_kernel(PhaseArgs a, cons
 }
 
 template <bool kDoc, int M>
-__global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const int4* __restrict__ chunks,
-                                                             int nchunks, int nrows,
+__global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, HugeWork w,
                                                              const int32_t* __restrict__ rows_post) {
     extern __shared__ __align__(16) int sm[];
     __shared__ int warp_tot[kWarps];
-    __shared__ int s_total;
+    __shared__ int s_total, s_r;
     const int K = a.K, tid = threadIdx.x;
-    int* P = sm;   // word phase: exclusive prefix of row_post, P[K] = L_w
+    int* P = sm;   // word phase: exclusive prefix of the post-acceptance row, P[K] = L_w
+    int* guide = P + K + 1;
     const uint32_t phase = kDoc ? kPhaseDoc : kPhaseWord;
     Checks chk;
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        int4 ch = chunks[c];
-        if (!chk(chunk_ok(a, ch, nrows), 0)) ch = make_int4(0, 0, 0, 0);
-        const int sb = a.seg_off[ch.y];
-        const int Ls = max(a.seg_off[ch.y + 1] - sb, 1);
-        const int p0 = ch.z, p1 = ch.z + ch.w;
-        if (!kDoc) {
-            const int32_t* rq = rows_post + (int64_t)ch.x * K;
-            int carry = 0;
-            for (int k0 = 0; k0 < K; k0 += kThreads) {
-                const int k = k0 + tid;
-                const int v = (k < K) ? rq[k] : 0;
-                const int e = block_excl_scan(v, warp_tot, &s_total);
-                if (k < K) P[k] = carry + e;
-                carry += s_total;
-            }
-            if (tid == 0) P[K] = carry;
-            __syncthreads();
-            // guide[b] = the answer for the smallest rank of bucket b,
-            // ceil(b L / 2^kGuideBits); a rank j's bucket is at least
-            // (j * floor(2^(32+kGuideBits) / L)) >> 32
-            int* guide = P + K + 1;
-            for (int b = tid; b < (1 << kGuideBits); b += kThreads) {
-                const int j = (int)((((int64_t)b * Ls) + (1 << kGuideBits) - 1) >> kGuideBits);
-                int lo = 0, hi = K - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (P[mid] <= j) lo = mid; else hi = mid - 1;
-                }
-                guide[b] = lo;
-            }
-        }
-        __syncthreads();
-        const float Lf = __int2float_rn(Ls);
-        const float LG = __fadd_rn(Lf, a.G);
-        if (kDoc) {
-            for (int p = p0 + tid; p < p1; p += kThreads) {
-                const int t = a.perm[p];
+    int pc0, pc1;
+    while (next_range(w, &s_r, chk, &pc0, &pc1)) {
+        for (int pc = pc0; pc < pc1; ++pc) {
+            const int4 ch = get_piece(a, w, pc, chk);
+            const int sb = a.seg_off[ch.y];
+            const int Ls = max(a.seg_off[ch.y + 1] - sb, 1);
+            const int p0 = ch.z, p1 = ch.z + ch.w;
+            const float Lf = __int2float_rn(Ls);
+            const float LG = __fadd_rn(Lf, a.G);
+            if (kDoc) {
+                for (int p = p0 + tid; p < p1; p += kThreads) {
+                    const int t = a.perm[p];
 #pragma unroll
-                for (int i = 0; i < M; ++i) {
-                    const uint4 r = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
-                    int k = (int)dice(r.z, (uint32_t)K);
-                    if (coin(r.y, Lf, LG)) {
-                        const int tq = a.perm[sb + (int)dice(r.z, (uint32_t)Ls)];
-                        if (chk.tok((uint32_t)tq < (uint32_t)a.N, 1)) k = a.z[tq];
+                    for (int i = 0; i < M; ++i) {
+                        const uint4 r = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
+                        int k = (int)dice(r.z, (uint32_t)K);
+                        if (coin(r.y, Lf, LG)) {
+                            const int tq = a.perm[sb + (int)dice(r.z, (uint32_t)Ls)];
+                            if (chk.tok((uint32_t)tq < (uint32_t)a.N, 2)) k = a.z[tq];
+                        }
+                        a.prop[(int64_t)t * M + i] = k;
                     }
-                    a.prop[(int64_t)t * M + i] = k;
                 }
+                continue;   // no shared state between pieces
             }
-        } else {
+            // exclusive prefix of the word's post-acceptance row: the row is
+            // copied in, each thread sums a contiguous run of topics, one
+            // block scan, then the runs become prefixes
+            const int32_t* rq = rows_post + (int64_t)ch.x * K;
+            for (int k = tid; k < K; k += kThreads) P[k] = rq[k];
+            __syncthreads();
+            const int per = (K + kThreads - 1) / kThreads;
+            const int k0 = min(K, tid * per), k1 = min(K, k0 + per);
+            int sum = 0;
+            for (int k = k0; k < k1; ++k) sum += P[k];
+            int run = block_excl_scan(sum, warp_tot, &s_total);
+            for (int k = k0; k < k1; ++k) {
+                const int c = P[k];
+                P[k] = run;
+                run += c;
+            }
+            if (tid == 0) P[K] = s_total;
+            __syncthreads();
+            // rank j lies in bucket B(j) = (j * floor(2^(32+gb) / L)) >> 32
+            // (non-decreasing in j).  Topic k fills the buckets that first
+            // occur inside its ranks, (B(P[k]-1), B(P[k+1]-1)], so guide[b]
+            // is the topic of the smallest rank of bucket b: a lower bound
+            // for every rank of the bucket, from which the lookup walks up
+            const int gb = w.guide_bits, nb = 1 << gb;
+            const uint64_t mult = (1ull << (32 + gb)) / (uint64_t)Ls;
+            auto bucket_of = [&](int j) { return j < 0 ? -1 : (int)(((uint64_t)j * mult) >> 32); };
+            for (int k = k0; k < k1; ++k) {
+                const int b0 = bucket_of(P[k] - 1) + 1, b1 = min(bucket_of(P[k + 1] - 1), nb - 1);
+                for (int b = b0; b <= b1; ++b) guide[b] = k;
+            }
+            for (int b = max(0, bucket_of(Ls - 1) + 1) + tid; b < nb; b += kThreads) guide[b] = K - 1;
+            __syncthreads();
             // resolve the picks the accept pass stored: a rank j < L_w becomes
             // the j-th smallest post-acceptance topic of the word
-            const uint64_t mult = (1ull << (32 + kGuideBits)) / (uint64_t)Ls;
-            const int* guide = P + K + 1;
             const int v0 = p0 >> 2, v1 = (p1 + 3) >> 2;
             int4* pv = reinterpret_cast<int4*>(a.prop);
-            for (int vb = v0 + tid; vb < v1; vb += kThreads * kVecUnroll) {
-                int4 y[kVecUnroll][M];
+            constexpr int kStep = kThreads * kVecUnroll;
+            int4 yn[kVecUnroll][M];
+            auto load = [&](int vb) {
 #pragma unroll
                 for (int u = 0; u < kVecUnroll; ++u) {
                     const int v = vb + u * kThreads;
                     if (v < v1)
 #pragma unroll
-                        for (int i = 0; i < M; ++i) y[u][i] = pv[(int64_t)v * M + i];
+                        for (int i = 0; i < M; ++i) yn[u][i] = pv[(int64_t)v * M + i];
                 }
+            };
+            load(v0 + tid);
+            for (int vb = v0 + tid; vb < v1; vb += kStep) {
+                int4 y[kVecUnroll][M];
+#pragma unroll
+                for (int u = 0; u < kVecUnroll; ++u)
+#pragma unroll
+                    for (int i = 0; i < M; ++i) y[u][i] = yn[u][i];
+                if (vb + kStep < v1) load(vb + kStep);
 #pragma unroll
                 for (int u = 0; u < kVecUnroll; ++u) {
                     const int v = vb + u * kThreads;
@@ -337,17 +385,17 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const 
                     int out[4 * M];
 #pragma unroll
                     for (int n = 0; n < 4 * M; ++n) {
-                        // only this chunk's tokens: an edge vector's other
-                        // entries belong to a neighbouring chunk or word
+                        // only this piece's tokens: an edge vector's other
+                        // entries belong to a neighbouring piece or word
                         const int q = 4 * v + n / M;
                         int pk = elem(y[u][n / 4], n % 4);
                         if (q < p0 || q >= p1) pk = 0;
                         if (pk < 0) {
                             int j = -pk - 1;
-                            if (!chk.tok((uint32_t)j < (uint32_t)Ls, 4)) j = 0;
-                            int k = guide[(int)(((uint64_t)j * mult) >> 32)];
+                            if (!chk.tok((uint32_t)j < (uint32_t)Ls, 5)) j = 0;
+                            int k = guide[bucket_of(j)];
                             while (k + 1 < K && P[k + 1] <= j) ++k;
-                            pk = chk.tok(P[k + 1] > j, 5) ? k : 0;
+                            pk = chk.tok(P[k + 1] > j, 6) ? k : 0;
                         }
                         out[n] = pk;
                     }
@@ -367,8 +415,8 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, const 
                     }
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
     chk.publish(a.fault, kSiteHugeDraw);
 }
@@ -378,18 +426,18 @@ static cudaError_t set_smem(F f, int smem) {
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
-cudaError_t launch_huge_hist(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
-                             int nrows, int32_t* rows, int grid, cudaStream_t st) {
-    if (nchunks <= 0) return cudaSuccess;
+cudaError_t launch_huge_hist(bool doc, const PhaseArgs& a, const HugeWork& w, int32_t* rows,
+                             int grid, cudaStream_t st) {
+    if (w.npieces <= 0) return cudaSuccess;
     const int smem = huge_smem_bytes(a.K, a.stage_ck, 0, doc);
     if (doc) {
         cudaError_t e = set_smem(huge_hist_kernel<true>, smem);
         if (e != cudaSuccess) return e;
-        huge_hist_kernel<true><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, nrows, rows);
+        huge_hist_kernel<true><<<grid, kThreads, smem, st>>>(a, w, rows);
     } else {
         cudaError_t e = set_smem(huge_hist_kernel<false>, smem);
         if (e != cudaSuccess) return e;
-        huge_hist_kernel<false><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, nrows, rows);
+        huge_hist_kernel<false><<<grid, kThreads, smem, st>>>(a, w, rows);
     }
     return cudaGetLastError();
 }
@@ -403,44 +451,43 @@ cudaError_t launch_huge_hist(bool doc, const PhaseArgs& a, const int4* chunks, i
         default: return cudaErrorInvalidValue;           \
     }
 
-cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
-                               int nrows, const int32_t* rows_pre, int32_t* rows_post, int grid,
-                               cudaStream_t st) {
-    if (nchunks <= 0) return cudaSuccess;
+cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const HugeWork& w,
+                               const int32_t* rows_pre, int grid, cudaStream_t st) {
+    if (w.npieces <= 0) return cudaSuccess;
     const int smem = huge_smem_bytes(a.K, a.stage_ck, 1, doc);
     cudaError_t e = cudaSuccess;
     if (doc) {
         WL_M_SWITCH({
             e = set_smem(huge_accept_kernel<true, MM>, smem);
             if (e != cudaSuccess) return e;
-            huge_accept_kernel<true, MM><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, nrows, rows_pre, rows_post);
+            huge_accept_kernel<true, MM><<<grid, kThreads, smem, st>>>(a, w, rows_pre);
         })
     } else {
         WL_M_SWITCH({
             e = set_smem(huge_accept_kernel<false, MM>, smem);
             if (e != cudaSuccess) return e;
-            huge_accept_kernel<false, MM><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, nrows, rows_pre, rows_post);
+            huge_accept_kernel<false, MM><<<grid, kThreads, smem, st>>>(a, w, rows_pre);
         })
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
-                             int nrows, const int32_t* rows_post, int grid, cudaStream_t st) {
-    if (nchunks <= 0) return cudaSuccess;
+cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const HugeWork& w,
+                             const int32_t* rows_post, int grid, cudaStream_t st) {
+    if (w.npieces <= 0) return cudaSuccess;
     const int smem = huge_smem_bytes(a.K, a.stage_ck, 2, doc);
     cudaError_t e = cudaSuccess;
     if (doc) {
         WL_M_SWITCH({
             e = set_smem(huge_draw_kernel<true, MM>, smem);
             if (e != cudaSuccess) return e;
-            huge_draw_kernel<true, MM><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, nrows, rows_post);
+            huge_draw_kernel<true, MM><<<grid, kThreads, smem, st>>>(a, w, rows_post);
         })
     } else {
         WL_M_SWITCH({
             e = set_smem(huge_draw_kernel<false, MM>, smem);
             if (e != cudaSuccess) return e;
-            huge_draw_kernel<false, MM><<<grid, kThreads, smem, st>>>(a, chunks, nchunks, nrows, rows_post);
+            huge_draw_kernel<false, MM><<<grid, kThreads, smem, st>>>(a, w, rows_post);
         })
     }
     return cudaGetLastError();

@@ -27,23 +27,24 @@ int docwarp_blocks_per_sm(int K, int stage_ck, int tpl, int M, int dense);
 cudaError_t launch_doc_warp(int tpl, bool dense, const PhaseArgs& a, const int32_t* docs, int ndocs,
                             int* counter, int grid, cudaStream_t st);
 
-// Multi-pass tier for segments too long for one block (wl_huge.cu).
-// chunk = {row, segment id, first token position, token count}
+// Multi-pass tier for segments too long for one block (wl_huge.cu); rows
+// are count rows of K ints, one per long segment.
+int huge_guide_bits(int K);
 int huge_smem_bytes(int K, int stage_ck, int pass, bool doc);
 int huge_blocks_per_sm(int K, int stage_ck, int pass, bool doc, int M);
-// chunks: {count row, segment, first position, length}; nrows rows of K ints.
-cudaError_t launch_huge_hist(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
-                             int nrows, int32_t* rows, int grid, cudaStream_t st);
-cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
-                               int nrows, const int32_t* rows_pre, int32_t* rows_post, int grid,
-                               cudaStream_t st);
-cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const int4* chunks, int nchunks,
-                             int nrows, const int32_t* rows_post, int grid, cudaStream_t st);
+cudaError_t launch_huge_hist(bool doc, const PhaseArgs& a, const HugeWork& w, int32_t* rows,
+                             int grid, cudaStream_t st);
+cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const HugeWork& w,
+                               const int32_t* rows_pre, int grid, cudaStream_t st);
+cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const HugeWork& w,
+                             const int32_t* rows_post, int grid, cudaStream_t st);
 
 // Initialisation, c_k, export, log-likelihood (wl_misc.cu).
 cudaError_t launch_init_z(int32_t* z, int32_t* prop, int64_t N, int K, int M, uint64_t seed,
                           cudaStream_t st);
-cudaError_t launch_topic_hist(const int32_t* z, int64_t N, int32_t* ck, int K, cudaStream_t st);
+// c_k = histogram of z (z 16-byte aligned); grid from topic_hist_blocks_per_sm
+int topic_hist_blocks_per_sm(int K);
+cudaError_t launch_topic_hist(const int32_t* z, int64_t N, int32_t* ck, int K, int grid, cudaStream_t st);
 cudaError_t launch_finalize_ck(const int32_t* ck, float* ckb, int K, float beta_bar,
                                int32_t* counters, int ncounters, cudaStream_t st);
 cudaError_t launch_zero(int32_t* p, int64_t n, cudaStream_t st);

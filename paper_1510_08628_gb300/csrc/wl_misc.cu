@@ -30,25 +30,53 @@ cudaError_t launch_init_z(int32_t* z, int32_t* prop, int64_t N, int K, int M, ui
     return cudaGetLastError();
 }
 
-__global__ void topic_hist_kernel(const int32_t* z, int64_t N, int32_t* ck, int K) {
+// c_k = histogram of z: per-block histograms in shared memory over 128-bit
+// loads, added into c_k once per block.
+__global__ void __launch_bounds__(kThreads) topic_hist_kernel(const int32_t* __restrict__ z, int64_t N,
+                                                              int32_t* __restrict__ ck, int K) {
     extern __shared__ int h[];
     for (int k = threadIdx.x; k < K; k += blockDim.x) h[k] = 0;
     __syncthreads();
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N;
-         t += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&h[z[t]], 1);
+    // topics are in [0, K) by construction; the clamp keeps a corrupt
+    // value from addressing outside the histogram
+    const uint32_t km = (uint32_t)K - 1u;
+    auto add = [&](int v) { atomicAdd(&h[min((uint32_t)v, km)], 1); };
+    const int4* zv = reinterpret_cast<const int4*>(z);
+    const int64_t n4 = N >> 2;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; i + stride < n4; i += 2 * stride) {
+        const int4 a = zv[i], b = zv[i + stride];
+        add(a.x); add(a.y); add(a.z); add(a.w);
+        add(b.x); add(b.y); add(b.z); add(b.w);
+    }
+    for (; i < n4; i += stride) {
+        const int4 a = zv[i];
+        add(a.x); add(a.y); add(a.z); add(a.w);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (N & 3)) add(z[(n4 << 2) + threadIdx.x]);
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x)
         if (h[k]) atomicAdd(&ck[k], h[k]);
 }
 
-cudaError_t launch_topic_hist(const int32_t* z, int64_t N, int32_t* ck, int K, cudaStream_t st) {
+int topic_hist_blocks_per_sm(int K) {
+    const int smem = K * 4;
+    if (cudaFuncSetAttribute(topic_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, topic_hist_kernel, kThreads, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t launch_topic_hist(const int32_t* z, int64_t N, int32_t* ck, int K, int grid, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(ck, 0, sizeof(int32_t) * K, st);
     if (e != cudaSuccess || N <= 0) return e;
     const int smem = K * 4;
     e = cudaFuncSetAttribute(topic_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    topic_hist_kernel<<<grid_for(N, kThreads * 64, 152 * 2), kThreads, smem, st>>>(z, N, ck, K);
+    topic_hist_kernel<<<grid, kThreads, smem, st>>>(z, N, ck, K);
     return cudaGetLastError();
 }
 
