@@ -87,6 +87,16 @@ def load(mutation: int = 0) -> ctypes.CDLL:
         lib.orc_cgs_sweeps.argtypes = [c.c_int64, c.c_int64, _i64p, _i32p, _i32p, c.c_int,
                                        c.c_float, c.c_float, c.c_uint64, c.c_uint32, c.c_int,
                                        _i32p]
+        _f32p = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+        _f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+        lib.orc_frozen_word_draw.argtypes = [c.c_uint32, c.c_uint32, _i32p, c.c_int, c.c_float]
+        lib.orc_frozen_word_draw.restype = c.c_int
+        lib.orc_foldin.argtypes = [c.c_int64, _i64p, _i32p, _i64p, c.c_int, c.c_int, c.c_float,
+                                   c.c_float, c.c_float, c.c_float, c.c_float, _i32p, _i32p,
+                                   c.c_uint64, c.c_int, _i32p, c.c_void_p]
+        lib.orc_cgs_foldin.argtypes = [c.c_int64, _i64p, _i32p, c.c_int, c.c_float, c.c_float,
+                                       c.c_float, _i32p, _i32p, c.c_uint64, c.c_int, c.c_int,
+                                       _f64p]
         lib.orc_num_threads.restype = c.c_int
         lib.orc_set_num_threads.argtypes = [c.c_int]
         _LIBS[mutation] = lib
@@ -179,3 +189,45 @@ def set_threads(n: int) -> None:
 
 def num_threads() -> int:
     return int(load().orc_num_threads())
+
+
+def word_topic_counts(z_wordmajor, word_ptr, V: int, K: int) -> np.ndarray:
+    """Dense C_w [V, K] (int32) of word-major topics (the frozen model of fold-in)."""
+    z = np.asarray(z_wordmajor, dtype=np.int64)
+    wp = np.asarray(word_ptr, dtype=np.int64)
+    w = np.repeat(np.arange(V, dtype=np.int64), np.diff(wp))
+    cw = np.zeros(V * K, dtype=np.int64)
+    np.add.at(cw, w * K + z[: len(w)], 1)
+    return cw.reshape(V, K).astype(np.int32)
+
+
+def foldin(doc_ptr, doc_word, cw, ck, K: int, M: int, alpha: float, beta: float, V: int,
+           seed: int, sweeps: int, doc_ids=None, theta: bool = True, mutation: int = 0):
+    """Fold-in of new documents against frozen counts (orc_foldin): (z, theta)."""
+    lib = load(mutation)
+    dp = np.ascontiguousarray(doc_ptr, dtype=np.int64)
+    dw = np.ascontiguousarray(doc_word, dtype=np.int32)
+    Dn = len(dp) - 1
+    ids = np.arange(Dn, dtype=np.int64) if doc_ids is None else np.ascontiguousarray(doc_ids, dtype=np.int64)
+    abar, bbar, kbeta = derived(K, V, alpha, beta)
+    z = np.zeros(max(int(dp[-1]), 1), dtype=np.int32)
+    th = np.zeros(max(Dn * K, 1), dtype=np.float32) if theta else None
+    lib.orc_foldin(Dn, dp, dw if len(dw) else np.zeros(1, np.int32), ids, K, M, f32(alpha), abar,
+                   f32(beta), kbeta, bbar, np.ascontiguousarray(cw, dtype=np.int32).ravel(),
+                   np.ascontiguousarray(ck, dtype=np.int32), seed, sweeps, z,
+                   th.ctypes.data if th is not None else None)
+    return z[: int(dp[-1])], (th[: Dn * K].reshape(Dn, K) if th is not None else None)
+
+
+def cgs_foldin_theta(doc_ptr, doc_word, cw, ck, K: int, alpha: float, beta: float, V: int,
+                     seed: int, sweeps: int, burn: int) -> np.ndarray:
+    """Mean theta over sweeps burn+1..sweeps of a plain collapsed Gibbs fold-in."""
+    lib = load()
+    dp = np.ascontiguousarray(doc_ptr, dtype=np.int64)
+    Dn = len(dp) - 1
+    acc = np.zeros(Dn * K, dtype=np.float64)
+    _, bbar, _ = derived(K, V, alpha, beta)
+    lib.orc_cgs_foldin(Dn, dp, np.ascontiguousarray(doc_word, dtype=np.int32), K, f32(alpha),
+                       f32(beta), bbar, np.ascontiguousarray(cw, dtype=np.int32).ravel(),
+                       np.ascontiguousarray(ck, dtype=np.int32), seed, sweeps, burn, acc)
+    return (acc / max(sweeps - burn, 1)).reshape(Dn, K)

@@ -43,6 +43,9 @@
  * step (1..M, 0 at init) and stream is 0 during training.  One block per
  * (token, phase, step): r0 -> accept, r1 -> mixture coin, r2 -> index/topic.
  *
+ * Fold-in of new documents against the frozen model (orc_foldin) carries
+ * its own readings F1-F4 at its definition.
+ *
  * Parity pins (tests/test_oracle_*.py): Philox against Triton's Philox
  * routine; count invariants after each phase; single-token chi-square of the
  * chained MH kernel against the exact Eq. 5 conditional; K = 1 and one-word
@@ -532,6 +535,206 @@ void orc_cgs_sweeps(int64_t D, int64_t V, const int64_t* doc_ptr, const int32_t*
         }
     }
     free(cwk); free(ck); free(cd); free(pk);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fold-in of new documents against a frozen model.                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The paper trains only; fold-in (inference of theta for unseen documents) is
+ * the sampler above with the word side frozen.  Readings:
+ *  F1  the frozen model is the trained word-topic counts C_w (dense [V*K])
+ *      and c_k; the new documents' tokens enter neither;
+ *  F2  a sweep is the document phase (pi^word against the document's own
+ *      phase-start c_d and the frozen c_k, then positioning over the
+ *      post-acceptance z_d) and the word phase (pi^doc against the frozen
+ *      C_w row of the token's word and the frozen c_k, then a word proposal
+ *      from the frozen row: with probability L_w / (L_w + K beta), L_w the
+ *      frozen row's total, the j-th smallest topic of the frozen word, j
+ *      uniform in [0, L_w) (the inverse CDF of the row, R7); else uniform);
+ *  F3  random numbers: counter = (position of the token in its document,
+ *      iteration, phase << 8 | i, document id), key = the fold-in seed,
+ *      phases 3 (init), 4 (document), 5 (word): a document's result depends
+ *      only on its words, its id, the seed and the model -- not on the other
+ *      documents folded in with it;
+ *  F4  output theta_dk = (C_dk + alpha) / (L_d + alpha_bar) from the final z
+ *      (Eq. 4), FP32: one add each, then one IEEE division.
+ */
+enum { ORC_PHASE_FINIT = 3, ORC_PHASE_FDOC = 4, ORC_PHASE_FWORD = 5 };
+
+/* The j-th smallest topic of a frozen word (inverse CDF of its count row,
+ * ascending k), by a plain scan: smallest k with C_0 + ... + C_k > j. */
+static int frozen_rank_topic(const int32_t* row, int K, int64_t j)
+{
+    int64_t cum = 0;
+    for (int k = 0; k < K; ++k) {
+        cum += row[k];
+#if ORC_MUTATION == 10
+        if (cum >= j) return k;                         /* rank off by one */
+#else
+        if (cum > j) return k;
+#endif
+    }
+    return K - 1;
+}
+
+/* Word proposal from a frozen row (F2): r1 -> coin, r2 -> rank or topic. */
+int orc_frozen_word_draw(uint32_t r1, uint32_t r2, const int32_t* row, int K, float K_beta)
+{
+    int64_t Lw = 0;
+    for (int k = 0; k < K; ++k) Lw += row[k];
+    float Lf = (float)Lw;
+    if (Lw > 0 && u24(r1) * (Lf + K_beta) < Lf)
+        return frozen_rank_topic(row, K, (int64_t)dice(r2, (uint32_t)Lw));
+    return (int)dice(r2, (uint32_t)K);
+}
+
+/*
+ * Fold-in of Dn documents (doc CSR doc_ptr[Dn+1], doc_word[Nn]) with ids
+ * doc_id[Dn] against the frozen C_w (cw[V*K]) and c_k (ck[K]), `sweeps`
+ * sweeps.  Writes the final z in document order (z_out[Nn]) and, if theta_out
+ * is not NULL, theta (theta_out[Dn*K], F4).  Word ids must be in [0, V).
+ */
+void orc_foldin(int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
+                const int64_t* doc_id, int K, int M, float alpha, float alpha_bar, float beta,
+                float K_beta, float beta_bar, const int32_t* cw, const int32_t* ck,
+                uint64_t seed, int sweeps, int32_t* z_out, float* theta_out)
+{
+    int64_t maxL = 1;
+    for (int64_t d = 0; d < Dn; ++d)
+        if (doc_ptr[d + 1] - doc_ptr[d] > maxL) maxL = doc_ptr[d + 1] - doc_ptr[d];
+#pragma omp parallel
+    {
+        int32_t* cd = (int32_t*)malloc((size_t)K * sizeof(int32_t));
+        int32_t* znew = (int32_t*)malloc((size_t)maxL * sizeof(int32_t));
+        int32_t* prop = (int32_t*)malloc((size_t)maxL * (size_t)M * sizeof(int32_t));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t d = 0; d < Dn; ++d) {
+            int64_t b = doc_ptr[d];
+            int L = (int)(doc_ptr[d + 1] - b);
+            uint32_t id = (uint32_t)doc_id[d];
+            int32_t* z = z_out + b;
+            uint32_t r[4];
+            for (int j = 0; j < L; ++j) {                       /* init (R4) */
+                draw_block(seed, (uint32_t)j, 0, ORC_PHASE_FINIT, 0, id, r);
+                z[j] = (int32_t)dice(r[0], (uint32_t)K);
+                for (int i = 0; i < M; ++i) prop[j * M + i] = z[j];
+            }
+            for (int it = 1; it <= sweeps; ++it) {
+                /* document phase */
+                for (int k = 0; k < K; ++k) cd[k] = 0;
+                for (int j = 0; j < L; ++j) cd[z[j]] += 1;
+                for (int j = 0; j < L; ++j) {
+                    int s = z[j];
+                    for (int i = 1; i <= M; ++i) {
+                        draw_block(seed, (uint32_t)j, (uint32_t)it, ORC_PHASE_FDOC, (uint32_t)i, id, r);
+                        int tp = prop[j * M + (i - 1)];
+                        s = orc_accept(r[0], s, tp, cd[s], cd[tp], ck[s], ck[tp], alpha, beta_bar);
+                    }
+                    znew[j] = s;
+                }
+                for (int j = 0; j < L; ++j)
+                    for (int i = 1; i <= M; ++i) {
+                        draw_block(seed, (uint32_t)j, (uint32_t)it, ORC_PHASE_FDOC, (uint32_t)i, id, r);
+                        prop[j * M + (i - 1)] = orc_draw_mixture(r[1], r[2], znew, L, K, alpha_bar);
+                    }
+                for (int j = 0; j < L; ++j) z[j] = znew[j];
+                /* word phase (frozen C_w, F2) */
+                for (int j = 0; j < L; ++j) {
+#if ORC_MUTATION == 11
+                    const int32_t* row = cw + (int64_t)doc_word[b + (j + 1) % L] * K;   /* neighbour's word */
+#else
+                    const int32_t* row = cw + (int64_t)doc_word[b + j] * K;
+#endif
+                    int s = z[j];
+                    for (int i = 1; i <= M; ++i) {
+                        draw_block(seed, (uint32_t)j, (uint32_t)it, ORC_PHASE_FWORD, (uint32_t)i, id, r);
+                        int tp = prop[j * M + (i - 1)];
+                        s = orc_accept(r[0], s, tp, row[s], row[tp], ck[s], ck[tp], beta, beta_bar);
+                    }
+                    z[j] = s;
+                    for (int i = 1; i <= M; ++i) {
+                        draw_block(seed, (uint32_t)j, (uint32_t)it, ORC_PHASE_FWORD, (uint32_t)i, id, r);
+                        prop[j * M + (i - 1)] = orc_frozen_word_draw(r[1], r[2], row, K, K_beta);
+                    }
+                }
+            }
+            if (theta_out) {                                    /* F4 */
+                for (int k = 0; k < K; ++k) cd[k] = 0;
+                for (int j = 0; j < L; ++j) cd[z[j]] += 1;
+#if ORC_MUTATION == 12
+                float den = (float)L + alpha;                   /* alpha for alpha_bar */
+#else
+                float den = (float)L + alpha_bar;
+#endif
+                for (int k = 0; k < K; ++k)
+                    theta_out[d * K + k] = ((float)cd[k] + alpha) / den;
+            }
+        }
+        free(cd);
+        free(znew);
+        free(prop);
+    }
+}
+
+/*
+ * Plain collapsed Gibbs fold-in (the yardstick of the fold-in statistics
+ * test): the exact O(K) conditional (C_dk^- + alpha)(C_wk + beta)/(c_k + beta_bar)
+ * with the frozen C_w and c_k and the token's own assignment removed from
+ * c_d; its own Philox stream (phase 6).  Accumulates, over sweeps
+ * burn+1..sweeps, the theta of Eq. 4 into theta_sum[Dn*K] (double).
+ */
+void orc_cgs_foldin(int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word, int K,
+                    float alpha_f, float beta_f, float beta_bar_f, const int32_t* cw,
+                    const int32_t* ck, uint64_t seed, int sweeps, int burn, double* theta_sum)
+{
+    double alpha = alpha_f, beta = beta_f, bbar = beta_bar_f;
+#pragma omp parallel
+    {
+        int32_t* cd = (int32_t*)malloc((size_t)K * sizeof(int32_t));
+        double* pk = (double*)malloc((size_t)K * sizeof(double));
+        int64_t maxL = 1;
+        for (int64_t d = 0; d < Dn; ++d)
+            if (doc_ptr[d + 1] - doc_ptr[d] > maxL) maxL = doc_ptr[d + 1] - doc_ptr[d];
+        int32_t* z = (int32_t*)malloc((size_t)maxL * sizeof(int32_t));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t d = 0; d < Dn; ++d) {
+            int64_t b = doc_ptr[d];
+            int L = (int)(doc_ptr[d + 1] - b);
+            uint32_t r[4];
+            for (int k = 0; k < K; ++k) cd[k] = 0;
+            for (int j = 0; j < L; ++j) {
+                draw_block(seed, (uint32_t)j, 0, 6, 0, (uint32_t)d, r);
+                z[j] = (int32_t)dice(r[0], (uint32_t)K);
+                cd[z[j]] += 1;
+            }
+            for (int s = 1; s <= sweeps; ++s) {
+                for (int j = 0; j < L; ++j) {
+                    const int32_t* row = cw + (int64_t)doc_word[b + j] * K;
+                    cd[z[j]] -= 1;
+                    double tot = 0.0;
+                    for (int k = 0; k < K; ++k) {
+                        tot += (cd[k] + alpha) * (row[k] + beta) / (ck[k] + bbar);
+                        pk[k] = tot;
+                    }
+                    draw_block(seed, (uint32_t)j, (uint32_t)s, 6, 1, (uint32_t)d, r);
+                    double u = ((double)(r[0] >> 5) * 67108864.0 + (double)(r[1] >> 6))
+                               * (1.0 / 9007199254740992.0) * tot;
+                    int k1 = 0;
+                    while (k1 < K - 1 && pk[k1] <= u) ++k1;
+                    z[j] = k1;
+                    cd[k1] += 1;
+                }
+                if (s > burn)
+                    for (int k = 0; k < K; ++k)
+                        theta_sum[d * K + k] += (cd[k] + alpha) / (L + K * alpha);
+            }
+        }
+        free(cd);
+        free(pk);
+        free(z);
+    }
 }
 
 /* Threads the parallel phases will use. */

@@ -13,6 +13,9 @@ least one of the distribution pins (test_oracle_law.py) or the Philox pin
   7  the document count c_d leaves out the document's last token
   8  every MH step starts from the phase-start z instead of the current state
   9  Philox with 9 rounds instead of 10
+ 10  fold-in: the frozen word's j-th smallest topic off by one rank
+ 11  fold-in: pi^doc and the word proposal read a neighbouring token's word row
+ 12  fold-in: theta normalised by L_d + alpha instead of L_d + alpha_bar
 """
 import numpy as np
 import pytest
@@ -61,3 +64,16 @@ def test_philox_pin_catches_round_count():
 
 def test_unmutated_oracle_passes_same_pins():
     assert not any(_fails(c) for c in _law_pins(0))
+
+
+def _foldin_pins(m):
+    from tests import test_oracle_foldin as fo
+    return [lambda: fo.check_frozen_word_law(mutation=m),
+            lambda: fo.check_theta_rows_normalised(mutation=m),
+            lambda: fo.check_separable_words(mutation=m),
+            lambda: fo.check_against_cgs(mutation=m)]
+
+
+@pytest.mark.parametrize("m", [10, 11, 12])
+def test_foldin_pins_catch_mutation(m):
+    assert any(_fails(c) for c in _foldin_pins(m)), f"mutation {m} not caught"
