@@ -183,6 +183,40 @@ int warplda_kernel_times(warplda_ctx* ctx, int32_t cap, const char** names, int6
                          double* total_ms);
 
 /*
+ * warplda_foldin -- theta (Eq. 4) of Dn new documents, sampled against the
+ * model frozen at the call: the word-topic counts C_w and the topic counts
+ * c_k of the context's current state (the paper trains only; fold-in is its
+ * sampler with the word side frozen).  Each of `sweeps` sweeps is the
+ * document phase of Sec. 4.4 (pi^word of Eq. 7 against the document's own
+ * phase-start counts and the frozen c_k, then positioning over the
+ * post-acceptance assignments) and the word phase with frozen counts (pi^doc
+ * against the frozen C_w row of each token's word; word proposals of Eq. 6
+ * drawn from that frozen row).  The new documents enter neither C_w nor c_k.
+ * Random numbers are keyed by `seed`, the document id and the token's
+ * position in its document, so a document's result does not depend on which
+ * other documents are folded in with it.
+ *   Dn, doc_ptr[Dn+1] (int64, host), doc_word[doc_ptr[Dn]] (int32, host):
+ *               the documents as a CSR; word ids in [0, V).
+ *   doc_ids     host int64[Dn] stream ids of the documents, or NULL for
+ *               0..Dn-1.
+ *   sweeps      fold-in sweeps (>= 0).
+ *   proposal    WARPLDA_PROPOSAL_PLAIN (the only one this library has).
+ *   theta_out   host float[Dn*K], theta_dk = (C_dk + alpha)/(L_d + K alpha)
+ *               of the final assignments; or NULL.
+ *   z_out       host int32[doc_ptr[Dn]], final topics in document order; or
+ *               NULL.
+ * The frozen model (V*(K+1) int32 of device memory, held by the context
+ * until warplda_destroy) is rebuilt when the context has swept since the
+ * last fold-in.  Documents may have at most 65535 tokens when K <= 2048,
+ * 4095 above.  Synchronous.  Errors: EINVAL (CSR, word id, length, proposal),
+ * ESTATE (a word phase is pending), ENOMEM, ECUDA.
+ */
+#define WARPLDA_PROPOSAL_PLAIN 0
+int warplda_foldin(warplda_ctx* ctx, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
+                   const int64_t* doc_ids, int32_t sweeps, uint64_t seed, int32_t proposal,
+                   float* theta_out, int32_t* z_out);
+
+/*
  * warplda_sync -- wait for the work queued on the context's stream and report
  * the kernels' index checks.  Every sampler kernel validates the indices it
  * takes from stored state (topics, proposals, token pointers, work lists)

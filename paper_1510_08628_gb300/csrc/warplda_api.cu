@@ -111,6 +111,11 @@ struct warplda_ctx {
     std::vector<int64_t> word_ptr_h;
     int grid_batch[2][2] = {{1, 1}, {1, 1}};   // [doc 0 / word 1][class]
     int grid_hist = 1, grid_acc_doc = 1, grid_acc_word = 1, grid_draw = 1, grid_topic = 1;
+    // frozen model of fold-in: per-word exclusive prefix of C_w ([V, K+1])
+    // and (float)c_k + beta_bar, taken after sweep model_iter
+    int32_t* model_P = nullptr;
+    float* model_ckb = nullptr;
+    int64_t model_iter = -1;
     bool prof = false;
     std::vector<Rec> recs;
     int64_t device_bytes = 0;
@@ -273,8 +278,9 @@ int check_record(warplda_ctx* c, const char* where) {
     if (f[0] == 0) return WARPLDA_OK;
     WL_CU(cudaMemsetAsync(c->d_fault, 0, sizeof(f), c->st), "clear check record");
     static const char* kSites[] = {"?", "doc batch", "word batch", "multi-pass hist",
-                                   "multi-pass accept", "multi-pass draw", "doc warp", "loglik"};
-    const char* site = (f[0] >= 1 && f[0] <= 7) ? kSites[f[0]] : "?";
+                                   "multi-pass accept", "multi-pass draw", "doc warp", "loglik",
+                                   "fold-in"};
+    const char* site = (f[0] >= 1 && f[0] <= 8) ? kSites[f[0]] : "?";
     return fail(WARPLDA_ECUDA, "index check failed (reported at %s): first in the %s kernel, checks 0x%x",
                 where, site, (unsigned)f[2]);
 }
@@ -446,6 +452,20 @@ int recount(warplda_ctx* c) {
 }  // namespace
 
 int wl::record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+// Device buffers of one fold-in call, freed on every return path.
+struct FoldBuffers {
+    std::vector<void*> p;
+    template <typename T>
+    cudaError_t get(T** out, int64_t n) {
+        cudaError_t e = cudaMalloc((void**)out, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
+        if (e == cudaSuccess) p.push_back(*out);
+        return e;
+    }
+    ~FoldBuffers() {
+        for (void* q : p) cudaFree(q);
+    }
+};
 
 extern "C" {
 
@@ -898,6 +918,114 @@ int warplda_kernel_times(warplda_ctx* c, int32_t cap, const char** names, int64_
         ++k;
     }
     return k;
+}
+
+int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
+                   const int64_t* doc_ids, int32_t sweeps, uint64_t seed, int32_t proposal,
+                   float* theta_out, int32_t* z_out) {
+    if (!c || !doc_ptr || Dn < 0 || sweeps < 0) return fail(WARPLDA_EINVAL, "bad fold-in arguments");
+    if (proposal != WARPLDA_PROPOSAL_PLAIN)
+        return fail(WARPLDA_EINVAL, "proposal %d is not available in this library", proposal);
+    if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
+    if (Dn > (int64_t)0x7FFFFFF0) return fail(WARPLDA_EINVAL, "too many documents");
+    if (doc_ptr[0] != 0) return fail(WARPLDA_EINVAL, "doc_ptr[0] must be 0");
+    const int K = c->K, M = c->M;
+    const int Lcap = K <= kDenseMaxK ? 65535 : (1 << kHashCountBits) - 1;
+    int64_t Lmax = 0;
+    for (int64_t d = 0; d < Dn; ++d) {
+        const int64_t L = doc_ptr[d + 1] - doc_ptr[d];
+        if (L < 0) return fail(WARPLDA_EINVAL, "doc_ptr decreases at %lld", (long long)d);
+        Lmax = std::max(Lmax, L);
+    }
+    if (Lmax > Lcap) return fail(WARPLDA_EINVAL, "a fold-in document has more than %d tokens", Lcap);
+    const int64_t Nn = doc_ptr[Dn];
+    if (Nn > (int64_t)0x7FFFFFF0) return fail(WARPLDA_EINVAL, "too many fold-in tokens");
+    if (Nn > 0 && !doc_word) return fail(WARPLDA_EINVAL, "null doc_word");
+    for (int64_t p = 0; p < Nn; ++p)
+        if (doc_word[p] < 0 || (int64_t)doc_word[p] >= c->V)
+            return fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", doc_word[p], (long long)p);
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+
+    // the frozen model: C_w prefix rows and c_k of the current state
+    if (c->model_iter != (int64_t)c->iter) {
+        int rc;
+        if (!c->model_P && (rc = dalloc(c, &c->model_P, c->V * (int64_t)(K + 1), "alloc fold-in model")))
+            return rc;
+        if (!c->model_ckb && (rc = dalloc(c, &c->model_ckb, K, "alloc fold-in c_k"))) return rc;
+        WL_CU(launch_model_build(c->z, c->word_off, c->V, K, c->model_P, c->d_fault,
+                                 4 * c->sms, c->st), "build fold-in model");
+        WL_CU(cudaMemcpyAsync(c->model_ckb, c->ckb, (size_t)K * sizeof(float), cudaMemcpyDeviceToDevice,
+                              c->st), "copy c_k");
+        c->model_iter = c->iter;
+    }
+
+    // documents longest first, so that the long ones start early
+    std::vector<int32_t> order((size_t)Dn), off((size_t)Dn + 1);
+    std::vector<int64_t> ids((size_t)Dn);
+    for (int64_t d = 0; d < Dn; ++d) {
+        order[d] = (int32_t)d;
+        ids[d] = doc_ids ? doc_ids[d] : d;
+    }
+    for (int64_t d = 0; d <= Dn; ++d) off[d] = (int32_t)doc_ptr[d];
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return off[a + 1] - off[a] > off[b + 1] - off[b];
+    });
+
+    FoldBuffers buf;
+    FoldArgs f{};
+    int32_t *d_z, *d_prop, *d_words, *d_off, *d_order, *d_counter;
+    int64_t* d_ids;
+    float* d_theta = nullptr;
+    WL_CU(buf.get(&d_z, Nn + 1), "alloc fold-in z");
+    WL_CU(buf.get(&d_prop, (Nn + 1) * M), "alloc fold-in proposals");
+    WL_CU(buf.get(&d_words, Nn + 1), "alloc fold-in words");
+    WL_CU(buf.get(&d_off, Dn + 1), "alloc fold-in offsets");
+    WL_CU(buf.get(&d_order, Dn + 1), "alloc fold-in order");
+    WL_CU(buf.get(&d_ids, Dn + 1), "alloc fold-in ids");
+    WL_CU(buf.get(&d_counter, 1), "alloc fold-in counter");
+    if (theta_out) WL_CU(buf.get(&d_theta, Dn * (int64_t)K + 1), "alloc fold-in theta");
+    if (Nn > 0)
+        WL_CU(cudaMemcpyAsync(d_words, doc_word, (size_t)Nn * 4, cudaMemcpyHostToDevice, c->st), "upload words");
+    WL_CU(cudaMemcpyAsync(d_off, off.data(), (size_t)(Dn + 1) * 4, cudaMemcpyHostToDevice, c->st), "upload offsets");
+    if (Dn > 0) {
+        WL_CU(cudaMemcpyAsync(d_order, order.data(), (size_t)Dn * 4, cudaMemcpyHostToDevice, c->st), "upload order");
+        WL_CU(cudaMemcpyAsync(d_ids, ids.data(), (size_t)Dn * 8, cudaMemcpyHostToDevice, c->st), "upload ids");
+    }
+    WL_CU(cudaMemsetAsync(d_counter, 0, 4, c->st), "reset counter");
+    f.z = d_z;
+    f.prop = d_prop;
+    f.words = d_words;
+    f.doc_off = d_off;
+    f.order = d_order;
+    f.ids = d_ids;
+    f.P = c->model_P;
+    f.ckb = c->model_ckb;
+    f.theta = d_theta;
+    f.counter = d_counter;
+    f.fault = c->d_fault;
+    f.Dn = (int)Dn;
+    f.K = K;
+    f.M = M;
+    f.V = (int)c->V;
+    f.sweeps = sweeps;
+    f.Lmax = (int)Lmax;
+    f.alpha = c->alpha;
+    f.abar = c->abar;
+    f.beta = c->beta;
+    f.kbeta = c->kbeta;
+    f.rk = round_keys(seed);
+    const int tab_words = foldin_table_words(K, (int)Lmax);
+    const int per_sm = foldin_blocks_per_sm(K, M, tab_words);
+    if (per_sm < 1) return fail(WARPLDA_EINVAL, "fold-in tables do not fit in shared memory");
+    const int warps = foldin_warps(tab_words);
+    const int grid = (int)std::min<int64_t>((int64_t)per_sm * c->sms, (Dn + warps - 1) / warps + 1);
+    WL_CU(launch_foldin(f, tab_words, grid, c->st), "fold-in");
+    if (z_out && Nn > 0)
+        WL_CU(cudaMemcpyAsync(z_out, d_z, (size_t)Nn * 4, cudaMemcpyDeviceToHost, c->st), "copy z");
+    if (theta_out && Dn > 0)
+        WL_CU(cudaMemcpyAsync(theta_out, d_theta, (size_t)Dn * K * 4, cudaMemcpyDeviceToHost, c->st), "copy theta");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    return check_record(c, "fold-in");
 }
 
 int warplda_sync(warplda_ctx* c) {

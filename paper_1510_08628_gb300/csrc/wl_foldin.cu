@@ -1,0 +1,274 @@
+// Fold-in of new documents against a frozen model: the document phase and
+// word phase of Sec. 4.4 with the word side frozen (the paper trains only;
+// the readings are those of the oracle's fold-in):
+//   model   : P_w[k] = C_w0 + ... + C_w,k-1 for every word (a dense
+//             [V, K+1] prefix table built from the trained z), frozen c_k;
+//   document: pi^word (Eq. 7) against the document's phase-start c_d and the
+//             frozen c_k, then positioning over the post-acceptance z_d
+//             (Sec. 4.3);
+//   word    : pi^doc against the frozen C_w row of the token's word
+//             (C_wk = P_w[k+1] - P_w[k]) and the frozen c_k, then a word
+//             proposal from the frozen row (Eq. 6): with probability
+//             L_w / (L_w + K beta) the j-th smallest topic of the word (the
+//             largest k with P_w[k] <= j), else uniform.
+// Random numbers: Philox keyed by the fold-in seed, counter = (position in
+// the document, iteration, phase << 8 | i, document id), phases 3/4/5, so a
+// document's result does not depend on the other documents of the call.
+// One warp per document, all sweeps in one launch: the document's count
+// table lives in the warp's slice of shared memory, its z and proposals in
+// global memory (document order, coalesced), the frozen rows in L2.
+#include "wl_block.cuh"
+#include "wl_kernels.h"
+
+namespace wl {
+
+enum : uint32_t { kPhaseFoldInit = 3, kPhaseFoldDoc = 4, kPhaseFoldWord = 5 };
+
+// ---------------------------------------------------------------------------
+// Frozen model: per-word topic counts of the trained state, then per-row
+// exclusive prefix (row of K+1 ints, last = L_w).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) model_counts_kernel(const int32_t* __restrict__ z,
+                                                                const int32_t* __restrict__ word_off,
+                                                                int64_t V, int K, int32_t* __restrict__ P,
+                                                                int32_t* fault) {
+    Checks chk;
+    for (int64_t w = blockIdx.x; w < V; w += gridDim.x) {
+        int32_t* row = P + w * (int64_t)(K + 1);
+        for (int t = word_off[w] + threadIdx.x; t < word_off[w + 1]; t += kThreads)
+            atomicAdd(&row[1 + chk.topic(z[t], K, 0)], 1);
+    }
+    chk.publish(fault, kSiteFoldin);
+}
+
+__global__ void __launch_bounds__(kThreads) model_scan_kernel(int64_t V, int K, int32_t* __restrict__ P) {
+    __shared__ int warp_tot[kWarps];
+    __shared__ int s_total;
+    const int n = K + 1;
+    const int per = (n + kThreads - 1) / kThreads;
+    for (int64_t w = blockIdx.x; w < V; w += gridDim.x) {
+        int32_t* row = P + w * (int64_t)n;
+        const int k0 = min(n, (int)threadIdx.x * per), k1 = min(n, k0 + per);
+        int sum = 0;
+        for (int k = k0; k < k1; ++k) sum += row[k];
+        int run = block_excl_scan(sum, warp_tot, &s_total);
+        // row[0] is 0 and row[k+1] holds C_wk: the inclusive prefix of the
+        // shifted counts is the exclusive prefix of the counts
+        for (int k = k0; k < k1; ++k) {
+            run += row[k];
+            row[k] = run;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_model_build(const int32_t* z, const int32_t* word_off, int64_t V, int K,
+                               int32_t* P, int32_t* fault, int grid, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(P, 0, (size_t)V * (K + 1) * sizeof(int32_t), st);
+    if (e != cudaSuccess || V <= 0) return e;
+    model_counts_kernel<<<grid, kThreads, 0, st>>>(z, word_off, V, K, P, fault);
+    model_scan_kernel<<<grid, kThreads, 0, st>>>(V, K, P);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The fold-in kernel.
+// ---------------------------------------------------------------------------
+int foldin_table_words(int K, int Lmax) {
+    if (K <= kDenseMaxK) return ((K + 1) / 2 + 3) & ~3;
+    return (int)pow2_above((uint32_t)min(2 * max(Lmax, 1), K));
+}
+
+__device__ __forceinline__ int fold_count(const uint32_t* tab, uint32_t cap, bool dense, int k) {
+    return dense ? (int)((tab[(uint32_t)k >> 1] >> (((uint32_t)k & 1) * 16)) & 0xFFFFu)
+                 : table_get(tab, cap, (uint32_t)k);
+}
+
+// The largest k < K with P[k] <= j (the topic of rank j of a frozen row).
+__device__ __forceinline__ int rank_topic(const int32_t* __restrict__ P, int K, int j) {
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(P + mid) <= j) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int M, bool kDense>
+__global__ void __launch_bounds__(kThreads) foldin_kernel(FoldArgs f, int tab_words) {
+    extern __shared__ __align__(16) uint32_t fsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* tab = fsm + warp * tab_words;
+    const int K = f.K;
+    const uint32_t km = (uint32_t)K - 1u;
+    Checks chk;
+    for (;;) {
+        int di = 0;
+        if (lane == 0) di = atomicAdd(f.counter, 1);
+        di = __shfl_sync(0xFFFFFFFFu, di, 0);
+        if (di >= f.Dn) break;
+        int d = f.order[di];
+        if (!chk(d >= 0 && d < f.Dn, 0)) d = 0;
+        const int b = f.doc_off[d];
+        int L = f.doc_off[d + 1] - b;
+        if (!chk(L >= 0 && L <= f.Lmax, 0)) L = 0;
+        const uint32_t id = (uint32_t)f.ids[d];
+        const uint32_t cap = kDense ? 0u : pow2_above((uint32_t)min(2 * max(L, 1), K));
+        const int words = kDense ? tab_words : (int)cap;
+        int32_t* z = f.z + b;
+        int32_t* prop = f.prop + (int64_t)b * M;
+        const int32_t* wd = f.words + b;
+        auto build_table = [&]() {
+            for (int i = lane; i < words; i += 32) tab[i] = 0u;
+            __syncwarp();
+            for (int j = lane; j < L; j += 32) {
+                const uint32_t k = min((uint32_t)z[j], km);
+                if (kDense) atomicAdd(&tab[k >> 1], (k & 1) ? 65536u : 1u);
+                else table_add(tab, cap, k);
+            }
+            __syncwarp();
+        };
+        // initialisation: z = Dice(K), proposals = z
+        for (int j = lane; j < L; j += 32) {
+            const uint4 r = draw((uint32_t)j, 0u, kPhaseFoldInit, 0u, id, f.rk);
+            const int z0 = (int)dice(r.x, (uint32_t)K);
+            z[j] = z0;
+#pragma unroll
+            for (int i = 0; i < M; ++i) prop[j * M + i] = z0;
+        }
+        __syncwarp();
+        const float Lf = __int2float_rn(L);
+        const float LG = __fadd_rn(Lf, f.abar);
+        for (int it = 1; it <= f.sweeps; ++it) {
+            // document phase: accept with the phase-start c_d ...
+            build_table();
+            for (int j = lane; j < L; j += 32) {
+                int s = min((uint32_t)z[j], km);
+                int cs = fold_count(tab, cap, kDense, s);
+                float ks = __ldg(f.ckb + s);
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldDoc, (uint32_t)(i + 1), id, f.rk);
+                    const int t = (int)min((uint32_t)prop[j * M + i], km);
+                    if (t != s) {
+                        const int ct = fold_count(tab, cap, kDense, t);
+                        const float kt = __ldg(f.ckb + t);
+                        if (accept(r.x, cs, ct, f.alpha, ks, kt)) {
+                            s = t;
+                            cs = ct;
+                            ks = kt;
+                        }
+                    }
+                }
+                z[j] = s;
+            }
+            __syncwarp();
+            // ... then positioning over the post-acceptance z_d
+            for (int j = lane; j < L; j += 32) {
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldDoc, (uint32_t)(i + 1), id, f.rk);
+                    prop[j * M + i] = coin(r.y, Lf, LG) ? z[dice(r.z, (uint32_t)L)] : (int)dice(r.z, (uint32_t)K);
+                }
+            }
+            __syncwarp();
+            // word phase against the frozen rows: accept, then a proposal
+            // from the token's frozen row (one Philox block per step)
+            for (int j = lane; j < L; j += 32) {
+                int w = wd[j];
+                if (!chk((uint32_t)w < (uint32_t)f.V, 1)) w = 0;
+                const int32_t* P = f.P + (int64_t)w * (K + 1);
+                const int Lw = __ldg(P + K);
+                const float Lwf = __int2float_rn(Lw);
+                const float LwG = __fadd_rn(Lwf, f.kbeta);
+                int s = min((uint32_t)z[j], km);
+                int cs = __ldg(P + s + 1) - __ldg(P + s);
+                float ks = __ldg(f.ckb + s);
+                uint32_t r1[M], r2[M];
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldWord, (uint32_t)(i + 1), id, f.rk);
+                    r1[i] = r.y;
+                    r2[i] = r.z;
+                    const int t = (int)min((uint32_t)prop[j * M + i], km);
+                    if (t != s) {
+                        const int ct = __ldg(P + t + 1) - __ldg(P + t);
+                        const float kt = __ldg(f.ckb + t);
+                        if (accept(r.x, cs, ct, f.beta, ks, kt)) {
+                            s = t;
+                            cs = ct;
+                            ks = kt;
+                        }
+                    }
+                }
+                z[j] = s;
+#pragma unroll
+                for (int i = 0; i < M; ++i)
+                    prop[j * M + i] = (Lw > 0 && coin(r1[i], Lwf, LwG))
+                                          ? rank_topic(P, K, (int)dice(r2[i], (uint32_t)Lw))
+                                          : (int)dice(r2[i], (uint32_t)K);
+            }
+            __syncwarp();
+        }
+        // theta (Eq. 4) of the final z
+        build_table();
+        if (f.theta) {
+            const float den = __fadd_rn(Lf, f.abar);
+            float* th = f.theta + (int64_t)d * K;
+            for (int k = lane; k < K; k += 32)
+                th[k] = __fdiv_rn(__fadd_rn(__int2float_rn(fold_count(tab, cap, kDense, k)), f.alpha), den);
+        }
+        __syncwarp();
+    }
+    chk.publish(f.fault, kSiteFoldin);
+}
+
+template <int M, bool kDense>
+static const void* fold_ptr() {
+    return (const void*)foldin_kernel<M, kDense>;
+}
+
+static const void* fold_pick(int M, bool dense) {
+    switch (M) {
+        case 1: return dense ? fold_ptr<1, true>() : fold_ptr<1, false>();
+        case 2: return dense ? fold_ptr<2, true>() : fold_ptr<2, false>();
+        case 3: return dense ? fold_ptr<3, true>() : fold_ptr<3, false>();
+        case 4: return dense ? fold_ptr<4, true>() : fold_ptr<4, false>();
+        default: return nullptr;
+    }
+}
+
+// Warps per block: as many as 8 whose count tables fit in 192 KB.
+int foldin_warps(int tab_words) {
+    const int w = (192 * 1024) / (tab_words * 4);
+    return w < 1 ? 0 : (w > kWarps ? kWarps : w);
+}
+
+cudaError_t launch_foldin(const FoldArgs& f, int tab_words, int grid, cudaStream_t st) {
+    if (f.Dn <= 0) return cudaSuccess;
+    const bool dense = f.K <= kDenseMaxK;
+    const void* fn = fold_pick(f.M, dense);
+    const int warps = foldin_warps(tab_words);
+    if (!fn || warps < 1) return cudaErrorInvalidValue;
+    const int smem = warps * tab_words * 4;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    FoldArgs args = f;
+    int tw = tab_words;
+    void* params[] = {&args, &tw};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(32 * warps), params, (size_t)smem, st);
+}
+
+int foldin_blocks_per_sm(int K, int M, int tab_words) {
+    const void* fn = fold_pick(M, K <= kDenseMaxK);
+    const int warps = foldin_warps(tab_words);
+    if (!fn || warps < 1) return 0;
+    const int smem = warps * tab_words * 4;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * warps, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+}  // namespace wl

@@ -39,6 +39,15 @@ cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const HugeWork& w,
 cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const HugeWork& w,
                              const int32_t* rows_post, int grid, cudaStream_t st);
 
+// Fold-in against a frozen model (wl_foldin.cu): P = [V, K+1] per-word
+// exclusive prefix of the trained C_w.
+cudaError_t launch_model_build(const int32_t* z, const int32_t* word_off, int64_t V, int K,
+                               int32_t* P, int32_t* fault, int grid, cudaStream_t st);
+int foldin_table_words(int K, int Lmax);
+int foldin_warps(int tab_words);
+int foldin_blocks_per_sm(int K, int M, int tab_words);
+cudaError_t launch_foldin(const FoldArgs& f, int tab_words, int grid, cudaStream_t st);
+
 // Initialisation, c_k, export, log-likelihood (wl_misc.cu).
 cudaError_t launch_init_z(int32_t* z, int32_t* prop, int64_t N, int K, int M, uint64_t seed,
                           cudaStream_t st);

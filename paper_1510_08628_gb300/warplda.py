@@ -69,6 +69,8 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double)]),
     "warplda_sync": (ctypes.c_int, [_P]),
+    "warplda_foldin": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int32,
+                                      ctypes.c_uint64, ctypes.c_int32, _P, _P]),
     "warplda_destroy": (None, [_P]),
     "warplda_loglik_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                               ctypes.c_int32, ctypes.c_float, ctypes.c_float,
@@ -200,6 +202,20 @@ class WarpLDA:
 
     def load_state(self, path: str) -> None:
         _check(load().warplda_load(self._h, path.encode()))
+
+    def foldin(self, doc_ptr, doc_word, sweeps: int, seed: int, doc_ids=None,
+               theta: bool = True, z: bool = True):
+        """Fold in new documents against the current model: (theta[Dn, K], z[Nn])."""
+        dp = np.ascontiguousarray(doc_ptr, dtype=np.int64)
+        dw = np.ascontiguousarray(doc_word, dtype=np.int32)
+        Dn, Nn = len(dp) - 1, int(dp[-1])
+        ids = None if doc_ids is None else np.ascontiguousarray(doc_ids, dtype=np.int64)
+        th = np.empty((Dn, self.K), dtype=np.float32) if theta else None
+        zo = np.empty(Nn, dtype=np.int32) if z else None
+        ptr = lambda a: a.ctypes.data if a is not None and a.size else None
+        _check(load().warplda_foldin(self._h, Dn, ptr(dp), ptr(dw), ptr(ids), int(sweeps),
+                                     int(seed), 0, ptr(th), ptr(zo)))
+        return th, zo
 
     def sync(self) -> None:
         """Wait for queued work; raise if a kernel's index check failed."""
