@@ -63,18 +63,29 @@ def measured_peaks() -> tuple[float, str]:
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def csrc_fingerprint() -> str:
+# the sources each kernel class is compiled from (its traffic record stays
+# valid while these files are unchanged)
+KERNEL_SOURCES = {
+    "doc_batch": ["wl_batch.cu", "wl_common.cuh", "wl_block.cuh"],
+    "word_batch": ["wl_batch.cu", "wl_common.cuh", "wl_block.cuh"],
+    "word_mega_accept": ["wl_huge.cu", "wl_common.cuh", "wl_block.cuh"],
+    "word_mega_draw": ["wl_huge.cu", "wl_common.cuh", "wl_block.cuh"],
+    "word_mega_hist": ["wl_huge.cu", "wl_common.cuh", "wl_block.cuh"],
+}
+
+
+def kernel_fingerprint(kernel: str) -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1510_08628_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES.get(kernel, sorted(os.listdir(d))):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from a committed ncu capture of the current
-    kernel sources, or None."""
+    """DRAM bytes per launch from a committed ncu capture of the kernel's
+    current sources, or None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
@@ -82,7 +93,7 @@ def recorded_traffic(kernel: str, workload: str):
     except Exception:
         return None
     e = rec.get(workload, {}).get(kernel)
-    if not e or e.get("csrc") != csrc_fingerprint():
+    if not e or e.get("sources") != kernel_fingerprint(kernel):
         return None
     return e.get("bytes_per_launch")
 
@@ -178,7 +189,51 @@ def oracle_rate(c, wl, seed: int, sweeps: int, warm: int = 0):
 
 
 def sample_docs(name: str) -> int | None:
-    return {"nytimes": 60_000, "pubmed": 600_000, "tiny": None}.get(name)
+    return {"nytimes": 300_000, "pubmed": 600_000, "tiny": None}.get(name)
+
+
+def foldin_bench(gpu, c, wl, args, torch, stream):
+    """Fold-in of unseen documents of the workload's generator (lengths
+    clipped to [20, 5000]) against the trained model: docs/s end to end
+    through warplda_foldin (host CSR in, theta out), and the CPU oracle on a
+    sample of the same requests."""
+    from paper_1510_08628_gb300 import corpus
+    rq = corpus.requests(args.workload, seed=args.corpus_seed, n=args.foldin_docs,
+                         doc_offset=c.D + 1000)
+    S = args.foldin_sweeps
+    small = int(rq.doc_ptr[min(64, rq.D)])
+    gpu.foldin(rq.doc_ptr[: min(64, rq.D) + 1], rq.doc_word[:small], sweeps=2, seed=1)  # model build
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    start.record(stream)
+    th, _ = gpu.foldin(rq.doc_ptr, rq.doc_word, sweeps=S, seed=args.seed + 17, z=False)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    dev_s = start.elapsed_time(stop) / 1000.0
+    out = {"docs": rq.D, "tokens": rq.N, "sweeps": S, "K": wl.K, "M": wl.M,
+           "docs_per_s": rq.D / wall, "tokens_sweeps_per_s": rq.N * S / wall, "seconds": wall,
+           "device_seconds": dev_s, "includes": "host checks + H2D of the CSR + fold-in kernel + "
+                                                 "D2H of theta (synchronous C ABI call)",
+           "proposal": "plain", "lengths": "lognormal of the workload, clipped to [20, 5000]"}
+    if not args.no_cpu_baseline:
+        import oracle
+        n = min(400, rq.D)
+        e = int(rq.doc_ptr[n])
+        z, ck = gpu.counts()
+        wp, perm = gpu.token_order()
+        zw = np.empty_like(z)
+        zw[perm] = z
+        cw = oracle.word_topic_counts(zw, wp, c.V, wl.K)
+        t = time.perf_counter()
+        oracle.foldin(rq.doc_ptr[: n + 1], rq.doc_word[:e], cw, ck, wl.K, wl.M, wl.alpha, wl.beta,
+                      c.V, seed=args.seed + 17, sweeps=S)
+        dt = time.perf_counter() - t
+        out["cpu_baseline"] = {"docs_per_s": n / dt, "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": f"first {n} requests ({e} tokens), "
+                                                           f"{S} sweeps ({dt:.1f} s)"}
+    return out
 
 
 def run_reference(args, ws, rank):
@@ -224,6 +279,9 @@ def main():
     ap.add_argument("--corpus-seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--foldin-docs", type=int, default=20000,
+                    help="fold-in requests timed after the sweeps (0: none)")
+    ap.add_argument("--foldin-sweeps", type=int, default=30)
     ap.add_argument("--docs", type=int, default=0,
                     help="use only the first DOCS documents of the workload (small profiling cases)")
     args = ap.parse_args()
@@ -259,9 +317,9 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         nd = sample_docs(args.workload)
         cs, wls = corpus.generate(args.workload, seed=args.corpus_seed, D=nd)
-        rate, cores, dt = oracle_rate(cs, wls, args.seed, sweeps=2)
+        rate, cores, dt = oracle_rate(cs, wls, args.seed, sweeps=4)
         cpu_base = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                    "sample": f"2 full sweeps of the first {cs.D} documents ({cs.N} tokens) of "
+                    "sample": f"4 full sweeps of the first {cs.D} documents ({cs.N} tokens) of "
                               f"the {args.workload} corpus ({dt:.1f} s)"}
         del cs
 
@@ -301,10 +359,13 @@ def main():
         "word_mega_draw": info["mega_word_tokens"], "doc_huge_hist": info["huge_doc_tokens"],
         "doc_huge_accept": info["huge_doc_tokens"], "doc_huge_draw": info["huge_doc_tokens"],
     }
+    # a kernel class may launch more than once per sweep (the block batches
+    # of two sizes): its algorithmic bytes per sweep are spread over them
     kernels = {}
     for k, (n, tot) in kt.items():
         avg = tot / n
-        alg = alg_bytes_per_token(k, wl.M) * tier_tokens.get(k, 0)
+        per_sweep = n / args.steps
+        alg = alg_bytes_per_token(k, wl.M) * tier_tokens.get(k, 0) / per_sweep
         kernels[k] = {"launches": n, "avg_ms": avg, "share": None,
                       "alg_bytes": alg, "gbs": (alg / (avg / 1000) / 1e9) if alg else None}
     total_k = sum(v["avg_ms"] * v["launches"] for v in kernels.values())
@@ -319,6 +380,10 @@ def main():
             "frac": d["gbs"] / peak, "peak_source": f"{peak_kind} hbm_gbs",
             "traffic": recorded_traffic(dom, args.workload),
             "alg_bytes_per_launch": d["alg_bytes"]}
+
+    foldin = None
+    if args.foldin_docs > 0 and rank == 0:
+        foldin = foldin_bench(gpu, c, wl, args, torch, stream)
 
     # end to end through the C ABI from pinned host buffers: init (H2D of the
     # corpus, token-order build) + K sweeps + D2H of z and c_k
@@ -358,6 +423,7 @@ def main():
             "cpu_baseline": cpu_base,
             "e2e": e2e,
             "gpu_launches": info["launches_per_sweep"] * args.steps,
+            "foldin": foldin,
             "clocks": clk.summary(),
             "paper_context": {"value": 110e6, "unit": UNIT,
                               "hardware": "2x Xeon E5-2692v2 (24 cores), NYTimes/PubMed, M=2"},

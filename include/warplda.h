@@ -205,9 +205,9 @@ int warplda_kernel_times(warplda_ctx* ctx, int32_t cap, const char** names, int6
  *               of the final assignments; or NULL.
  *   z_out       host int32[doc_ptr[Dn]], final topics in document order; or
  *               NULL.
- * The frozen model (V*(K+1) int32 of device memory, held by the context
- * until warplda_destroy) is rebuilt when the context has swept since the
- * last fold-in.  Documents may have at most 65535 tokens when K <= 2048,
+ * The frozen model (C_w as V*K int32 and each word's topics in ascending
+ * order, N int32, held by the context until warplda_destroy) is rebuilt when
+ * the context has swept since the last fold-in.  Documents may have at most 65535 tokens when K <= 2048,
  * 4095 above.  Synchronous.  Errors: EINVAL (CSR, word id, length, proposal),
  * ESTATE (a word phase is pending), ENOMEM, ECUDA.
  */

@@ -170,3 +170,13 @@ def from_lengths(lens, V: int, seed: int, K_true: int = 8, zipf_s: float = 1.0,
     """Small corpus with given document lengths (edge-case tests)."""
     model = TopicModel(V, K_true, zipf_s, 0.01, seed)
     return generate_docs(model, np.asarray(lens, dtype=np.int64), doc_alpha, seed)
+
+
+def requests(name: str, seed: int, n: int, doc_offset: int, lo: int = 20, hi: int = 5000) -> Corpus:
+    """Unseen documents of a workload's generator (its topics, its length law
+    clipped to [lo, hi]) -- fold-in requests; doc_offset keeps their streams
+    apart from the training corpus."""
+    wl = WORKLOADS[name]
+    model = TopicModel(wl.V, wl.K_true, wl.zipf_s, wl.conc_c, seed)
+    lens = lengths(n, wl.len_kind, wl.len_mean, wl.len_sigma, seed, doc_offset, lo, hi)
+    return generate_docs(model, lens, wl.doc_alpha, seed, doc_offset)

@@ -111,9 +111,10 @@ struct warplda_ctx {
     std::vector<int64_t> word_ptr_h;
     int grid_batch[2][2] = {{1, 1}, {1, 1}};   // [doc 0 / word 1][class]
     int grid_hist = 1, grid_acc_doc = 1, grid_acc_word = 1, grid_draw = 1, grid_topic = 1;
-    // frozen model of fold-in: per-word exclusive prefix of C_w ([V, K+1])
-    // and (float)c_k + beta_bar, taken after sweep model_iter
-    int32_t* model_P = nullptr;
+    // frozen model of fold-in, taken after sweep model_iter: C_w ([V, K]),
+    // each word's topics ascending ([N]) and (float)c_k + beta_bar
+    int32_t* model_cw = nullptr;
+    int32_t* model_zs = nullptr;
     float* model_ckb = nullptr;
     int64_t model_iter = -1;
     bool prof = false;
@@ -949,10 +950,11 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
     // the frozen model: C_w prefix rows and c_k of the current state
     if (c->model_iter != (int64_t)c->iter) {
         int rc;
-        if (!c->model_P && (rc = dalloc(c, &c->model_P, c->V * (int64_t)(K + 1), "alloc fold-in model")))
+        if (!c->model_cw && (rc = dalloc(c, &c->model_cw, c->V * (int64_t)K, "alloc fold-in model")))
             return rc;
+        if (!c->model_zs && (rc = dalloc(c, &c->model_zs, c->N + 4, "alloc fold-in topics"))) return rc;
         if (!c->model_ckb && (rc = dalloc(c, &c->model_ckb, K, "alloc fold-in c_k"))) return rc;
-        WL_CU(launch_model_build(c->z, c->word_off, c->V, K, c->model_P, c->d_fault,
+        WL_CU(launch_model_build(c->z, c->word_off, c->V, K, c->model_cw, c->model_zs, c->d_fault,
                                  4 * c->sms, c->st), "build fold-in model");
         WL_CU(cudaMemcpyAsync(c->model_ckb, c->ckb, (size_t)K * sizeof(float), cudaMemcpyDeviceToDevice,
                               c->st), "copy c_k");
@@ -998,7 +1000,9 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
     f.doc_off = d_off;
     f.order = d_order;
     f.ids = d_ids;
-    f.P = c->model_P;
+    f.Cw = c->model_cw;
+    f.Zs = c->model_zs;
+    f.word_off = c->word_off;
     f.ckb = c->model_ckb;
     f.theta = d_theta;
     f.counter = d_counter;

@@ -216,22 +216,4 @@ enum : int {
     kSiteHugeDraw = 5, kSiteDocWarp = 6, kSiteLoglik = 7, kSiteFoldin = 8
 };
 
-// Fold-in of new documents against a frozen model (wl_foldin.cu).
-struct FoldArgs {
-    int32_t* z;              // [Nn] topics, document order
-    int32_t* prop;           // [Nn * M] proposals
-    const int32_t* words;    // [Nn] word ids
-    const int32_t* doc_off;  // [Dn + 1] token offsets
-    const int32_t* order;    // [Dn] documents, longest first
-    const int64_t* ids;      // [Dn] document ids (Philox stream)
-    const int32_t* P;        // [V * (K + 1)] frozen per-word exclusive prefix of C_w
-    const float* ckb;        // [K] frozen (float)c_k + beta_bar
-    float* theta;            // [Dn * K] or null
-    int32_t* counter;        // work counter (zero on entry)
-    int32_t* fault;          // index-check record
-    int Dn, K, M, V, sweeps, Lmax;
-    float alpha, abar, beta, kbeta;
-    RoundKeys rk;
-};
-
 }  // namespace wl

@@ -1,16 +1,15 @@
 // Fold-in of new documents against a frozen model: the document phase and
 // word phase of Sec. 4.4 with the word side frozen (the paper trains only;
 // the readings are those of the oracle's fold-in):
-//   model   : P_w[k] = C_w0 + ... + C_w,k-1 for every word (a dense
-//             [V, K+1] prefix table built from the trained z), frozen c_k;
+//   model   : the trained C_w as a dense [V, K] table, each word's trained
+//             topics sorted ascending (word-major, [N]), frozen c_k;
 //   document: pi^word (Eq. 7) against the document's phase-start c_d and the
 //             frozen c_k, then positioning over the post-acceptance z_d
 //             (Sec. 4.3);
-//   word    : pi^doc against the frozen C_w row of the token's word
-//             (C_wk = P_w[k+1] - P_w[k]) and the frozen c_k, then a word
-//             proposal from the frozen row (Eq. 6): with probability
-//             L_w / (L_w + K beta) the j-th smallest topic of the word (the
-//             largest k with P_w[k] <= j), else uniform.
+//   word    : pi^doc against the frozen C_w row of the token's word and the
+//             frozen c_k, then a word proposal from the frozen row (Eq. 6):
+//             with probability L_w / (L_w + K beta) the j-th smallest topic
+//             of the word (one load from its sorted topics), else uniform.
 // Random numbers: Philox keyed by the fold-in seed, counter = (position in
 // the document, iteration, phase << 8 | i, document id), phases 3/4/5, so a
 // document's result does not depend on the other documents of the call.
@@ -25,49 +24,48 @@ namespace wl {
 enum : uint32_t { kPhaseFoldInit = 3, kPhaseFoldDoc = 4, kPhaseFoldWord = 5 };
 
 // ---------------------------------------------------------------------------
-// Frozen model: per-word topic counts of the trained state, then per-row
-// exclusive prefix (row of K+1 ints, last = L_w).
+// Frozen model: per-word topic counts of the trained state (dense [V, K]),
+// then each word's topics in ascending order (a counting sort through its
+// row: topic k fills C_wk consecutive slots).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) model_counts_kernel(const int32_t* __restrict__ z,
                                                                 const int32_t* __restrict__ word_off,
-                                                                int64_t V, int K, int32_t* __restrict__ P,
+                                                                int64_t V, int K, int32_t* __restrict__ Cw,
                                                                 int32_t* fault) {
     Checks chk;
     for (int64_t w = blockIdx.x; w < V; w += gridDim.x) {
-        int32_t* row = P + w * (int64_t)(K + 1);
+        int32_t* row = Cw + w * (int64_t)K;
         for (int t = word_off[w] + threadIdx.x; t < word_off[w + 1]; t += kThreads)
-            atomicAdd(&row[1 + chk.topic(z[t], K, 0)], 1);
+            atomicAdd(&row[chk.topic(z[t], K, 0)], 1);
     }
     chk.publish(fault, kSiteFoldin);
 }
 
-__global__ void __launch_bounds__(kThreads) model_scan_kernel(int64_t V, int K, int32_t* __restrict__ P) {
+__global__ void __launch_bounds__(kThreads) model_sort_kernel(const int32_t* __restrict__ word_off,
+                                                              int64_t V, int K, const int32_t* __restrict__ Cw,
+                                                              int32_t* __restrict__ Zs) {
     __shared__ int warp_tot[kWarps];
     __shared__ int s_total;
-    const int n = K + 1;
-    const int per = (n + kThreads - 1) / kThreads;
+    const int per = (K + kThreads - 1) / kThreads;
     for (int64_t w = blockIdx.x; w < V; w += gridDim.x) {
-        int32_t* row = P + w * (int64_t)n;
-        const int k0 = min(n, (int)threadIdx.x * per), k1 = min(n, k0 + per);
+        const int32_t* row = Cw + w * (int64_t)K;
+        const int base = word_off[w], Lw = word_off[w + 1] - base;
+        const int k0 = min(K, (int)threadIdx.x * per), k1 = min(K, k0 + per);
         int sum = 0;
         for (int k = k0; k < k1; ++k) sum += row[k];
         int run = block_excl_scan(sum, warp_tot, &s_total);
-        // row[0] is 0 and row[k+1] holds C_wk: the inclusive prefix of the
-        // shifted counts is the exclusive prefix of the counts
-        for (int k = k0; k < k1; ++k) {
-            run += row[k];
-            row[k] = run;
-        }
+        for (int k = k0; k < k1; ++k)
+            for (int c = row[k]; c > 0 && run < Lw; --c) Zs[base + run++] = k;
         __syncthreads();
     }
 }
 
 cudaError_t launch_model_build(const int32_t* z, const int32_t* word_off, int64_t V, int K,
-                               int32_t* P, int32_t* fault, int grid, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(P, 0, (size_t)V * (K + 1) * sizeof(int32_t), st);
+                               int32_t* Cw, int32_t* Zs, int32_t* fault, int grid, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(Cw, 0, (size_t)V * K * sizeof(int32_t), st);
     if (e != cudaSuccess || V <= 0) return e;
-    model_counts_kernel<<<grid, kThreads, 0, st>>>(z, word_off, V, K, P, fault);
-    model_scan_kernel<<<grid, kThreads, 0, st>>>(V, K, P);
+    model_counts_kernel<<<grid, kThreads, 0, st>>>(z, word_off, V, K, Cw, fault);
+    model_sort_kernel<<<grid, kThreads, 0, st>>>(word_off, V, K, Cw, Zs);
     return cudaGetLastError();
 }
 
@@ -82,16 +80,6 @@ int foldin_table_words(int K, int Lmax) {
 __device__ __forceinline__ int fold_count(const uint32_t* tab, uint32_t cap, bool dense, int k) {
     return dense ? (int)((tab[(uint32_t)k >> 1] >> (((uint32_t)k & 1) * 16)) & 0xFFFFu)
                  : table_get(tab, cap, (uint32_t)k);
-}
-
-// The largest k < K with P[k] <= j (the topic of rank j of a frozen row).
-__device__ __forceinline__ int rank_topic(const int32_t* __restrict__ P, int K, int j) {
-    int lo = 0, hi = K - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(P + mid) <= j) lo = mid; else hi = mid - 1;
-    }
-    return lo;
 }
 
 template <int M, bool kDense>
@@ -177,12 +165,13 @@ __global__ void __launch_bounds__(kThreads) foldin_kernel(FoldArgs f, int tab_wo
             for (int j = lane; j < L; j += 32) {
                 int w = wd[j];
                 if (!chk((uint32_t)w < (uint32_t)f.V, 1)) w = 0;
-                const int32_t* P = f.P + (int64_t)w * (K + 1);
-                const int Lw = __ldg(P + K);
+                const int32_t* row = f.Cw + (int64_t)w * K;
+                const int wb = __ldg(f.word_off + w);
+                const int Lw = __ldg(f.word_off + w + 1) - wb;
                 const float Lwf = __int2float_rn(Lw);
                 const float LwG = __fadd_rn(Lwf, f.kbeta);
                 int s = min((uint32_t)z[j], km);
-                int cs = __ldg(P + s + 1) - __ldg(P + s);
+                int cs = __ldg(row + s);
                 float ks = __ldg(f.ckb + s);
                 uint32_t r1[M], r2[M];
 #pragma unroll
@@ -192,7 +181,7 @@ __global__ void __launch_bounds__(kThreads) foldin_kernel(FoldArgs f, int tab_wo
                     r2[i] = r.z;
                     const int t = (int)min((uint32_t)prop[j * M + i], km);
                     if (t != s) {
-                        const int ct = __ldg(P + t + 1) - __ldg(P + t);
+                        const int ct = __ldg(row + t);
                         const float kt = __ldg(f.ckb + t);
                         if (accept(r.x, cs, ct, f.beta, ks, kt)) {
                             s = t;
@@ -205,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) foldin_kernel(FoldArgs f, int tab_wo
 #pragma unroll
                 for (int i = 0; i < M; ++i)
                     prop[j * M + i] = (Lw > 0 && coin(r1[i], Lwf, LwG))
-                                          ? rank_topic(P, K, (int)dice(r2[i], (uint32_t)Lw))
+                                          ? __ldg(f.Zs + wb + (int)dice(r2[i], (uint32_t)Lw))
                                           : (int)dice(r2[i], (uint32_t)K);
             }
             __syncwarp();

@@ -39,10 +39,30 @@ cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const HugeWork& w,
 cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const HugeWork& w,
                              const int32_t* rows_post, int grid, cudaStream_t st);
 
-// Fold-in against a frozen model (wl_foldin.cu): P = [V, K+1] per-word
-// exclusive prefix of the trained C_w.
+// Fold-in of new documents against a frozen model (wl_foldin.cu).
+struct FoldArgs {
+    int32_t* z;              // [Nn] topics, document order
+    int32_t* prop;           // [Nn * M] proposals
+    const int32_t* words;    // [Nn] word ids
+    const int32_t* doc_off;  // [Dn + 1] token offsets
+    const int32_t* order;    // [Dn] documents, longest first
+    const int64_t* ids;      // [Dn] document ids (Philox stream)
+    const int32_t* Cw;       // [V * K] frozen C_w
+    const int32_t* Zs;       // [N] frozen topics of each word, ascending (word-major)
+    const int32_t* word_off; // [V + 1] token offsets of the words
+    const float* ckb;        // [K] frozen (float)c_k + beta_bar
+    float* theta;            // [Dn * K] or null
+    int32_t* counter;        // work counter (zero on entry)
+    int32_t* fault;          // index-check record
+    int Dn, K, M, V, sweeps, Lmax;
+    float alpha, abar, beta, kbeta;
+    RoundKeys rk;
+};
+
+// Fold-in against a frozen model (wl_foldin.cu): Cw = [V, K] trained counts,
+// Zs = [N] each word's trained topics in ascending order.
 cudaError_t launch_model_build(const int32_t* z, const int32_t* word_off, int64_t V, int K,
-                               int32_t* P, int32_t* fault, int grid, cudaStream_t st);
+                               int32_t* Cw, int32_t* Zs, int32_t* fault, int grid, cudaStream_t st);
 int foldin_table_words(int K, int Lmax);
 int foldin_warps(int tab_words);
 int foldin_blocks_per_sm(int K, int M, int tab_words);
