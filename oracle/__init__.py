@@ -97,6 +97,13 @@ def load(mutation: int = 0) -> ctypes.CDLL:
         lib.orc_cgs_foldin.argtypes = [c.c_int64, _i64p, _i32p, c.c_int, c.c_float, c.c_float,
                                        c.c_float, _i32p, _i32p, c.c_uint64, c.c_int, c.c_int,
                                        _f64p]
+        lib.orc_alias_build.argtypes = [_f32p, c.c_int, _f32p, _i32p]
+        lib.orc_alias_draw.argtypes = [c.c_uint32, c.c_uint32, _f32p, _i32p, c.c_int]
+        lib.orc_alias_draw.restype = c.c_int
+        lib.orc_foldin_learned.argtypes = [c.c_int64, _i64p, _i32p, _i64p, c.c_int, c.c_int,
+                                           c.c_float, c.c_float, c.c_float, c.c_float, c.c_float,
+                                           _i32p, _i32p, _f32p, c.c_uint64, c.c_int, _i32p,
+                                           c.c_void_p]
         lib.orc_num_threads.restype = c.c_int
         lib.orc_set_num_threads.argtypes = [c.c_int]
         _LIBS[mutation] = lib
@@ -231,3 +238,34 @@ def cgs_foldin_theta(doc_ptr, doc_word, cw, ck, K: int, alpha: float, beta: floa
                        f32(beta), bbar, np.ascontiguousarray(cw, dtype=np.int32).ravel(),
                        np.ascontiguousarray(ck, dtype=np.int32), seed, sweeps, burn, acc)
     return (acc / max(sweeps - burn, 1)).reshape(Dn, K)
+
+
+def alias_table(q, mutation: int = 0):
+    """Walker/Vose alias table of q (orc_alias_build): (prob, alias)."""
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    K = len(q)
+    prob = np.zeros(K, dtype=np.float32)
+    alias = np.zeros(K, dtype=np.int32)
+    load(mutation).orc_alias_build(q, K, prob, alias)
+    return prob, alias
+
+
+def foldin_learned(doc_ptr, doc_word, cw, ck, q, K: int, M: int, alpha: float, beta: float,
+                   V: int, seed: int, sweeps: int, doc_ids=None, theta: bool = True,
+                   mutation: int = 0):
+    """Fold-in with the learned proposal q[Dn, K] (orc_foldin_learned): (z, theta)."""
+    lib = load(mutation)
+    dp = np.ascontiguousarray(doc_ptr, dtype=np.int64)
+    dw = np.ascontiguousarray(doc_word, dtype=np.int32)
+    Dn = len(dp) - 1
+    ids = np.arange(Dn, dtype=np.int64) if doc_ids is None else np.ascontiguousarray(doc_ids, dtype=np.int64)
+    abar, bbar, kbeta = derived(K, V, alpha, beta)
+    z = np.zeros(max(int(dp[-1]), 1), dtype=np.int32)
+    th = np.zeros(max(Dn * K, 1), dtype=np.float32) if theta else None
+    lib.orc_foldin_learned(Dn, dp, dw if len(dw) else np.zeros(1, np.int32), ids, K, M,
+                           f32(alpha), f32(beta), abar, kbeta, bbar,
+                           np.ascontiguousarray(cw, dtype=np.int32).ravel(),
+                           np.ascontiguousarray(ck, dtype=np.int32),
+                           np.ascontiguousarray(q, dtype=np.float32).ravel(), seed, sweeps, z,
+                           th.ctypes.data if th is not None else None)
+    return z[: int(dp[-1])], (th[: Dn * K].reshape(Dn, K) if th is not None else None)

@@ -679,6 +679,155 @@ void orc_foldin(int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
 }
 
 /*
+ * Walker's alias table for a discrete distribution q[K] (Vose's construction,
+ * "A linear algorithm for generating random numbers with a given
+ * distribution", IEEE TSE 1991): scaled weights p_k = K q_k; columns below 1
+ * and at or above 1 go on two stacks in index order; repeatedly the top small
+ * column l keeps probability p_l and aliases the top large column g, whose
+ * weight becomes (p_g + p_l) - 1.  FP32, every operation one RN operation in
+ * this order.  Readings L6: the learned proposal is this table.
+ */
+void orc_alias_build(const float* q, int K, float* prob, int32_t* alias)
+{
+    float* p = (float*)malloc((size_t)K * sizeof(float));
+    int32_t* small = (int32_t*)malloc((size_t)K * sizeof(int32_t));
+    int32_t* large = (int32_t*)malloc((size_t)K * sizeof(int32_t));
+    int ns = 0, nl = 0;
+    for (int k = 0; k < K; ++k) {
+        p[k] = q[k] * (float)K;
+        if (p[k] < 1.0f) small[ns++] = k; else large[nl++] = k;
+    }
+    while (ns > 0 && nl > 0) {
+        int l = small[--ns], g = large[--nl];
+        prob[l] = p[l];
+        alias[l] = g;
+        p[g] = (p[g] + p[l]) - 1.0f;
+        if (p[g] < 1.0f) small[ns++] = g; else large[nl++] = g;
+    }
+    while (nl > 0) { int g = large[--nl]; prob[g] = 1.0f; alias[g] = g; }
+    while (ns > 0) { int l = small[--ns]; prob[l] = 1.0f; alias[l] = l; }
+    free(p); free(small); free(large);
+}
+
+/* One draw from an alias table: column Dice(K) by r2, kept iff u(r1) < prob. */
+int orc_alias_draw(uint32_t r1, uint32_t r2, const float* prob, const int32_t* alias, int K)
+{
+    int k = (int)dice(r2, (uint32_t)K);
+    return u24(r1) < prob[k] ? k : alias[k];
+}
+
+/*
+ * Fold-in with a learned document proposal (the scope's next row 2; not in
+ * the paper).  Readings L6-L7:
+ *  L6  q[d*K + k] is the document's proposal distribution (the encoder's
+ *      softmax, FP32), drawn through the alias table above;
+ *  L7  a sweep is the document phase of orc_foldin with its draw replaced by
+ *      M independent draws from the alias table (r1, r2 of the same Philox
+ *      blocks), and the word phase of orc_foldin with pi^doc replaced by the
+ *      independence-sampler rate of Alg. 1,
+ *        min{1, p(t) q(s) / (p(s) q(t))},  p(k) = (C_dk + alpha)(C_wk + beta) / (c_k + beta_bar)
+ *      (the Eq. 5 conditional with the word phase's phase-start c_d, the
+ *      frozen C_w and c_k), accepted iff u * den < num with
+ *        num = (((C_dt + alpha) * (C_wt + beta)) * ckb_s) * q_s,
+ *        den = (((C_ds + alpha) * (C_ws + beta)) * ckb_t) * q_t,
+ *      ckb_k = c_k + beta_bar, every + and * one FP32 RN operation.
+ * Everything else (init, streams, word proposals, theta) is orc_foldin's.
+ */
+void orc_foldin_learned(int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
+                        const int64_t* doc_id, int K, int M, float alpha, float beta,
+                        float alpha_bar, float K_beta, float beta_bar, const int32_t* cw,
+                        const int32_t* ck, const float* q, uint64_t seed, int sweeps,
+                        int32_t* z_out, float* theta_out)
+{
+    int64_t maxL = 1;
+    for (int64_t d = 0; d < Dn; ++d)
+        if (doc_ptr[d + 1] - doc_ptr[d] > maxL) maxL = doc_ptr[d + 1] - doc_ptr[d];
+#pragma omp parallel
+    {
+        int32_t* cd = (int32_t*)malloc((size_t)K * sizeof(int32_t));
+        int32_t* znew = (int32_t*)malloc((size_t)maxL * sizeof(int32_t));
+        int32_t* prop = (int32_t*)malloc((size_t)maxL * (size_t)M * sizeof(int32_t));
+        float* prob = (float*)malloc((size_t)K * sizeof(float));
+        int32_t* alias = (int32_t*)malloc((size_t)K * sizeof(int32_t));
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t d = 0; d < Dn; ++d) {
+            int64_t b = doc_ptr[d];
+            int L = (int)(doc_ptr[d + 1] - b);
+            uint32_t id = (uint32_t)doc_id[d];
+            const float* qd = q + d * K;
+            int32_t* z = z_out + b;
+            uint32_t r[4];
+            orc_alias_build(qd, K, prob, alias);
+            for (int j = 0; j < L; ++j) {
+                draw_block(seed, (uint32_t)j, 0, ORC_PHASE_FINIT, 0, id, r);
+                z[j] = (int32_t)dice(r[0], (uint32_t)K);
+                for (int i = 0; i < M; ++i) prop[j * M + i] = z[j];
+            }
+            for (int it = 1; it <= sweeps; ++it) {
+                /* document phase: pi^word, then learned proposals */
+                for (int k = 0; k < K; ++k) cd[k] = 0;
+                for (int j = 0; j < L; ++j) cd[z[j]] += 1;
+                for (int j = 0; j < L; ++j) {
+                    int s = z[j];
+                    for (int i = 1; i <= M; ++i) {
+                        draw_block(seed, (uint32_t)j, (uint32_t)it, ORC_PHASE_FDOC, (uint32_t)i, id, r);
+                        int tp = prop[j * M + (i - 1)];
+                        s = orc_accept(r[0], s, tp, cd[s], cd[tp], ck[s], ck[tp], alpha, beta_bar);
+                    }
+                    znew[j] = s;
+                }
+                for (int j = 0; j < L; ++j) {
+                    z[j] = znew[j];
+                    for (int i = 1; i <= M; ++i) {
+                        draw_block(seed, (uint32_t)j, (uint32_t)it, ORC_PHASE_FDOC, (uint32_t)i, id, r);
+                        prop[j * M + (i - 1)] = orc_alias_draw(r[1], r[2], prob, alias, K);
+                    }
+                }
+                /* word phase: independence-sampler rate (L7), frozen word proposals */
+                for (int k = 0; k < K; ++k) cd[k] = 0;
+                for (int j = 0; j < L; ++j) cd[z[j]] += 1;
+                for (int j = 0; j < L; ++j) {
+                    const int32_t* row = cw + (int64_t)doc_word[b + j] * K;
+                    int s = z[j];
+                    for (int i = 1; i <= M; ++i) {
+                        draw_block(seed, (uint32_t)j, (uint32_t)it, ORC_PHASE_FWORD, (uint32_t)i, id, r);
+                        int t = prop[j * M + (i - 1)];
+                        if (t != s) {
+#if ORC_MUTATION == 13
+                            float num = ((((float)cd[t] + alpha) * ((float)row[t] + beta))
+                                         * ((float)ck[s] + beta_bar)) * qd[t];   /* q terms swapped */
+                            float den = ((((float)cd[s] + alpha) * ((float)row[s] + beta))
+                                         * ((float)ck[t] + beta_bar)) * qd[s];
+#else
+                            float num = ((((float)cd[t] + alpha) * ((float)row[t] + beta))
+                                         * ((float)ck[s] + beta_bar)) * qd[s];
+                            float den = ((((float)cd[s] + alpha) * ((float)row[s] + beta))
+                                         * ((float)ck[t] + beta_bar)) * qd[t];
+#endif
+                            if (u24(r[0]) * den < num) s = t;
+                        }
+                    }
+                    znew[j] = s;
+                    for (int i = 1; i <= M; ++i) {
+                        draw_block(seed, (uint32_t)j, (uint32_t)it, ORC_PHASE_FWORD, (uint32_t)i, id, r);
+                        prop[j * M + (i - 1)] = orc_frozen_word_draw(r[1], r[2], row, K, K_beta);
+                    }
+                }
+                for (int j = 0; j < L; ++j) z[j] = znew[j];
+            }
+            if (theta_out) {
+                for (int k = 0; k < K; ++k) cd[k] = 0;
+                for (int j = 0; j < L; ++j) cd[z[j]] += 1;
+                float den = (float)L + alpha_bar;
+                for (int k = 0; k < K; ++k)
+                    theta_out[d * K + k] = ((float)cd[k] + alpha) / den;
+            }
+        }
+        free(cd); free(znew); free(prop); free(prob); free(alias);
+    }
+}
+
+/*
  * Plain collapsed Gibbs fold-in (the yardstick of the fold-in statistics
  * test): the exact O(K) conditional (C_dk^- + alpha)(C_wk + beta)/(c_k + beta_bar)
  * with the frozen C_w and c_k and the token's own assignment removed from

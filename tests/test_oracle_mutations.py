@@ -16,6 +16,7 @@ least one of the distribution pins (test_oracle_law.py) or the Philox pin
  10  fold-in: the frozen word's j-th smallest topic off by one rank
  11  fold-in: pi^doc and the word proposal read a neighbouring token's word row
  12  fold-in: theta normalised by L_d + alpha instead of L_d + alpha_bar
+ 13  learned fold-in: q(s) and q(t) swapped in the independence-sampler rate
 """
 import numpy as np
 import pytest
@@ -77,3 +78,8 @@ def _foldin_pins(m):
 @pytest.mark.parametrize("m", [10, 11, 12])
 def test_foldin_pins_catch_mutation(m):
     assert any(_fails(c) for c in _foldin_pins(m)), f"mutation {m} not caught"
+
+
+def test_learned_pin_catches_mutation():
+    from tests import test_oracle_learned as le
+    assert _fails(lambda: le.check_learned_against_cgs(mutation=13))
