@@ -217,6 +217,21 @@ int warplda_foldin(warplda_ctx* ctx, int64_t Dn, const int64_t* doc_ptr, const i
                    float* theta_out, int32_t* z_out);
 
 /*
+ * warplda_gemm_bf16 -- the tensor-core (tcgen05) GEMM of the fold-in
+ * encoder's second layer and its backward products, exposed for testing:
+ *   C[M, N] = A[M, K] * B[N, K]^T (+ bias[N]).
+ *   A_dev, B_dev  device BF16, row-major (K contiguous), 16-byte aligned.
+ *   C_dev         device float32 [M, N], row-major.
+ *   bias_dev      device float32 [N] or NULL.
+ *   M, N multiples of 128, K a multiple of 64.
+ * Synchronous on cuda_stream (NULL: the default stream).  Errors: EINVAL
+ * (shapes, alignment), ETIMEDOUT (a bounded tensor-core wait ran out), ECUDA.
+ * The paper has no counterpart.
+ */
+int warplda_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, const float* bias_dev,
+                      int32_t M, int32_t N, int32_t K, void* cuda_stream);
+
+/*
  * warplda_sync -- wait for the work queued on the context's stream and report
  * the kernels' index checks.  Every sampler kernel validates the indices it
  * takes from stored state (topics, proposals, token pointers, work lists)

@@ -1032,6 +1032,28 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
     return check_record(c, "fold-in");
 }
 
+int warplda_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, const float* bias_dev,
+                      int32_t M, int32_t N, int32_t K, void* cuda_stream) {
+    if (!A_dev || !B_dev || !C_dev) return fail(WARPLDA_EINVAL, "null matrix pointer");
+    if (M < 0 || N < 0 || K < 0 || M % 128 || N % 128 || K % 64)
+        return fail(WARPLDA_EINVAL, "GEMM needs M, N multiples of 128 and K a multiple of 64");
+    if (((uintptr_t)A_dev | (uintptr_t)B_dev | (uintptr_t)C_dev) & 15)
+        return fail(WARPLDA_EINVAL, "GEMM operands must be 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int32_t* status = nullptr;
+    WL_CU(cudaMalloc((void**)&status, sizeof(int32_t)), "alloc GEMM status");
+    int32_t h = 0;
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+    if (e == cudaSuccess)
+        e = launch_gemm_bf16((const uint16_t*)A_dev, (const uint16_t*)B_dev, C_dev, bias_dev, M, N, K, status, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(status);
+    if (e != cudaSuccess) return cuda_fail(e, "GEMM");
+    if (h) return fail(WARPLDA_ETIMEDOUT, "GEMM: a tensor-core wait ran out");
+    return WARPLDA_OK;
+}
+
 int warplda_sync(warplda_ctx* c) {
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");

@@ -68,6 +68,13 @@ int foldin_warps(int tab_words);
 int foldin_blocks_per_sm(int K, int M, int tab_words);
 cudaError_t launch_foldin(const FoldArgs& f, int tab_words, int grid, cudaStream_t st);
 
+// Tensor-core BF16 GEMM (wl_gemm.cu): C[M,N] = A[M,K] B[N,K]^T (+ bias[N]),
+// FP32 C; M, N multiples of 128, K a multiple of 64; *status set to 1 if a
+// bounded wait ran out.
+int gemm_smem_bytes();
+cudaError_t launch_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, const float* bias,
+                             int M, int N, int K, int32_t* status, cudaStream_t st);
+
 // Initialisation, c_k, export, log-likelihood (wl_misc.cu).
 cudaError_t launch_init_z(int32_t* z, int32_t* prop, int64_t N, int K, int M, uint64_t seed,
                           cudaStream_t st);

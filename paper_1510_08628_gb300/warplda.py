@@ -69,6 +69,8 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double)]),
     "warplda_sync": (ctypes.c_int, [_P]),
+    "warplda_gemm_bf16": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int32, _P]),
     "warplda_foldin": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int32,
                                       ctypes.c_uint64, ctypes.c_int32, _P, _P]),
     "warplda_destroy": (None, [_P]),
@@ -253,3 +255,13 @@ class WarpLDA:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def gemm_bf16(A, B, C, bias=None, stream=None) -> None:
+    """C = A @ B.T (+ bias) on the tensor cores; torch tensors on the device
+    (A, B bfloat16 [M, K] / [N, K], C float32 [M, N])."""
+    M, K = A.shape
+    N = B.shape[0]
+    st = stream.cuda_stream if stream is not None else None
+    _check(load().warplda_gemm_bf16(A.data_ptr(), B.data_ptr(), C.data_ptr(),
+                                    bias.data_ptr() if bias is not None else None, M, N, K, st))
