@@ -200,7 +200,13 @@ int warplda_kernel_times(warplda_ctx* ctx, int32_t cap, const char** names, int6
  *   doc_ids     host int64[Dn] stream ids of the documents, or NULL for
  *               0..Dn-1.
  *   sweeps      fold-in sweeps (>= 0).
- *   proposal    WARPLDA_PROPOSAL_PLAIN (the only one this library has).
+ *   proposal    WARPLDA_PROPOSAL_PLAIN, or WARPLDA_PROPOSAL_LEARNED: the
+ *               document proposal is the encoder's softmax q_d (see
+ *               warplda_encoder_init) drawn through a Walker alias table, and
+ *               the word phase accepts it with the independence-sampler rate
+ *               of Alg. 1, min{1, p(t) q_d(s) / (p(s) q_d(t))}, p the Eq. 5
+ *               conditional with the document's phase-start counts, the frozen
+ *               C_w and c_k; the chain keeps its target.
  *   theta_out   host float[Dn*K], theta_dk = (C_dk + alpha)/(L_d + K alpha)
  *               of the final assignments; or NULL.
  *   z_out       host int32[doc_ptr[Dn]], final topics in document order; or
@@ -212,9 +218,45 @@ int warplda_kernel_times(warplda_ctx* ctx, int32_t cap, const char** names, int6
  * ESTATE (a word phase is pending), ENOMEM, ECUDA.
  */
 #define WARPLDA_PROPOSAL_PLAIN 0
+#define WARPLDA_PROPOSAL_LEARNED 1
 int warplda_foldin(warplda_ctx* ctx, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
                    const int64_t* doc_ids, int32_t sweeps, uint64_t seed, int32_t proposal,
                    float* theta_out, int32_t* z_out);
+
+/*
+ * The fold-in encoder: the learned document proposal of fold-in (the paper
+ * has no counterpart).  A document's input is its hashed bag of words,
+ * x_f = (# tokens whose word w has f(w) = ((w * 2654435761) mod 2^32) >>
+ * (32 - log2_features)) / L_d; h = ReLU(b1 + W1^T x) (W1: [F, H]); q =
+ * softmax(b2 + W2^T bf16(h)) (W2: [H, K]).  BF16 weights, FP32 accumulation;
+ * the second layer and its backward products run on the tensor cores.
+ *
+ * warplda_encoder_init -- allocate and initialise (W1 ~ U(-1, 1), W2 Glorot
+ *   uniform, biases 0; seeded).  log2_features in [6, 20]; hidden and
+ *   batch_rows multiples of 128 up to 2048.  ESTATE if already initialised.
+ * warplda_encoder_weights -- get (set = 0) or set (set = 1) the FP32 master
+ *   weights: W1 host float[F*H] row-major, b1 [H], W2 [H*K] row-major, b2 [K].
+ *   Setting leaves the optimiser state as it is.
+ * warplda_encoder_grad -- one forward and backward pass on Dn (1..batch_rows)
+ *   host documents (CSR, word ids in [0, V)) against host targets
+ *   theta[Dn*K]; writes the mean soft cross-entropy and the gradients (same
+ *   layouts as the weights); no update.
+ * warplda_encoder_train -- `epochs` passes of Adam (lr; beta1 0.9, beta2
+ *   0.999, eps 1e-8) over the context's own documents in seeded random
+ *   batches of batch_rows, targets theta of Eq. 4 from the current
+ *   assignments; epoch_loss[epochs] (or NULL) receives each epoch's mean loss.
+ * warplda_encoder_proposal -- q_out[Dn*K] (host) for Dn host documents.
+ * All synchronous.  Errors: EINVAL, ESTATE, ENOMEM, ETIMEDOUT (a bounded
+ * tensor-core wait ran out), ECUDA.
+ */
+int warplda_encoder_init(warplda_ctx* ctx, int32_t log2_features, int32_t hidden, int32_t batch_rows,
+                         uint64_t seed);
+int warplda_encoder_weights(warplda_ctx* ctx, int32_t set, float* W1, float* b1, float* W2, float* b2);
+int warplda_encoder_grad(warplda_ctx* ctx, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
+                         const float* theta, double* loss, float* gW1, float* gb1, float* gW2, float* gb2);
+int warplda_encoder_train(warplda_ctx* ctx, int32_t epochs, float lr, uint64_t seed, double* epoch_loss);
+int warplda_encoder_proposal(warplda_ctx* ctx, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
+                             float* q_out);
 
 /*
  * warplda_gemm_bf16 -- the tensor-core (tcgen05) GEMM of the fold-in

@@ -121,6 +121,19 @@ struct warplda_ctx {
     std::vector<Rec> recs;
     int64_t device_bytes = 0;
     std::vector<void*> allocs;
+    // fold-in encoder (learned document proposal)
+    struct Encoder {
+        int log2F = 0, H = 0, Kp = 0, B = 256, step = 0;
+        float *W1 = nullptr, *b1 = nullptr, *W2t = nullptr, *b2 = nullptr;   // FP32 masters
+        float *mW1, *vW1, *mb1, *vb1, *mW2, *vW2, *mb2, *vb2;               // Adam moments
+        uint16_t *W1b, *W2tb, *W2nb;                                          // BF16 copies
+        float *gW1, *gb1, *gW2t, *gb2;                                        // gradients
+        float *h_pre, *logits, *dH;
+        uint16_t *hb, *hbT, *dl, *dlT;
+        int32_t *cnt, *ids, *docword = nullptr;
+        double* loss;
+        bool ready = false;
+    } enc;
 };
 
 namespace {
@@ -467,6 +480,112 @@ struct FoldBuffers {
         for (void* q : p) cudaFree(q);
     }
 };
+
+namespace {
+
+int64_t enc_F(const warplda_ctx* c) { return (int64_t)1 << c->enc.log2F; }
+
+// Forward pass of one batch (rows of b), logits into enc.logits; with
+// dl_targets the softmax also writes the loss, dlogits and gb2 (targets
+// given rows, or theta of the context's own assignments when tgt is null);
+// q_out receives the proposal rows.
+int enc_forward(warplda_ctx* c, const EncBatch& b, float* q_out, bool grads, const float* tgt) {
+    auto& e = c->enc;
+    WL_CU(launch_enc_l1_fwd(b, e.B, e.W1b, e.b1, e.H, e.log2F, e.h_pre, e.hb, e.hbT, c->st), "encoder layer 1");
+    // the GEMM's status flag reuses the check record's last word
+    WL_CU(launch_gemm_bf16(e.hb, e.W2tb, e.logits, e.b2, e.B, e.Kp, e.H, c->d_fault + 3, c->st), "encoder layer 2");
+    WL_CU(launch_enc_softmax(b, e.B, e.logits, c->K, e.Kp, q_out, tgt, c->z, c->perm, c->alpha, c->abar,
+                             grads ? e.dl : nullptr, e.dlT, e.gb2, e.loss, e.cnt, c->st), "encoder softmax");
+    return WARPLDA_OK;
+}
+
+int enc_backward(warplda_ctx* c, const EncBatch& b) {
+    auto& e = c->enc;
+    WL_CU(launch_gemm_bf16(e.dl, e.W2nb, e.dH, nullptr, e.B, e.H, e.Kp, c->d_fault + 3, c->st), "encoder dH");
+    WL_CU(launch_gemm_bf16(e.dlT, e.hbT, e.gW2t, nullptr, e.Kp, e.H, e.B, c->d_fault + 3, c->st), "encoder dW2");
+    WL_CU(launch_enc_l1_bwd(b, e.B, e.dH, e.h_pre, e.H, e.log2F, e.gW1, e.gb1, c->st), "encoder layer 1 backward");
+    return WARPLDA_OK;
+}
+
+int enc_zero_grads(warplda_ctx* c) {
+    auto& e = c->enc;
+    WL_CU(cudaMemsetAsync(e.gW1, 0, (size_t)enc_F(c) * e.H * 4, c->st), "zero gradients");
+    WL_CU(cudaMemsetAsync(e.gb1, 0, (size_t)e.H * 4, c->st), "zero gradients");
+    WL_CU(cudaMemsetAsync(e.gb2, 0, (size_t)e.Kp * 4, c->st), "zero gradients");
+    return WARPLDA_OK;
+}
+
+int enc_adam_step(warplda_ctx* c, float lr) {
+    auto& e = c->enc;
+    e.step += 1;
+    WL_CU(launch_enc_adam(e.W1, e.mW1, e.vW1, e.gW1, enc_F(c) * e.H, lr, e.step, e.W1b, c->st), "Adam W1");
+    WL_CU(launch_enc_adam(e.b1, e.mb1, e.vb1, e.gb1, e.H, lr, e.step, nullptr, c->st), "Adam b1");
+    WL_CU(launch_enc_adam(e.W2t, e.mW2, e.vW2, e.gW2t, (int64_t)e.Kp * e.H, lr, e.step, nullptr, c->st), "Adam W2");
+    WL_CU(launch_enc_adam(e.b2, e.mb2, e.vb2, e.gb2, e.Kp, lr, e.step, nullptr, c->st), "Adam b2");
+    WL_CU(launch_enc_w2_copies(e.W2t, e.Kp, e.H, e.W2tb, e.W2nb, c->st), "W2 copies");
+    return WARPLDA_OK;
+}
+
+// Reads the GEMM status word (synchronises).
+int enc_status(warplda_ctx* c) {
+    int32_t h = 0;
+    WL_CU(cudaMemcpyAsync(&h, c->d_fault + 3, 4, cudaMemcpyDeviceToHost, c->st), "read GEMM status");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    if (h) {
+        WL_CU(cudaMemsetAsync(c->d_fault + 3, 0, 4, c->st), "clear GEMM status");
+        return fail(WARPLDA_ETIMEDOUT, "encoder GEMM: a tensor-core wait ran out");
+    }
+    return WARPLDA_OK;
+}
+
+// Device copies of a host document CSR for encoder / fold-in calls.
+struct HostDocs {
+    int32_t *off = nullptr, *words = nullptr, *ids = nullptr;
+};
+
+int upload_docs(warplda_ctx* c, FoldBuffers& buf, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
+                HostDocs* out) {
+    const int64_t Nn = doc_ptr[Dn];
+    std::vector<int32_t> off((size_t)Dn + 1), ids((size_t)std::max<int64_t>(Dn, 1));
+    for (int64_t d = 0; d <= Dn; ++d) off[d] = (int32_t)doc_ptr[d];
+    for (int64_t d = 0; d < Dn; ++d) ids[d] = (int32_t)d;
+    WL_CU(buf.get(&out->off, Dn + 1), "alloc offsets");
+    WL_CU(buf.get(&out->words, Nn + 1), "alloc words");
+    WL_CU(buf.get(&out->ids, Dn + 1), "alloc ids");
+    WL_CU(cudaMemcpyAsync(out->off, off.data(), (size_t)(Dn + 1) * 4, cudaMemcpyHostToDevice, c->st), "upload offsets");
+    if (Nn > 0)
+        WL_CU(cudaMemcpyAsync(out->words, doc_word, (size_t)Nn * 4, cudaMemcpyHostToDevice, c->st), "upload words");
+    if (Dn > 0)
+        WL_CU(cudaMemcpyAsync(out->ids, ids.data(), (size_t)Dn * 4, cudaMemcpyHostToDevice, c->st), "upload ids");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");   // the host vectors go out of scope
+    return WARPLDA_OK;
+}
+
+int check_docs(const warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word) {
+    if (Dn < 0 || !doc_ptr || doc_ptr[0] != 0) return fail(WARPLDA_EINVAL, "bad document CSR");
+    for (int64_t d = 0; d < Dn; ++d)
+        if (doc_ptr[d + 1] < doc_ptr[d]) return fail(WARPLDA_EINVAL, "doc_ptr decreases at %lld", (long long)d);
+    const int64_t Nn = doc_ptr[Dn];
+    if (Nn > (int64_t)0x7FFFFFF0) return fail(WARPLDA_EINVAL, "too many tokens");
+    if (Nn > 0 && !doc_word) return fail(WARPLDA_EINVAL, "null doc_word");
+    for (int64_t p = 0; p < Nn; ++p)
+        if (doc_word[p] < 0 || (int64_t)doc_word[p] >= c->V)
+            return fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", doc_word[p], (long long)p);
+    return WARPLDA_OK;
+}
+
+// Proposal rows q[Dn, K] of host documents (device output).
+int enc_proposal_dev(warplda_ctx* c, int64_t Dn, const HostDocs& hd, float* q_dev) {
+    auto& e = c->enc;
+    for (int64_t b0 = 0; b0 < Dn; b0 += e.B) {
+        EncBatch b{hd.ids + b0, hd.off, hd.words, (int)std::min<int64_t>(e.B, Dn - b0)};
+        int rc = enc_forward(c, b, q_dev + b0 * c->K, false, nullptr);
+        if (rc) return rc;
+    }
+    return enc_status(c);
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -925,8 +1044,10 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
                    const int64_t* doc_ids, int32_t sweeps, uint64_t seed, int32_t proposal,
                    float* theta_out, int32_t* z_out) {
     if (!c || !doc_ptr || Dn < 0 || sweeps < 0) return fail(WARPLDA_EINVAL, "bad fold-in arguments");
-    if (proposal != WARPLDA_PROPOSAL_PLAIN)
-        return fail(WARPLDA_EINVAL, "proposal %d is not available in this library", proposal);
+    if (proposal != WARPLDA_PROPOSAL_PLAIN && proposal != WARPLDA_PROPOSAL_LEARNED)
+        return fail(WARPLDA_EINVAL, "unknown proposal %d", proposal);
+    if (proposal == WARPLDA_PROPOSAL_LEARNED && !c->enc.ready)
+        return fail(WARPLDA_ESTATE, "the learned proposal needs an initialised encoder");
     if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
     if (Dn > (int64_t)0x7FFFFFF0) return fail(WARPLDA_EINVAL, "too many documents");
     if (doc_ptr[0] != 0) return fail(WARPLDA_EINVAL, "doc_ptr[0] must be 0");
@@ -1018,6 +1139,29 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
     f.beta = c->beta;
     f.kbeta = c->kbeta;
     f.rk = round_keys(seed);
+    if (proposal == WARPLDA_PROPOSAL_LEARNED && Dn > 0) {
+        // the encoder's proposal rows and their alias tables
+        HostDocs hd;
+        float *q, *prob;
+        int32_t *alias, *stack, *ident;
+        std::vector<int32_t> idv((size_t)Dn);
+        for (int64_t d = 0; d < Dn; ++d) idv[d] = (int32_t)d;
+        WL_CU(buf.get(&ident, Dn), "alloc ids");
+        WL_CU(buf.get(&q, Dn * (int64_t)K), "alloc proposals");
+        WL_CU(buf.get(&prob, Dn * (int64_t)K), "alloc alias tables");
+        WL_CU(buf.get(&alias, Dn * (int64_t)K), "alloc alias tables");
+        WL_CU(buf.get(&stack, Dn * (int64_t)K), "alloc alias scratch");
+        WL_CU(cudaMemcpyAsync(ident, idv.data(), (size_t)Dn * 4, cudaMemcpyHostToDevice, c->st), "upload ids");
+        hd.off = d_off;
+        hd.words = d_words;
+        hd.ids = ident;
+        int rc2 = enc_proposal_dev(c, Dn, hd, q);   // synchronises
+        if (rc2) return rc2;
+        WL_CU(launch_enc_alias(q, Dn, K, prob, alias, stack, c->st), "alias tables");
+        f.q = q;
+        f.aprob = prob;
+        f.alias = alias;
+    }
     const int tab_words = foldin_table_words(K, (int)Lmax);
     const int per_sm = foldin_blocks_per_sm(K, M, tab_words);
     if (per_sm < 1) return fail(WARPLDA_EINVAL, "fold-in tables do not fit in shared memory");
@@ -1030,6 +1174,192 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
         WL_CU(cudaMemcpyAsync(theta_out, d_theta, (size_t)Dn * K * 4, cudaMemcpyDeviceToHost, c->st), "copy theta");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     return check_record(c, "fold-in");
+}
+
+static uint64_t splitmix64(uint64_t* x) {
+    uint64_t z = (*x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static float unit_uniform(uint64_t* x) { return (float)((splitmix64(x) >> 40) * (1.0 / 16777216.0)); }
+
+int warplda_encoder_init(warplda_ctx* c, int32_t log2_features, int32_t hidden, int32_t batch_rows,
+                         uint64_t seed) {
+    if (!c) return fail(WARPLDA_EINVAL, "null context");
+    auto& e = c->enc;
+    if (e.ready) return fail(WARPLDA_ESTATE, "the encoder is already initialised");
+    if (log2_features < 6 || log2_features > 20) return fail(WARPLDA_EINVAL, "log2_features must be in [6, 20]");
+    if (hidden < 128 || hidden > 2048 || hidden % 128) return fail(WARPLDA_EINVAL, "hidden must be a multiple of 128 in [128, 2048]");
+    if (batch_rows < 128 || batch_rows > 2048 || batch_rows % 128)
+        return fail(WARPLDA_EINVAL, "batch_rows must be a multiple of 128 in [128, 2048]");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    e.log2F = log2_features;
+    e.H = hidden;
+    e.B = batch_rows;
+    e.Kp = (c->K + 127) / 128 * 128;
+    const int64_t F = enc_F(c), H = e.H, Kp = e.Kp, B = e.B;
+    int rc;
+#define WL_A(ptr, n) if ((rc = dalloc(c, &(ptr), (n), "alloc encoder"))) return rc
+    WL_A(e.W1, F * H); WL_A(e.b1, H); WL_A(e.W2t, Kp * H); WL_A(e.b2, Kp);
+    WL_A(e.mW1, F * H); WL_A(e.vW1, F * H); WL_A(e.mb1, H); WL_A(e.vb1, H);
+    WL_A(e.mW2, Kp * H); WL_A(e.vW2, Kp * H); WL_A(e.mb2, Kp); WL_A(e.vb2, Kp);
+    WL_A(e.W1b, F * H); WL_A(e.W2tb, Kp * H); WL_A(e.W2nb, Kp * H);
+    WL_A(e.gW1, F * H); WL_A(e.gb1, H); WL_A(e.gW2t, Kp * H); WL_A(e.gb2, Kp);
+    WL_A(e.h_pre, B * H); WL_A(e.logits, B * Kp); WL_A(e.dH, B * H);
+    WL_A(e.hb, B * H); WL_A(e.hbT, B * H); WL_A(e.dl, B * Kp); WL_A(e.dlT, B * Kp);
+    WL_A(e.cnt, B * (int64_t)c->K); WL_A(e.loss, 1); WL_A(e.ids, std::max<int64_t>(c->D, 1));
+#undef WL_A
+    // W1 ~ U(-1, 1); W2 ~ U(-a, a), a = sqrt(6 / (H + K)) (Glorot); biases 0
+    std::vector<float> w1((size_t)(F * H)), w2((size_t)(Kp * H), 0.0f);
+    uint64_t st = seed;
+    for (auto& v : w1) v = 2.0f * unit_uniform(&st) - 1.0f;
+    const float a = std::sqrt(6.0f / (float)(H + c->K));
+    for (int64_t k = 0; k < c->K; ++k)
+        for (int64_t j = 0; j < H; ++j) w2[k * H + j] = a * (2.0f * unit_uniform(&st) - 1.0f);
+    WL_CU(cudaMemcpyAsync(e.W1, w1.data(), w1.size() * 4, cudaMemcpyHostToDevice, c->st), "upload W1");
+    WL_CU(cudaMemcpyAsync(e.W2t, w2.data(), w2.size() * 4, cudaMemcpyHostToDevice, c->st), "upload W2");
+    WL_CU(cudaMemsetAsync(e.b1, 0, H * 4, c->st), "zero");
+    WL_CU(cudaMemsetAsync(e.b2, 0, Kp * 4, c->st), "zero");
+    WL_CU(cudaMemsetAsync(e.mW1, 0, F * H * 4, c->st), "zero");
+    WL_CU(cudaMemsetAsync(e.vW1, 0, F * H * 4, c->st), "zero");
+    WL_CU(cudaMemsetAsync(e.mb1, 0, H * 4, c->st), "zero");
+    WL_CU(cudaMemsetAsync(e.vb1, 0, H * 4, c->st), "zero");
+    WL_CU(cudaMemsetAsync(e.mW2, 0, Kp * H * 4, c->st), "zero");
+    WL_CU(cudaMemsetAsync(e.vW2, 0, Kp * H * 4, c->st), "zero");
+    WL_CU(cudaMemsetAsync(e.mb2, 0, Kp * 4, c->st), "zero");
+    WL_CU(cudaMemsetAsync(e.vb2, 0, Kp * 4, c->st), "zero");
+    WL_CU(launch_enc_to_bf16(e.W1, F * H, e.W1b, c->st), "W1 copy");
+    WL_CU(launch_enc_w2_copies(e.W2t, (int)Kp, (int)H, e.W2tb, e.W2nb, c->st), "W2 copies");
+    WL_CU(cudaMemsetAsync(c->d_fault + 3, 0, 4, c->st), "clear GEMM status");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    e.step = 0;
+    e.ready = true;
+    return WARPLDA_OK;
+}
+
+int warplda_encoder_weights(warplda_ctx* c, int32_t set, float* W1, float* b1, float* W2, float* b2) {
+    if (!c || !W1 || !b1 || !W2 || !b2) return fail(WARPLDA_EINVAL, "null argument");
+    auto& e = c->enc;
+    if (!e.ready) return fail(WARPLDA_ESTATE, "the encoder is not initialised");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    const int64_t F = enc_F(c), H = e.H, Kp = e.Kp, K = c->K;
+    std::vector<float> w2t((size_t)(Kp * H), 0.0f);
+    if (set) {
+        for (int64_t j = 0; j < H; ++j)
+            for (int64_t k = 0; k < K; ++k) w2t[k * H + j] = W2[j * K + k];
+        WL_CU(cudaMemcpyAsync(e.W1, W1, (size_t)(F * H) * 4, cudaMemcpyHostToDevice, c->st), "upload W1");
+        WL_CU(cudaMemcpyAsync(e.b1, b1, (size_t)H * 4, cudaMemcpyHostToDevice, c->st), "upload b1");
+        WL_CU(cudaMemcpyAsync(e.W2t, w2t.data(), w2t.size() * 4, cudaMemcpyHostToDevice, c->st), "upload W2");
+        WL_CU(cudaMemsetAsync(e.b2, 0, (size_t)Kp * 4, c->st), "zero b2");
+        WL_CU(cudaMemcpyAsync(e.b2, b2, (size_t)K * 4, cudaMemcpyHostToDevice, c->st), "upload b2");
+        WL_CU(launch_enc_to_bf16(e.W1, F * H, e.W1b, c->st), "W1 copy");
+        WL_CU(launch_enc_w2_copies(e.W2t, (int)Kp, (int)H, e.W2tb, e.W2nb, c->st), "W2 copies");
+        WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+        return WARPLDA_OK;
+    }
+    WL_CU(cudaMemcpyAsync(W1, e.W1, (size_t)(F * H) * 4, cudaMemcpyDeviceToHost, c->st), "copy W1");
+    WL_CU(cudaMemcpyAsync(b1, e.b1, (size_t)H * 4, cudaMemcpyDeviceToHost, c->st), "copy b1");
+    WL_CU(cudaMemcpyAsync(w2t.data(), e.W2t, w2t.size() * 4, cudaMemcpyDeviceToHost, c->st), "copy W2");
+    WL_CU(cudaMemcpyAsync(b2, e.b2, (size_t)K * 4, cudaMemcpyDeviceToHost, c->st), "copy b2");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    for (int64_t j = 0; j < H; ++j)
+        for (int64_t k = 0; k < K; ++k) W2[j * K + k] = w2t[k * H + j];
+    return WARPLDA_OK;
+}
+
+int warplda_encoder_grad(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
+                         const float* theta, double* loss, float* gW1, float* gb1, float* gW2, float* gb2) {
+    if (!c || !theta || !loss || !gW1 || !gb1 || !gW2 || !gb2) return fail(WARPLDA_EINVAL, "null argument");
+    auto& e = c->enc;
+    if (!e.ready) return fail(WARPLDA_ESTATE, "the encoder is not initialised");
+    if (Dn < 1 || Dn > e.B) return fail(WARPLDA_EINVAL, "Dn must be in [1, batch_rows]");
+    int rc = check_docs(c, Dn, doc_ptr, doc_word);
+    if (rc) return rc;
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    FoldBuffers buf;
+    HostDocs hd;
+    if ((rc = upload_docs(c, buf, Dn, doc_ptr, doc_word, &hd))) return rc;
+    const int64_t F = enc_F(c), H = e.H, Kp = e.Kp, K = c->K;
+    float* tg;
+    WL_CU(buf.get(&tg, Dn * K), "alloc targets");
+    WL_CU(cudaMemcpyAsync(tg, theta, (size_t)(Dn * K) * 4, cudaMemcpyHostToDevice, c->st), "upload targets");
+    if ((rc = enc_zero_grads(c))) return rc;
+    WL_CU(cudaMemsetAsync(e.loss, 0, 8, c->st), "zero loss");
+    EncBatch b{hd.ids, hd.off, hd.words, (int)Dn};
+    if ((rc = enc_forward(c, b, nullptr, true, tg))) return rc;
+    if ((rc = enc_backward(c, b))) return rc;
+    if ((rc = enc_status(c))) return rc;
+    std::vector<float> g2((size_t)(Kp * H));
+    WL_CU(cudaMemcpyAsync(loss, e.loss, 8, cudaMemcpyDeviceToHost, c->st), "copy loss");
+    WL_CU(cudaMemcpyAsync(gW1, e.gW1, (size_t)(F * H) * 4, cudaMemcpyDeviceToHost, c->st), "copy gW1");
+    WL_CU(cudaMemcpyAsync(gb1, e.gb1, (size_t)H * 4, cudaMemcpyDeviceToHost, c->st), "copy gb1");
+    WL_CU(cudaMemcpyAsync(g2.data(), e.gW2t, g2.size() * 4, cudaMemcpyDeviceToHost, c->st), "copy gW2");
+    WL_CU(cudaMemcpyAsync(gb2, e.gb2, (size_t)K * 4, cudaMemcpyDeviceToHost, c->st), "copy gb2");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    for (int64_t j = 0; j < H; ++j)
+        for (int64_t k = 0; k < K; ++k) gW2[j * K + k] = g2[k * H + j];
+    return WARPLDA_OK;
+}
+
+int warplda_encoder_train(warplda_ctx* c, int32_t epochs, float lr, uint64_t seed, double* epoch_loss) {
+    if (!c || epochs < 0 || !(lr > 0.0f)) return fail(WARPLDA_EINVAL, "bad training arguments");
+    auto& e = c->enc;
+    if (!e.ready) return fail(WARPLDA_ESTATE, "the encoder is not initialised");
+    if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    int rc;
+    if (!e.docword) {
+        if ((rc = dalloc(c, &e.docword, c->N + 4, "alloc document words"))) return rc;
+        WL_CU(launch_enc_docword(c->perm, c->word_off, c->N, c->V, e.docword, c->st), "document words");
+    }
+    std::vector<int32_t> docs;
+    std::vector<int32_t> off((size_t)c->D + 1);
+    WL_CU(cudaMemcpyAsync(off.data(), c->doc_off, (size_t)(c->D + 1) * 4, cudaMemcpyDeviceToHost, c->st), "copy offsets");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    for (int64_t d = 0; d < c->D; ++d)
+        if (off[d + 1] > off[d]) docs.push_back((int32_t)d);
+    const int64_t nd = (int64_t)docs.size();
+    uint64_t rs = seed;
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int64_t i = nd - 1; i > 0; --i) std::swap(docs[i], docs[splitmix64(&rs) % (uint64_t)(i + 1)]);
+        if (nd > 0)
+            WL_CU(cudaMemcpyAsync(e.ids, docs.data(), (size_t)nd * 4, cudaMemcpyHostToDevice, c->st), "upload order");
+        WL_CU(cudaMemsetAsync(e.loss, 0, 8, c->st), "zero loss");
+        int64_t nb = 0;
+        for (int64_t b0 = 0; b0 < nd; b0 += e.B, ++nb) {
+            EncBatch b{e.ids + b0, c->doc_off, e.docword, (int)std::min<int64_t>(e.B, nd - b0)};
+            if ((rc = enc_zero_grads(c))) return rc;
+            if ((rc = enc_forward(c, b, nullptr, true, nullptr))) return rc;
+            if ((rc = enc_backward(c, b))) return rc;
+            if ((rc = enc_adam_step(c, lr))) return rc;
+        }
+        double l = 0.0;
+        WL_CU(cudaMemcpyAsync(&l, e.loss, 8, cudaMemcpyDeviceToHost, c->st), "copy loss");
+        if ((rc = enc_status(c))) return rc;   // synchronises (the order upload reads `docs`)
+        if (epoch_loss) epoch_loss[ep] = nb ? l / (double)nb : 0.0;
+    }
+    return check_record(c, "encoder training");
+}
+
+int warplda_encoder_proposal(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
+                             float* q_out) {
+    if (!c || !q_out) return fail(WARPLDA_EINVAL, "null argument");
+    if (!c->enc.ready) return fail(WARPLDA_ESTATE, "the encoder is not initialised");
+    int rc = check_docs(c, Dn, doc_ptr, doc_word);
+    if (rc) return rc;
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    FoldBuffers buf;
+    HostDocs hd;
+    if ((rc = upload_docs(c, buf, Dn, doc_ptr, doc_word, &hd))) return rc;
+    float* q;
+    WL_CU(buf.get(&q, Dn * (int64_t)c->K), "alloc proposals");
+    if ((rc = enc_proposal_dev(c, Dn, hd, q))) return rc;
+    if (Dn > 0)
+        WL_CU(cudaMemcpyAsync(q_out, q, (size_t)Dn * c->K * 4, cudaMemcpyDeviceToHost, c->st), "copy proposals");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    return WARPLDA_OK;
 }
 
 int warplda_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, const float* bias_dev,

@@ -82,7 +82,12 @@ __device__ __forceinline__ int fold_count(const uint32_t* tab, uint32_t cap, boo
                  : table_get(tab, cap, (uint32_t)k);
 }
 
-template <int M, bool kDense>
+// kLearned: the learned document proposal (the encoder's q through its alias
+// table) replaces positioning, and the word phase accepts it with the
+// independence-sampler rate min{1, p(t) q(s) / (p(s) q(t))} of Alg. 1,
+// p(k) = (C_dk + alpha)(C_wk + beta)/(c_k + beta_bar) with the word phase's
+// phase-start c_d (the oracle's readings L6-L7).
+template <int M, bool kDense, bool kLearned>
 __global__ void __launch_bounds__(kThreads) foldin_kernel(FoldArgs f, int tab_words) {
     extern __shared__ __align__(16) uint32_t fsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -151,15 +156,25 @@ __global__ void __launch_bounds__(kThreads) foldin_kernel(FoldArgs f, int tab_wo
                 z[j] = s;
             }
             __syncwarp();
-            // ... then positioning over the post-acceptance z_d
+            // ... then positioning over the post-acceptance z_d (or draws
+            // from the learned proposal's alias table)
+            const float* qd = kLearned ? f.q + (int64_t)d * K : nullptr;
+            const float* pd = kLearned ? f.aprob + (int64_t)d * K : nullptr;
+            const int32_t* ad = kLearned ? f.alias + (int64_t)d * K : nullptr;
             for (int j = lane; j < L; j += 32) {
 #pragma unroll
                 for (int i = 0; i < M; ++i) {
                     const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldDoc, (uint32_t)(i + 1), id, f.rk);
-                    prop[j * M + i] = coin(r.y, Lf, LG) ? z[dice(r.z, (uint32_t)L)] : (int)dice(r.z, (uint32_t)K);
+                    if (kLearned) {
+                        const int k = (int)dice(r.z, (uint32_t)K);
+                        prop[j * M + i] = u24(r.y) < __ldg(pd + k) ? k : (int)min((uint32_t)__ldg(ad + k), km);
+                    } else {
+                        prop[j * M + i] = coin(r.y, Lf, LG) ? z[dice(r.z, (uint32_t)L)] : (int)dice(r.z, (uint32_t)K);
+                    }
                 }
             }
             __syncwarp();
+            if (kLearned) build_table();   // the word phase's phase-start c_d
             // word phase against the frozen rows: accept, then a proposal
             // from the token's frozen row (one Philox block per step)
             for (int j = lane; j < L; j += 32) {
@@ -183,7 +198,21 @@ __global__ void __launch_bounds__(kThreads) foldin_kernel(FoldArgs f, int tab_wo
                     if (t != s) {
                         const int ct = __ldg(row + t);
                         const float kt = __ldg(f.ckb + t);
-                        if (accept(r.x, cs, ct, f.beta, ks, kt)) {
+                        bool acc;
+                        if (kLearned) {
+                            const float cds = __int2float_rn(fold_count(tab, cap, kDense, s));
+                            const float cdt = __int2float_rn(fold_count(tab, cap, kDense, t));
+                            const float num = __fmul_rn(__fmul_rn(__fmul_rn(__fadd_rn(cdt, f.alpha),
+                                                                            __fadd_rn(__int2float_rn(ct), f.beta)),
+                                                                  ks), __ldg(qd + s));
+                            const float den = __fmul_rn(__fmul_rn(__fmul_rn(__fadd_rn(cds, f.alpha),
+                                                                            __fadd_rn(__int2float_rn(cs), f.beta)),
+                                                                  kt), __ldg(qd + t));
+                            acc = __fmul_rn(u24(r.x), den) < num;
+                        } else {
+                            acc = accept(r.x, cs, ct, f.beta, ks, kt);
+                        }
+                        if (acc) {
                             s = t;
                             cs = ct;
                             ks = kt;
@@ -213,16 +242,16 @@ __global__ void __launch_bounds__(kThreads) foldin_kernel(FoldArgs f, int tab_wo
 }
 
 template <int M, bool kDense>
-static const void* fold_ptr() {
-    return (const void*)foldin_kernel<M, kDense>;
+static const void* fold_ptr(bool learned) {
+    return learned ? (const void*)foldin_kernel<M, kDense, true> : (const void*)foldin_kernel<M, kDense, false>;
 }
 
-static const void* fold_pick(int M, bool dense) {
+static const void* fold_pick(int M, bool dense, bool learned) {
     switch (M) {
-        case 1: return dense ? fold_ptr<1, true>() : fold_ptr<1, false>();
-        case 2: return dense ? fold_ptr<2, true>() : fold_ptr<2, false>();
-        case 3: return dense ? fold_ptr<3, true>() : fold_ptr<3, false>();
-        case 4: return dense ? fold_ptr<4, true>() : fold_ptr<4, false>();
+        case 1: return dense ? fold_ptr<1, true>(learned) : fold_ptr<1, false>(learned);
+        case 2: return dense ? fold_ptr<2, true>(learned) : fold_ptr<2, false>(learned);
+        case 3: return dense ? fold_ptr<3, true>(learned) : fold_ptr<3, false>(learned);
+        case 4: return dense ? fold_ptr<4, true>(learned) : fold_ptr<4, false>(learned);
         default: return nullptr;
     }
 }
@@ -236,7 +265,7 @@ int foldin_warps(int tab_words) {
 cudaError_t launch_foldin(const FoldArgs& f, int tab_words, int grid, cudaStream_t st) {
     if (f.Dn <= 0) return cudaSuccess;
     const bool dense = f.K <= kDenseMaxK;
-    const void* fn = fold_pick(f.M, dense);
+    const void* fn = fold_pick(f.M, dense, f.q != nullptr);
     const int warps = foldin_warps(tab_words);
     if (!fn || warps < 1) return cudaErrorInvalidValue;
     const int smem = warps * tab_words * 4;
@@ -249,7 +278,7 @@ cudaError_t launch_foldin(const FoldArgs& f, int tab_words, int grid, cudaStream
 }
 
 int foldin_blocks_per_sm(int K, int M, int tab_words) {
-    const void* fn = fold_pick(M, K <= kDenseMaxK);
+    const void* fn = fold_pick(M, K <= kDenseMaxK, false);
     const int warps = foldin_warps(tab_words);
     if (!fn || warps < 1) return 0;
     const int smem = warps * tab_words * 4;

@@ -52,6 +52,9 @@ struct FoldArgs {
     const int32_t* word_off; // [V + 1] token offsets of the words
     const float* ckb;        // [K] frozen (float)c_k + beta_bar
     float* theta;            // [Dn * K] or null
+    const float* q;          // learned proposal [Dn * K] or null (plain fold-in)
+    const float* aprob;      // its alias tables [Dn * K]
+    const int32_t* alias;
     int32_t* counter;        // work counter (zero on entry)
     int32_t* fault;          // index-check record
     int Dn, K, M, V, sweeps, Lmax;
@@ -74,6 +77,33 @@ cudaError_t launch_foldin(const FoldArgs& f, int tab_words, int grid, cudaStream
 int gemm_smem_bytes();
 cudaError_t launch_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, const float* bias,
                              int M, int N, int K, int32_t* status, cudaStream_t st);
+
+// Fold-in encoder (wl_encoder.cu).  A batch is rows r = 0..B-1 of document
+// docs[r] (r < nreal; the other rows are padding), tokens at
+// [doc_off[d], doc_off[d+1]) of words (document-major word ids).
+struct EncBatch {
+    const int32_t* docs;
+    const int32_t* doc_off;
+    const int32_t* words;
+    int nreal;
+};
+cudaError_t launch_enc_docword(const int32_t* perm, const int32_t* word_off, int64_t N, int64_t V,
+                               int32_t* out, cudaStream_t st);
+cudaError_t launch_enc_l1_fwd(const EncBatch& b, int B, const uint16_t* W1b, const float* b1, int H, int log2F,
+                              float* h_pre, uint16_t* hb, uint16_t* hbT, cudaStream_t st);
+cudaError_t launch_enc_softmax(const EncBatch& b, int B, const float* logits, int K, int Kp, float* q_out,
+                               const float* tgt, const int32_t* z, const int32_t* perm, float alpha, float abar,
+                               uint16_t* dl, uint16_t* dlT, float* gb2, double* loss, int32_t* cnt,
+                               cudaStream_t st);
+cudaError_t launch_enc_l1_bwd(const EncBatch& b, int B, const float* dH, const float* h_pre, int H, int log2F,
+                              float* gW1, float* gb1, cudaStream_t st);
+cudaError_t launch_enc_adam(float* w, float* m, float* v, const float* g, int64_t n, float lr, int step,
+                            uint16_t* wb, cudaStream_t st);
+cudaError_t launch_enc_w2_copies(const float* W2t, int Kp, int H, uint16_t* W2tb, uint16_t* W2nb,
+                                 cudaStream_t st);
+cudaError_t launch_enc_to_bf16(const float* x, int64_t n, uint16_t* y, cudaStream_t st);
+cudaError_t launch_enc_alias(const float* q, int64_t Dn, int K, float* prob, int32_t* alias, int32_t* stack,
+                             cudaStream_t st);
 
 // Initialisation, c_k, export, log-likelihood (wl_misc.cu).
 cudaError_t launch_init_z(int32_t* z, int32_t* prop, int64_t N, int K, int M, uint64_t seed,

@@ -69,6 +69,12 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double)]),
     "warplda_sync": (ctypes.c_int, [_P]),
+    "warplda_encoder_init": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_uint64]),
+    "warplda_encoder_weights": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P]),
+    "warplda_encoder_grad": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "warplda_encoder_train": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_float, ctypes.c_uint64, _P]),
+    "warplda_encoder_proposal": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
     "warplda_gemm_bf16": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int32, _P]),
     "warplda_foldin": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, ctypes.c_int32,
@@ -206,8 +212,9 @@ class WarpLDA:
         _check(load().warplda_load(self._h, path.encode()))
 
     def foldin(self, doc_ptr, doc_word, sweeps: int, seed: int, doc_ids=None,
-               theta: bool = True, z: bool = True):
-        """Fold in new documents against the current model: (theta[Dn, K], z[Nn])."""
+               theta: bool = True, z: bool = True, learned: bool = False):
+        """Fold in new documents against the current model: (theta[Dn, K], z[Nn]);
+        learned=True uses the encoder's proposal."""
         dp = np.ascontiguousarray(doc_ptr, dtype=np.int64)
         dw = np.ascontiguousarray(doc_word, dtype=np.int32)
         Dn, Nn = len(dp) - 1, int(dp[-1])
@@ -216,8 +223,57 @@ class WarpLDA:
         zo = np.empty(Nn, dtype=np.int32) if z else None
         ptr = lambda a: a.ctypes.data if a is not None and a.size else None
         _check(load().warplda_foldin(self._h, Dn, ptr(dp), ptr(dw), ptr(ids), int(sweeps),
-                                     int(seed), 0, ptr(th), ptr(zo)))
+                                     int(seed), 1 if learned else 0, ptr(th), ptr(zo)))
         return th, zo
+
+    # ---- fold-in encoder (learned document proposal) ----
+    def encoder_init(self, log2_features: int = 16, hidden: int = 512, batch_rows: int = 256,
+                     seed: int = 1) -> None:
+        self._enc = (int(log2_features), int(hidden))
+        _check(load().warplda_encoder_init(self._h, log2_features, hidden, batch_rows, int(seed)))
+
+    def encoder_weights(self, set_to=None):
+        F, H = 1 << self._enc[0], self._enc[1]
+        if set_to is not None:
+            W1, b1, W2, b2 = (np.ascontiguousarray(a, dtype=np.float32) for a in set_to)
+            _check(load().warplda_encoder_weights(self._h, 1, W1.ctypes.data, b1.ctypes.data,
+                                                  W2.ctypes.data, b2.ctypes.data))
+            return None
+        W1 = np.empty((F, H), np.float32)
+        b1 = np.empty(H, np.float32)
+        W2 = np.empty((H, self.K), np.float32)
+        b2 = np.empty(self.K, np.float32)
+        _check(load().warplda_encoder_weights(self._h, 0, W1.ctypes.data, b1.ctypes.data,
+                                              W2.ctypes.data, b2.ctypes.data))
+        return W1, b1, W2, b2
+
+    def encoder_grad(self, doc_ptr, doc_word, theta):
+        F, H = 1 << self._enc[0], self._enc[1]
+        dp = np.ascontiguousarray(doc_ptr, dtype=np.int64)
+        dw = np.ascontiguousarray(doc_word, dtype=np.int32)
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        loss = ctypes.c_double()
+        g = (np.empty((F, H), np.float32), np.empty(H, np.float32),
+             np.empty((H, self.K), np.float32), np.empty(self.K, np.float32))
+        _check(load().warplda_encoder_grad(self._h, len(dp) - 1, dp.ctypes.data, dw.ctypes.data,
+                                           th.ctypes.data, ctypes.byref(loss),
+                                           *(a.ctypes.data for a in g)))
+        return float(loss.value), g
+
+    def encoder_train(self, epochs: int, lr: float, seed: int = 1):
+        out = np.zeros(max(epochs, 1), np.float64)
+        _check(load().warplda_encoder_train(self._h, int(epochs), ctypes.c_float(lr), int(seed),
+                                            out.ctypes.data))
+        return out[:epochs]
+
+    def encoder_proposal(self, doc_ptr, doc_word):
+        dp = np.ascontiguousarray(doc_ptr, dtype=np.int64)
+        dw = np.ascontiguousarray(doc_word, dtype=np.int32)
+        q = np.empty((len(dp) - 1, self.K), np.float32)
+        _check(load().warplda_encoder_proposal(self._h, len(dp) - 1, dp.ctypes.data,
+                                               dw.ctypes.data if dw.size else None,
+                                               q.ctypes.data if q.size else None))
+        return q
 
     def sync(self) -> None:
         """Wait for queued work; raise if a kernel's index check failed."""
