@@ -192,6 +192,99 @@ def sample_docs(name: str) -> int | None:
     return {"nytimes": 300_000, "pubmed": 600_000, "tiny": None}.get(name)
 
 
+def heldout_split(rq):
+    """Document completion: even in-document positions are folded in, odd ones
+    are held out."""
+    obs_len, ho_len, obs, ho = [], [], [], []
+    for d in range(rq.D):
+        w = rq.doc_word[rq.doc_ptr[d]: rq.doc_ptr[d + 1]]
+        obs.append(w[0::2])
+        ho.append(w[1::2])
+        obs_len.append(len(w[0::2]))
+        ho_len.append(len(w[1::2]))
+    optr = np.concatenate([[0], np.cumsum(obs_len)]).astype(np.int64)
+    hptr = np.concatenate([[0], np.cumsum(ho_len)]).astype(np.int64)
+    return optr, np.concatenate(obs).astype(np.int32), hptr, np.concatenate(ho).astype(np.int32)
+
+
+def heldout_ll(theta, hptr, hwords, cw, ck, beta, bbar):
+    """Mean over held-out tokens of log sum_k theta_dk phi_wk, phi of Eq. 4."""
+    denom = ck.astype(np.float64) + bbar
+    tot, n = 0.0, 0
+    for d in range(len(hptr) - 1):
+        w = hwords[hptr[d]: hptr[d + 1]]
+        if len(w) == 0:
+            continue
+        phi = (cw[w].astype(np.float64) + beta) / denom
+        tot += float(np.log(phi @ theta[d].astype(np.float64)).sum())
+        n += len(w)
+    return tot / max(n, 1)
+
+
+def learned_curve(gpu, c, wl, name, seed, corpus_seed, n_req, sweeps):
+    """Held-out log-likelihood (document completion) after S fold-in sweeps,
+    plain vs learned, and the sweeps each needs to come within 0.5% of plain
+    fold-in's value at the largest S."""
+    from paper_1510_08628_gb300 import corpus
+    rq = corpus.requests(name, seed=corpus_seed, n=n_req, doc_offset=c.D + 700_000)
+    optr, owords, hptr, hwords = heldout_split(rq)
+    cw = gpu.word_counts()
+    _, ck = gpu.counts(want_z=False)
+    bbar = float(np.float32(c.V) * np.float32(wl.beta))
+    curve = {"plain": {}, "learned": {}}
+    for S in sweeps:
+        for kind in ("plain", "learned"):
+            th, _ = gpu.foldin(optr, owords, sweeps=S, seed=seed + 29, z=False,
+                               learned=(kind == "learned"))
+            curve[kind][S] = heldout_ll(th, hptr, hwords, cw, ck, wl.beta, bbar)
+    target = curve["plain"][sweeps[-1]]
+    tol = 0.005 * abs(target)
+    need = {k: next((S for S in sweeps if curve[k][S] >= target - tol), None) for k in curve}
+    return {"docs": rq.D, "split": "even positions folded in, odd held out",
+            "ll_per_token": {k: {str(S): v for S, v in curve[k].items()} for k in curve},
+            "target": "plain fold-in after %d sweeps, within 0.5%%" % sweeps[-1],
+            "sweeps_to_target": need}
+
+
+def learned_bench(gpu, c, wl, args):
+    """The learned document proposal for fold-in: encoder training on the
+    corpus's own (document, theta) pairs, then held-out log-likelihood after
+    S fold-in sweeps, plain vs learned, and fold-in throughput; the same
+    curve on the tiny workload (16 strongly separated topics), where the
+    generator leaves more topic signal in the words."""
+    from paper_1510_08628_gb300 import corpus
+    from paper_1510_08628_gb300.warplda import WarpLDA
+    gpu.encoder_init(log2_features=16, hidden=512, batch_rows=256, seed=args.seed)
+    t = time.perf_counter()
+    losses = gpu.encoder_train(epochs=args.encoder_epochs, lr=1e-3, seed=args.seed)
+    train_s = time.perf_counter() - t
+    heldout = learned_curve(gpu, c, wl, args.workload, args.seed, args.corpus_seed, 1000,
+                            [1, 2, 3, 4, 6, 8, 12, 16, 24, 30])
+    ct, wt = corpus.generate("tiny", seed=1)
+    gt = WarpLDA(ct.doc_ptr, ct.doc_word, ct.V, wt.K, wt.alpha, wt.beta, 2, 7)
+    gt.sweep(200)
+    gt.encoder_init(log2_features=12, hidden=128, batch_rows=256, seed=3)
+    tl = gt.encoder_train(epochs=60, lr=3e-3, seed=4)
+    tiny = learned_curve(gt, ct, wt, "tiny", 71, 1, 500, [1, 2, 3, 4, 8, 16])
+    tiny["encoder_loss"] = [float(tl[0]), float(tl[-1])]
+    tiny["model"] = "tiny workload (D=1000, K=16, M=2), 200 sweeps; encoder 2^12 features, 128 hidden, 60 epochs"
+    gt.close()
+
+    # throughput of the learned fold-in (encoder forward + alias tables + sweeps)
+    big = corpus.requests(args.workload, seed=args.corpus_seed, n=args.foldin_docs,
+                          doc_offset=c.D + 1000)
+    t = time.perf_counter()
+    gpu.foldin(big.doc_ptr, big.doc_word, sweeps=args.foldin_sweeps, seed=args.seed + 17, z=False,
+               learned=True)
+    wall = time.perf_counter() - t
+    return {"encoder": {"features": 1 << 16, "hidden": 512, "K": wl.K, "epochs": args.encoder_epochs,
+                        "train_seconds": train_s, "epoch_loss": [float(x) for x in losses],
+                        "pairs": "the corpus's own documents with theta of Eq. 4 of the current z"},
+            "heldout": heldout, "heldout_tiny": tiny,
+            "docs_per_s": big.D / wall, "docs": big.D, "sweeps": args.foldin_sweeps,
+            "includes": "encoder forward + alias tables + fold-in kernel + H2D/D2H (C ABI call)"}
+
+
 def foldin_bench(gpu, c, wl, args, torch, stream):
     """Fold-in of unseen documents of the workload's generator (lengths
     clipped to [20, 5000]) against the trained model: docs/s end to end
@@ -282,6 +375,10 @@ def main():
     ap.add_argument("--foldin-docs", type=int, default=20000,
                     help="fold-in requests timed after the sweeps (0: none)")
     ap.add_argument("--foldin-sweeps", type=int, default=30)
+    ap.add_argument("--model-sweeps", type=int, default=100,
+                    help="sweeps the model has when the fold-in measurements start")
+    ap.add_argument("--encoder-epochs", type=int, default=4,
+                    help="epochs of encoder training for the learned fold-in proposal (0: skip)")
     ap.add_argument("--docs", type=int, default=0,
                     help="use only the first DOCS documents of the workload (small profiling cases)")
     args = ap.parse_args()
@@ -383,7 +480,11 @@ def main():
 
     foldin = None
     if args.foldin_docs > 0 and rank == 0:
+        gpu.sweep(max(0, args.model_sweeps - (args.warmup + 2 * args.steps)))   # train the model
         foldin = foldin_bench(gpu, c, wl, args, torch, stream)
+        foldin["model_sweeps"] = max(args.model_sweeps, args.warmup + 2 * args.steps)
+        if args.encoder_epochs > 0:
+            foldin["learned"] = learned_bench(gpu, c, wl, args)
 
     # end to end through the C ABI from pinned host buffers: init (H2D of the
     # corpus, token-order build) + K sweeps + D2H of z and c_k

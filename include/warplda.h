@@ -224,6 +224,14 @@ int warplda_foldin(warplda_ctx* ctx, int64_t Dn, const int64_t* doc_ptr, const i
                    float* theta_out, int32_t* z_out);
 
 /*
+ * warplda_word_counts -- the word-topic counts C_w of the current state
+ * (Sec. 2.1): host int32[V*K], row-major by word.  This is the frozen model
+ * fold-in uses (built on the device, kept until the context sweeps again).
+ * Errors: EINVAL, ESTATE (a word phase is pending), ENOMEM, ECUDA.
+ */
+int warplda_word_counts(warplda_ctx* ctx, int32_t* cw);
+
+/*
  * The fold-in encoder: the learned document proposal of fold-in (the paper
  * has no counterpart).  A document's input is its hashed bag of words,
  * x_f = (# tokens whose word w has f(w) = ((w * 2654435761) mod 2^32) >>

@@ -585,6 +585,22 @@ int enc_proposal_dev(warplda_ctx* c, int64_t Dn, const HostDocs& hd, float* q_de
     return enc_status(c);
 }
 
+// Builds the fold-in model of the current state if it is stale.
+int ensure_model(warplda_ctx* c) {
+    if (c->model_iter == (int64_t)c->iter) return WARPLDA_OK;
+    const int K = c->K;
+    int rc;
+    if (!c->model_cw && (rc = dalloc(c, &c->model_cw, c->V * (int64_t)K, "alloc fold-in model"))) return rc;
+    if (!c->model_zs && (rc = dalloc(c, &c->model_zs, c->N + 4, "alloc fold-in topics"))) return rc;
+    if (!c->model_ckb && (rc = dalloc(c, &c->model_ckb, K, "alloc fold-in c_k"))) return rc;
+    WL_CU(launch_model_build(c->z, c->word_off, c->V, K, c->model_cw, c->model_zs, c->d_fault, 4 * c->sms,
+                             c->st), "build fold-in model");
+    WL_CU(cudaMemcpyAsync(c->model_ckb, c->ckb, (size_t)K * sizeof(float), cudaMemcpyDeviceToDevice, c->st),
+          "copy c_k");
+    c->model_iter = c->iter;
+    return WARPLDA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1069,17 +1085,9 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
 
     // the frozen model: C_w prefix rows and c_k of the current state
-    if (c->model_iter != (int64_t)c->iter) {
-        int rc;
-        if (!c->model_cw && (rc = dalloc(c, &c->model_cw, c->V * (int64_t)K, "alloc fold-in model")))
-            return rc;
-        if (!c->model_zs && (rc = dalloc(c, &c->model_zs, c->N + 4, "alloc fold-in topics"))) return rc;
-        if (!c->model_ckb && (rc = dalloc(c, &c->model_ckb, K, "alloc fold-in c_k"))) return rc;
-        WL_CU(launch_model_build(c->z, c->word_off, c->V, K, c->model_cw, c->model_zs, c->d_fault,
-                                 4 * c->sms, c->st), "build fold-in model");
-        WL_CU(cudaMemcpyAsync(c->model_ckb, c->ckb, (size_t)K * sizeof(float), cudaMemcpyDeviceToDevice,
-                              c->st), "copy c_k");
-        c->model_iter = c->iter;
+    {
+        int rc = ensure_model(c);
+        if (rc) return rc;
     }
 
     // documents longest first, so that the long ones start early
@@ -1174,6 +1182,17 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
         WL_CU(cudaMemcpyAsync(theta_out, d_theta, (size_t)Dn * K * 4, cudaMemcpyDeviceToHost, c->st), "copy theta");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     return check_record(c, "fold-in");
+}
+
+int warplda_word_counts(warplda_ctx* c, int32_t* cw) {
+    if (!c || !cw) return fail(WARPLDA_EINVAL, "null argument");
+    if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    int rc = ensure_model(c);
+    if (rc) return rc;
+    WL_CU(cudaMemcpyAsync(cw, c->model_cw, (size_t)c->V * c->K * 4, cudaMemcpyDeviceToHost, c->st), "copy C_w");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    return check_record(c, "word counts");
 }
 
 static uint64_t splitmix64(uint64_t* x) {

@@ -69,6 +69,7 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double)]),
     "warplda_sync": (ctypes.c_int, [_P]),
+    "warplda_word_counts": (ctypes.c_int, [_P, _P]),
     "warplda_encoder_init": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_uint64]),
     "warplda_encoder_weights": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P]),
@@ -274,6 +275,12 @@ class WarpLDA:
                                                dw.ctypes.data if dw.size else None,
                                                q.ctypes.data if q.size else None))
         return q
+
+    def word_counts(self):
+        """C_w [V, K] (int32) of the current state."""
+        cw = np.empty((self.V, self.K), np.int32)
+        _check(load().warplda_word_counts(self._h, cw.ctypes.data))
+        return cw
 
     def sync(self) -> None:
         """Wait for queued work; raise if a kernel's index check failed."""

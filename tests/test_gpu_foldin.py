@@ -85,3 +85,8 @@ def test_foldin_rejects_bad_input():
         g.foldin(dp, dw, sweeps=1, seed=1)
     th, z = g.foldin(np.array([0]), np.zeros(0, np.int32), sweeps=3, seed=1)
     assert th.shape == (0, 3000) and z.shape == (0,)
+
+
+def test_word_counts_match_oracle():
+    g, o, cw, c, wl = _model(40, 2, sweeps=3)
+    assert np.array_equal(g.word_counts(), cw)
