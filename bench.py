@@ -285,6 +285,48 @@ def learned_bench(gpu, c, wl, args):
             "includes": "encoder forward + alias tables + fold-in kernel + H2D/D2H (C ABI call)"}
 
 
+def serving_bench(gpu, c, wl, args, learned: bool, rate: float, n: int = 6000):
+    """Fold-in requests arriving as a Poisson stream at `rate` docs/s, served
+    with continuous batching (warplda_server_*): each step advances every
+    admitted request by one sweep; requests arriving meanwhile join the next
+    step.  Latency = completion (poll) time - arrival time."""
+    from paper_1510_08628_gb300 import corpus
+    from paper_1510_08628_gb300.warplda import Server
+    rq = corpus.requests(args.workload, seed=args.corpus_seed, n=n, doc_offset=c.D + 2_000_000)
+    rng = np.random.default_rng(args.seed)
+    arrive = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    S = args.foldin_sweeps
+    srv = Server(gpu, slots=8192, pool_tokens=4_000_000, max_doc_tokens=5000, sweeps=S,
+                 seed=args.seed + 41, learned=learned)
+    lat = np.zeros(n)
+    got, nxt, queue, steps = 0, 0, [], 0
+    t0 = time.perf_counter()
+    while got < n:
+        now = time.perf_counter() - t0
+        while nxt < n and arrive[nxt] <= now:
+            queue.append(nxt)
+            nxt += 1
+        while queue:
+            d = queue[0]
+            if not srv.submit(d, rq.doc_word[rq.doc_ptr[d]: rq.doc_ptr[d + 1]]):
+                break
+            queue.pop(0)
+        active = srv.step()
+        steps += 1
+        ids, _ = srv.poll()
+        t = time.perf_counter() - t0
+        for i in ids:
+            lat[int(i)] = t - arrive[int(i)]
+        got += len(ids)
+        if active == 0 and not queue and nxt < n:
+            time.sleep(max(0.0, min(0.001, arrive[nxt] - (time.perf_counter() - t0))))
+    wall = time.perf_counter() - t0
+    srv.close()
+    return {"proposal": "learned" if learned else "plain", "offered_docs_per_s": rate, "docs": n,
+            "sweeps": S, "docs_per_s": n / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "steps": steps}
+
+
 def foldin_bench(gpu, c, wl, args, torch, stream):
     """Fold-in of unseen documents of the workload's generator (lengths
     clipped to [20, 5000]) against the trained model: docs/s end to end
@@ -485,6 +527,12 @@ def main():
         foldin["model_sweeps"] = max(args.model_sweeps, args.warmup + 2 * args.steps)
         if args.encoder_epochs > 0:
             foldin["learned"] = learned_bench(gpu, c, wl, args)
+        # serving at equal load for both proposals: half the plain fold-in's
+        # measured throughput, capped
+        rate = min(0.5 * foldin["docs_per_s"], 100_000.0)
+        foldin["serving"] = [serving_bench(gpu, c, wl, args, False, rate)]
+        if args.encoder_epochs > 0:
+            foldin["serving"].append(serving_bench(gpu, c, wl, args, True, rate))
 
     # end to end through the C ABI from pinned host buffers: init (H2D of the
     # corpus, token-order build) + K sweeps + D2H of z and c_k

@@ -42,11 +42,13 @@ extern "C" {
 #define WARPLDA_ETIMEDOUT (-4) /* a bounded device wait gave up */
 #define WARPLDA_ESTATE (-5)    /* call not valid in the context's state */
 #define WARPLDA_EIO (-6)       /* checkpoint file could not be read or written */
+#define WARPLDA_EBUSY (-7)     /* no serving slot or pool memory free now: retry later */
 
 #define WARPLDA_PHASE_DOC 1
 #define WARPLDA_PHASE_WORD 2
 
 typedef struct warplda_ctx warplda_ctx;
+typedef struct warplda_server warplda_server;
 
 /*
  * Launch tuning.  Any field left 0 takes its default.  Results are identical
@@ -265,6 +267,41 @@ int warplda_encoder_grad(warplda_ctx* ctx, int64_t Dn, const int64_t* doc_ptr, c
 int warplda_encoder_train(warplda_ctx* ctx, int32_t epochs, float lr, uint64_t seed, double* epoch_loss);
 int warplda_encoder_proposal(warplda_ctx* ctx, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
                              float* q_out);
+
+/*
+ * Serving fold-in requests with continuous batching (the paper has no
+ * counterpart).  The context's model is frozen when the server is created
+ * (as for warplda_foldin); each request is one new document, folded in for
+ * `sweeps` sweeps exactly as warplda_foldin would fold it in with doc id =
+ * the request id and the same seed and proposal -- bit for bit, alone or in
+ * any mix.  Per-request z, proposals and theta stay on the device.
+ *
+ * warplda_server_create -- `slots` requests in flight at most; a device
+ *   token pool of pool_tokens (each admitted request holds L_d contiguous
+ *   tokens until its result is polled); requests of at most max_doc_tokens
+ *   (<= 65535 when K <= 2048, <= 4095 above).  Errors: EINVAL, ESTATE,
+ *   ENOMEM, ECUDA.
+ * warplda_server_submit -- admit request `id` (host word ids words[L], in
+ *   [0, V); copied).  Returns OK, or EBUSY when no slot or no contiguous
+ *   pool range is free: admission is by memory, the caller retries after a
+ *   poll has retired finished requests.
+ * warplda_server_step -- launch one sweep for every admitted, unfinished
+ *   request (new ones are initialised first; a request's last sweep also
+ *   writes its theta); asynchronous.  *active_out (or NULL) = requests
+ *   advanced.  Requests admitted while a step runs join the next step.
+ * warplda_server_poll -- wait at most timeout_ms for the last step (else
+ *   ETIMEDOUT), then hand over up to max_results finished requests: ids[n]
+ *   and theta[n*K] (Eq. 4), *n_out = n; their slots and pool memory are
+ *   freed.
+ * warplda_server_destroy -- wait for the stream and free the server.
+ */
+int warplda_server_create(warplda_ctx* ctx, int32_t slots, int64_t pool_tokens, int32_t max_doc_tokens,
+                          int32_t sweeps, uint64_t seed, int32_t proposal, warplda_server** out);
+int warplda_server_submit(warplda_server* srv, int64_t id, int32_t L, const int32_t* words);
+int warplda_server_step(warplda_server* srv, int32_t* active_out);
+int warplda_server_poll(warplda_server* srv, int32_t max_results, int64_t* ids, float* theta, int32_t* n_out,
+                        int32_t timeout_ms);
+void warplda_server_destroy(warplda_server* srv);
 
 /*
  * warplda_gemm_bf16 -- the tensor-core (tcgen05) GEMM of the fold-in

@@ -178,5 +178,5 @@ def requests(name: str, seed: int, n: int, doc_offset: int, lo: int = 20, hi: in
     apart from the training corpus."""
     wl = WORKLOADS[name]
     model = TopicModel(wl.V, wl.K_true, wl.zipf_s, wl.conc_c, seed)
-    lens = lengths(n, wl.len_kind, wl.len_mean, wl.len_sigma, seed, doc_offset, lo, hi)
+    lens = np.clip(lengths(n, wl.len_kind, wl.len_mean, wl.len_sigma, seed, doc_offset), lo, hi)
     return generate_docs(model, lens, wl.doc_alpha, seed, doc_offset)

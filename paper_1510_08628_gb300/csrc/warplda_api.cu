@@ -12,6 +12,9 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <thread>
+#include <chrono>
+#include <map>
 
 #include "../../include/warplda.h"
 #include "wl_kernels.h"
@@ -598,6 +601,140 @@ int ensure_model(warplda_ctx* c) {
     WL_CU(cudaMemcpyAsync(c->model_ckb, c->ckb, (size_t)K * sizeof(float), cudaMemcpyDeviceToDevice, c->st),
           "copy c_k");
     c->model_iter = c->iter;
+    return WARPLDA_OK;
+}
+
+}  // namespace
+
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching of fold-in requests.
+// ---------------------------------------------------------------------------
+struct warplda_server {
+    warplda_ctx* c = nullptr;
+    int nslots = 0, sweeps = 0, proposal = 0, max_tokens = 0, tab_words = 0, grid = 1;
+    int64_t pool_tokens = 0;
+    uint64_t seed = 0;
+    int4* d_info = nullptr;
+    int32_t *d_active = nullptr, *d_z = nullptr, *d_prop = nullptr, *d_words = nullptr, *d_counter = nullptr;
+    float *d_theta = nullptr, *d_q = nullptr, *d_prob = nullptr;
+    int32_t* d_alias = nullptr;
+    float* h_theta = nullptr;   // pinned staging of finished rows [nslots * K]
+    cudaEvent_t tick = nullptr;
+    struct Slot {
+        bool used = false, fresh = false;
+        int64_t id = 0;
+        int32_t off = 0, L = 0, done = 0;
+        std::vector<int32_t> words;   // kept until the proposal rows are made (learned)
+    };
+    std::vector<Slot> slots;
+    std::vector<int32_t> free_slots;
+    std::map<int64_t, int64_t> free_ranges;   // pool start -> length
+    std::vector<int32_t> finished;             // slots whose theta is staged
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+// First fit in the token pool; -1 if no free range is long enough.
+int64_t pool_take(warplda_server* s, int64_t n) {
+    for (auto it = s->free_ranges.begin(); it != s->free_ranges.end(); ++it) {
+        if (it->second < n) continue;
+        const int64_t start = it->first, len = it->second;
+        s->free_ranges.erase(it);
+        if (len > n) s->free_ranges[start + n] = len - n;
+        return start;
+    }
+    return -1;
+}
+
+void pool_give(warplda_server* s, int64_t start, int64_t n) {
+    if (n <= 0) return;
+    auto it = s->free_ranges.emplace(start, n).first;
+    auto nx = std::next(it);
+    if (nx != s->free_ranges.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        s->free_ranges.erase(nx);
+    }
+    if (it != s->free_ranges.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            s->free_ranges.erase(it);
+        }
+    }
+}
+
+template <typename T>
+int salloc(warplda_server* s, T** p, int64_t n) {
+    cudaError_t e = cudaMalloc((void**)p, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(e, "alloc server");
+    s->allocs.push_back(*p);
+    return WARPLDA_OK;
+}
+
+void server_free(warplda_server* s) {
+    for (void* p : s->allocs) cudaFree(p);
+    s->allocs.clear();
+    if (s->h_theta) cudaFreeHost(s->h_theta);
+    if (s->tick) cudaEventDestroy(s->tick);
+}
+
+FoldArgs server_args(warplda_server* s) {
+    warplda_ctx* c = s->c;
+    FoldArgs f{};
+    f.Cw = c->model_cw;
+    f.Zs = c->model_zs;
+    f.word_off = c->word_off;
+    f.ckb = c->model_ckb;
+    f.counter = s->d_counter;
+    f.fault = c->d_fault;
+    f.K = c->K;
+    f.M = c->M;
+    f.V = (int)c->V;
+    f.sweeps = s->sweeps;
+    f.Lmax = s->max_tokens;
+    f.alpha = c->alpha;
+    f.abar = c->abar;
+    f.beta = c->beta;
+    f.kbeta = c->kbeta;
+    f.rk = round_keys(s->seed);
+    return f;
+}
+
+// Proposal rows and alias tables of the requests admitted since the last
+// step (learned proposal): the encoder runs on a CSR of their words.
+int server_proposals(warplda_server* s, const std::vector<int32_t>& fresh) {
+    warplda_ctx* c = s->c;
+    const int K = c->K;
+    std::vector<int64_t> ptr(1, 0);
+    std::vector<int32_t> words;
+    for (int32_t sl : fresh) {
+        const auto& w = s->slots[sl].words;
+        words.insert(words.end(), w.begin(), w.end());
+        ptr.push_back((int64_t)words.size());
+    }
+    const int64_t Dn = (int64_t)fresh.size();
+    FoldBuffers buf;
+    HostDocs hd;
+    int rc = upload_docs(c, buf, Dn, ptr.data(), words.data(), &hd);
+    if (rc) return rc;
+    float *q, *prob;
+    int32_t *alias, *stack;
+    WL_CU(buf.get(&q, Dn * K), "alloc proposals");
+    WL_CU(buf.get(&prob, Dn * K), "alloc alias tables");
+    WL_CU(buf.get(&alias, Dn * K), "alloc alias tables");
+    WL_CU(buf.get(&stack, Dn * K), "alloc alias scratch");
+    if ((rc = enc_proposal_dev(c, Dn, hd, q))) return rc;
+    WL_CU(launch_enc_alias(q, Dn, K, prob, alias, stack, c->st), "alias tables");
+    for (int64_t i = 0; i < Dn; ++i) {
+        const int64_t sl = fresh[i];
+        WL_CU(cudaMemcpyAsync(s->d_q + sl * K, q + i * K, (size_t)K * 4, cudaMemcpyDeviceToDevice, c->st), "copy q");
+        WL_CU(cudaMemcpyAsync(s->d_prob + sl * K, prob + i * K, (size_t)K * 4, cudaMemcpyDeviceToDevice, c->st), "copy alias");
+        WL_CU(cudaMemcpyAsync(s->d_alias + sl * K, alias + i * K, (size_t)K * 4, cudaMemcpyDeviceToDevice, c->st), "copy alias");
+    }
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");   // the temporaries are freed on return
+    for (int32_t sl : fresh) std::vector<int32_t>().swap(s->slots[sl].words);
     return WARPLDA_OK;
 }
 
@@ -1401,6 +1538,185 @@ int warplda_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, const 
     if (e != cudaSuccess) return cuda_fail(e, "GEMM");
     if (h) return fail(WARPLDA_ETIMEDOUT, "GEMM: a tensor-core wait ran out");
     return WARPLDA_OK;
+}
+
+
+int warplda_server_create(warplda_ctx* c, int32_t slots, int64_t pool_tokens, int32_t max_doc_tokens,
+                          int32_t sweeps, uint64_t seed, int32_t proposal, warplda_server** out) {
+    if (!c || !out) return fail(WARPLDA_EINVAL, "null argument");
+    *out = nullptr;
+    if (slots < 1 || slots > (1 << 20) || pool_tokens < 1 || pool_tokens > (int64_t)0x7FFFFFF0 || sweeps < 1 ||
+        max_doc_tokens < 1)
+        return fail(WARPLDA_EINVAL, "bad server sizes");
+    const int Lcap = c->K <= kDenseMaxK ? 65535 : (1 << kHashCountBits) - 1;
+    if (max_doc_tokens > Lcap) return fail(WARPLDA_EINVAL, "max_doc_tokens above %d", Lcap);
+    if (proposal != WARPLDA_PROPOSAL_PLAIN && proposal != WARPLDA_PROPOSAL_LEARNED)
+        return fail(WARPLDA_EINVAL, "unknown proposal %d", proposal);
+    if (proposal == WARPLDA_PROPOSAL_LEARNED && !c->enc.ready)
+        return fail(WARPLDA_ESTATE, "the learned proposal needs an initialised encoder");
+    if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    int rc = ensure_model(c);
+    if (rc) return rc;
+    auto* s = new warplda_server();
+    s->c = c;
+    s->nslots = slots;
+    s->pool_tokens = pool_tokens;
+    s->max_tokens = max_doc_tokens;
+    s->sweeps = sweeps;
+    s->seed = seed;
+    s->proposal = proposal;
+    const int K = c->K, M = c->M;
+    auto bail = [&](int code) {
+        server_free(s);
+        delete s;
+        return code;
+    };
+    if ((rc = salloc(s, &s->d_info, slots)) || (rc = salloc(s, &s->d_active, slots)) ||
+        (rc = salloc(s, &s->d_z, pool_tokens + 4)) || (rc = salloc(s, &s->d_prop, (pool_tokens + 4) * M)) ||
+        (rc = salloc(s, &s->d_words, pool_tokens + 4)) || (rc = salloc(s, &s->d_counter, 1)) ||
+        (rc = salloc(s, &s->d_theta, (int64_t)slots * K)))
+        return bail(rc);
+    if (proposal == WARPLDA_PROPOSAL_LEARNED &&
+        ((rc = salloc(s, &s->d_q, (int64_t)slots * K)) || (rc = salloc(s, &s->d_prob, (int64_t)slots * K)) ||
+         (rc = salloc(s, &s->d_alias, (int64_t)slots * K))))
+        return bail(rc);
+    if (cudaMallocHost((void**)&s->h_theta, (size_t)slots * K * 4) != cudaSuccess)
+        return bail(fail(WARPLDA_ENOMEM, "pinned staging"));
+    if (cudaEventCreateWithFlags(&s->tick, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(WARPLDA_ECUDA, "event"));
+    s->slots.resize(slots);
+    for (int i = slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->free_ranges[0] = pool_tokens;
+    s->tab_words = foldin_table_words(K, max_doc_tokens);
+    const int per_sm = foldin_blocks_per_sm(K, M, s->tab_words);
+    if (per_sm < 1) return bail(fail(WARPLDA_EINVAL, "serving tables do not fit in shared memory"));
+    s->grid = per_sm * c->sms;
+    *out = s;
+    return WARPLDA_OK;
+}
+
+int warplda_server_submit(warplda_server* s, int64_t id, int32_t L, const int32_t* words) {
+    if (!s || L < 0 || (L > 0 && !words)) return fail(WARPLDA_EINVAL, "bad request");
+    warplda_ctx* c = s->c;
+    if (L > s->max_tokens) return fail(WARPLDA_EINVAL, "request longer than max_doc_tokens");
+    for (int32_t j = 0; j < L; ++j)
+        if (words[j] < 0 || (int64_t)words[j] >= c->V) return fail(WARPLDA_EINVAL, "word id outside [0, V)");
+    if (s->free_slots.empty()) return WARPLDA_EBUSY;
+    const int64_t off = pool_take(s, std::max(L, 1));
+    if (off < 0) return WARPLDA_EBUSY;   // admission by memory
+    const int32_t sl = s->free_slots.back();
+    s->free_slots.pop_back();
+    auto& S = s->slots[sl];
+    S.used = true;
+    S.fresh = true;
+    S.id = id;
+    S.off = (int32_t)off;
+    S.L = L;
+    S.done = 0;
+    if (s->proposal == WARPLDA_PROPOSAL_LEARNED) S.words.assign(words, words + L);
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    if (L > 0)
+        WL_CU(cudaMemcpyAsync(s->d_words + off, words, (size_t)L * 4, cudaMemcpyHostToDevice, c->st), "upload request");
+    const int4 info = make_int4((int)off, L, 0, (int)(uint32_t)id);
+    WL_CU(cudaMemcpyAsync(s->d_info + sl, &info, sizeof(int4), cudaMemcpyHostToDevice, c->st), "upload slot");
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");   // sources are the caller's and the stack's
+    return WARPLDA_OK;
+}
+
+int warplda_server_step(warplda_server* s, int32_t* active_out) {
+    if (!s) return fail(WARPLDA_EINVAL, "null server");
+    warplda_ctx* c = s->c;
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    std::vector<int32_t> active, fresh;
+    for (int i = 0; i < s->nslots; ++i) {
+        const auto& S = s->slots[i];
+        if (!S.used || S.done >= s->sweeps) continue;
+        active.push_back(i);
+        if (S.fresh && s->proposal == WARPLDA_PROPOSAL_LEARNED) fresh.push_back(i);
+    }
+    if (active_out) *active_out = (int32_t)active.size();
+    if (active.empty()) return WARPLDA_OK;
+    int rc;
+    if (!fresh.empty() && (rc = server_proposals(s, fresh))) return rc;
+    for (int32_t i : active) s->slots[i].fresh = false;
+    WL_CU(cudaMemcpyAsync(s->d_active, active.data(), active.size() * 4, cudaMemcpyHostToDevice, c->st), "upload active");
+    WL_CU(cudaMemsetAsync(s->d_counter, 0, 4, c->st), "reset counter");
+    FoldArgs f = server_args(s);
+    ServeSlots sl{};
+    sl.info = s->d_info;
+    sl.active = s->d_active;
+    sl.nactive = (int)active.size();
+    sl.nslots = s->nslots;
+    sl.pool_tokens = s->pool_tokens;
+    sl.z = s->d_z;
+    sl.prop = s->d_prop;
+    sl.words = s->d_words;
+    sl.theta = s->d_theta;
+    sl.q = s->d_q;
+    sl.prob = s->d_prob;
+    sl.alias = s->d_alias;
+    const int grid = (int)std::min<int64_t>(s->grid, ((int64_t)active.size() + kWarps - 1) / kWarps + 1);
+    WL_CU(launch_serve(f, sl, s->tab_words, grid, c->st), "serve");
+    for (int32_t i : active) {
+        auto& S = s->slots[i];
+        S.done += 1;
+        if (S.done >= s->sweeps) {
+            WL_CU(cudaMemcpyAsync(s->h_theta + (int64_t)i * c->K, s->d_theta + (int64_t)i * c->K,
+                                  (size_t)c->K * 4, cudaMemcpyDeviceToHost, c->st), "stage theta");
+            s->finished.push_back(i);
+        }
+    }
+    WL_CU(cudaEventRecord(s->tick, c->st), "record tick");
+    return WARPLDA_OK;
+}
+
+int warplda_server_poll(warplda_server* s, int32_t max_results, int64_t* ids, float* theta, int32_t* n_out,
+                        int32_t timeout_ms) {
+    if (!s || !n_out || max_results < 0 || (max_results > 0 && (!ids || !theta)))
+        return fail(WARPLDA_EINVAL, "bad poll arguments");
+    *n_out = 0;
+    warplda_ctx* c = s->c;
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    // bounded wait for the last step
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(s->tick);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "serve step");
+        const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+        if (ms > timeout_ms) return fail(WARPLDA_ETIMEDOUT, "a serving step did not finish within %d ms", timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    int rc = check_record(c, "serving");
+    if (rc) return rc;
+    const int K = c->K;
+    int n = 0;
+    std::vector<int32_t> keep;
+    for (int32_t i : s->finished) {
+        if (n >= max_results) {
+            keep.push_back(i);
+            continue;
+        }
+        auto& S = s->slots[i];
+        ids[n] = S.id;
+        std::memcpy(theta + (int64_t)n * K, s->h_theta + (int64_t)i * K, (size_t)K * 4);
+        pool_give(s, S.off, std::max(S.L, 1));
+        S.used = false;
+        s->free_slots.push_back(i);
+        ++n;
+    }
+    s->finished.swap(keep);
+    *n_out = n;
+    return WARPLDA_OK;
+}
+
+void warplda_server_destroy(warplda_server* s) {
+    if (!s) return;
+    cudaSetDevice(s->c->dev);
+    cudaStreamSynchronize(s->c->st);
+    server_free(s);
+    delete s;
 }
 
 int warplda_sync(warplda_ctx* c) {

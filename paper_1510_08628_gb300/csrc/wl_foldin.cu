@@ -70,7 +70,8 @@ cudaError_t launch_model_build(const int32_t* z, const int32_t* word_off, int64_
 }
 
 // ---------------------------------------------------------------------------
-// The fold-in kernel.
+// The fold-in sweep of one document by one warp (shared by the batch fold-in
+// kernel and the serving kernel).
 // ---------------------------------------------------------------------------
 int foldin_table_words(int K, int Lmax) {
     if (K <= kDenseMaxK) return ((K + 1) / 2 + 3) & ~3;
@@ -82,18 +83,173 @@ __device__ __forceinline__ int fold_count(const uint32_t* tab, uint32_t cap, boo
                  : table_get(tab, cap, (uint32_t)k);
 }
 
-// kLearned: the learned document proposal (the encoder's q through its alias
-// table) replaces positioning, and the word phase accepts it with the
-// independence-sampler rate min{1, p(t) q(s) / (p(s) q(t))} of Alg. 1,
-// p(k) = (C_dk + alpha)(C_wk + beta)/(c_k + beta_bar) with the word phase's
-// phase-start c_d (the oracle's readings L6-L7).
+// One document's state: its tokens' word ids, z and proposals (document
+// order), its stream id, and (learned proposal) its proposal row and alias
+// table.
+struct FoldDoc {
+    int32_t* z;
+    int32_t* prop;
+    const int32_t* words;
+    int L;
+    uint32_t id;
+    const float* q;
+    const float* prob;
+    const int32_t* alias;
+};
+
+// The warp's count table of the document's current z (dense, or a hash of
+// capacity cap).
+template <bool kDense>
+__device__ __forceinline__ void fold_table(uint32_t* tab, int words, uint32_t cap, const FoldDoc& doc,
+                                           uint32_t km, int lane) {
+    for (int i = lane; i < words; i += 32) tab[i] = 0u;
+    __syncwarp();
+    for (int j = lane; j < doc.L; j += 32) {
+        const uint32_t k = min((uint32_t)doc.z[j], km);
+        if (kDense) atomicAdd(&tab[k >> 1], (k & 1) ? 65536u : 1u);
+        else table_add(tab, cap, k);
+    }
+    __syncwarp();
+}
+
+// Initialisation: z = Dice(K), proposals = z.
+template <int M>
+__device__ __forceinline__ void fold_init(const FoldArgs& f, const FoldDoc& doc, int lane) {
+    for (int j = lane; j < doc.L; j += 32) {
+        const uint4 r = draw((uint32_t)j, 0u, kPhaseFoldInit, 0u, doc.id, f.rk);
+        const int z0 = (int)dice(r.x, (uint32_t)f.K);
+#pragma unroll
+        for (int i = 0; i < M; ++i) doc.prop[j * M + i] = z0;
+        doc.z[j] = z0;
+    }
+    __syncwarp();
+}
+
+// Sweep `it` of one document: the document phase, then the word phase
+// against the frozen rows.  kLearned: the learned document proposal (the
+// encoder's q through its alias table) replaces positioning, and the word
+// phase accepts it with the independence-sampler rate min{1, p(t) q(s) /
+// (p(s) q(t))} of Alg. 1, p(k) = (C_dk + alpha)(C_wk + beta)/(c_k + beta_bar)
+// with the word phase's phase-start c_d (the oracle's readings L6-L7).
+template <int M, bool kDense, bool kLearned>
+__device__ void fold_sweep(const FoldArgs& f, const FoldDoc& doc, int it, uint32_t* tab, int words,
+                           uint32_t cap, Checks& chk, int lane) {
+    const int K = f.K, L = doc.L;
+    const uint32_t km = (uint32_t)K - 1u;
+    int32_t* z = doc.z;
+    int32_t* prop = doc.prop;
+    const float Lf = __int2float_rn(L);
+    const float LG = __fadd_rn(Lf, f.abar);
+    // document phase: accept with the phase-start c_d ...
+    fold_table<kDense>(tab, words, cap, doc, km, lane);
+    for (int j = lane; j < L; j += 32) {
+        int s = min((uint32_t)z[j], km);
+        int cs = fold_count(tab, cap, kDense, s);
+        float ks = __ldg(f.ckb + s);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldDoc, (uint32_t)(i + 1), doc.id, f.rk);
+            const int t = (int)min((uint32_t)prop[j * M + i], km);
+            if (t != s) {
+                const int ct = fold_count(tab, cap, kDense, t);
+                const float kt = __ldg(f.ckb + t);
+                if (accept(r.x, cs, ct, f.alpha, ks, kt)) {
+                    s = t;
+                    cs = ct;
+                    ks = kt;
+                }
+            }
+        }
+        z[j] = s;
+    }
+    __syncwarp();
+    // ... then positioning over the post-acceptance z_d (or draws from the
+    // learned proposal's alias table)
+    for (int j = lane; j < L; j += 32) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldDoc, (uint32_t)(i + 1), doc.id, f.rk);
+            if (kLearned) {
+                const int k = (int)dice(r.z, (uint32_t)K);
+                prop[j * M + i] = u24(r.y) < __ldg(doc.prob + k) ? k : (int)min((uint32_t)__ldg(doc.alias + k), km);
+            } else {
+                prop[j * M + i] = coin(r.y, Lf, LG) ? z[dice(r.z, (uint32_t)L)] : (int)dice(r.z, (uint32_t)K);
+            }
+        }
+    }
+    __syncwarp();
+    if (kLearned) fold_table<kDense>(tab, words, cap, doc, km, lane);   // the word phase's phase-start c_d
+    // word phase against the frozen rows: accept, then a proposal from the
+    // token's frozen row (one Philox block per step)
+    for (int j = lane; j < L; j += 32) {
+        int w = doc.words[j];
+        if (!chk((uint32_t)w < (uint32_t)f.V, 1)) w = 0;
+        const int32_t* row = f.Cw + (int64_t)w * K;
+        const int wb = __ldg(f.word_off + w);
+        const int Lw = __ldg(f.word_off + w + 1) - wb;
+        const float Lwf = __int2float_rn(Lw);
+        const float LwG = __fadd_rn(Lwf, f.kbeta);
+        int s = min((uint32_t)z[j], km);
+        int cs = __ldg(row + s);
+        float ks = __ldg(f.ckb + s);
+        uint32_t r1[M], r2[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldWord, (uint32_t)(i + 1), doc.id, f.rk);
+            r1[i] = r.y;
+            r2[i] = r.z;
+            const int t = (int)min((uint32_t)prop[j * M + i], km);
+            if (t != s) {
+                const int ct = __ldg(row + t);
+                const float kt = __ldg(f.ckb + t);
+                bool acc;
+                if (kLearned) {
+                    const float cds = __int2float_rn(fold_count(tab, cap, kDense, s));
+                    const float cdt = __int2float_rn(fold_count(tab, cap, kDense, t));
+                    const float num = __fmul_rn(__fmul_rn(__fmul_rn(__fadd_rn(cdt, f.alpha),
+                                                                    __fadd_rn(__int2float_rn(ct), f.beta)),
+                                                          ks), __ldg(doc.q + s));
+                    const float den = __fmul_rn(__fmul_rn(__fmul_rn(__fadd_rn(cds, f.alpha),
+                                                                    __fadd_rn(__int2float_rn(cs), f.beta)),
+                                                          kt), __ldg(doc.q + t));
+                    acc = __fmul_rn(u24(r.x), den) < num;
+                } else {
+                    acc = accept(r.x, cs, ct, f.beta, ks, kt);
+                }
+                if (acc) {
+                    s = t;
+                    cs = ct;
+                    ks = kt;
+                }
+            }
+        }
+        z[j] = s;
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            prop[j * M + i] = (Lw > 0 && coin(r1[i], Lwf, LwG))
+                                  ? __ldg(f.Zs + wb + (int)dice(r2[i], (uint32_t)Lw))
+                                  : (int)dice(r2[i], (uint32_t)K);
+    }
+    __syncwarp();
+}
+
+// theta (Eq. 4) of the document's current z.
+template <bool kDense>
+__device__ __forceinline__ void fold_theta(const FoldArgs& f, const FoldDoc& doc, float* th, uint32_t* tab,
+                                           int words, uint32_t cap, int lane) {
+    fold_table<kDense>(tab, words, cap, doc, (uint32_t)f.K - 1u, lane);
+    const float den = __fadd_rn(__int2float_rn(doc.L), f.abar);
+    for (int k = lane; k < f.K; k += 32)
+        th[k] = __fdiv_rn(__fadd_rn(__int2float_rn(fold_count(tab, cap, kDense, k)), f.alpha), den);
+    __syncwarp();
+}
+
 template <int M, bool kDense, bool kLearned>
 __global__ void __launch_bounds__(kThreads) foldin_kernel(FoldArgs f, int tab_words) {
     extern __shared__ __align__(16) uint32_t fsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t* tab = fsm + warp * tab_words;
     const int K = f.K;
-    const uint32_t km = (uint32_t)K - 1u;
     Checks chk;
     for (;;) {
         int di = 0;
@@ -105,153 +261,77 @@ __global__ void __launch_bounds__(kThreads) foldin_kernel(FoldArgs f, int tab_wo
         const int b = f.doc_off[d];
         int L = f.doc_off[d + 1] - b;
         if (!chk(L >= 0 && L <= f.Lmax, 0)) L = 0;
-        const uint32_t id = (uint32_t)f.ids[d];
+        FoldDoc doc;
+        doc.z = f.z + b;
+        doc.prop = f.prop + (int64_t)b * M;
+        doc.words = f.words + b;
+        doc.L = L;
+        doc.id = (uint32_t)f.ids[d];
+        doc.q = kLearned ? f.q + (int64_t)d * K : nullptr;
+        doc.prob = kLearned ? f.aprob + (int64_t)d * K : nullptr;
+        doc.alias = kLearned ? f.alias + (int64_t)d * K : nullptr;
         const uint32_t cap = kDense ? 0u : pow2_above((uint32_t)min(2 * max(L, 1), K));
         const int words = kDense ? tab_words : (int)cap;
-        int32_t* z = f.z + b;
-        int32_t* prop = f.prop + (int64_t)b * M;
-        const int32_t* wd = f.words + b;
-        auto build_table = [&]() {
-            for (int i = lane; i < words; i += 32) tab[i] = 0u;
-            __syncwarp();
-            for (int j = lane; j < L; j += 32) {
-                const uint32_t k = min((uint32_t)z[j], km);
-                if (kDense) atomicAdd(&tab[k >> 1], (k & 1) ? 65536u : 1u);
-                else table_add(tab, cap, k);
-            }
-            __syncwarp();
-        };
-        // initialisation: z = Dice(K), proposals = z
-        for (int j = lane; j < L; j += 32) {
-            const uint4 r = draw((uint32_t)j, 0u, kPhaseFoldInit, 0u, id, f.rk);
-            const int z0 = (int)dice(r.x, (uint32_t)K);
-            z[j] = z0;
-#pragma unroll
-            for (int i = 0; i < M; ++i) prop[j * M + i] = z0;
-        }
-        __syncwarp();
-        const float Lf = __int2float_rn(L);
-        const float LG = __fadd_rn(Lf, f.abar);
-        for (int it = 1; it <= f.sweeps; ++it) {
-            // document phase: accept with the phase-start c_d ...
-            build_table();
-            for (int j = lane; j < L; j += 32) {
-                int s = min((uint32_t)z[j], km);
-                int cs = fold_count(tab, cap, kDense, s);
-                float ks = __ldg(f.ckb + s);
-#pragma unroll
-                for (int i = 0; i < M; ++i) {
-                    const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldDoc, (uint32_t)(i + 1), id, f.rk);
-                    const int t = (int)min((uint32_t)prop[j * M + i], km);
-                    if (t != s) {
-                        const int ct = fold_count(tab, cap, kDense, t);
-                        const float kt = __ldg(f.ckb + t);
-                        if (accept(r.x, cs, ct, f.alpha, ks, kt)) {
-                            s = t;
-                            cs = ct;
-                            ks = kt;
-                        }
-                    }
-                }
-                z[j] = s;
-            }
-            __syncwarp();
-            // ... then positioning over the post-acceptance z_d (or draws
-            // from the learned proposal's alias table)
-            const float* qd = kLearned ? f.q + (int64_t)d * K : nullptr;
-            const float* pd = kLearned ? f.aprob + (int64_t)d * K : nullptr;
-            const int32_t* ad = kLearned ? f.alias + (int64_t)d * K : nullptr;
-            for (int j = lane; j < L; j += 32) {
-#pragma unroll
-                for (int i = 0; i < M; ++i) {
-                    const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldDoc, (uint32_t)(i + 1), id, f.rk);
-                    if (kLearned) {
-                        const int k = (int)dice(r.z, (uint32_t)K);
-                        prop[j * M + i] = u24(r.y) < __ldg(pd + k) ? k : (int)min((uint32_t)__ldg(ad + k), km);
-                    } else {
-                        prop[j * M + i] = coin(r.y, Lf, LG) ? z[dice(r.z, (uint32_t)L)] : (int)dice(r.z, (uint32_t)K);
-                    }
-                }
-            }
-            __syncwarp();
-            if (kLearned) build_table();   // the word phase's phase-start c_d
-            // word phase against the frozen rows: accept, then a proposal
-            // from the token's frozen row (one Philox block per step)
-            for (int j = lane; j < L; j += 32) {
-                int w = wd[j];
-                if (!chk((uint32_t)w < (uint32_t)f.V, 1)) w = 0;
-                const int32_t* row = f.Cw + (int64_t)w * K;
-                const int wb = __ldg(f.word_off + w);
-                const int Lw = __ldg(f.word_off + w + 1) - wb;
-                const float Lwf = __int2float_rn(Lw);
-                const float LwG = __fadd_rn(Lwf, f.kbeta);
-                int s = min((uint32_t)z[j], km);
-                int cs = __ldg(row + s);
-                float ks = __ldg(f.ckb + s);
-                uint32_t r1[M], r2[M];
-#pragma unroll
-                for (int i = 0; i < M; ++i) {
-                    const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldWord, (uint32_t)(i + 1), id, f.rk);
-                    r1[i] = r.y;
-                    r2[i] = r.z;
-                    const int t = (int)min((uint32_t)prop[j * M + i], km);
-                    if (t != s) {
-                        const int ct = __ldg(row + t);
-                        const float kt = __ldg(f.ckb + t);
-                        bool acc;
-                        if (kLearned) {
-                            const float cds = __int2float_rn(fold_count(tab, cap, kDense, s));
-                            const float cdt = __int2float_rn(fold_count(tab, cap, kDense, t));
-                            const float num = __fmul_rn(__fmul_rn(__fmul_rn(__fadd_rn(cdt, f.alpha),
-                                                                            __fadd_rn(__int2float_rn(ct), f.beta)),
-                                                                  ks), __ldg(qd + s));
-                            const float den = __fmul_rn(__fmul_rn(__fmul_rn(__fadd_rn(cds, f.alpha),
-                                                                            __fadd_rn(__int2float_rn(cs), f.beta)),
-                                                                  kt), __ldg(qd + t));
-                            acc = __fmul_rn(u24(r.x), den) < num;
-                        } else {
-                            acc = accept(r.x, cs, ct, f.beta, ks, kt);
-                        }
-                        if (acc) {
-                            s = t;
-                            cs = ct;
-                            ks = kt;
-                        }
-                    }
-                }
-                z[j] = s;
-#pragma unroll
-                for (int i = 0; i < M; ++i)
-                    prop[j * M + i] = (Lw > 0 && coin(r1[i], Lwf, LwG))
-                                          ? __ldg(f.Zs + wb + (int)dice(r2[i], (uint32_t)Lw))
-                                          : (int)dice(r2[i], (uint32_t)K);
-            }
-            __syncwarp();
-        }
-        // theta (Eq. 4) of the final z
-        build_table();
-        if (f.theta) {
-            const float den = __fadd_rn(Lf, f.abar);
-            float* th = f.theta + (int64_t)d * K;
-            for (int k = lane; k < K; k += 32)
-                th[k] = __fdiv_rn(__fadd_rn(__int2float_rn(fold_count(tab, cap, kDense, k)), f.alpha), den);
-        }
-        __syncwarp();
+        fold_init<M>(f, doc, lane);
+        for (int it = 1; it <= f.sweeps; ++it) fold_sweep<M, kDense, kLearned>(f, doc, it, tab, words, cap, chk, lane);
+        if (f.theta) fold_theta<kDense>(f, doc, f.theta + (int64_t)d * K, tab, words, cap, lane);
+    }
+    chk.publish(f.fault, kSiteFoldin);
+}
+
+// Serving: one launch advances every active slot by one sweep (a slot's
+// first launch initialises it; its last writes theta).  Slots are taken by
+// warps from a work counter.
+template <int M, bool kDense, bool kLearned>
+__global__ void __launch_bounds__(kThreads) serve_kernel(FoldArgs f, ServeSlots sl, int tab_words) {
+    extern __shared__ __align__(16) uint32_t fsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* tab = fsm + warp * tab_words;
+    const int K = f.K;
+    Checks chk;
+    for (;;) {
+        int si = 0;
+        if (lane == 0) si = atomicAdd(f.counter, 1);
+        si = __shfl_sync(0xFFFFFFFFu, si, 0);
+        if (si >= sl.nactive) break;
+        int s = sl.active[si];
+        if (!chk(s >= 0 && s < sl.nslots, 0)) continue;
+        const int4 info = sl.info[s];   // {token offset, L, sweeps done, stream id}
+        int L = info.y;
+        if (!chk(info.x >= 0 && L >= 0 && L <= f.Lmax && (int64_t)info.x + L <= sl.pool_tokens, 0)) continue;
+        FoldDoc doc;
+        doc.z = sl.z + info.x;
+        doc.prop = sl.prop + (int64_t)info.x * M;
+        doc.words = sl.words + info.x;
+        doc.L = L;
+        doc.id = (uint32_t)info.w;
+        doc.q = kLearned ? sl.q + (int64_t)s * K : nullptr;
+        doc.prob = kLearned ? sl.prob + (int64_t)s * K : nullptr;
+        doc.alias = kLearned ? sl.alias + (int64_t)s * K : nullptr;
+        const uint32_t cap = kDense ? 0u : pow2_above((uint32_t)min(2 * max(L, 1), K));
+        const int words = kDense ? tab_words : (int)cap;
+        const int done = info.z;
+        if (done == 0) fold_init<M>(f, doc, lane);
+        fold_sweep<M, kDense, kLearned>(f, doc, done + 1, tab, words, cap, chk, lane);
+        if (done + 1 >= f.sweeps) fold_theta<kDense>(f, doc, sl.theta + (int64_t)s * K, tab, words, cap, lane);
+        if (lane == 0) sl.info[s].z = done + 1;
     }
     chk.publish(f.fault, kSiteFoldin);
 }
 
 template <int M, bool kDense>
-static const void* fold_ptr(bool learned) {
+static const void* fold_ptr(bool learned, bool serve) {
+    if (serve)
+        return learned ? (const void*)serve_kernel<M, kDense, true> : (const void*)serve_kernel<M, kDense, false>;
     return learned ? (const void*)foldin_kernel<M, kDense, true> : (const void*)foldin_kernel<M, kDense, false>;
 }
 
-static const void* fold_pick(int M, bool dense, bool learned) {
+static const void* fold_pick(int M, bool dense, bool learned, bool serve = false) {
     switch (M) {
-        case 1: return dense ? fold_ptr<1, true>(learned) : fold_ptr<1, false>(learned);
-        case 2: return dense ? fold_ptr<2, true>(learned) : fold_ptr<2, false>(learned);
-        case 3: return dense ? fold_ptr<3, true>(learned) : fold_ptr<3, false>(learned);
-        case 4: return dense ? fold_ptr<4, true>(learned) : fold_ptr<4, false>(learned);
+        case 1: return dense ? fold_ptr<1, true>(learned, serve) : fold_ptr<1, false>(learned, serve);
+        case 2: return dense ? fold_ptr<2, true>(learned, serve) : fold_ptr<2, false>(learned, serve);
+        case 3: return dense ? fold_ptr<3, true>(learned, serve) : fold_ptr<3, false>(learned, serve);
+        case 4: return dense ? fold_ptr<4, true>(learned, serve) : fold_ptr<4, false>(learned, serve);
         default: return nullptr;
     }
 }
@@ -274,6 +354,22 @@ cudaError_t launch_foldin(const FoldArgs& f, int tab_words, int grid, cudaStream
     FoldArgs args = f;
     int tw = tab_words;
     void* params[] = {&args, &tw};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(32 * warps), params, (size_t)smem, st);
+}
+
+cudaError_t launch_serve(const FoldArgs& f, const ServeSlots& sl, int tab_words, int grid, cudaStream_t st) {
+    if (sl.nactive <= 0) return cudaSuccess;
+    const bool dense = f.K <= kDenseMaxK;
+    const void* fn = fold_pick(f.M, dense, sl.q != nullptr, true);
+    const int warps = foldin_warps(tab_words);
+    if (!fn || warps < 1) return cudaErrorInvalidValue;
+    const int smem = warps * tab_words * 4;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    FoldArgs args = f;
+    ServeSlots slots = sl;
+    int tw = tab_words;
+    void* params[] = {&args, &slots, &tw};
     return cudaLaunchKernel(fn, dim3(grid), dim3(32 * warps), params, (size_t)smem, st);
 }
 

@@ -71,6 +71,25 @@ int foldin_warps(int tab_words);
 int foldin_blocks_per_sm(int K, int M, int tab_words);
 cudaError_t launch_foldin(const FoldArgs& f, int tab_words, int grid, cudaStream_t st);
 
+// Serving slots (continuous batching of fold-in requests): per slot
+// info = {token offset in the pool, L, sweeps done, stream id}; the pool holds
+// the active requests' word ids, z and proposals; theta (and, with the
+// learned proposal, q and its alias table) per slot.
+struct ServeSlots {
+    int4* info;
+    const int32_t* active;   // [nactive] slots advanced by this launch
+    int nactive, nslots;
+    int64_t pool_tokens;
+    int32_t* z;
+    int32_t* prop;
+    const int32_t* words;
+    float* theta;
+    const float* q;
+    const float* prob;
+    const int32_t* alias;
+};
+cudaError_t launch_serve(const FoldArgs& f, const ServeSlots& sl, int tab_words, int grid, cudaStream_t st);
+
 // Tensor-core BF16 GEMM (wl_gemm.cu): C[M,N] = A[M,K] B[N,K]^T (+ bias[N]),
 // FP32 C; M, N multiples of 128, K a multiple of 64; *status set to 1 if a
 // bounded wait ran out.

@@ -69,6 +69,12 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_double)]),
     "warplda_sync": (ctypes.c_int, [_P]),
+    "warplda_server_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, _P]),
+    "warplda_server_submit": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _P]),
+    "warplda_server_step": (ctypes.c_int, [_P, _P]),
+    "warplda_server_poll": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, ctypes.c_int32]),
+    "warplda_server_destroy": (None, [_P]),
     "warplda_word_counts": (ctypes.c_int, [_P, _P]),
     "warplda_encoder_init": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                             ctypes.c_uint64]),
@@ -328,3 +334,55 @@ def gemm_bf16(A, B, C, bias=None, stream=None) -> None:
     st = stream.cuda_stream if stream is not None else None
     _check(load().warplda_gemm_bf16(A.data_ptr(), B.data_ptr(), C.data_ptr(),
                                     bias.data_ptr() if bias is not None else None, M, N, K, st))
+
+
+EBUSY = -7
+
+
+class Server:
+    """Continuous batching of fold-in requests (warplda_server_*): submit()
+    admits a request if a slot and pool memory are free (False otherwise),
+    step() advances every admitted request by one sweep, poll() returns the
+    finished ones as (ids, theta)."""
+
+    def __init__(self, model: "WarpLDA", slots: int, pool_tokens: int, max_doc_tokens: int,
+                 sweeps: int, seed: int, learned: bool = False):
+        self.K = model.K
+        self._model = model
+        h = ctypes.c_void_p()
+        _check(load().warplda_server_create(model._h, slots, pool_tokens, max_doc_tokens, sweeps,
+                                            int(seed), 1 if learned else 0, ctypes.byref(h)))
+        self._h = h
+        self._slots = slots
+
+    def submit(self, rid: int, words) -> bool:
+        w = np.ascontiguousarray(words, dtype=np.int32)
+        rc = load().warplda_server_submit(self._h, int(rid), len(w), w.ctypes.data if w.size else None)
+        if rc == EBUSY:
+            return False
+        _check(rc)
+        return True
+
+    def step(self) -> int:
+        n = ctypes.c_int32()
+        _check(load().warplda_server_step(self._h, ctypes.byref(n)))
+        return int(n.value)
+
+    def poll(self, timeout_ms: int = 60000):
+        ids = np.empty(self._slots, np.int64)
+        th = np.empty((self._slots, self.K), np.float32)
+        n = ctypes.c_int32()
+        _check(load().warplda_server_poll(self._h, self._slots, ids.ctypes.data, th.ctypes.data,
+                                          ctypes.byref(n), int(timeout_ms)))
+        return ids[: n.value], th[: n.value]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().warplda_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
