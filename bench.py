@@ -268,6 +268,12 @@ def learned_bench(gpu, c, wl, args):
     tiny = learned_curve(gt, ct, wt, "tiny", 71, 1, 500, [1, 2, 3, 4, 8, 16])
     tiny["encoder_loss"] = [float(tl[0]), float(tl[-1])]
     tiny["model"] = "tiny workload (D=1000, K=16, M=2), 200 sweeps; encoder 2^12 features, 128 hidden, 60 epochs"
+    # serving at equal load, each proposal with the sweeps it needs to reach
+    # the held-out target
+    need = tiny["sweeps_to_target"]
+    tiny["serving_at_target"] = [
+        serving_bench(gt, ct, wt, args, kind == "learned", 20_000.0, n=4000, name="tiny",
+                      sweeps=need[kind] or 16) for kind in ("plain", "learned")]
     gt.close()
 
     # throughput of the learned fold-in (encoder forward + alias tables + sweeps)
@@ -285,17 +291,17 @@ def learned_bench(gpu, c, wl, args):
             "includes": "encoder forward + alias tables + fold-in kernel + H2D/D2H (C ABI call)"}
 
 
-def serving_bench(gpu, c, wl, args, learned: bool, rate: float, n: int = 6000):
+def serving_bench(gpu, c, wl, args, learned: bool, rate: float, n: int = 6000, name=None, sweeps=None):
     """Fold-in requests arriving as a Poisson stream at `rate` docs/s, served
     with continuous batching (warplda_server_*): each step advances every
     admitted request by one sweep; requests arriving meanwhile join the next
     step.  Latency = completion (poll) time - arrival time."""
     from paper_1510_08628_gb300 import corpus
     from paper_1510_08628_gb300.warplda import Server
-    rq = corpus.requests(args.workload, seed=args.corpus_seed, n=n, doc_offset=c.D + 2_000_000)
+    rq = corpus.requests(name or args.workload, seed=args.corpus_seed, n=n, doc_offset=c.D + 2_000_000)
     rng = np.random.default_rng(args.seed)
     arrive = np.cumsum(rng.exponential(1.0 / rate, size=n))
-    S = args.foldin_sweeps
+    S = sweeps or args.foldin_sweeps
     srv = Server(gpu, slots=8192, pool_tokens=4_000_000, max_doc_tokens=5000, sweeps=S,
                  seed=args.seed + 41, learned=learned)
     lat = np.zeros(n)

@@ -282,17 +282,20 @@ int warplda_encoder_proposal(warplda_ctx* ctx, int64_t Dn, const int64_t* doc_pt
  *   (<= 65535 when K <= 2048, <= 4095 above).  Errors: EINVAL, ESTATE,
  *   ENOMEM, ECUDA.
  * warplda_server_submit -- admit request `id` (host word ids words[L], in
- *   [0, V); copied).  Returns OK, or EBUSY when no slot or no contiguous
- *   pool range is free: admission is by memory, the caller retries after a
- *   poll has retired finished requests.
- * warplda_server_step -- launch one sweep for every admitted, unfinished
- *   request (new ones are initialised first; a request's last sweep also
- *   writes its theta); asynchronous.  *active_out (or NULL) = requests
- *   advanced.  Requests admitted while a step runs join the next step.
+ *   [0, V); copied on the host, uploaded by the next step).  Returns OK, or
+ *   EBUSY when no slot or no contiguous pool range is free: admission is by
+ *   memory, the caller retries after a poll has retired finished requests.
+ * warplda_server_step -- upload the requests admitted since the last step,
+ *   then launch one sweep for every admitted, unfinished request (new ones
+ *   are initialised first; a request's last sweep writes its theta);
+ *   asynchronous.  *active_out (or NULL) = requests advanced.  Requests
+ *   submitted while a step runs join the next step.  The previous step's
+ *   results must have been polled (else ESTATE).
  * warplda_server_poll -- wait at most timeout_ms for the last step (else
- *   ETIMEDOUT), then hand over up to max_results finished requests: ids[n]
- *   and theta[n*K] (Eq. 4), *n_out = n; their slots and pool memory are
- *   freed.
+ *   ETIMEDOUT), then hand over the requests it finished: ids[n] and
+ *   theta[n*K] (Eq. 4), *n_out = n <= max_results (else EINVAL; max_results
+ *   = slots always suffices); their slots and pool memory are freed.
+ * Not thread-safe: one thread drives a server.
  * warplda_server_destroy -- wait for the stream and free the server.
  */
 int warplda_server_create(warplda_ctx* ctx, int32_t slots, int64_t pool_tokens, int32_t max_doc_tokens,

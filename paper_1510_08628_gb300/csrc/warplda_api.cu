@@ -617,20 +617,28 @@ struct warplda_server {
     uint64_t seed = 0;
     int4* d_info = nullptr;
     int32_t *d_active = nullptr, *d_z = nullptr, *d_prop = nullptr, *d_words = nullptr, *d_counter = nullptr;
-    float *d_theta = nullptr, *d_q = nullptr, *d_prob = nullptr;
-    int32_t* d_alias = nullptr;
-    float* h_theta = nullptr;   // pinned staging of finished rows [nslots * K]
+    float *d_fin_theta = nullptr, *d_q = nullptr, *d_prob = nullptr;
+    int32_t *d_fin_slot = nullptr, *d_alias = nullptr;
+    int32_t* d_staged = nullptr;   // words of requests admitted since the last step
+    int4* d_req = nullptr;          // their {slot, pool offset, L, id}
+    int32_t* d_src = nullptr;       // their offsets in the staged words
+    int64_t staged_cap = 0;
+    float* h_theta = nullptr;       // pinned: finished rows of the last step
+    int32_t* h_fin_slot = nullptr;
+    int n_fin_staged = 0;
     cudaEvent_t tick = nullptr;
     struct Slot {
-        bool used = false, fresh = false;
+        bool used = false;
         int64_t id = 0;
         int32_t off = 0, L = 0, done = 0;
-        std::vector<int32_t> words;   // kept until the proposal rows are made (learned)
     };
     std::vector<Slot> slots;
     std::vector<int32_t> free_slots;
     std::map<int64_t, int64_t> free_ranges;   // pool start -> length
-    std::vector<int32_t> finished;             // slots whose theta is staged
+    // admitted since the last step
+    std::vector<int32_t> new_words, new_src;
+    std::vector<int4> new_req;
+    std::vector<int64_t> new_ptr{0};
     std::vector<void*> allocs;
 };
 
@@ -677,6 +685,7 @@ void server_free(warplda_server* s) {
     for (void* p : s->allocs) cudaFree(p);
     s->allocs.clear();
     if (s->h_theta) cudaFreeHost(s->h_theta);
+    if (s->h_fin_slot) cudaFreeHost(s->h_fin_slot);
     if (s->tick) cudaEventDestroy(s->tick);
 }
 
@@ -702,39 +711,67 @@ FoldArgs server_args(warplda_server* s) {
     return f;
 }
 
-// Proposal rows and alias tables of the requests admitted since the last
-// step (learned proposal): the encoder runs on a CSR of their words.
-int server_proposals(warplda_server* s, const std::vector<int32_t>& fresh) {
+// Uploads the requests admitted since the last step (one copy of their
+// words, one of their descriptors, one admission kernel) and, with the
+// learned proposal, makes their proposal rows and alias tables.
+int server_admit(warplda_server* s) {
     warplda_ctx* c = s->c;
-    const int K = c->K;
-    std::vector<int64_t> ptr(1, 0);
-    std::vector<int32_t> words;
-    for (int32_t sl : fresh) {
-        const auto& w = s->slots[sl].words;
-        words.insert(words.end(), w.begin(), w.end());
-        ptr.push_back((int64_t)words.size());
+    const int n = (int)s->new_req.size();
+    if (n == 0) return WARPLDA_OK;
+    const int64_t nw = (int64_t)s->new_words.size();
+    if (nw + 4 > s->staged_cap) {
+        int64_t cap = std::max<int64_t>(nw + 4, 2 * s->staged_cap);
+        int32_t* p = nullptr;
+        WL_CU(cudaMalloc((void**)&p, (size_t)cap * 4), "alloc staging");
+        s->allocs.push_back(p);
+        s->d_staged = p;
+        s->staged_cap = cap;
     }
-    const int64_t Dn = (int64_t)fresh.size();
-    FoldBuffers buf;
-    HostDocs hd;
-    int rc = upload_docs(c, buf, Dn, ptr.data(), words.data(), &hd);
-    if (rc) return rc;
-    float *q, *prob;
-    int32_t *alias, *stack;
-    WL_CU(buf.get(&q, Dn * K), "alloc proposals");
-    WL_CU(buf.get(&prob, Dn * K), "alloc alias tables");
-    WL_CU(buf.get(&alias, Dn * K), "alloc alias tables");
-    WL_CU(buf.get(&stack, Dn * K), "alloc alias scratch");
-    if ((rc = enc_proposal_dev(c, Dn, hd, q))) return rc;
-    WL_CU(launch_enc_alias(q, Dn, K, prob, alias, stack, c->st), "alias tables");
-    for (int64_t i = 0; i < Dn; ++i) {
-        const int64_t sl = fresh[i];
-        WL_CU(cudaMemcpyAsync(s->d_q + sl * K, q + i * K, (size_t)K * 4, cudaMemcpyDeviceToDevice, c->st), "copy q");
-        WL_CU(cudaMemcpyAsync(s->d_prob + sl * K, prob + i * K, (size_t)K * 4, cudaMemcpyDeviceToDevice, c->st), "copy alias");
-        WL_CU(cudaMemcpyAsync(s->d_alias + sl * K, alias + i * K, (size_t)K * 4, cudaMemcpyDeviceToDevice, c->st), "copy alias");
+    if (nw > 0)
+        WL_CU(cudaMemcpyAsync(s->d_staged, s->new_words.data(), (size_t)nw * 4, cudaMemcpyHostToDevice, c->st), "upload requests");
+    WL_CU(cudaMemcpyAsync(s->d_req, s->new_req.data(), (size_t)n * sizeof(int4), cudaMemcpyHostToDevice, c->st), "upload requests");
+    WL_CU(cudaMemcpyAsync(s->d_src, s->new_src.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c->st), "upload requests");
+    WL_CU(launch_serve_admit(s->d_staged, s->d_req, s->d_src, n, s->nslots, s->pool_tokens, s->d_words, s->d_info,
+                             c->st), "admit requests");
+    if (s->proposal == WARPLDA_PROPOSAL_LEARNED) {
+        const int K = c->K;
+        FoldBuffers buf;
+        HostDocs hd;
+        float *q, *prob;
+        int32_t *alias, *stack, *off, *ids, *slots;
+        std::vector<int32_t> offv((size_t)n + 1), idv((size_t)n), slv((size_t)n);
+        for (int i = 0; i <= n; ++i) offv[i] = (int32_t)s->new_ptr[i];
+        for (int i = 0; i < n; ++i) {
+            idv[i] = i;
+            slv[i] = s->new_req[i].x;
+        }
+        WL_CU(buf.get(&off, n + 1), "alloc offsets");
+        WL_CU(buf.get(&ids, n), "alloc ids");
+        WL_CU(buf.get(&slots, n), "alloc slots");
+        WL_CU(buf.get(&q, (int64_t)n * K), "alloc proposals");
+        WL_CU(buf.get(&prob, (int64_t)n * K), "alloc alias tables");
+        WL_CU(buf.get(&alias, (int64_t)n * K), "alloc alias tables");
+        WL_CU(buf.get(&stack, (int64_t)n * K), "alloc alias scratch");
+        WL_CU(cudaMemcpyAsync(off, offv.data(), (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, c->st), "upload offsets");
+        WL_CU(cudaMemcpyAsync(ids, idv.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c->st), "upload ids");
+        WL_CU(cudaMemcpyAsync(slots, slv.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c->st), "upload slots");
+        hd.off = off;
+        hd.words = s->d_staged;
+        hd.ids = ids;
+        int rc = enc_proposal_dev(c, n, hd, q);   // synchronises
+        if (rc) return rc;
+        WL_CU(launch_enc_alias(q, n, K, prob, alias, stack, c->st), "alias tables");
+        WL_CU(launch_serve_rows(q, slots, n, K, s->nslots, s->d_q, c->st), "proposal rows");
+        WL_CU(launch_serve_rows(prob, slots, n, K, s->nslots, s->d_prob, c->st), "alias rows");
+        WL_CU(launch_serve_rows(alias, slots, n, K, s->nslots, s->d_alias, c->st), "alias rows");
+        WL_CU(cudaStreamSynchronize(c->st), "synchronize");   // the temporaries are freed on return
+    } else {
+        WL_CU(cudaStreamSynchronize(c->st), "synchronize");   // the host vectors are reused
     }
-    WL_CU(cudaStreamSynchronize(c->st), "synchronize");   // the temporaries are freed on return
-    for (int32_t sl : fresh) std::vector<int32_t>().swap(s->slots[sl].words);
+    s->new_words.clear();
+    s->new_src.clear();
+    s->new_req.clear();
+    s->new_ptr.assign(1, 0);
     return WARPLDA_OK;
 }
 
@@ -1574,14 +1611,16 @@ int warplda_server_create(warplda_ctx* c, int32_t slots, int64_t pool_tokens, in
     };
     if ((rc = salloc(s, &s->d_info, slots)) || (rc = salloc(s, &s->d_active, slots)) ||
         (rc = salloc(s, &s->d_z, pool_tokens + 4)) || (rc = salloc(s, &s->d_prop, (pool_tokens + 4) * M)) ||
-        (rc = salloc(s, &s->d_words, pool_tokens + 4)) || (rc = salloc(s, &s->d_counter, 1)) ||
-        (rc = salloc(s, &s->d_theta, (int64_t)slots * K)))
+        (rc = salloc(s, &s->d_words, pool_tokens + 4)) || (rc = salloc(s, &s->d_counter, 2)) ||
+        (rc = salloc(s, &s->d_fin_theta, (int64_t)slots * K)) || (rc = salloc(s, &s->d_fin_slot, slots)) ||
+        (rc = salloc(s, &s->d_req, slots)) || (rc = salloc(s, &s->d_src, slots)))
         return bail(rc);
     if (proposal == WARPLDA_PROPOSAL_LEARNED &&
         ((rc = salloc(s, &s->d_q, (int64_t)slots * K)) || (rc = salloc(s, &s->d_prob, (int64_t)slots * K)) ||
          (rc = salloc(s, &s->d_alias, (int64_t)slots * K))))
         return bail(rc);
-    if (cudaMallocHost((void**)&s->h_theta, (size_t)slots * K * 4) != cudaSuccess)
+    if (cudaMallocHost((void**)&s->h_theta, (size_t)slots * K * 4) != cudaSuccess ||
+        cudaMallocHost((void**)&s->h_fin_slot, (size_t)slots * 4) != cudaSuccess)
         return bail(fail(WARPLDA_ENOMEM, "pinned staging"));
     if (cudaEventCreateWithFlags(&s->tick, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(WARPLDA_ECUDA, "event"));
@@ -1609,18 +1648,15 @@ int warplda_server_submit(warplda_server* s, int64_t id, int32_t L, const int32_
     s->free_slots.pop_back();
     auto& S = s->slots[sl];
     S.used = true;
-    S.fresh = true;
     S.id = id;
     S.off = (int32_t)off;
     S.L = L;
     S.done = 0;
-    if (s->proposal == WARPLDA_PROPOSAL_LEARNED) S.words.assign(words, words + L);
-    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
-    if (L > 0)
-        WL_CU(cudaMemcpyAsync(s->d_words + off, words, (size_t)L * 4, cudaMemcpyHostToDevice, c->st), "upload request");
-    const int4 info = make_int4((int)off, L, 0, (int)(uint32_t)id);
-    WL_CU(cudaMemcpyAsync(s->d_info + sl, &info, sizeof(int4), cudaMemcpyHostToDevice, c->st), "upload slot");
-    WL_CU(cudaStreamSynchronize(c->st), "synchronize");   // sources are the caller's and the stack's
+    // staged on the host; the next step uploads every new request at once
+    s->new_src.push_back((int32_t)s->new_words.size());
+    s->new_words.insert(s->new_words.end(), words, words + L);
+    s->new_ptr.push_back((int64_t)s->new_words.size());
+    s->new_req.push_back(make_int4(sl, (int)off, L, (int)(uint32_t)id));
     return WARPLDA_OK;
 }
 
@@ -1628,20 +1664,21 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     if (!s) return fail(WARPLDA_EINVAL, "null server");
     warplda_ctx* c = s->c;
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
-    std::vector<int32_t> active, fresh;
+    if (s->n_fin_staged > 0) return fail(WARPLDA_ESTATE, "poll the previous step's results first");
+    int rc = server_admit(s);
+    if (rc) return rc;
+    std::vector<int32_t> active;
+    int nfin = 0;
     for (int i = 0; i < s->nslots; ++i) {
         const auto& S = s->slots[i];
         if (!S.used || S.done >= s->sweeps) continue;
         active.push_back(i);
-        if (S.fresh && s->proposal == WARPLDA_PROPOSAL_LEARNED) fresh.push_back(i);
+        if (S.done + 1 >= s->sweeps) ++nfin;
     }
     if (active_out) *active_out = (int32_t)active.size();
     if (active.empty()) return WARPLDA_OK;
-    int rc;
-    if (!fresh.empty() && (rc = server_proposals(s, fresh))) return rc;
-    for (int32_t i : active) s->slots[i].fresh = false;
     WL_CU(cudaMemcpyAsync(s->d_active, active.data(), active.size() * 4, cudaMemcpyHostToDevice, c->st), "upload active");
-    WL_CU(cudaMemsetAsync(s->d_counter, 0, 4, c->st), "reset counter");
+    WL_CU(cudaMemsetAsync(s->d_counter, 0, 8, c->st), "reset counters");
     FoldArgs f = server_args(s);
     ServeSlots sl{};
     sl.info = s->d_info;
@@ -1652,21 +1689,21 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     sl.z = s->d_z;
     sl.prop = s->d_prop;
     sl.words = s->d_words;
-    sl.theta = s->d_theta;
+    sl.fin_theta = s->d_fin_theta;
+    sl.fin_slot = s->d_fin_slot;
+    sl.fin_count = s->d_counter + 1;
     sl.q = s->d_q;
     sl.prob = s->d_prob;
     sl.alias = s->d_alias;
     const int grid = (int)std::min<int64_t>(s->grid, ((int64_t)active.size() + kWarps - 1) / kWarps + 1);
     WL_CU(launch_serve(f, sl, s->tab_words, grid, c->st), "serve");
-    for (int32_t i : active) {
-        auto& S = s->slots[i];
-        S.done += 1;
-        if (S.done >= s->sweeps) {
-            WL_CU(cudaMemcpyAsync(s->h_theta + (int64_t)i * c->K, s->d_theta + (int64_t)i * c->K,
-                                  (size_t)c->K * 4, cudaMemcpyDeviceToHost, c->st), "stage theta");
-            s->finished.push_back(i);
-        }
+    for (int32_t i : active) s->slots[i].done += 1;
+    if (nfin > 0) {
+        WL_CU(cudaMemcpyAsync(s->h_fin_slot, s->d_fin_slot, (size_t)nfin * 4, cudaMemcpyDeviceToHost, c->st), "copy finished");
+        WL_CU(cudaMemcpyAsync(s->h_theta, s->d_fin_theta, (size_t)nfin * c->K * 4, cudaMemcpyDeviceToHost, c->st),
+              "copy finished");
     }
+    s->n_fin_staged = nfin;
     WL_CU(cudaEventRecord(s->tick, c->st), "record tick");
     return WARPLDA_OK;
 }
@@ -1686,27 +1723,23 @@ int warplda_server_poll(warplda_server* s, int32_t max_results, int64_t* ids, fl
         if (e != cudaErrorNotReady) return cuda_fail(e, "serve step");
         const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
         if (ms > timeout_ms) return fail(WARPLDA_ETIMEDOUT, "a serving step did not finish within %d ms", timeout_ms);
-        std::this_thread::sleep_for(std::chrono::microseconds(50));
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
     int rc = check_record(c, "serving");
     if (rc) return rc;
-    const int K = c->K;
-    int n = 0;
-    std::vector<int32_t> keep;
-    for (int32_t i : s->finished) {
-        if (n >= max_results) {
-            keep.push_back(i);
-            continue;
-        }
-        auto& S = s->slots[i];
-        ids[n] = S.id;
-        std::memcpy(theta + (int64_t)n * K, s->h_theta + (int64_t)i * K, (size_t)K * 4);
+    const int K = c->K, n = s->n_fin_staged;
+    if (n > max_results) return fail(WARPLDA_EINVAL, "max_results below the %d finished requests", n);
+    for (int i = 0; i < n; ++i) {
+        const int32_t sl = s->h_fin_slot[i];
+        if (sl < 0 || sl >= s->nslots || !s->slots[sl].used) return fail(WARPLDA_ECUDA, "bad finished slot");
+        auto& S = s->slots[sl];
+        ids[i] = S.id;
+        std::memcpy(theta + (int64_t)i * K, s->h_theta + (int64_t)i * K, (size_t)K * 4);
         pool_give(s, S.off, std::max(S.L, 1));
         S.used = false;
-        s->free_slots.push_back(i);
-        ++n;
+        s->free_slots.push_back(sl);
     }
-    s->finished.swap(keep);
+    s->n_fin_staged = 0;
     *n_out = n;
     return WARPLDA_OK;
 }

@@ -16,6 +16,8 @@
 // One warp per document, all sweeps in one launch: the document's count
 // table lives in the warp's slice of shared memory, its z and proposals in
 // global memory (document order, coalesced), the frozen rows in L2.
+#include <algorithm>
+
 #include "wl_block.cuh"
 #include "wl_kernels.h"
 
@@ -313,7 +315,16 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(FoldArgs f, ServeSlots 
         const int done = info.z;
         if (done == 0) fold_init<M>(f, doc, lane);
         fold_sweep<M, kDense, kLearned>(f, doc, done + 1, tab, words, cap, chk, lane);
-        if (done + 1 >= f.sweeps) fold_theta<kDense>(f, doc, sl.theta + (int64_t)s * K, tab, words, cap, lane);
+        if (done + 1 >= f.sweeps) {
+            // finished: theta into the next row of the step's output
+            int oi = 0;
+            if (lane == 0) oi = atomicAdd(sl.fin_count, 1);
+            oi = __shfl_sync(0xFFFFFFFFu, oi, 0);
+            if (chk(oi < sl.nslots, 0)) {
+                fold_theta<kDense>(f, doc, sl.fin_theta + (int64_t)oi * K, tab, words, cap, lane);
+                if (lane == 0) sl.fin_slot[oi] = s;
+            }
+        }
         if (lane == 0) sl.info[s].z = done + 1;
     }
     chk.publish(f.fault, kSiteFoldin);
@@ -355,6 +366,43 @@ cudaError_t launch_foldin(const FoldArgs& f, int tab_words, int grid, cudaStream
     int tw = tab_words;
     void* params[] = {&args, &tw};
     return cudaLaunchKernel(fn, dim3(grid), dim3(32 * warps), params, (size_t)smem, st);
+}
+
+// Admission of staged requests: request i (slot, pool offset, L, id) copies
+// its words from the staging buffer into the pool and sets its slot.
+__global__ void serve_admit_kernel(const int32_t* __restrict__ staged, const int4* __restrict__ req,
+                                   const int32_t* __restrict__ src, int n, int nslots, int64_t pool_tokens,
+                                   int32_t* __restrict__ pool_words, int4* __restrict__ info) {
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const int4 r = req[i];   // {slot, pool offset, L, id}
+        if (r.x < 0 || r.x >= nslots || r.y < 0 || r.z < 0 || (int64_t)r.y + r.z > pool_tokens) continue;
+        for (int j = threadIdx.x; j < r.z; j += blockDim.x) pool_words[r.y + j] = staged[src[i] + j];
+        if (threadIdx.x == 0) info[r.x] = make_int4(r.y, r.z, 0, r.w);
+    }
+}
+
+// Rows i of src (n rows of K words) to rows slots[i] of dst.
+__global__ void serve_rows_kernel(const uint32_t* __restrict__ src, const int32_t* __restrict__ slots, int n,
+                                  int K, int nslots, uint32_t* __restrict__ dst) {
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        const int s = slots[i];
+        if (s < 0 || s >= nslots) continue;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) dst[(int64_t)s * K + k] = src[(int64_t)i * K + k];
+    }
+}
+
+cudaError_t launch_serve_admit(const int32_t* staged, const int4* req, const int32_t* src, int n, int nslots,
+                               int64_t pool_tokens, int32_t* pool_words, int4* info, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    serve_admit_kernel<<<std::min(n, 4096), 256, 0, st>>>(staged, req, src, n, nslots, pool_tokens, pool_words, info);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_serve_rows(const void* src, const int32_t* slots, int n, int K, int nslots, void* dst,
+                              cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    serve_rows_kernel<<<std::min(n, 4096), 256, 0, st>>>((const uint32_t*)src, slots, n, K, nslots, (uint32_t*)dst);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_serve(const FoldArgs& f, const ServeSlots& sl, int tab_words, int grid, cudaStream_t st) {

@@ -83,11 +83,17 @@ struct ServeSlots {
     int32_t* z;
     int32_t* prop;
     const int32_t* words;
-    float* theta;
+    float* fin_theta;        // theta rows of the requests finishing in this launch
+    int32_t* fin_slot;       // their slots
+    int32_t* fin_count;      // rows written (zero on entry)
     const float* q;
     const float* prob;
     const int32_t* alias;
 };
+cudaError_t launch_serve_admit(const int32_t* staged, const int4* req, const int32_t* src, int n, int nslots,
+                               int64_t pool_tokens, int32_t* pool_words, int4* info, cudaStream_t st);
+cudaError_t launch_serve_rows(const void* src, const int32_t* slots, int n, int K, int nslots, void* dst,
+                              cudaStream_t st);
 cudaError_t launch_serve(const FoldArgs& f, const ServeSlots& sl, int tab_words, int grid, cudaStream_t st);
 
 // Tensor-core BF16 GEMM (wl_gemm.cu): C[M,N] = A[M,K] B[N,K]^T (+ bias[N]),
