@@ -333,6 +333,33 @@ def serving_bench(gpu, c, wl, args, learned: bool, rate: float, n: int = 6000, n
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "steps": steps}
 
 
+def m_sweep(c, wl, args, stream, iters: int = 100, every: int = 10):
+    """Joint log-likelihood (Sec. 6.1) against iterations for M = 1, 2, 4 on
+    the same corpus and seed (the paper's Fig. 7 comparison), and for M = 2
+    with the paper's literal storage-order word positioning against the
+    order-statistic rule; with the device time per sweep of each."""
+    import torch
+    from paper_1510_08628_gb300.warplda import WarpLDA
+    out = {}
+    for label, M, tun in (("M=1", 1, None), ("M=2", 2, None), ("M=4", 4, None),
+                          ("M=2 storage-order word positioning", 2, {"word_positioning": 1})):
+        g = WarpLDA(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, M, args.seed, stream=stream,
+                    tuning=tun)
+        pts = [(0, g.loglik())]
+        ms = 0.0
+        for it in range(every, iters + 1, every):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.sweep(every)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+            pts.append((it, g.loglik()))
+        g.close()
+        out[label] = {"loglik": pts, "ms_per_sweep": ms / iters}
+    return {"iterations": iters, "runs": out}
+
+
 def foldin_bench(gpu, c, wl, args, torch, stream):
     """Fold-in of unseen documents of the workload's generator (lengths
     clipped to [20, 5000]) against the trained model: docs/s end to end
@@ -427,6 +454,8 @@ def main():
                     help="sweeps the model has when the fold-in measurements start")
     ap.add_argument("--encoder-epochs", type=int, default=4,
                     help="epochs of encoder training for the learned fold-in proposal (0: skip)")
+    ap.add_argument("--m-sweep", action="store_true",
+                    help="also record log-likelihood against iterations for M = 1, 2, 4 (Fig. 7)")
     ap.add_argument("--docs", type=int, default=0,
                     help="use only the first DOCS documents of the workload (small profiling cases)")
     args = ap.parse_args()
@@ -540,6 +569,8 @@ def main():
         if args.encoder_epochs > 0:
             foldin["serving"].append(serving_bench(gpu, c, wl, args, True, rate))
 
+    msweep = m_sweep(c, wl, args, stream) if (args.m_sweep and rank == 0) else None
+
     # end to end through the C ABI from pinned host buffers: init (H2D of the
     # corpus, token-order build) + K sweeps + D2H of z and c_k
     e2e = None
@@ -579,6 +610,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": info["launches_per_sweep"] * args.steps,
             "foldin": foldin,
+            "m_sweep": msweep,
             "clocks": clk.summary(),
             "paper_context": {"value": 110e6, "unit": UNIT,
                               "hardware": "2x Xeon E5-2692v2 (24 cores), NYTimes/PubMed, M=2"},

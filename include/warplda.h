@@ -64,13 +64,19 @@ typedef struct warplda_server warplda_server;
  *   doc_warp_max      documents with at most this many tokens (capped at 512
  *                     with dense count tables, 256 with hash tables) are
  *                     sampled one warp per document; 0 (default) or -1: off.
+ * One field changes the sampler (a different, equally valid chain):
+ *   word_positioning  the word proposal's p_A branch (Eq. 6): 0 (default) =
+ *                     the j-th smallest post-acceptance topic of the word;
+ *                     1 = the paper's random positioning (Sec. 4.3) over the
+ *                     word's tokens in storage order -- the same law, no sort.
  */
 typedef struct warplda_tuning {
     int32_t batch_max_tokens;
     int32_t huge_chunk;
     int32_t region_budget;
     int32_t doc_warp_max;
-    int32_t reserved[4];
+    int32_t word_positioning;
+    int32_t reserved[3];
 } warplda_tuning;
 
 /*

@@ -104,6 +104,12 @@ def load(mutation: int = 0) -> ctypes.CDLL:
                                            c.c_float, c.c_float, c.c_float, c.c_float, c.c_float,
                                            _i32p, _i32p, _f32p, c.c_uint64, c.c_int, _i32p,
                                            c.c_void_p]
+        lib.orc_word_phase_rule.argtypes = [c.c_int64, c.c_int64, _i64p, c.c_int, c.c_int,
+                                            c.c_float, c.c_float, c.c_float, c.c_uint64, c.c_uint32,
+                                            _i32p, _i32p, _i32p, c.c_int]
+        lib.orc_sweeps_rule.argtypes = [c.c_int64, c.c_int64, _i64p, _i32p, _i64p, c.c_int, c.c_int,
+                                        c.c_float, c.c_float, c.c_float, c.c_float, c.c_float,
+                                        c.c_uint64, c.c_uint32, c.c_int, _i32p, _i32p, _i32p, c.c_int]
         lib.orc_num_threads.restype = c.c_int
         lib.orc_set_num_threads.argtypes = [c.c_int]
         _LIBS[mutation] = lib
@@ -128,8 +134,10 @@ class Oracle:
     position -> word-major index), word_ptr[V+1], ck[K].
     """
 
-    def __init__(self, doc_ptr, doc_word, V, K, alpha, beta, M, seed, mutation: int = 0):
+    def __init__(self, doc_ptr, doc_word, V, K, alpha, beta, M, seed, mutation: int = 0,
+                 word_rule: int = 0):
         self.lib = load(mutation)
+        self.word_rule = int(word_rule)   # 0: j-th smallest topic (R7); 1: storage order (R7')
         self.doc_ptr = np.ascontiguousarray(doc_ptr, dtype=np.int64)
         self.doc_word = np.ascontiguousarray(doc_word, dtype=np.int32)
         self.D = len(self.doc_ptr) - 1
@@ -162,17 +170,18 @@ class Oracle:
     def word_phase(self, it=None, w0=0, w1=None):
         it = self.iteration + 1 if it is None else it
         w1 = self.V if w1 is None else w1
-        self.lib.orc_word_phase(w0, w1, self.word_ptr, self.K, self.M, self.beta, self.K_beta,
-                                self.beta_bar, self.seed, it, self.z, self.prop, self.ck)
+        self.lib.orc_word_phase_rule(w0, w1, self.word_ptr, self.K, self.M, self.beta, self.K_beta,
+                                     self.beta_bar, self.seed, it, self.z, self.prop, self.ck,
+                                     self.word_rule)
 
     def recount(self):
         self.lib.orc_topic_counts(self.N, self.K, self.z, self.ck)
 
     def sweep(self, n: int = 1):
-        self.lib.orc_sweeps(self.D, self.V, self.doc_ptr, self.perm, self.word_ptr, self.K,
-                            self.M, self.alpha, self.beta, self.alpha_bar, self.beta_bar,
-                            self.K_beta, self.seed, self.iteration, n, self.z, self.prop,
-                            self.ck)
+        self.lib.orc_sweeps_rule(self.D, self.V, self.doc_ptr, self.perm, self.word_ptr, self.K,
+                                 self.M, self.alpha, self.beta, self.alpha_bar, self.beta_bar,
+                                 self.K_beta, self.seed, self.iteration, n, self.z, self.prop,
+                                 self.ck, self.word_rule)
         self.iteration += n
 
     def loglik(self) -> float:

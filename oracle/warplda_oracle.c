@@ -310,7 +310,8 @@ static int cmp_int(const void* a, const void* b)
  */
 static void word_one(int64_t w, const int64_t* word_ptr, int K, int M, float beta,
                      float K_beta, float beta_bar, uint64_t seed, uint32_t iter,
-                     int32_t* z, int32_t* prop, const int32_t* ck, int32_t* cw, int32_t* znew)
+                     int32_t* z, int32_t* prop, const int32_t* ck, int32_t* cw, int32_t* znew,
+                     int storage)
 {
     int64_t b = word_ptr[w];
     int L = (int)(word_ptr[w + 1] - b);
@@ -332,7 +333,7 @@ static void word_one(int64_t w, const int64_t* word_ptr, int K, int M, float bet
     for (int j = 0; j < L; ++j) znew[j] = z[b + j];   /* pre-acceptance z_w */
 #endif
     for (int j = 0; j < L; ++j) z[b + j] = znew[j];
-    qsort(znew, (size_t)L, sizeof(int), cmp_int);
+    if (!storage) qsort(znew, (size_t)L, sizeof(int), cmp_int);
     for (int j = 0; j < L; ++j) {
         int64_t t = b + j;
         for (int i = 1; i <= M; ++i) {
@@ -344,9 +345,15 @@ static void word_one(int64_t w, const int64_t* word_ptr, int K, int M, float bet
 }
 
 /* Words [w0, w1); ck is the phase-start topic count vector (R5). */
-void orc_word_phase(int64_t w0, int64_t w1, const int64_t* word_ptr, int K, int M, float beta,
-                    float K_beta, float beta_bar, uint64_t seed, uint32_t iter, int32_t* z,
-                    int32_t* prop, const int32_t* ck)
+/*
+ * Words [w0, w1) with the word proposal rule `storage`: 0 = R7 (the j-th
+ * smallest post-acceptance topic); 1 = the paper's literal random
+ * positioning (Sec. 4.3) applied to words, the post-acceptance topic of the
+ * word's j-th token in storage (word-major) order -- the same law (R7').
+ */
+void orc_word_phase_rule(int64_t w0, int64_t w1, const int64_t* word_ptr, int K, int M, float beta,
+                         float K_beta, float beta_bar, uint64_t seed, uint32_t iter, int32_t* z,
+                         int32_t* prop, const int32_t* ck, int storage)
 {
     int64_t maxL = 0;
     for (int64_t w = w0; w < w1; ++w)
@@ -357,10 +364,18 @@ void orc_word_phase(int64_t w0, int64_t w1, const int64_t* word_ptr, int K, int 
         int32_t* znew = (int32_t*)malloc((size_t)(maxL > 0 ? maxL : 1) * sizeof(int32_t));
 #pragma omp for schedule(dynamic, 16)
         for (int64_t w = w0; w < w1; ++w)
-            word_one(w, word_ptr, K, M, beta, K_beta, beta_bar, seed, iter, z, prop, ck, cw, znew);
+            word_one(w, word_ptr, K, M, beta, K_beta, beta_bar, seed, iter, z, prop, ck, cw, znew,
+                     storage);
         free(cw);
         free(znew);
     }
+}
+
+void orc_word_phase(int64_t w0, int64_t w1, const int64_t* word_ptr, int K, int M, float beta,
+                    float K_beta, float beta_bar, uint64_t seed, uint32_t iter, int32_t* z,
+                    int32_t* prop, const int32_t* ck)
+{
+    orc_word_phase_rule(w0, w1, word_ptr, K, M, beta, K_beta, beta_bar, seed, iter, z, prop, ck, 0);
 }
 
 /*
@@ -369,19 +384,29 @@ void orc_word_phase(int64_t w0, int64_t w1, const int64_t* word_ptr, int K, int 
  * on exit.  alpha_bar = (float)K * alpha, beta_bar = (float)V * beta and
  * K_beta = (float)K * beta are single FP32 products formed by the caller.
  */
-void orc_sweeps(int64_t D, int64_t V, const int64_t* doc_ptr, const int32_t* perm,
-                const int64_t* word_ptr, int K, int M, float alpha, float beta,
-                float alpha_bar, float beta_bar, float K_beta, uint64_t seed, uint32_t iter0,
-                int n, int32_t* z, int32_t* prop, int32_t* ck)
+void orc_sweeps_rule(int64_t D, int64_t V, const int64_t* doc_ptr, const int32_t* perm,
+                     const int64_t* word_ptr, int K, int M, float alpha, float beta,
+                     float alpha_bar, float beta_bar, float K_beta, uint64_t seed, uint32_t iter0,
+                     int n, int32_t* z, int32_t* prop, int32_t* ck, int storage)
 {
     int64_t N = doc_ptr[D];
     for (int s = 1; s <= n; ++s) {
         uint32_t it = iter0 + (uint32_t)s;
         orc_doc_phase(0, D, doc_ptr, perm, K, M, alpha, alpha_bar, beta_bar, seed, it, z, prop, ck);
         orc_topic_counts(N, K, z, ck);
-        orc_word_phase(0, V, word_ptr, K, M, beta, K_beta, beta_bar, seed, it, z, prop, ck);
+        orc_word_phase_rule(0, V, word_ptr, K, M, beta, K_beta, beta_bar, seed, it, z, prop, ck,
+                            storage);
         orc_topic_counts(N, K, z, ck);
     }
+}
+
+void orc_sweeps(int64_t D, int64_t V, const int64_t* doc_ptr, const int32_t* perm,
+                const int64_t* word_ptr, int K, int M, float alpha, float beta,
+                float alpha_bar, float beta_bar, float K_beta, uint64_t seed, uint32_t iter0,
+                int n, int32_t* z, int32_t* prop, int32_t* ck)
+{
+    orc_sweeps_rule(D, V, doc_ptr, perm, word_ptr, K, M, alpha, beta, alpha_bar, beta_bar, K_beta,
+                    seed, iter0, n, z, prop, ck, 0);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -108,6 +108,7 @@ struct warplda_ctx {
     int32_t* d_bad = nullptr;
     int32_t* d_fault = nullptr;   // index-check record of the kernels
     bool sync_check = false;      // WARPLDA_SYNC_CHECK=1: read the record after every launch
+    int word_storage = 0;         // word proposals by storage-order positioning
     int32_t *rows_doc = nullptr, *rows_pre = nullptr, *rows_post = nullptr;
     int64_t rows_words = 0;
     Tier docs, words;
@@ -340,6 +341,7 @@ PhaseArgs phase_args(warplda_ctx* c, bool doc, uint32_t iter) {
     a.iter = iter;
     a.rk = round_keys(c->seed);
     a.ck = c->ck;
+    a.word_storage = c->word_storage;
     a.stage_ck = c->stage_ck;
     a.N = c->N;
     a.nseg_total = doc ? c->D : c->V;
@@ -417,7 +419,7 @@ int run_phase(warplda_ctx* c, bool doc) {
                                       q->doc ? cc->grid_acc_doc : cc->grid_acc_word, cc->st);
         }, &pc);
         if (rc) return rc;
-        if (!doc) {
+        if (!doc && !c->word_storage) {
             // the word draw takes its ranks from the post-acceptance counts
             rc = launch_rec(c, kcWordMegaHistPost, [](warplda_ctx* cc, void* p) {
                 PhaseCall* q = (PhaseCall*)p;
@@ -456,7 +458,7 @@ int run_phase(warplda_ctx* c, bool doc) {
 
 int launches_per_phase(const warplda_ctx* c, bool doc) {
     const Tier& T = doc ? c->docs : c->words;
-    return (T.chunks.empty() ? 0 : (doc ? 4 : 5)) + (T.batches[0].empty() ? 0 : 1) +
+    return (T.chunks.empty() ? 0 : ((doc || c->word_storage) ? 4 : 5)) + (T.batches[0].empty() ? 0 : 1) +
            (T.batches[1].empty() ? 0 : 1) + (T.warp_list.empty() ? 0 : 1) + (c->stage_ck ? 1 : 2);
 }
 
@@ -840,6 +842,11 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     // the doc-order sweep over the word columns that makes the perm gather
     // hit L2 (Sec. 5.2)
     int warp_max = 0;
+    if (tuning && (tuning->word_positioning < 0 || tuning->word_positioning > 1)) {
+        delete c;
+        return fail(WARPLDA_EINVAL, "word_positioning must be 0 or 1");
+    }
+    c->word_storage = (tuning && tuning->word_positioning == 1) ? 1 : 0;
     if (tuning && tuning->doc_warp_max > 0)
         warp_max = std::min(std::min(32 * c->warp_tpl, bmax), (int)tuning->doc_warp_max);
 

@@ -342,15 +342,18 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
                     atomicAdd(&dck_s[s], 1);
                 }
                 zz[j] = mine ? s : zz[j];
-                if ((kDoc || kRadix) && mine) {
+                if ((kDoc || kRadix || a.word_storage) && mine) {
+                    // document phase and storage-order word positioning: the
+                    // new topic at its position; radix sort: the sort key
                     const int p = kDoc ? lp[j] : tk[j] - base;
-                    stage[pad(p)] = kDoc ? (uint32_t)s : (((uint32_t)sl[j] << kbits) | (uint32_t)s);
+                    stage[pad(p)] = (kDoc || a.word_storage) ? (uint32_t)s
+                                                             : (((uint32_t)sl[j] << kbits) | (uint32_t)s);
                 }
             }
         }
         __syncthreads();
 
-        if (!kDoc && kDense) {
+        if (!kDoc && kDense && !a.word_storage) {
             // counting sort of each word's post-acceptance topics through its
             // dense table: post-acceptance counts, a block-wide exclusive scan
             // of the tables in place (16-bit prefixes), then each token takes
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
             __syncthreads();
         }
         const int ntok = end - base;
-        if (kRadix) {
+        if (kRadix && !a.word_storage) {
             // padding keys sort last; then the word's post-acceptance topics
             // are contiguous and ascending at [seg_tok[slot], seg_tok[slot+1])
             for (int p = ntok + tid; p < kThreads * TPT; p += kThreads) stage[pad(p)] = 0xFFFFFFFFu;
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
         }
 
         // resolve picks and write back
-        const uint32_t kmask = kRadix ? ((1u << kbits) - 1u) : 0xFFFFFFFFu;
+        const uint32_t kmask = (kRadix && !a.word_storage) ? ((1u << kbits) - 1u) : 0xFFFFFFFFu;
         if (kDoc) {
 #pragma unroll
             for (int j = 0; j < TPT; ++j) {

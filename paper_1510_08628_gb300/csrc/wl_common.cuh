@@ -151,6 +151,7 @@ struct PhaseArgs {
     uint32_t iter;           // iteration
     RoundKeys rk;            // Philox key schedule
     int32_t* ck;             // [K] c_k; with stage_ck it receives the phase's deltas
+    int32_t word_storage;    // word proposals by positioning in storage order (else j-th smallest)
     int32_t stage_ck;        // 1 (dense tables): c_k table and deltas in shared memory;
                              // 0: kernels leave c_k alone, a histogram pass rebuilds it
     int64_t N;               // tokens

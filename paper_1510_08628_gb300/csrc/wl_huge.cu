@@ -323,10 +323,15 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, HugeWo
                 }
                 continue;   // no shared state between pieces
             }
+            const bool storage = a.word_storage != 0;   // uniform
+            const int gb = w.guide_bits, nb = 1 << gb;
+            const uint64_t mult = (1ull << (32 + gb)) / (uint64_t)Ls;
+            auto bucket_of = [&](int j) { return j < 0 ? -1 : (int)(((uint64_t)j * mult) >> 32); };
             // exclusive prefix of the word's post-acceptance row: the row is
             // copied in, each thread sums a contiguous run of topics, one
             // block scan, then the runs become prefixes
             const int32_t* rq = rows_post + (int64_t)ch.x * K;
+            if (!storage) {
             for (int k = tid; k < K; k += kThreads) P[k] = rq[k];
             __syncthreads();
             const int per = (K + kThreads - 1) / kThreads;
@@ -346,15 +351,14 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, HugeWo
             // occur inside its ranks, (B(P[k]-1), B(P[k+1]-1)], so guide[b]
             // is the topic of the smallest rank of bucket b: a lower bound
             // for every rank of the bucket, from which the lookup walks up
-            const int gb = w.guide_bits, nb = 1 << gb;
-            const uint64_t mult = (1ull << (32 + gb)) / (uint64_t)Ls;
-            auto bucket_of = [&](int j) { return j < 0 ? -1 : (int)(((uint64_t)j * mult) >> 32); };
+
             for (int k = k0; k < k1; ++k) {
                 const int b0 = bucket_of(P[k] - 1) + 1, b1 = min(bucket_of(P[k + 1] - 1), nb - 1);
                 for (int b = b0; b <= b1; ++b) guide[b] = k;
             }
             for (int b = max(0, bucket_of(Ls - 1) + 1) + tid; b < nb; b += kThreads) guide[b] = K - 1;
             __syncthreads();
+            }
             // resolve the picks the accept pass stored: a rank j < L_w becomes
             // the j-th smallest post-acceptance topic of the word
             const int v0 = p0 >> 2, v1 = (p1 + 3) >> 2;
@@ -393,9 +397,14 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, HugeWo
                         if (pk < 0) {
                             int j = -pk - 1;
                             if (!chk.tok((uint32_t)j < (uint32_t)Ls, 5)) j = 0;
-                            int k = guide[bucket_of(j)];
-                            while (k + 1 < K && P[k + 1] <= j) ++k;
-                            pk = chk.tok(P[k + 1] > j, 6) ? k : 0;
+                            if (storage) {
+                                // positioning: the j-th token's new topic
+                                pk = a.z[sb + min(j, Ls - 1)];
+                            } else {
+                                int k = guide[bucket_of(j)];
+                                while (k + 1 < K && P[k + 1] <= j) ++k;
+                                pk = chk.tok(P[k + 1] > j, 6) ? k : 0;
+                            }
                         }
                         out[n] = pk;
                     }

@@ -31,7 +31,7 @@ class WarpLDAError(RuntimeError):
 class Tuning(ctypes.Structure):
     _fields_ = [("batch_max_tokens", ctypes.c_int32), ("huge_chunk", ctypes.c_int32),
                 ("region_budget", ctypes.c_int32), ("doc_warp_max", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("word_positioning", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Info(ctypes.Structure):

@@ -206,3 +206,21 @@ def test_sync_reports_clean_checks(tiny_corpus):
     g.sync()
     g.phase(2)
     g.sync()
+
+
+@pytest.mark.parametrize("kind,K,M,tuning", [("mixed", 7, 3, None), ("mixed", 5000, 2, None),
+                                             ("giant_word", 30, 2, None),
+                                             ("giant_word", 200, 4, {"huge_chunk": 300}),
+                                             ("mixed", 50, 2, {"batch_max_tokens": 64})])
+def test_storage_order_word_positioning_bit_exact(kind, K, M, tuning):
+    """The paper's literal word positioning (storage order; tuning
+    word_positioning = 1) against the oracle's rule-1 word phase."""
+    c = _edge_corpus(kind)
+    t = dict(tuning or {})
+    t["word_positioning"] = 1
+    gpu = _gpu(c, c.V, K, 0.3, 0.02, M, 99, tuning=t)
+    ref = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, K, 0.3, 0.02, M, 99, word_rule=1)
+    for s in (1, 2):
+        gpu.sweep(s)
+        ref.sweep(s)
+        _same_state(gpu, ref, f"storage {kind} K={K} M={M}")

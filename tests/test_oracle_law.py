@@ -109,7 +109,7 @@ def run_doc_law(M, mutation=0, seed=3):
                               G=abar, M=M)
 
 
-def run_word_law(M, mutation=0, seed=4):
+def run_word_law(M, mutation=0, seed=4, rule=0):
     K = 3
     z0 = np.array([0, 2, 2])
     props = np.array([[1, 0], [0, 1], [1, 2]])[:, :M]
@@ -120,8 +120,8 @@ def run_word_law(M, mutation=0, seed=4):
     z = np.tile(z0, S).astype(np.int32)
     prop = np.tile(props, (S, 1)).astype(np.int32).ravel()
     lib = oracle.load(mutation)
-    lib.orc_word_phase(0, S, word_ptr, K, M, oracle.f32(beta), oracle.f32(kbeta),
-                       oracle.f32(bbar), seed, 1, z, prop, ck)
+    lib.orc_word_phase_rule(0, S, word_ptr, K, M, oracle.f32(beta), oracle.f32(kbeta),
+                            oracle.f32(bbar), seed, 1, z, prop, ck, rule)
     obs_z = z.reshape(S, L)
     obs_p = prop.reshape(S, L, M)
     cw = np.bincount(z0, minlength=K)
@@ -136,8 +136,11 @@ def test_doc_phase_law(M):
 
 
 @pytest.mark.parametrize("M", [1, 2])
-def test_word_phase_law(M):
-    obs_z, obs_p, ex = run_word_law(M)
+@pytest.mark.parametrize("rule", [0, 1])
+def test_word_phase_law(M, rule):
+    # rule 1: the paper's literal positioning over the word's tokens in
+    # storage order -- the same law as the order-statistic rule (R7')
+    obs_z, obs_p, ex = run_word_law(M, rule=rule)
     _check_joint(obs_z, obs_p, tag="word", **ex)
 
 
