@@ -96,6 +96,11 @@ struct warplda_ctx {
     cudaStream_t st = nullptr;
     int dev = 0, sms = 0;
     int bmax[2] = {0, 0}, region[2] = {0, 0}, chunk = 0, stage_ck = 0, kbits = 0;
+    // tokens per thread of the small batch class, per phase [doc, word]: 4
+    // for documents with hash tables (more resident blocks for the
+    // latency-bound gather and probe loops), else 8
+    int tpt0[2] = {8, 8};
+    int dbmax[2] = {0, 0};
     bool dense = true;   // 16-bit dense count tables (K <= kDenseMaxK), else hash tables
     int warp_tpl = 16;   // tokens per lane of the document warp tier
     int grid_doc_warp = 1;
@@ -293,8 +298,9 @@ int check_record(warplda_ctx* c, const char* where) {
     int32_t f[4] = {0, 0, 0, 0};
     WL_CU(cudaMemcpyAsync(f, c->d_fault, sizeof(f), cudaMemcpyDeviceToHost, c->st), "read check record");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
-    if (f[0] == 0) return WARPLDA_OK;
+    if (f[0] == 0 && f[3] == 0) return WARPLDA_OK;
     WL_CU(cudaMemsetAsync(c->d_fault, 0, sizeof(f), c->st), "clear check record");
+    if (f[0] == 0) return fail(WARPLDA_ETIMEDOUT, "a tensor-core wait ran out (reported at %s)", where);
     static const char* kSites[] = {"?", "doc batch", "word batch", "multi-pass hist",
                                    "multi-pass accept", "multi-pass draw", "doc warp", "loglik",
                                    "fold-in"};
@@ -403,7 +409,7 @@ int run_phase(warplda_ctx* c, bool doc) {
             PhaseCall* q = (PhaseCall*)p;
             Tier& TT = q->doc ? cc->docs : cc->words;
             const int k = q->cls;
-            return launch_batch_phase(q->doc, cc->dense, k ? 16 : 8, q->a, TT.d_batches[k],
+            return launch_batch_phase(q->doc, cc->dense, k ? 16 : cc->tpt0[q->doc ? 0 : 1], q->a, TT.d_batches[k],
                                       (int)TT.batches[k].size(),
                                       cc->counters + 2 * k + (q->doc ? 0 : 1), TT.d_region,
                                       cc->region[k], cc->kbits, cc->grid_batch[q->doc ? 0 : 1][k],
@@ -627,6 +633,12 @@ struct warplda_server {
     int64_t staged_cap = 0;
     float* h_theta = nullptr;       // pinned: finished rows of the last step
     int32_t* h_fin_slot = nullptr;
+    int32_t* h_stage = nullptr;     // pinned upload staging: words, then requests, sources, active list
+    int64_t h_stage_cap = 0;
+    // learned proposal: admission scratch for up to nslots new requests
+    int32_t *d_aoff = nullptr, *d_aids = nullptr, *d_aslots = nullptr, *d_astack = nullptr;
+    float *d_aq = nullptr, *d_aprob = nullptr;
+    int32_t* d_aalias = nullptr;
     int n_fin_staged = 0;
     cudaEvent_t tick = nullptr;
     struct Slot {
@@ -688,6 +700,7 @@ void server_free(warplda_server* s) {
     s->allocs.clear();
     if (s->h_theta) cudaFreeHost(s->h_theta);
     if (s->h_fin_slot) cudaFreeHost(s->h_fin_slot);
+    if (s->h_stage) cudaFreeHost(s->h_stage);
     if (s->tick) cudaEventDestroy(s->tick);
 }
 
@@ -713,62 +726,69 @@ FoldArgs server_args(warplda_server* s) {
     return f;
 }
 
-// Uploads the requests admitted since the last step (one copy of their
-// words, one of their descriptors, one admission kernel) and, with the
-// learned proposal, makes their proposal rows and alias tables.
-int server_admit(warplda_server* s) {
+// Pinned staging of at least n ints.
+int stage_room(warplda_server* s, int64_t n) {
+    if (n <= s->h_stage_cap) return WARPLDA_OK;
+    if (s->h_stage) cudaFreeHost(s->h_stage);
+    s->h_stage = nullptr;
+    const int64_t cap = std::max<int64_t>(n, 2 * s->h_stage_cap);
+    if (cudaMallocHost((void**)&s->h_stage, (size_t)cap * 4) != cudaSuccess) {
+        s->h_stage_cap = 0;
+        return fail(WARPLDA_ENOMEM, "pinned staging");
+    }
+    s->h_stage_cap = cap;
+    return WARPLDA_OK;
+}
+
+// Uploads the requests admitted since the last step (one copy from pinned
+// staging, one admission kernel) and, with the learned proposal, makes their
+// proposal rows and alias tables -- all queued on the stream, no host wait.
+// The staging also carries the step's active list (written at `act_off`).
+int server_admit(warplda_server* s, const std::vector<int32_t>& active, int64_t* act_off) {
     warplda_ctx* c = s->c;
     const int n = (int)s->new_req.size();
-    if (n == 0) return WARPLDA_OK;
     const int64_t nw = (int64_t)s->new_words.size();
-    if (nw + 4 > s->staged_cap) {
-        int64_t cap = std::max<int64_t>(nw + 4, 2 * s->staged_cap);
+    // layout: words | req (4 ints each) | src | offsets (n+1) | ids | slots | active
+    // (the int4 descriptors start 16-byte aligned)
+    const int64_t o_req = r4(nw), o_src = o_req + 4 * (int64_t)n, o_off = o_src + n, o_ids = o_off + n + 1,
+                  o_sl = o_ids + n, o_act = o_sl + n, total = o_act + (int64_t)active.size();
+    int rc = stage_room(s, total + 4);
+    if (rc) return rc;
+    if (total + 4 > s->staged_cap) {
+        int64_t cap = std::max<int64_t>(total + 4, 2 * s->staged_cap);
         int32_t* p = nullptr;
         WL_CU(cudaMalloc((void**)&p, (size_t)cap * 4), "alloc staging");
         s->allocs.push_back(p);
         s->d_staged = p;
         s->staged_cap = cap;
     }
-    if (nw > 0)
-        WL_CU(cudaMemcpyAsync(s->d_staged, s->new_words.data(), (size_t)nw * 4, cudaMemcpyHostToDevice, c->st), "upload requests");
-    WL_CU(cudaMemcpyAsync(s->d_req, s->new_req.data(), (size_t)n * sizeof(int4), cudaMemcpyHostToDevice, c->st), "upload requests");
-    WL_CU(cudaMemcpyAsync(s->d_src, s->new_src.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c->st), "upload requests");
-    WL_CU(launch_serve_admit(s->d_staged, s->d_req, s->d_src, n, s->nslots, s->pool_tokens, s->d_words, s->d_info,
-                             c->st), "admit requests");
-    if (s->proposal == WARPLDA_PROPOSAL_LEARNED) {
+    int32_t* h = s->h_stage;
+    if (nw) std::memcpy(h, s->new_words.data(), (size_t)nw * 4);
+    if (n) std::memcpy(h + o_req, s->new_req.data(), (size_t)n * sizeof(int4));
+    for (int i = 0; i < n; ++i) {
+        h[o_src + i] = s->new_src[i];
+        h[o_ids + i] = i;
+        h[o_sl + i] = s->new_req[i].x;
+    }
+    for (int i = 0; i <= n; ++i) h[o_off + i] = (int32_t)s->new_ptr[i];
+    if (!active.empty()) std::memcpy(h + o_act, active.data(), active.size() * 4);
+    WL_CU(cudaMemcpyAsync(s->d_staged, h, (size_t)total * 4, cudaMemcpyHostToDevice, c->st), "upload requests");
+    *act_off = o_act;
+    const int32_t* d = s->d_staged;
+    if (n > 0)
+        WL_CU(launch_serve_admit(d, reinterpret_cast<const int4*>(d + o_req), d + o_src, n, s->nslots, s->pool_tokens,
+                                 s->d_words, s->d_info, c->st), "admit requests");
+    if (n > 0 && s->proposal == WARPLDA_PROPOSAL_LEARNED) {
         const int K = c->K;
-        FoldBuffers buf;
-        HostDocs hd;
-        float *q, *prob;
-        int32_t *alias, *stack, *off, *ids, *slots;
-        std::vector<int32_t> offv((size_t)n + 1), idv((size_t)n), slv((size_t)n);
-        for (int i = 0; i <= n; ++i) offv[i] = (int32_t)s->new_ptr[i];
-        for (int i = 0; i < n; ++i) {
-            idv[i] = i;
-            slv[i] = s->new_req[i].x;
+        auto& e = c->enc;
+        for (int b0 = 0; b0 < n; b0 += e.B) {
+            EncBatch b{d + o_ids + b0, d + o_off, d, std::min(e.B, n - b0)};
+            if ((rc = enc_forward(c, b, s->d_aq + (int64_t)b0 * K, false, nullptr))) return rc;
         }
-        WL_CU(buf.get(&off, n + 1), "alloc offsets");
-        WL_CU(buf.get(&ids, n), "alloc ids");
-        WL_CU(buf.get(&slots, n), "alloc slots");
-        WL_CU(buf.get(&q, (int64_t)n * K), "alloc proposals");
-        WL_CU(buf.get(&prob, (int64_t)n * K), "alloc alias tables");
-        WL_CU(buf.get(&alias, (int64_t)n * K), "alloc alias tables");
-        WL_CU(buf.get(&stack, (int64_t)n * K), "alloc alias scratch");
-        WL_CU(cudaMemcpyAsync(off, offv.data(), (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, c->st), "upload offsets");
-        WL_CU(cudaMemcpyAsync(ids, idv.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c->st), "upload ids");
-        WL_CU(cudaMemcpyAsync(slots, slv.data(), (size_t)n * 4, cudaMemcpyHostToDevice, c->st), "upload slots");
-        hd.off = off;
-        hd.words = s->d_staged;
-        hd.ids = ids;
-        int rc = enc_proposal_dev(c, n, hd, q);   // synchronises
-        if (rc) return rc;
-        WL_CU(launch_enc_alias(q, n, K, prob, alias, stack, c->st), "alias tables");
-        WL_CU(launch_serve_rows(q, slots, n, K, s->nslots, s->d_q, c->st), "proposal rows");
-        WL_CU(launch_serve_rows(prob, slots, n, K, s->nslots, s->d_prob, c->st), "alias rows");
-        WL_CU(launch_serve_rows(alias, slots, n, K, s->nslots, s->d_alias, c->st), "alias rows");
-        WL_CU(cudaStreamSynchronize(c->st), "synchronize");   // the temporaries are freed on return
-    } else {
-        WL_CU(cudaStreamSynchronize(c->st), "synchronize");   // the host vectors are reused
+        WL_CU(launch_enc_alias(s->d_aq, n, K, s->d_aprob, s->d_aalias, s->d_astack, c->st), "alias tables");
+        WL_CU(launch_serve_rows(s->d_aq, d + o_sl, n, K, s->nslots, s->d_q, c->st), "proposal rows");
+        WL_CU(launch_serve_rows(s->d_aprob, d + o_sl, n, K, s->nslots, s->d_prob, c->st), "alias rows");
+        WL_CU(launch_serve_rows(s->d_aalias, d + o_sl, n, K, s->nslots, s->d_alias, c->st), "alias rows");
     }
     s->new_words.clear();
     s->new_src.clear();
@@ -833,6 +853,10 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     const int rb = (tuning && tuning->region_budget > 0) ? ((tuning->region_budget + 3) & ~3) : 0;
     c->bmax[0] = std::min(bmax, kThreads * 8 - 3);
     c->bmax[1] = std::min(bmax, std::min(kMaxBatchTokens, kThreads * 16 - 3));
+    c->tpt0[0] = (K > kDenseMaxK) ? 4 : 8;
+    c->tpt0[1] = 8;
+    c->dbmax[0] = std::min(bmax, kThreads * c->tpt0[0] - 3);
+    c->dbmax[1] = c->bmax[1];
     c->region[0] = rb ? rb : 8192;
     c->region[1] = rb ? rb : 8192;
     // documents of up to 32 * warp_tpl tokens go to the warp tier; the
@@ -871,7 +895,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         for (int64_t p = 0; p < N; ++p) perm[p] = (int32_t)(fill[doc_word[p]]++);
     }
     // multi-pass ranges: four per SM, so that blocks that finish early take more
-    build_tier(doc_off, D, K, c->dense, warp_max, c->bmax, c->region, c->chunk, 4 * c->sms, &c->docs);
+    build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->region, c->chunk, 4 * c->sms, &c->docs);
     build_tier(word_off, V, K, c->dense, 0, c->bmax, c->region, c->chunk, 4 * c->sms, &c->words);
 
     // document batches list their tokens in word-major order, with each
@@ -971,7 +995,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     auto fit = [&](int per_sm) { return std::max(1, per_sm) * c->sms; };
     for (int w = 0; w < 2; ++w)
         for (int k = 0; k < 2; ++k) {
-            const int per_sm = batch_blocks_per_sm(K, c->stage_ck, c->region[k], k ? 16 : 8, w, M, c->dense);
+            const int per_sm = batch_blocks_per_sm(K, c->stage_ck, c->region[k], k ? 16 : c->tpt0[w], w, M, c->dense);
             if (per_sm < 1)
                 return bail(fail(WARPLDA_EINVAL, "batch kernel does not fit (region_budget too large?)"));
             const int64_t nb = (int64_t)(w ? c->words : c->docs).batches[k].size();
@@ -1624,7 +1648,9 @@ int warplda_server_create(warplda_ctx* c, int32_t slots, int64_t pool_tokens, in
         return bail(rc);
     if (proposal == WARPLDA_PROPOSAL_LEARNED &&
         ((rc = salloc(s, &s->d_q, (int64_t)slots * K)) || (rc = salloc(s, &s->d_prob, (int64_t)slots * K)) ||
-         (rc = salloc(s, &s->d_alias, (int64_t)slots * K))))
+         (rc = salloc(s, &s->d_alias, (int64_t)slots * K)) || (rc = salloc(s, &s->d_aq, (int64_t)slots * K)) ||
+         (rc = salloc(s, &s->d_aprob, (int64_t)slots * K)) || (rc = salloc(s, &s->d_aalias, (int64_t)slots * K)) ||
+         (rc = salloc(s, &s->d_astack, (int64_t)slots * K))))
         return bail(rc);
     if (cudaMallocHost((void**)&s->h_theta, (size_t)slots * K * 4) != cudaSuccess ||
         cudaMallocHost((void**)&s->h_fin_slot, (size_t)slots * 4) != cudaSuccess)
@@ -1672,8 +1698,8 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     warplda_ctx* c = s->c;
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
     if (s->n_fin_staged > 0) return fail(WARPLDA_ESTATE, "poll the previous step's results first");
-    int rc = server_admit(s);
-    if (rc) return rc;
+    // the pinned staging is reused: the previous step's upload must be done
+    WL_CU(cudaEventSynchronize(s->tick), "previous step");
     std::vector<int32_t> active;
     int nfin = 0;
     for (int i = 0; i < s->nslots; ++i) {
@@ -1684,12 +1710,14 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     }
     if (active_out) *active_out = (int32_t)active.size();
     if (active.empty()) return WARPLDA_OK;
-    WL_CU(cudaMemcpyAsync(s->d_active, active.data(), active.size() * 4, cudaMemcpyHostToDevice, c->st), "upload active");
+    int64_t act_off = 0;
+    int rc = server_admit(s, active, &act_off);
+    if (rc) return rc;
     WL_CU(cudaMemsetAsync(s->d_counter, 0, 8, c->st), "reset counters");
     FoldArgs f = server_args(s);
     ServeSlots sl{};
     sl.info = s->d_info;
-    sl.active = s->d_active;
+    sl.active = s->d_staged + act_off;
     sl.nactive = (int)active.size();
     sl.nslots = s->nslots;
     sl.pool_tokens = s->pool_tokens;

@@ -97,7 +97,7 @@ __device__ __forceinline__ int tab_get(const uint32_t* tab, uint32_t cap, uint32
 
 // Resident blocks per SM the register allocation is held to.
 template <bool kDoc, int TPT>
-constexpr int batch_min_blocks() { return TPT == 8 ? 2 : 1; }
+constexpr int batch_min_blocks() { return TPT == 4 ? 3 : (TPT == 8 ? 2 : 1); }
 
 template <bool kDoc, bool kDense, int TPT, int M>
 __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) batch_phase_kernel(
@@ -499,7 +499,7 @@ static const void* pick_kernel(bool doc, bool dense, int tpt, int M) {
             default: return nullptr;                                       \
         }                                                                  \
     }
-    WL_K(true, true, 8) WL_K(true, true, 16) WL_K(true, false, 8) WL_K(true, false, 16)
+    WL_K(true, true, 8) WL_K(true, true, 16) WL_K(true, false, 4) WL_K(true, false, 8) WL_K(true, false, 16)
     WL_K(false, true, 8) WL_K(false, true, 16) WL_K(false, false, 8) WL_K(false, false, 16)
 #undef WL_K
     return nullptr;
