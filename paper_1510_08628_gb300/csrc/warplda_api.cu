@@ -292,6 +292,28 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
     }
 }
 
+// Runs fn(thread, begin, end) over [0, n) split into contiguous chunks on up
+// to `threads` host threads (the token-order build at init).
+template <typename F>
+void parallel_chunks(int threads, int64_t n, F&& fn) {
+    if (threads <= 1 || n < 100000) {
+        fn(0, (int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> ts;
+    for (int t = 0; t < threads; ++t) {
+        const int64_t b = n * t / threads, e = n * (t + 1) / threads;
+        ts.emplace_back([&fn, t, b, e]() { fn(t, b, e); });
+    }
+    for (auto& th : ts) th.join();
+}
+
+int host_threads(int64_t n) {
+    if (n < 100000) return 1;
+    const unsigned hw = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(hw ? hw : 1u, 32u));
+}
+
 // Reads the index-check record of the kernels (synchronises); a non-zero
 // record means a kernel met a bad index and skipped the access.
 int check_record(warplda_ctx* c, const char* where) {
@@ -819,12 +841,30 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     if (doc_ptr[0] != 0 || doc_ptr[D] != N) return fail(WARPLDA_EINVAL, "doc_ptr must run from 0 to N");
     for (int64_t d = 0; d < D; ++d)
         if (doc_ptr[d + 1] < doc_ptr[d]) return fail(WARPLDA_EINVAL, "doc_ptr decreases at %lld", (long long)d);
+    // per-thread word histograms of contiguous token chunks (they also give
+    // the stable scatter offsets of the word-major order below)
+    const int nthr = host_threads(N);
+    std::vector<std::vector<int32_t>> whist((size_t)nthr);
+    std::vector<int64_t> bad((size_t)nthr, -1);
+    parallel_chunks(nthr, N, [&](int t, int64_t b, int64_t e) {
+        auto& h = whist[t];
+        h.assign((size_t)V, 0);
+        for (int64_t p = b; p < e; ++p) {
+            const int32_t w = doc_word[p];
+            if (w < 0 || (int64_t)w >= V) {
+                bad[t] = p;
+                return;
+            }
+            h[w] += 1;
+        }
+    });
+    for (int t = 0; t < nthr; ++t)
+        if (bad[t] >= 0)
+            return fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", doc_word[bad[t]], (long long)bad[t]);
+    if ((int)whist.size() < 1 || whist[0].empty()) whist.assign(1, std::vector<int32_t>((size_t)V, 0));
     std::vector<int64_t> wcount(V + 1, 0);
-    for (int64_t p = 0; p < N; ++p) {
-        const int32_t w = doc_word[p];
-        if (w < 0 || (int64_t)w >= V) return fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", w, (long long)p);
-        wcount[w + 1] += 1;
-    }
+    for (const auto& h : whist)
+        for (int64_t w = 0; w < V; ++w) wcount[w + 1] += h[w];
 
     warplda_ctx* c = new warplda_ctx();
     c->D = D; c->V = V; c->N = N; c->K = K; c->M = M;
@@ -891,8 +931,20 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     for (int64_t w = 0; w < V; ++w) c->word_ptr_h[w + 1] = c->word_ptr_h[w] + wcount[w + 1];
     for (int64_t w = 0; w <= V; ++w) word_off[w] = (int32_t)c->word_ptr_h[w];
     {
-        std::vector<int64_t> fill(c->word_ptr_h.begin(), c->word_ptr_h.end() - 1);
-        for (int64_t p = 0; p < N; ++p) perm[p] = (int32_t)(fill[doc_word[p]]++);
+        // stable: thread t's tokens of word w follow those of threads < t
+        const int nt = (int)whist.size();
+        std::vector<int64_t> base(c->word_ptr_h.begin(), c->word_ptr_h.end() - 1);
+        for (int t = 0; t < nt; ++t)
+            for (int64_t w = 0; w < V; ++w) {
+                const int64_t cnt = whist[t][w];
+                whist[t][w] = (int32_t)base[w];
+                base[w] += cnt;
+            }
+        parallel_chunks(nt, N, [&](int t, int64_t b, int64_t e) {
+            auto& fill = whist[t];
+            for (int64_t p = b; p < e; ++p) perm[p] = fill[doc_word[p]]++;
+        });
+        std::vector<std::vector<int32_t>>().swap(whist);
     }
     // multi-pass ranges: four per SM, so that blocks that finish early take more
     build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->region, c->chunk, 4 * c->sms, &c->docs);
@@ -913,16 +965,44 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
                 bfill.push_back(doc_off[br.x]);
             }
         std::vector<int32_t> inv((size_t)std::max<int64_t>(N, 1)), dop((size_t)std::max<int64_t>(N, 1));
-        for (int64_t p = 0; p < N; ++p) inv[perm[p]] = (int32_t)p;
-        for (int64_t d = 0; d < D; ++d)
-            for (int32_t p = doc_off[d]; p < doc_off[d + 1]; ++p) dop[p] = (int32_t)d;
-        for (int64_t t = 0; t < N; ++t) {
-            const int32_t p = inv[t], d = dop[p], b = bod[d];
-            if (b < 0) continue;
-            const int32_t q = bfill[b]++;
-            sperm[q] = (int32_t)t;
-            sinfo[q] = ((uint32_t)(d - bfirst[b]) << 16) | (uint32_t)(p - doc_off[bfirst[b]]);
+        const int nt = host_threads(N);
+        parallel_chunks(nt, N, [&](int, int64_t b, int64_t e) {
+            for (int64_t p = b; p < e; ++p) inv[perm[p]] = (int32_t)p;
+        });
+        parallel_chunks(nt, D, [&](int, int64_t b, int64_t e) {
+            for (int64_t d = b; d < e; ++d)
+                for (int32_t p = doc_off[d]; p < doc_off[d + 1]; ++p) dop[p] = (int32_t)d;
+        });
+        // word-major order grouped by batch, stable: per-thread counts per
+        // batch over contiguous ranges of t, then each thread's slots follow
+        // those of the threads before it
+        const int64_t nb = (int64_t)bfirst.size();
+        std::vector<std::vector<int32_t>> bcnt((size_t)nt, std::vector<int32_t>((size_t)std::max<int64_t>(nb, 1), 0));
+        parallel_chunks(nt, N, [&](int th, int64_t b, int64_t e) {
+            auto& cnt = bcnt[th];
+            for (int64_t t = b; t < e; ++t) {
+                const int32_t bb = bod[dop[inv[t]]];
+                if (bb >= 0) cnt[bb] += 1;
+            }
+        });
+        for (int64_t bb = 0; bb < nb; ++bb) {
+            int32_t at = bfill[bb];
+            for (int th = 0; th < nt; ++th) {
+                const int32_t cnt = bcnt[th][bb];
+                bcnt[th][bb] = at;
+                at += cnt;
+            }
         }
+        parallel_chunks(nt, N, [&](int th, int64_t b, int64_t e) {
+            auto& fill = bcnt[th];
+            for (int64_t t = b; t < e; ++t) {
+                const int32_t p = inv[t], d = dop[p], bb = bod[d];
+                if (bb < 0) continue;
+                const int32_t q = fill[bb]++;
+                sperm[q] = (int32_t)t;
+                sinfo[q] = ((uint32_t)(d - bfirst[bb]) << 16) | (uint32_t)(p - doc_off[bfirst[bb]]);
+            }
+        });
     }
 
     int rc;
