@@ -88,7 +88,14 @@ typedef struct warplda_tuning {
  *              document.  Empty documents are allowed.
  *   doc_word   host int32[N], word id in [0, V) of each token, in document
  *              order.  Empty words are allowed.
- *   K          topics, 1 <= K <= 16384.
+ *   K          topics, 1 <= K <= 1048575 (2^20 - 1).  Above 16384 the
+ *              long documents and words of the multi-pass tier count into
+ *              hash rows in device memory (capacity the power of two above
+ *              min(2 L, K) per row) instead of dense K-wide rows, and word
+ *              proposals use positioning in storage order (as tuning
+ *              word_positioning = 1, which is forced).  Fold-in, the
+ *              encoder, serving and warplda_word_counts keep a dense
+ *              [V, K] model and return EINVAL above 16384.
  *   alpha      symmetric document Dirichlet parameter (> 0, FP32; the paper's
  *              alpha after its alpha' - 1 shift, Sec. 4.2).
  *   beta       symmetric word Dirichlet parameter (> 0, FP32).

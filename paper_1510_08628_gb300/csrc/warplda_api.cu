@@ -57,6 +57,10 @@ const char* kClassNames[kcCount] = {
     "doc_warp", "doc_batch", "doc_huge_hist", "doc_huge_accept", "doc_huge_draw",
     "word_batch", "word_mega_hist", "word_mega_accept", "word_mega_hist_post", "word_mega_draw",
     "count_ck", "finalize_ck", "zero_rows"};
+// topics: packed hash entries hold (topic + 1) << 12 in 32 bits
+constexpr int kMaxTopics = (1 << 20) - 1;
+// above this K the multi-pass tier's count rows are sparse (global hash)
+constexpr int kDenseRowMaxK = 16384;
 // work counters: 0-3 batches [class][phase], 4 doc warp tier, 5-8 the
 // multi-pass passes (hist, accept, post hist, draw), 9 log-likelihood hist
 constexpr int kCounters = 12;
@@ -71,6 +75,7 @@ struct Tier {
     std::vector<int4> batches[2];    // {first segment, end segment, table words, 0}: small, large
     std::vector<int32_t> warp_list;  // segments of the warp tier (documents only)
     std::vector<int4> chunks;        // pieces {row, segment, first position, count}
+    std::vector<int32_t> row_len;    // tokens of each long segment (row)
     std::vector<int32_t> range_off;  // range r = pieces [range_off[r], range_off[r+1])
     std::vector<int32_t> region;     // table offset of each batched segment in its batch
     std::vector<int4> ll_batches;    // log-likelihood batches over all non-chunked segments
@@ -116,6 +121,12 @@ struct warplda_ctx {
     int word_storage = 0;         // word proposals by storage-order positioning
     int32_t *rows_doc = nullptr, *rows_pre = nullptr, *rows_post = nullptr;
     int64_t rows_words = 0;
+    // K above a shared-memory row: long segments count into sparse hash rows
+    // in global memory ([0] documents, [1] words)
+    bool sparse = false;
+    int64_t* d_soff[2] = {nullptr, nullptr};
+    int32_t *skeys[2] = {nullptr, nullptr}, *scnts[2] = {nullptr, nullptr};
+    int64_t sn[2] = {0, 0};
     Tier docs, words;
     std::vector<int64_t> word_ptr_h;
     int grid_batch[2][2] = {{1, 1}, {1, 1}};   // [doc 0 / word 1][class]
@@ -196,6 +207,7 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
     for (auto& b : t->batches) b.clear();
     t->warp_list.clear();
     t->chunks.clear();
+    t->row_len.clear();
     t->range_off.clear();
     t->ll_batches.clear();
     std::vector<int4> longs;   // {row, segment, first position, length}
@@ -235,6 +247,7 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
             lclose((int)s);
             const int row = (int)t->nrows++;
             t->row_tokens += L;
+            t->row_len.push_back(L);
             longs.push_back(make_int4(row, (int)s, off[s], L));
             continue;
         }
@@ -401,7 +414,22 @@ int run_phase(warplda_ctx* c, bool doc) {
     Tier& T = doc ? c->docs : c->words;
     const int nch = (int)T.chunks.size();
     int rc;
-    if (nch > 0) {
+    if (nch > 0 && c->sparse) {
+        rc = launch_rec(c, kcZero, [](warplda_ctx* cc, void* p) {
+            const int k = ((PhaseCall*)p)->doc ? 0 : 1;
+            cudaError_t e = cudaMemsetAsync(cc->skeys[k], 0, (size_t)cc->sn[k] * 4, cc->st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(cc->scnts[k], 0, (size_t)cc->sn[k] * 4, cc->st);
+            return e;
+        }, &pc);
+        if (rc) return rc;
+        rc = launch_rec(c, doc ? kcDocHugeHist : kcWordMegaHist, [](warplda_ctx* cc, void* p) {
+            PhaseCall* q = (PhaseCall*)p;
+            const int k = q->doc ? 0 : 1;
+            return launch_sparse_hist(q->doc, q->a, huge_work(cc, q->doc ? cc->docs : cc->words, kCtrHist),
+                                      SparseRows{cc->d_soff[k], cc->skeys[k], cc->scnts[k]}, cc->grid_hist, cc->st);
+        }, &pc);
+        if (rc) return rc;
+    } else if (nch > 0) {
         rc = launch_rec(c, kcZero, [](warplda_ctx* cc, void* p) {
             const bool d = ((PhaseCall*)p)->doc;
             return d ? launch_zero(cc->rows_doc, r4(cc->docs.nrows * (int64_t)cc->K), cc->st)
@@ -442,9 +470,14 @@ int run_phase(warplda_ctx* c, bool doc) {
     if (nch > 0) {
         rc = launch_rec(c, doc ? kcDocHugeAccept : kcWordMegaAccept, [](warplda_ctx* cc, void* p) {
             PhaseCall* q = (PhaseCall*)p;
-            return launch_huge_accept(q->doc, q->a, huge_work(cc, q->doc ? cc->docs : cc->words, kCtrAccept),
-                                      q->doc ? cc->rows_doc : cc->rows_pre,
-                                      q->doc ? cc->grid_acc_doc : cc->grid_acc_word, cc->st);
+            const HugeWork w = huge_work(cc, q->doc ? cc->docs : cc->words, kCtrAccept);
+            const int grid = q->doc ? cc->grid_acc_doc : cc->grid_acc_word;
+            if (cc->sparse) {
+                const int k = q->doc ? 0 : 1;
+                return launch_sparse_accept(q->doc, q->a, w, SparseRows{cc->d_soff[k], cc->skeys[k], cc->scnts[k]},
+                                            grid, cc->st);
+            }
+            return launch_huge_accept(q->doc, q->a, w, q->doc ? cc->rows_doc : cc->rows_pre, grid, cc->st);
         }, &pc);
         if (rc) return rc;
         if (!doc && !c->word_storage) {
@@ -833,7 +866,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     if (D < 0 || V < 1) return fail(WARPLDA_EINVAL, "need D >= 0 and V >= 1");
     if (N < 0 || N > (int64_t)0x7FFFFFF0) return fail(WARPLDA_EINVAL, "N must be in [0, 2^31 - 16]");
     if (V > (int64_t)0x7FFFFFF0 || D > (int64_t)0x7FFFFFF0) return fail(WARPLDA_EINVAL, "D, V too large");
-    if (K < 1 || K > 16384) return fail(WARPLDA_EINVAL, "K must be in [1, 16384]");
+    if (K < 1 || K > kMaxTopics) return fail(WARPLDA_EINVAL, "K must be in [1, %d]", kMaxTopics);
     if (M < 1 || M > 4) return fail(WARPLDA_EINVAL, "M must be in [1, 4]");
     if (!(alpha > 0.0f) || !std::isfinite(alpha)) return fail(WARPLDA_EINVAL, "alpha must be > 0");
     if (!(beta > 0.0f) || !std::isfinite(beta)) return fail(WARPLDA_EINVAL, "beta must be > 0");
@@ -911,6 +944,8 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         return fail(WARPLDA_EINVAL, "word_positioning must be 0 or 1");
     }
     c->word_storage = (tuning && tuning->word_positioning == 1) ? 1 : 0;
+    c->sparse = K > kDenseRowMaxK;
+    if (c->sparse) c->word_storage = 1;   // ranks need sorted rows; sparse rows use positioning
     if (tuning && tuning->doc_warp_max > 0)
         warp_max = std::min(std::min(32 * c->warp_tpl, bmax), (int)tuning->doc_warp_max);
 
@@ -1021,12 +1056,29 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     if ((rc = dalloc(c, &c->d_fault, 4, "alloc check record"))) return bail(rc);
     // count rows of the multi-pass tier; each row set starts 16-byte aligned
     // and is zeroed in whole int4 units
-    const int64_t rd = r4(c->docs.nrows * (int64_t)K), rw = r4(c->words.nrows * (int64_t)K);
+    const int64_t rd = c->sparse ? 0 : r4(c->docs.nrows * (int64_t)K);
+    const int64_t rw = c->sparse ? 0 : r4(c->words.nrows * (int64_t)K);
     c->rows_words = rd + 2 * rw + 4;
     if ((rc = dalloc(c, &c->rows, c->rows_words, "alloc count rows"))) return bail(rc);
     c->rows_doc = c->rows;
     c->rows_pre = c->rows + rd;
     c->rows_post = c->rows_pre + rw;
+    if (c->sparse) {
+        for (int k = 0; k < 2; ++k) {
+            const Tier& T = k ? c->words : c->docs;
+            std::vector<int64_t> off(T.row_len.size() + 1, 0);
+            for (size_t r = 0; r < T.row_len.size(); ++r)
+                off[r + 1] = off[r] + (int64_t)pow2_above((uint32_t)std::min(2 * T.row_len[r], K));
+            c->sn[k] = off.back();
+            if ((rc = dalloc(c, &c->d_soff[k], (int64_t)off.size(), "alloc sparse rows"))) return bail(rc);
+            if ((rc = dalloc(c, &c->skeys[k], c->sn[k] + 4, "alloc sparse rows"))) return bail(rc);
+            if ((rc = dalloc(c, &c->scnts[k], c->sn[k] + 4, "alloc sparse rows"))) return bail(rc);
+            if ((e = cudaMemcpyAsync(c->d_soff[k], off.data(), off.size() * 8, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+                return bail(cuda_fail(e, "upload sparse rows"));
+            if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess)   // `off` goes out of scope
+                return bail(cuda_fail(e, "synchronize"));
+        }
+    }
     for (Tier* t : {&c->docs, &c->words}) {
         for (int k = 0; k < 2; ++k) {
             if ((rc = dalloc(c, &t->d_batches[k], (int64_t)t->batches[k].size(), "alloc batches"))) return bail(rc);
@@ -1087,10 +1139,15 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         const int64_t need = ((int64_t)c->docs.warp_list.size() + kWarps - 1) / kWarps;
         c->grid_doc_warp = (int)std::min<int64_t>(fit(per_sm), std::max<int64_t>(1, need));
     }
-    c->grid_hist = fit(huge_blocks_per_sm(K, c->stage_ck, 0, false, M));
-    c->grid_acc_doc = fit(huge_blocks_per_sm(K, c->stage_ck, 1, true, M));
-    c->grid_acc_word = fit(huge_blocks_per_sm(K, c->stage_ck, 1, false, M));
-    c->grid_draw = fit(huge_blocks_per_sm(K, c->stage_ck, 2, false, M));
+    if (c->sparse) {
+        // no shared-memory rows: blocks of 256 threads, as many as fit
+        c->grid_hist = c->grid_acc_doc = c->grid_acc_word = c->grid_draw = fit(8);
+    } else {
+        c->grid_hist = fit(huge_blocks_per_sm(K, c->stage_ck, 0, false, M));
+        c->grid_acc_doc = fit(huge_blocks_per_sm(K, c->stage_ck, 1, true, M));
+        c->grid_acc_word = fit(huge_blocks_per_sm(K, c->stage_ck, 1, false, M));
+        c->grid_draw = fit(huge_blocks_per_sm(K, c->stage_ck, 2, false, M));
+    }
     c->grid_topic = (int)std::min<int64_t>(fit(topic_hist_blocks_per_sm(K)), std::max<int64_t>(1, (N + 8191) / 8192));
 
     // z = Dice(K), proposals = z (Alg. 2); c_k = histogram of z
@@ -1219,7 +1276,16 @@ int warplda_loglik(warplda_ctx* c, double* out) {
         Tier& T = doc ? c->docs : c->words;
         PhaseArgs pa = phase_args(c, doc, c->iter);
         int32_t* rows = doc ? c->rows_doc : c->rows_pre;
-        if (!T.chunks.empty()) {
+        if (!T.chunks.empty() && c->sparse) {
+            const int k = doc ? 0 : 1;
+            WL_CU(cudaMemsetAsync(c->skeys[k], 0, (size_t)c->sn[k] * 4, c->st), "zero rows");
+            WL_CU(cudaMemsetAsync(c->scnts[k], 0, (size_t)c->sn[k] * 4, c->st), "zero rows");
+            WL_CU(cudaMemsetAsync(c->counters + kCtrLoglik, 0, sizeof(int32_t), c->st), "reset counter");
+            WL_CU(launch_sparse_hist(doc, pa, huge_work(c, T, kCtrLoglik), SparseRows{c->d_soff[k], c->skeys[k], c->scnts[k]},
+                                     c->grid_hist, c->st), "loglik rows");
+            WL_CU(cudaMemsetAsync(c->counters + kCtrLoglik, 0, sizeof(int32_t), c->st), "reset counter");
+            WL_CU(launch_sparse_loglik(c->scnts[k], c->sn[k], doc ? a : b, c->d_ll, c->st), "loglik rows");
+        } else if (!T.chunks.empty()) {
             WL_CU(launch_zero(rows, r4(T.nrows * (int64_t)c->K), c->st), "zero rows");
             WL_CU(cudaMemsetAsync(c->counters + kCtrLoglik, 0, sizeof(int32_t), c->st), "reset counter");
             WL_CU(launch_huge_hist(doc, pa, huge_work(c, T, kCtrLoglik), rows, c->grid_hist, c->st),
@@ -1347,6 +1413,7 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
     if (!c || !doc_ptr || Dn < 0 || sweeps < 0) return fail(WARPLDA_EINVAL, "bad fold-in arguments");
     if (proposal != WARPLDA_PROPOSAL_PLAIN && proposal != WARPLDA_PROPOSAL_LEARNED)
         return fail(WARPLDA_EINVAL, "unknown proposal %d", proposal);
+    if (c->K > kDenseRowMaxK) return fail(WARPLDA_EINVAL, "fold-in keeps a dense [V, K] model: K must be <= %d", kDenseRowMaxK);
     if (proposal == WARPLDA_PROPOSAL_LEARNED && !c->enc.ready)
         return fail(WARPLDA_ESTATE, "the learned proposal needs an initialised encoder");
     if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
@@ -1471,6 +1538,7 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
 
 int warplda_word_counts(warplda_ctx* c, int32_t* cw) {
     if (!c || !cw) return fail(WARPLDA_EINVAL, "null argument");
+    if (c->K > kDenseRowMaxK) return fail(WARPLDA_EINVAL, "dense C_w needs K <= %d", kDenseRowMaxK);
     if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
     int rc = ensure_model(c);
@@ -1494,6 +1562,7 @@ int warplda_encoder_init(warplda_ctx* c, int32_t log2_features, int32_t hidden, 
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     auto& e = c->enc;
     if (e.ready) return fail(WARPLDA_ESTATE, "the encoder is already initialised");
+    if (c->K > kDenseRowMaxK) return fail(WARPLDA_EINVAL, "the encoder needs K <= %d", kDenseRowMaxK);
     if (log2_features < 6 || log2_features > 20) return fail(WARPLDA_EINVAL, "log2_features must be in [6, 20]");
     if (hidden < 128 || hidden > 2048 || hidden % 128) return fail(WARPLDA_EINVAL, "hidden must be a multiple of 128 in [128, 2048]");
     if (batch_rows < 128 || batch_rows > 2048 || batch_rows % 128)
@@ -1702,6 +1771,7 @@ int warplda_server_create(warplda_ctx* c, int32_t slots, int64_t pool_tokens, in
         return fail(WARPLDA_EINVAL, "unknown proposal %d", proposal);
     if (proposal == WARPLDA_PROPOSAL_LEARNED && !c->enc.ready)
         return fail(WARPLDA_ESTATE, "the learned proposal needs an initialised encoder");
+    if (c->K > kDenseRowMaxK) return fail(WARPLDA_EINVAL, "serving keeps a dense [V, K] model: K must be <= %d", kDenseRowMaxK);
     if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
     int rc = ensure_model(c);

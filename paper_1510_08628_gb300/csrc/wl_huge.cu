@@ -18,6 +18,8 @@
 // blocks once and stores its picks in the consumed proposal slots; the draw
 // pass only resolves ranks.  For long documents the draw pass recomputes the
 // blocks.
+#include <algorithm>
+
 #include "wl_block.cuh"
 #include "wl_kernels.h"
 
@@ -484,7 +486,8 @@ cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const HugeWork& w,
 cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const HugeWork& w,
                              const int32_t* rows_post, int grid, cudaStream_t st) {
     if (w.npieces <= 0) return cudaSuccess;
-    const int smem = huge_smem_bytes(a.K, a.stage_ck, 2, doc);
+    // storage-order word positioning reads z directly: no prefix, no guide
+    const int smem = a.word_storage ? 0 : huge_smem_bytes(a.K, a.stage_ck, 2, doc);
     cudaError_t e = cudaSuccess;
     if (doc) {
         WL_M_SWITCH({
@@ -499,6 +502,168 @@ cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const HugeWork& w,
             huge_draw_kernel<false, MM><<<grid, kThreads, smem, st>>>(a, w, rows_post);
         })
     }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Sparse count rows (K above what a shared-memory row holds): a long
+// segment's counts live in an open-addressing hash in global memory, keys
+// (topic + 1) and counts in two arrays, capacity a power of two of at least
+// 2 min(L, K) (so that probing ends), multiplicative hash, linear probing.
+// Word proposals then use positioning in storage order (reads z), so no
+// post-acceptance row is needed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t sparse_slot(uint32_t k, uint32_t mask) {
+    return (k * 2654435761u) & mask;   // cap <= 2^31: the low bits of the product
+}
+
+__device__ __forceinline__ void sparse_add(int32_t* keys, int32_t* cnts, uint32_t cap, uint32_t k) {
+    const uint32_t mask = cap - 1u;
+    uint32_t h = sparse_slot(k, mask);
+    for (uint32_t probe = 0; probe < cap; ++probe) {
+        const int32_t old = atomicCAS(&keys[h], 0, (int32_t)(k + 1));
+        if (old == 0 || old == (int32_t)(k + 1)) {
+            atomicAdd(&cnts[h], 1);
+            return;
+        }
+        h = (h + 1) & mask;
+    }
+}
+
+__device__ __forceinline__ int sparse_get(const int32_t* keys, const int32_t* cnts, uint32_t cap, uint32_t k) {
+    const uint32_t mask = cap - 1u;
+    uint32_t h = sparse_slot(k, mask);
+    for (uint32_t probe = 0; probe < cap; ++probe) {
+        const int32_t v = __ldg(keys + h);
+        if (v == (int32_t)(k + 1)) return __ldg(cnts + h);
+        if (v == 0) return 0;
+        h = (h + 1) & mask;
+    }
+    return 0;
+}
+
+template <bool kDoc>
+__global__ void __launch_bounds__(kThreads) sparse_hist_kernel(PhaseArgs a, HugeWork w, SparseRows r) {
+    __shared__ int s_r;
+    const int K = a.K, tid = threadIdx.x;
+    Checks chk;
+    int pc0, pc1;
+    while (next_range(w, &s_r, chk, &pc0, &pc1)) {
+        for (int pc = pc0; pc < pc1; ++pc) {
+            const int4 ch = get_piece(a, w, pc, chk);
+            const int64_t base = r.off[ch.x];
+            const uint32_t cap = (uint32_t)(r.off[ch.x + 1] - base);
+            if (!chk(cap > 0 && (cap & (cap - 1)) == 0, 7)) continue;
+            int32_t* keys = r.keys + base;
+            int32_t* cnts = r.cnts + base;
+            for (int p = ch.z + tid; p < ch.z + ch.w; p += kThreads) {
+                int t = kDoc ? a.perm[p] : p;
+                if (!chk.tok((uint32_t)t < (uint32_t)a.N, 2)) continue;
+                sparse_add(keys, cnts, cap, (uint32_t)chk.topic(a.z[t], K, 3));
+            }
+        }
+    }
+    chk.publish(a.fault, kSiteHugeHist);
+}
+
+template <bool kDoc, int M>
+__global__ void __launch_bounds__(kThreads) sparse_accept_kernel(PhaseArgs a, HugeWork w, SparseRows r) {
+    __shared__ int s_r;
+    const int K = a.K, tid = threadIdx.x;
+    const uint32_t phase = kDoc ? kPhaseDoc : kPhaseWord;
+    Checks chk;
+    int pc0, pc1;
+    while (next_range(w, &s_r, chk, &pc0, &pc1)) {
+        for (int pc = pc0; pc < pc1; ++pc) {
+            const int4 ch = get_piece(a, w, pc, chk);
+            const int64_t base = r.off[ch.x];
+            const uint32_t cap = (uint32_t)(r.off[ch.x + 1] - base);
+            if (!chk(cap > 0 && (cap & (cap - 1)) == 0, 7)) continue;
+            const int32_t* keys = r.keys + base;
+            const int32_t* cnts = r.cnts + base;
+            const int Ls = a.seg_off[ch.y + 1] - a.seg_off[ch.y];
+            const float Lf = __int2float_rn(Ls);
+            const float LG = __fadd_rn(Lf, a.G);
+            for (int p = ch.z + tid; p < ch.z + ch.w; p += kThreads) {
+                const int t = kDoc ? a.perm[p] : p;
+                if (!chk.tok((uint32_t)t < (uint32_t)a.N, 2)) continue;
+                const int z0 = chk.topic(a.z[t], K, 3);
+                int s = z0;
+                int cs = sparse_get(keys, cnts, cap, (uint32_t)s);
+                float ks = __ldg(a.ckb + s);
+                int pk[M];
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    const uint4 rr = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
+                    const int tp = chk.topic(a.prop[(int64_t)t * M + i], K, 4);
+                    if (tp != s) {
+                        const int ct = sparse_get(keys, cnts, cap, (uint32_t)tp);
+                        const float kt = __ldg(a.ckb + tp);
+                        if (accept(rr.x, cs, ct, a.g, ks, kt)) {
+                            s = tp;
+                            cs = ct;
+                            ks = kt;
+                        }
+                    }
+                    // words: the pick of Eq. 6 (a topic, or -(rank + 1)) over the
+                    // consumed proposal, resolved by the draw pass
+                    if (!kDoc)
+                        pk[i] = coin(rr.y, Lf, LG) ? -(int)(dice(rr.z, (uint32_t)Ls) + 1) : (int)dice(rr.z, (uint32_t)K);
+                }
+                if (s != z0) a.z[t] = s;
+                if (!kDoc) {
+#pragma unroll
+                    for (int i = 0; i < M; ++i) a.prop[(int64_t)t * M + i] = pk[i];
+                }
+            }
+        }
+    }
+    chk.publish(a.fault, kSiteHugeAccept);
+}
+
+cudaError_t launch_sparse_hist(bool doc, const PhaseArgs& a, const HugeWork& w, const SparseRows& r, int grid,
+                               cudaStream_t st) {
+    if (w.npieces <= 0) return cudaSuccess;
+    if (doc) sparse_hist_kernel<true><<<grid, kThreads, 0, st>>>(a, w, r);
+    else sparse_hist_kernel<false><<<grid, kThreads, 0, st>>>(a, w, r);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_accept(bool doc, const PhaseArgs& a, const HugeWork& w, const SparseRows& r, int grid,
+                                 cudaStream_t st) {
+    if (w.npieces <= 0) return cudaSuccess;
+    if (doc) {
+        WL_M_SWITCH({ sparse_accept_kernel<true, MM><<<grid, kThreads, 0, st>>>(a, w, r); })
+    } else {
+        WL_M_SWITCH({ sparse_accept_kernel<false, MM><<<grid, kThreads, 0, st>>>(a, w, r); })
+    }
+    return cudaGetLastError();
+}
+
+// Log-likelihood terms of sparse rows: sum over entries with a count of
+// lnG(g + count) - lnG(g).
+__global__ void sparse_loglik_kernel(const int32_t* __restrict__ cnts, int64_t n, double g, double* out) {
+    __shared__ double red[kWarps];
+    const double lg = lgamma(g);
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = cnts[i];
+        if (c > 0) acc += lgamma(g + (double)c) - lg;
+    }
+    for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < kWarps; ++i) s += red[i];
+        atomicAdd(out, s);
+    }
+}
+
+cudaError_t launch_sparse_loglik(const int32_t* cnts, int64_t n, double g, double* out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>(4096, (n + kThreads - 1) / kThreads);
+    sparse_loglik_kernel<<<grid, kThreads, 0, st>>>(cnts, n, g, out);
     return cudaGetLastError();
 }
 

@@ -60,7 +60,11 @@ __global__ void __launch_bounds__(kThreads) topic_hist_kernel(const int32_t* __r
         if (h[k]) atomicAdd(&ck[k], h[k]);
 }
 
+// above this K the histogram is kept in global memory
+constexpr int kTopicHistSmemMaxK = 24 * 1024;
+
 int topic_hist_blocks_per_sm(int K) {
+    if (K > kTopicHistSmemMaxK) return 8;
     const int smem = K * 4;
     if (cudaFuncSetAttribute(topic_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
         return 0;
@@ -70,9 +74,21 @@ int topic_hist_blocks_per_sm(int K) {
     return n;
 }
 
+// c_k = histogram of z for K too large for a shared-memory histogram: global
+// atomics (topics are spread over K addresses).
+__global__ void topic_hist_global_kernel(const int32_t* __restrict__ z, int64_t N, int32_t* __restrict__ ck, int K) {
+    const uint32_t km = (uint32_t)K - 1u;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&ck[min((uint32_t)z[t], km)], 1);
+}
+
 cudaError_t launch_topic_hist(const int32_t* z, int64_t N, int32_t* ck, int K, int grid, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(ck, 0, sizeof(int32_t) * K, st);
     if (e != cudaSuccess || N <= 0) return e;
+    if (K > kTopicHistSmemMaxK) {
+        topic_hist_global_kernel<<<grid_for(N), kThreads, 0, st>>>(z, N, ck, K);
+        return cudaGetLastError();
+    }
     const int smem = K * 4;
     e = cudaFuncSetAttribute(topic_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

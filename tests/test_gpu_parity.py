@@ -186,7 +186,7 @@ def test_counts_dev_and_bad_state(tiny_corpus):
 def test_invalid_arguments_rejected():
     from paper_1510_08628_gb300.warplda import WarpLDA, WarpLDAError
     c = corpus.from_lengths([3, 4], V=10, seed=1)
-    for kw in ({"K": 0}, {"K": 20000}, {"M": 0}, {"M": 5}, {"alpha": 0.0}, {"beta": -1.0}):
+    for kw in ({"K": 0}, {"K": 1 << 20}, {"M": 0}, {"M": 5}, {"alpha": 0.0}, {"beta": -1.0}):
         args = dict(K=4, alpha=0.1, beta=0.1, M=1)
         args.update(kw)
         with pytest.raises(WarpLDAError):
@@ -224,3 +224,34 @@ def test_storage_order_word_positioning_bit_exact(kind, K, M, tuning):
         gpu.sweep(s)
         ref.sweep(s)
         _same_state(gpu, ref, f"storage {kind} K={K} M={M}")
+
+
+@pytest.mark.parametrize("kind,K,M,tuning", [("giant_word", 100000, 2, None),
+                                             ("mixed", 20000, 3, {"batch_max_tokens": 64}),
+                                             ("giant_doc", (1 << 20) - 1, 1, None),
+                                             ("giant_word", 16385, 4, {"huge_chunk": 300})])
+def test_large_K_sparse_rows_bit_exact(kind, K, M, tuning):
+    """K above 16384: long segments count into hash rows in device memory and
+    word proposals use storage-order positioning (forced), so the oracle runs
+    its rule-1 word phase.  Covers the largest K the packed tables allow."""
+    c = _edge_corpus(kind)
+    gpu = _gpu(c, c.V, K, 0.3, 0.02, M, 99, tuning=tuning)
+    ref = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, K, 0.3, 0.02, M, 99, word_rule=1)
+    for s in (1, 2):
+        gpu.sweep(s)
+        ref.sweep(s)
+        _same_state(gpu, ref, f"large K {kind} K={K} M={M}")
+    gpu.sync()
+    ll, want = gpu.loglik(), ref.loglik()
+    assert abs(ll - want) <= 1e-9 * abs(want)
+
+
+def test_large_K_dense_model_calls_rejected():
+    from paper_1510_08628_gb300.warplda import WarpLDA, WarpLDAError
+    c = corpus.from_lengths([30, 40, 5], V=50, seed=1)
+    g = WarpLDA(c.doc_ptr, c.doc_word, 50, 30000, 0.1, 0.01, 1, 1)
+    g.sweep(1)
+    with pytest.raises(WarpLDAError, match="16384"):
+        g.word_counts()
+    with pytest.raises(WarpLDAError, match="16384"):
+        g.foldin(c.doc_ptr, c.doc_word, 2, 1)
