@@ -333,6 +333,20 @@ def serving_bench(gpu, c, wl, args, learned: bool, rate: float, n: int = 6000, n
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "steps": steps}
 
 
+TUNING_KEYS = ("batch_max_tokens", "huge_chunk", "region_budget", "doc_warp_max", "word_positioning")
+
+
+def parse_tuning(text: str) -> dict | None:
+    """`key=value,key=value` -> the sampler's tuning fields (None: defaults)."""
+    out = {}
+    for item in filter(None, (x.strip() for x in text.split(","))):
+        k, _, v = item.partition("=")
+        if k not in TUNING_KEYS or not v:
+            raise SystemExit(f"bad --tuning item {item!r}; keys: {', '.join(TUNING_KEYS)}")
+        out[k] = int(v)
+    return out or None
+
+
 def m_sweep(c, wl, args, stream, iters: int = 100, every: int = 10):
     """Joint log-likelihood (Sec. 6.1) against iterations for M = 1, 2, 4 on
     the same corpus and seed (the paper's Fig. 7 comparison), and for M = 2
@@ -456,6 +470,9 @@ def main():
                     help="epochs of encoder training for the learned fold-in proposal (0: skip)")
     ap.add_argument("--m-sweep", action="store_true",
                     help="also record log-likelihood against iterations for M = 1, 2, 4 (Fig. 7)")
+    ap.add_argument("--tuning", default="",
+                    help="launch tuning of the sampler as key=value pairs separated by commas "
+                         "(batch_max_tokens, huge_chunk, region_budget, doc_warp_max, word_positioning)")
     ap.add_argument("--docs", type=int, default=0,
                     help="use only the first DOCS documents of the workload (small profiling cases)")
     args = ap.parse_args()
@@ -500,7 +517,9 @@ def main():
     c, wl = corpus.generate(args.workload, seed=args.corpus_seed, D=args.docs or None)
     seed = args.seed + 1000 * rank
     stream = torch.cuda.current_stream()
-    gpu = WarpLDA(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, seed, stream=stream)
+    tun = parse_tuning(args.tuning)
+    gpu = WarpLDA(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, seed, stream=stream,
+                  tuning=tun)
     info = gpu.info()
     gpu.sweep(args.warmup)
     torch.cuda.synchronize()
@@ -580,7 +599,7 @@ def main():
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
-        g2 = WarpLDA(dp, dw, c.V, wl.K, wl.alpha, wl.beta, wl.M, seed, stream=stream)
+        g2 = WarpLDA(dp, dw, c.V, wl.K, wl.alpha, wl.beta, wl.M, seed, stream=stream, tuning=tun)
         g2.sweep(args.steps)
         z, ck = g2.counts()
         t1 = time.perf_counter()
@@ -601,7 +620,7 @@ def main():
                        "M": wl.M, "alpha": wl.alpha, "beta": wl.beta,
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": f"inputs larger than L2 (state {info['device_bytes'] / 1e9:.2f} GB)",
-                       "accept_arith": "FP32 RN, no FMA"},
+                       "accept_arith": "FP32 RN, no FMA", "tuning": tun or "defaults"},
             "roofline": roof,
             "sweep_roofline": {"alg_bytes_per_token": sweep_alg_bytes(wl.M), "achieved": sweep_gbs,
                                "peak": peak, "unit": "GB/s", "frac": sweep_gbs / peak},

@@ -62,6 +62,11 @@ def _lib():
                                        _f32p, _i32p, _i32p, c.c_void_p]
             lib.gen_words.argtypes = [c.c_int64, _i64p, c.c_int64, c.c_int, c.c_double, _f32p,
                                       _i32p, c.c_uint64, c.c_int64, _i32p, c.c_void_p]
+            lib.gen_topics_sparse.argtypes = [c.c_int64, c.c_int, c.c_double, c.c_double, c.c_uint64,
+                                              c.c_double, c.c_int, _i32p, _i64p, c.c_void_p,
+                                              c.c_void_p, c.c_void_p, c.c_void_p]
+            lib.gen_words_sparse.argtypes = [c.c_int64, _i64p, c.c_int, c.c_double, _i64p, _i32p,
+                                             _f32p, _i32p, c.c_uint64, c.c_int64, _i32p, c.c_void_p]
             _LIB = lib
         return _LIB
 
@@ -118,6 +123,35 @@ class Corpus:
         return int(self.doc_ptr[-1])
 
 
+# Above this many K_true x V entries the topic rows are truncated (sparse).
+SPARSE_TOPICS_ENTRIES = 1 << 30
+SPARSE_TOPICS_CUT = 1e-9
+
+
+class SparseTopicModel:
+    """Topic-word rows with entries below 1e-9 of each row's mass dropped
+    (renormalised), for ClueWeb-shaped vocabularies: per topic the kept word
+    ids and an alias table over them."""
+
+    def __init__(self, V: int, K_true: int, zipf_s: float, conc_c: float, seed: int,
+                 cut: float = SPARSE_TOPICS_CUT):
+        self.V, self.K_true, self.cut = int(V), int(K_true), float(cut)
+        self.rank_to_word = np.zeros(self.V, dtype=np.int32)
+        nnz = np.zeros(self.K_true, dtype=np.int64)
+        lib = _lib()
+        lib.gen_topics_sparse(self.V, self.K_true, zipf_s, conc_c, seed, self.cut, 0,
+                              self.rank_to_word, nnz, None, None, None, None)
+        self.off = np.zeros(self.K_true + 1, dtype=np.int64)
+        np.cumsum(nnz, out=self.off[1:])
+        n = int(self.off[-1])
+        self.words = np.zeros(n, dtype=np.int32)
+        self.prob = np.zeros(n, dtype=np.float32)
+        self.alias = np.zeros(n, dtype=np.int32)
+        lib.gen_topics_sparse(self.V, self.K_true, zipf_s, conc_c, seed, self.cut, 1,
+                              self.rank_to_word, nnz, self.off.ctypes.data, self.words.ctypes.data,
+                              self.prob.ctypes.data, self.alias.ctypes.data)
+
+
 class TopicModel:
     """The generating topic-word rows (alias tables) of one workload."""
 
@@ -131,6 +165,13 @@ class TopicModel:
         _lib().gen_topics(self.V, self.K_true, zipf_s, conc_c, seed, self.prob, self.alias,
                           self.rank_to_word,
                           self.phi.ctypes.data if self.phi is not None else None)
+
+
+def topic_model(wl: Workload, seed: int):
+    """Dense alias tables, or truncated rows when K_true x V is too large."""
+    if wl.K_true * wl.V > SPARSE_TOPICS_ENTRIES:
+        return SparseTopicModel(wl.V, wl.K_true, wl.zipf_s, wl.conc_c, seed)
+    return TopicModel(wl.V, wl.K_true, wl.zipf_s, wl.conc_c, seed)
 
 
 def lengths(D: int, kind: int, mean: float, sigma: float, seed: int, doc_offset: int = 0,
@@ -148,8 +189,13 @@ def generate_docs(model: TopicModel, lens: np.ndarray, doc_alpha: float, seed: i
     N = int(doc_ptr[-1])
     doc_word = np.zeros(max(N, 1), dtype=np.int32)
     tz = np.zeros(max(N, 1), dtype=np.int32) if keep_z else None
-    _lib().gen_words(D, doc_ptr, model.V, model.K_true, doc_alpha, model.prob, model.alias,
-                     seed, doc_offset, doc_word, tz.ctypes.data if tz is not None else None)
+    if isinstance(model, SparseTopicModel):
+        _lib().gen_words_sparse(D, doc_ptr, model.K_true, doc_alpha, model.off, model.words,
+                                model.prob, model.alias, seed, doc_offset, doc_word,
+                                tz.ctypes.data if tz is not None else None)
+    else:
+        _lib().gen_words(D, doc_ptr, model.V, model.K_true, doc_alpha, model.prob, model.alias,
+                         seed, doc_offset, doc_word, tz.ctypes.data if tz is not None else None)
     return Corpus(doc_ptr, doc_word[:N], model.V, tz[:N] if tz is not None else None)
 
 
@@ -159,7 +205,7 @@ def generate(name: str, seed: int = 1234, D: int | None = None, doc_offset: int 
     first D documents of the full corpus, same generator streams)."""
     wl = WORKLOADS[name]
     nd = wl.D if D is None else int(D)
-    model = TopicModel(wl.V, wl.K_true, wl.zipf_s, wl.conc_c, seed)
+    model = topic_model(wl, seed)
     lens = lengths(nd, wl.len_kind, wl.len_mean, wl.len_sigma, seed, doc_offset, wl.len_lo,
                    wl.len_hi)
     return generate_docs(model, lens, wl.doc_alpha, seed, doc_offset, keep_z), wl
@@ -177,6 +223,6 @@ def requests(name: str, seed: int, n: int, doc_offset: int, lo: int = 20, hi: in
     clipped to [lo, hi]) -- fold-in requests; doc_offset keeps their streams
     apart from the training corpus."""
     wl = WORKLOADS[name]
-    model = TopicModel(wl.V, wl.K_true, wl.zipf_s, wl.conc_c, seed)
+    model = topic_model(wl, seed)
     lens = np.clip(lengths(n, wl.len_kind, wl.len_mean, wl.len_sigma, seed, doc_offset), lo, hi)
     return generate_docs(model, lens, wl.doc_alpha, seed, doc_offset)

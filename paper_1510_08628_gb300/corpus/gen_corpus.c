@@ -201,6 +201,143 @@ void gen_topics(int64_t V, int K_true, double zipf_s, double conc_c, uint64_t se
 }
 
 /*
+ * Truncated topic-word rows for vocabularies where K_true * V dense tables do
+ * not fit (ClueWeb-shaped: 5,000 x 10^6): phi_k ~ Dir(c V zipf_s) as above,
+ * then every entry below `cut` of the row's mass is dropped and the rest
+ * renormalised.  A shape a < 1 draws U first: when ln(U) / a < -60 the
+ * entry is below e^-60 times a Gamma(1 + a) variate, far under the cut for
+ * any row (the top entries have shapes in the hundreds), so its Gamma part
+ * is not drawn.  Pass 1 (fill == 0) writes nnz[k]; pass 2 redraws the same
+ * rows and writes, for topic k at [off[k], off[k+1]), the kept word ids and
+ * their alias table over the kept entries.  rank_to_word as in gen_topics.
+ */
+static int64_t sparse_row(int64_t V, double zipf_s, double conc_c, double H, uint64_t seed, int k,
+                          double cut, const int32_t* rank_to_word, double* lw, int64_t* keep,
+                          double* pw, int64_t* small, int64_t* large, int32_t* words, float* prob,
+                          int32_t* alias)
+{
+    rng_t r;
+    rng_seed(&r, seed, TAG_PHI, (uint64_t)k);
+    double mx = -INFINITY;
+    for (int64_t rk = 0; rk < V; ++rk) {
+        double a = conc_c * (double)V * pow((double)(rk + 1), -zipf_s) / H;
+        double g;
+        if (a < 1.0) {
+            double boost = log(rng_u(&r)) / a;
+            g = boost < -60.0 ? -INFINITY : rng_log_gamma(&r, a + 1.0) + boost;
+        } else {
+            g = rng_log_gamma(&r, a);
+        }
+        lw[rank_to_word[rk]] = g;
+        if (g > mx) mx = g;
+    }
+    double tot = 0.0;
+    for (int64_t w = 0; w < V; ++w) tot += exp(lw[w] - mx);
+    const double lcut = log(cut * tot) + mx;   /* keep exp(lw - mx) / tot >= cut */
+    int64_t n = 0;
+    double kept = 0.0;
+    for (int64_t w = 0; w < V; ++w)
+        if (lw[w] >= lcut) {
+            keep[n] = w;
+            pw[n] = exp(lw[w] - mx);
+            kept += pw[n];
+            ++n;
+        }
+    if (!words) return n;
+    int64_t ns = 0, nl = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        words[i] = (int32_t)keep[i];
+        pw[i] = pw[i] / kept * (double)n;
+        if (pw[i] < 1.0) small[ns++] = i; else large[nl++] = i;
+    }
+    while (ns > 0 && nl > 0) {
+        int64_t sm = small[--ns], l = large[--nl];
+        prob[sm] = (float)pw[sm];
+        alias[sm] = (int32_t)l;
+        pw[l] = (pw[l] + pw[sm]) - 1.0;
+        if (pw[l] < 1.0) small[ns++] = l; else large[nl++] = l;
+    }
+    while (nl > 0) { int64_t l = large[--nl]; prob[l] = 1.0f; alias[l] = (int32_t)l; }
+    while (ns > 0) { int64_t sm = small[--ns]; prob[sm] = 1.0f; alias[sm] = (int32_t)sm; }
+    return n;
+}
+
+void gen_topics_sparse(int64_t V, int K_true, double zipf_s, double conc_c, uint64_t seed,
+                       double cut, int fill, int32_t* rank_to_word, int64_t* nnz,
+                       const int64_t* off, int32_t* words, float* prob, int32_t* alias)
+{
+    double H = 0.0;
+    for (int64_t r = 1; r <= V; ++r) H += pow((double)r, -zipf_s);
+    if (!fill) {
+        rng_t pr;
+        rng_seed(&pr, seed, TAG_PERM, 0);
+        for (int64_t i = 0; i < V; ++i) rank_to_word[i] = (int32_t)i;
+        for (int64_t i = V - 1; i > 0; --i) {
+            int64_t j = (int64_t)rng_below(&pr, (uint64_t)(i + 1));
+            int32_t t = rank_to_word[i];
+            rank_to_word[i] = rank_to_word[j];
+            rank_to_word[j] = t;
+        }
+    }
+#pragma omp parallel
+    {
+        double* lw = (double*)malloc((size_t)V * sizeof(double));
+        double* pw = (double*)malloc((size_t)V * sizeof(double));
+        int64_t* keep = (int64_t*)malloc((size_t)V * sizeof(int64_t));
+        int64_t* small = (int64_t*)malloc((size_t)V * sizeof(int64_t));
+        int64_t* large = (int64_t*)malloc((size_t)V * sizeof(int64_t));
+#pragma omp for schedule(dynamic, 1)
+        for (int k = 0; k < K_true; ++k) {
+            if (!fill)
+                nnz[k] = sparse_row(V, zipf_s, conc_c, H, seed, k, cut, rank_to_word, lw, keep, pw, small,
+                                    large, NULL, NULL, NULL);
+            else
+                sparse_row(V, zipf_s, conc_c, H, seed, k, cut, rank_to_word, lw, keep, pw, small, large,
+                           words + off[k], prob + off[k], alias + off[k]);
+        }
+        free(lw); free(pw); free(keep); free(small); free(large);
+    }
+}
+
+/* gen_words over truncated rows: w = words[off[z] + alias draw over nnz_z]. */
+void gen_words_sparse(int64_t D, const int64_t* doc_ptr, int K_true, double a0, const int64_t* off,
+                      const int32_t* words, const float* prob, const int32_t* alias, uint64_t seed,
+                      int64_t doc_offset, int32_t* doc_word, int32_t* true_z_out)
+{
+#pragma omp parallel
+    {
+        int64_t cap = 0;
+        int32_t* zs = NULL;
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t d = 0; d < D; ++d) {
+            int64_t b = doc_ptr[d], L = doc_ptr[d + 1] - b;
+            if (L > cap) {
+                free(zs);
+                cap = L;
+                zs = (int32_t*)malloc((size_t)cap * sizeof(int32_t));
+            }
+            rng_t r;
+            rng_seed(&r, seed, TAG_DOC, (uint64_t)(doc_offset + d));
+            double ka = (double)K_true * a0;
+            for (int64_t n = 0; n < L; ++n) {
+                int32_t z;
+                if (rng_u(&r) * ((double)n + ka) < (double)n)
+                    z = zs[rng_below(&r, (uint64_t)n)];
+                else
+                    z = (int32_t)rng_below(&r, (uint64_t)K_true);
+                zs[n] = z;
+                int64_t base = off[z], nz = off[z + 1] - base;
+                int64_t bin = base + (int64_t)rng_below(&r, (uint64_t)nz);
+                int32_t w = (rng_u(&r) < (double)prob[bin]) ? words[bin] : words[base + alias[bin]];
+                doc_word[b + n] = w;
+                if (true_z_out) true_z_out[b + n] = z;
+            }
+        }
+        free(zs);
+    }
+}
+
+/*
  * Tokens of documents [doc_offset, doc_offset + D) with the given CSR
  * offsets: z by the Polya urn of Dir(a0) over K_true topics, w ~ phi_z by the
  * alias tables.  true_z_out (optional) receives the generating topics.

@@ -124,8 +124,9 @@ struct warplda_ctx {
     // K above a shared-memory row: long segments count into sparse hash rows
     // in global memory ([0] documents, [1] words)
     bool sparse = false;
+    int ck_delta = 0;   // kernels apply c_k deltas in global memory (sparse mode)
     int64_t* d_soff[2] = {nullptr, nullptr};
-    int32_t *skeys[2] = {nullptr, nullptr}, *scnts[2] = {nullptr, nullptr};
+    unsigned long long* sslots[2] = {nullptr, nullptr};
     int64_t sn[2] = {0, 0};
     Tier docs, words;
     std::vector<int64_t> word_ptr_h;
@@ -384,6 +385,7 @@ PhaseArgs phase_args(warplda_ctx* c, bool doc, uint32_t iter) {
     a.ck = c->ck;
     a.word_storage = c->word_storage;
     a.stage_ck = c->stage_ck;
+    a.ck_delta = c->ck_delta;
     a.N = c->N;
     a.nseg_total = doc ? c->D : c->V;
     a.fault = c->d_fault;
@@ -417,16 +419,14 @@ int run_phase(warplda_ctx* c, bool doc) {
     if (nch > 0 && c->sparse) {
         rc = launch_rec(c, kcZero, [](warplda_ctx* cc, void* p) {
             const int k = ((PhaseCall*)p)->doc ? 0 : 1;
-            cudaError_t e = cudaMemsetAsync(cc->skeys[k], 0, (size_t)cc->sn[k] * 4, cc->st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(cc->scnts[k], 0, (size_t)cc->sn[k] * 4, cc->st);
-            return e;
+            return cudaMemsetAsync(cc->sslots[k], 0, (size_t)cc->sn[k] * 8, cc->st);
         }, &pc);
         if (rc) return rc;
         rc = launch_rec(c, doc ? kcDocHugeHist : kcWordMegaHist, [](warplda_ctx* cc, void* p) {
             PhaseCall* q = (PhaseCall*)p;
             const int k = q->doc ? 0 : 1;
             return launch_sparse_hist(q->doc, q->a, huge_work(cc, q->doc ? cc->docs : cc->words, kCtrHist),
-                                      SparseRows{cc->d_soff[k], cc->skeys[k], cc->scnts[k]}, cc->grid_hist, cc->st);
+                                      SparseRows{cc->d_soff[k], cc->sslots[k]}, cc->grid_hist, cc->st);
         }, &pc);
         if (rc) return rc;
     } else if (nch > 0) {
@@ -474,7 +474,7 @@ int run_phase(warplda_ctx* c, bool doc) {
             const int grid = q->doc ? cc->grid_acc_doc : cc->grid_acc_word;
             if (cc->sparse) {
                 const int k = q->doc ? 0 : 1;
-                return launch_sparse_accept(q->doc, q->a, w, SparseRows{cc->d_soff[k], cc->skeys[k], cc->scnts[k]},
+                return launch_sparse_accept(q->doc, q->a, w, SparseRows{cc->d_soff[k], cc->sslots[k]},
                                             grid, cc->st);
             }
             return launch_huge_accept(q->doc, q->a, w, q->doc ? cc->rows_doc : cc->rows_pre, grid, cc->st);
@@ -498,7 +498,7 @@ int run_phase(warplda_ctx* c, bool doc) {
     }
     // c_k of the new assignments (per-block partials, one global pass;
     // Sec. 5.4), then the FP32 operands of the next phase
-    if (!c->stage_ck) {
+    if (!c->stage_ck && !c->ck_delta) {
         rc = launch_rec(c, kcCountCk, [](warplda_ctx* cc, void*) {
             return launch_topic_hist(cc->z, cc->N, cc->ck, cc->K, cc->grid_topic, cc->st);
         }, nullptr);
@@ -520,7 +520,7 @@ int run_phase(warplda_ctx* c, bool doc) {
 int launches_per_phase(const warplda_ctx* c, bool doc) {
     const Tier& T = doc ? c->docs : c->words;
     return (T.chunks.empty() ? 0 : ((doc || c->word_storage) ? 4 : 5)) + (T.batches[0].empty() ? 0 : 1) +
-           (T.batches[1].empty() ? 0 : 1) + (T.warp_list.empty() ? 0 : 1) + (c->stage_ck ? 1 : 2);
+           (T.batches[1].empty() ? 0 : 1) + (T.warp_list.empty() ? 0 : 1) + ((c->stage_ck || c->ck_delta) ? 1 : 2);
 }
 
 int recount(warplda_ctx* c) {
@@ -946,6 +946,9 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     c->word_storage = (tuning && tuning->word_positioning == 1) ? 1 : 0;
     c->sparse = K > kDenseRowMaxK;
     if (c->sparse) c->word_storage = 1;   // ranks need sorted rows; sparse rows use positioning
+    // with 10^5..10^6 topics the deltas' global atomics rarely collide and
+    // touch only the tokens that change; the histogram pass touches all
+    c->ck_delta = c->sparse ? 1 : 0;
     if (tuning && tuning->doc_warp_max > 0)
         warp_max = std::min(std::min(32 * c->warp_tpl, bmax), (int)tuning->doc_warp_max);
 
@@ -982,8 +985,13 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         std::vector<std::vector<int32_t>>().swap(whist);
     }
     // multi-pass ranges: four per SM, so that blocks that finish early take more
-    build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->region, c->chunk, 4 * c->sms, &c->docs);
-    build_tier(word_off, V, K, c->dense, 0, c->bmax, c->region, c->chunk, 4 * c->sms, &c->words);
+    // dense rows live in shared memory: one range per block slot suffices.
+    // Sparse rows live in global memory: ranges of ~4K tokens taken in
+    // order keep the rows that the resident blocks touch at once few enough
+    // to stay in L2.
+    const int ranges_target = c->sparse ? (1 << 30) : 4 * c->sms;
+    build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->region, c->chunk, ranges_target, &c->docs);
+    build_tier(word_off, V, K, c->dense, 0, c->bmax, c->region, c->chunk, ranges_target, &c->words);
 
     // document batches list their tokens in word-major order, with each
     // token's segment slot and position (document order) in the batch: a
@@ -1071,8 +1079,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
                 off[r + 1] = off[r] + (int64_t)pow2_above((uint32_t)std::min(2 * T.row_len[r], K));
             c->sn[k] = off.back();
             if ((rc = dalloc(c, &c->d_soff[k], (int64_t)off.size(), "alloc sparse rows"))) return bail(rc);
-            if ((rc = dalloc(c, &c->skeys[k], c->sn[k] + 4, "alloc sparse rows"))) return bail(rc);
-            if ((rc = dalloc(c, &c->scnts[k], c->sn[k] + 4, "alloc sparse rows"))) return bail(rc);
+            if ((rc = dalloc(c, &c->sslots[k], c->sn[k] + 2, "alloc sparse rows"))) return bail(rc);
             if ((e = cudaMemcpyAsync(c->d_soff[k], off.data(), off.size() * 8, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
                 return bail(cuda_fail(e, "upload sparse rows"));
             if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess)   // `off` goes out of scope
@@ -1278,13 +1285,12 @@ int warplda_loglik(warplda_ctx* c, double* out) {
         int32_t* rows = doc ? c->rows_doc : c->rows_pre;
         if (!T.chunks.empty() && c->sparse) {
             const int k = doc ? 0 : 1;
-            WL_CU(cudaMemsetAsync(c->skeys[k], 0, (size_t)c->sn[k] * 4, c->st), "zero rows");
-            WL_CU(cudaMemsetAsync(c->scnts[k], 0, (size_t)c->sn[k] * 4, c->st), "zero rows");
+            WL_CU(cudaMemsetAsync(c->sslots[k], 0, (size_t)c->sn[k] * 8, c->st), "zero rows");
             WL_CU(cudaMemsetAsync(c->counters + kCtrLoglik, 0, sizeof(int32_t), c->st), "reset counter");
-            WL_CU(launch_sparse_hist(doc, pa, huge_work(c, T, kCtrLoglik), SparseRows{c->d_soff[k], c->skeys[k], c->scnts[k]},
+            WL_CU(launch_sparse_hist(doc, pa, huge_work(c, T, kCtrLoglik), SparseRows{c->d_soff[k], c->sslots[k]},
                                      c->grid_hist, c->st), "loglik rows");
             WL_CU(cudaMemsetAsync(c->counters + kCtrLoglik, 0, sizeof(int32_t), c->st), "reset counter");
-            WL_CU(launch_sparse_loglik(c->scnts[k], c->sn[k], doc ? a : b, c->d_ll, c->st), "loglik rows");
+            WL_CU(launch_sparse_loglik(c->sslots[k], c->sn[k], doc ? a : b, c->d_ll, c->st), "loglik rows");
         } else if (!T.chunks.empty()) {
             WL_CU(launch_zero(rows, r4(T.nrows * (int64_t)c->K), c->st), "zero rows");
             WL_CU(cudaMemsetAsync(c->counters + kCtrLoglik, 0, sizeof(int32_t), c->st), "reset counter");

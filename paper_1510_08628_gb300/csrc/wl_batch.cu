@@ -340,6 +340,9 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
                 if (kDense && mine && s != z0) {
                     atomicSub(&dck_s[z0], 1);
                     atomicAdd(&dck_s[s], 1);
+                } else if (!kDense && a.ck_delta && mine && s != z0) {
+                    atomicSub(&a.ck[z0], 1);
+                    atomicAdd(&a.ck[s], 1);
                 }
                 zz[j] = mine ? s : zz[j];
                 if ((kDoc || kRadix || a.word_storage) && mine) {

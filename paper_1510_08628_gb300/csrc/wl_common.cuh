@@ -154,6 +154,8 @@ struct PhaseArgs {
     int32_t word_storage;    // word proposals by positioning in storage order (else j-th smallest)
     int32_t stage_ck;        // 1 (dense tables): c_k table and deltas in shared memory;
                              // 0: kernels leave c_k alone, a histogram pass rebuilds it
+    int32_t ck_delta;        // 1 (K above a shared-memory row): kernels add each changed
+                             // token's -1 / +1 to c_k in global memory (no histogram pass)
     int64_t N;               // tokens
     int64_t nseg_total;      // documents (document phase) or words (word phase)
     int32_t* fault;          // index-check record {kernel site, 0, check bits, 0}

@@ -141,6 +141,9 @@ __global__ void __launch_bounds__(kThreads, (docwarp_min_blocks<TPL>())) doc_war
                 if (a.stage_ck && s != z0) {
                     atomicSub(&dck_s[z0], 1);
                     atomicAdd(&dck_s[s], 1);
+                } else if (a.ck_delta && s != z0) {
+                    atomicSub(&a.ck[z0], 1);
+                    atomicAdd(&a.ck[s], 1);
                 }
                 zz[m] = s;
                 zst[j] = (uint32_t)s;

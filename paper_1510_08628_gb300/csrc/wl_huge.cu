@@ -168,6 +168,9 @@ __global__ void __launch_bounds__(kThreads, (M <= 2 ? 3 : 2)) huge_accept_kernel
         if (a.stage_ck && s != z0) {
             atomicSub(&dck_s[z0], 1);
             atomicAdd(&dck_s[s], 1);
+        } else if (a.ck_delta && s != z0) {
+            atomicSub(&a.ck[z0], 1);
+            atomicAdd(&a.ck[s], 1);
         }
     };
     const uint32_t phase = kDoc ? kPhaseDoc : kPhaseWord;
@@ -507,36 +510,47 @@ cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const HugeWork& w,
 
 // ---------------------------------------------------------------------------
 // Sparse count rows (K above what a shared-memory row holds): a long
-// segment's counts live in an open-addressing hash in global memory, keys
-// (topic + 1) and counts in two arrays, capacity a power of two of at least
-// 2 min(L, K) (so that probing ends), multiplicative hash, linear probing.
-// Word proposals then use positioning in storage order (reads z), so no
+// segment's counts live in an open-addressing hash in global memory, one
+// 64-bit slot per entry ((topic + 1) << 32 | count), capacity a power of two
+// above min(2 L, K) (so that probing ends), multiplicative hash, linear
+// probing.  A token costs one atomic when its topic is present.  Word
+// proposals then use positioning in storage order (reads z), so no
 // post-acceptance row is needed.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t sparse_slot(uint32_t k, uint32_t mask) {
     return (k * 2654435761u) & mask;   // cap <= 2^31: the low bits of the product
 }
 
-__device__ __forceinline__ void sparse_add(int32_t* keys, int32_t* cnts, uint32_t cap, uint32_t k) {
+__device__ __forceinline__ void sparse_add(unsigned long long* slots, uint32_t cap, uint32_t k, uint32_t n) {
     const uint32_t mask = cap - 1u;
+    const unsigned long long key = (unsigned long long)(k + 1u) << 32;
     uint32_t h = sparse_slot(k, mask);
     for (uint32_t probe = 0; probe < cap; ++probe) {
-        const int32_t old = atomicCAS(&keys[h], 0, (int32_t)(k + 1));
-        if (old == 0 || old == (int32_t)(k + 1)) {
-            atomicAdd(&cnts[h], 1);
+        // a stale empty read is settled by the CAS below
+        const unsigned long long v = __ldcg(slots + h);
+        if ((v >> 32) == (k + 1u)) {
+            atomicAdd(slots + h, (unsigned long long)n);
             return;
+        }
+        if (v == 0ull) {
+            const unsigned long long old = atomicCAS(slots + h, 0ull, key | n);
+            if (old == 0ull) return;
+            if ((old >> 32) == (k + 1u)) {
+                atomicAdd(slots + h, (unsigned long long)n);
+                return;
+            }
         }
         h = (h + 1) & mask;
     }
 }
 
-__device__ __forceinline__ int sparse_get(const int32_t* keys, const int32_t* cnts, uint32_t cap, uint32_t k) {
+__device__ __forceinline__ int sparse_get(const unsigned long long* slots, uint32_t cap, uint32_t k) {
     const uint32_t mask = cap - 1u;
     uint32_t h = sparse_slot(k, mask);
     for (uint32_t probe = 0; probe < cap; ++probe) {
-        const int32_t v = __ldg(keys + h);
-        if (v == (int32_t)(k + 1)) return __ldg(cnts + h);
-        if (v == 0) return 0;
+        const unsigned long long v = __ldg(slots + h);
+        if ((v >> 32) == (k + 1u)) return (int)(uint32_t)v;
+        if (v == 0ull) return 0;
         h = (h + 1) & mask;
     }
     return 0;
@@ -554,12 +568,15 @@ __global__ void __launch_bounds__(kThreads) sparse_hist_kernel(PhaseArgs a, Huge
             const int64_t base = r.off[ch.x];
             const uint32_t cap = (uint32_t)(r.off[ch.x + 1] - base);
             if (!chk(cap > 0 && (cap & (cap - 1)) == 0, 7)) continue;
-            int32_t* keys = r.keys + base;
-            int32_t* cnts = r.cnts + base;
+            unsigned long long* slots = r.slots + base;
             for (int p = ch.z + tid; p < ch.z + ch.w; p += kThreads) {
                 int t = kDoc ? a.perm[p] : p;
                 if (!chk.tok((uint32_t)t < (uint32_t)a.N, 2)) continue;
-                sparse_add(keys, cnts, cap, (uint32_t)chk.topic(a.z[t], K, 3));
+                // lanes of a warp count tokens of the same segment: one
+                // insert per distinct topic among them
+                const uint32_t k = (uint32_t)chk.topic(a.z[t], K, 3);
+                const unsigned m = __match_any_sync(__activemask(), k);
+                if ((threadIdx.x & 31) == __ffs(m) - 1) sparse_add(slots, cap, k, (uint32_t)__popc(m));
             }
         }
     }
@@ -579,8 +596,7 @@ __global__ void __launch_bounds__(kThreads) sparse_accept_kernel(PhaseArgs a, Hu
             const int64_t base = r.off[ch.x];
             const uint32_t cap = (uint32_t)(r.off[ch.x + 1] - base);
             if (!chk(cap > 0 && (cap & (cap - 1)) == 0, 7)) continue;
-            const int32_t* keys = r.keys + base;
-            const int32_t* cnts = r.cnts + base;
+            const unsigned long long* slots = r.slots + base;
             const int Ls = a.seg_off[ch.y + 1] - a.seg_off[ch.y];
             const float Lf = __int2float_rn(Ls);
             const float LG = __fadd_rn(Lf, a.G);
@@ -589,7 +605,7 @@ __global__ void __launch_bounds__(kThreads) sparse_accept_kernel(PhaseArgs a, Hu
                 if (!chk.tok((uint32_t)t < (uint32_t)a.N, 2)) continue;
                 const int z0 = chk.topic(a.z[t], K, 3);
                 int s = z0;
-                int cs = sparse_get(keys, cnts, cap, (uint32_t)s);
+                int cs = sparse_get(slots, cap, (uint32_t)s);
                 float ks = __ldg(a.ckb + s);
                 int pk[M];
 #pragma unroll
@@ -597,7 +613,7 @@ __global__ void __launch_bounds__(kThreads) sparse_accept_kernel(PhaseArgs a, Hu
                     const uint4 rr = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
                     const int tp = chk.topic(a.prop[(int64_t)t * M + i], K, 4);
                     if (tp != s) {
-                        const int ct = sparse_get(keys, cnts, cap, (uint32_t)tp);
+                        const int ct = sparse_get(slots, cap, (uint32_t)tp);
                         const float kt = __ldg(a.ckb + tp);
                         if (accept(rr.x, cs, ct, a.g, ks, kt)) {
                             s = tp;
@@ -610,7 +626,13 @@ __global__ void __launch_bounds__(kThreads) sparse_accept_kernel(PhaseArgs a, Hu
                     if (!kDoc)
                         pk[i] = coin(rr.y, Lf, LG) ? -(int)(dice(rr.z, (uint32_t)Ls) + 1) : (int)dice(rr.z, (uint32_t)K);
                 }
-                if (s != z0) a.z[t] = s;
+                if (s != z0) {
+                    a.z[t] = s;
+                    if (a.ck_delta) {
+                        atomicSub(&a.ck[z0], 1);
+                        atomicAdd(&a.ck[s], 1);
+                    }
+                }
                 if (!kDoc) {
 #pragma unroll
                     for (int i = 0; i < M; ++i) a.prop[(int64_t)t * M + i] = pk[i];
@@ -642,12 +664,13 @@ cudaError_t launch_sparse_accept(bool doc, const PhaseArgs& a, const HugeWork& w
 
 // Log-likelihood terms of sparse rows: sum over entries with a count of
 // lnG(g + count) - lnG(g).
-__global__ void sparse_loglik_kernel(const int32_t* __restrict__ cnts, int64_t n, double g, double* out) {
+__global__ void sparse_loglik_kernel(const unsigned long long* __restrict__ slots, int64_t n, double g,
+                                     double* out) {
     __shared__ double red[kWarps];
     const double lg = lgamma(g);
     double acc = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = cnts[i];
+        const int c = (int)(uint32_t)slots[i];
         if (c > 0) acc += lgamma(g + (double)c) - lg;
     }
     for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
@@ -660,10 +683,11 @@ __global__ void sparse_loglik_kernel(const int32_t* __restrict__ cnts, int64_t n
     }
 }
 
-cudaError_t launch_sparse_loglik(const int32_t* cnts, int64_t n, double g, double* out, cudaStream_t st) {
+cudaError_t launch_sparse_loglik(const unsigned long long* slots, int64_t n, double g, double* out,
+                                 cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     const int grid = (int)std::min<int64_t>(4096, (n + kThreads - 1) / kThreads);
-    sparse_loglik_kernel<<<grid, kThreads, 0, st>>>(cnts, n, g, out);
+    sparse_loglik_kernel<<<grid, kThreads, 0, st>>>(slots, n, g, out);
     return cudaGetLastError();
 }
 

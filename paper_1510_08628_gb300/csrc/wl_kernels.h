@@ -39,17 +39,18 @@ cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const HugeWork& w,
 cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const HugeWork& w,
                              const int32_t* rows_post, int grid, cudaStream_t st);
 // Sparse count rows (large K): row r's hash occupies [off[r], off[r+1]) of
-// keys (topic + 1, 0 = empty) and cnts; capacities are powers of two.
+// slots, each (topic + 1) << 32 | count (0 = empty); capacities are powers
+// of two.
 struct SparseRows {
     const int64_t* off;
-    int32_t* keys;
-    int32_t* cnts;
+    unsigned long long* slots;
 };
 cudaError_t launch_sparse_hist(bool doc, const PhaseArgs& a, const HugeWork& w, const SparseRows& r, int grid,
                                cudaStream_t st);
 cudaError_t launch_sparse_accept(bool doc, const PhaseArgs& a, const HugeWork& w, const SparseRows& r, int grid,
                                  cudaStream_t st);
-cudaError_t launch_sparse_loglik(const int32_t* cnts, int64_t n, double g, double* out, cudaStream_t st);
+cudaError_t launch_sparse_loglik(const unsigned long long* slots, int64_t n, double g, double* out,
+                                 cudaStream_t st);
 
 // Fold-in of new documents against a frozen model (wl_foldin.cu).
 struct FoldArgs {
