@@ -608,7 +608,7 @@ def main():
         e2e = {"value": c.N * args.steps * ws / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int((dp.nbytes + dw.nbytes) / args.steps),
                "d2h_bytes_per_step": int((z.nbytes + ck.nbytes) / args.steps),
-               "seconds": e2e_s, "includes": "init (host token-order build + H2D) + sweeps + "
+               "seconds": e2e_s, "includes": "init (H2D of the corpus, device token-order build) + sweeps + "
                                              "D2H of z and c_k"}
 
     if rank == 0:

@@ -11,8 +11,8 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
-#include <vector>
 #include <thread>
+#include <vector>
 #include <chrono>
 #include <map>
 
@@ -304,28 +304,6 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
         }
         if (fill > 0) t->range_off.push_back((int32_t)t->chunks.size());
     }
-}
-
-// Runs fn(thread, begin, end) over [0, n) split into contiguous chunks on up
-// to `threads` host threads (the token-order build at init).
-template <typename F>
-void parallel_chunks(int threads, int64_t n, F&& fn) {
-    if (threads <= 1 || n < 100000) {
-        fn(0, (int64_t)0, n);
-        return;
-    }
-    std::vector<std::thread> ts;
-    for (int t = 0; t < threads; ++t) {
-        const int64_t b = n * t / threads, e = n * (t + 1) / threads;
-        ts.emplace_back([&fn, t, b, e]() { fn(t, b, e); });
-    }
-    for (auto& th : ts) th.join();
-}
-
-int host_threads(int64_t n) {
-    if (n < 100000) return 1;
-    const unsigned hw = std::thread::hardware_concurrency();
-    return (int)std::max(1u, std::min(hw ? hw : 1u, 32u));
 }
 
 // Reads the index-check record of the kernels (synchronises); a non-zero
@@ -874,31 +852,6 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     if (doc_ptr[0] != 0 || doc_ptr[D] != N) return fail(WARPLDA_EINVAL, "doc_ptr must run from 0 to N");
     for (int64_t d = 0; d < D; ++d)
         if (doc_ptr[d + 1] < doc_ptr[d]) return fail(WARPLDA_EINVAL, "doc_ptr decreases at %lld", (long long)d);
-    // per-thread word histograms of contiguous token chunks (they also give
-    // the stable scatter offsets of the word-major order below)
-    const int nthr = host_threads(N);
-    std::vector<std::vector<int32_t>> whist((size_t)nthr);
-    std::vector<int64_t> bad((size_t)nthr, -1);
-    parallel_chunks(nthr, N, [&](int t, int64_t b, int64_t e) {
-        auto& h = whist[t];
-        h.assign((size_t)V, 0);
-        for (int64_t p = b; p < e; ++p) {
-            const int32_t w = doc_word[p];
-            if (w < 0 || (int64_t)w >= V) {
-                bad[t] = p;
-                return;
-            }
-            h[w] += 1;
-        }
-    });
-    for (int t = 0; t < nthr; ++t)
-        if (bad[t] >= 0)
-            return fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", doc_word[bad[t]], (long long)bad[t]);
-    if ((int)whist.size() < 1 || whist[0].empty()) whist.assign(1, std::vector<int32_t>((size_t)V, 0));
-    std::vector<int64_t> wcount(V + 1, 0);
-    for (const auto& h : whist)
-        for (int64_t w = 0; w < V; ++w) wcount[w + 1] += h[w];
-
     warplda_ctx* c = new warplda_ctx();
     c->D = D; c->V = V; c->N = N; c->K = K; c->M = M;
     c->alpha = alpha; c->beta = beta;
@@ -962,92 +915,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaDeviceGetAttribute"));
 
-    // word-major order: stable counting sort of the tokens by word (Sec. 5.2)
-    std::vector<int32_t> doc_off(D + 1), word_off(V + 1), perm((size_t)N + 4, 0);
-    for (int64_t d = 0; d <= D; ++d) doc_off[d] = (int32_t)doc_ptr[d];
-    c->word_ptr_h.assign(V + 1, 0);
-    for (int64_t w = 0; w < V; ++w) c->word_ptr_h[w + 1] = c->word_ptr_h[w] + wcount[w + 1];
-    for (int64_t w = 0; w <= V; ++w) word_off[w] = (int32_t)c->word_ptr_h[w];
-    {
-        // stable: thread t's tokens of word w follow those of threads < t
-        const int nt = (int)whist.size();
-        std::vector<int64_t> base(c->word_ptr_h.begin(), c->word_ptr_h.end() - 1);
-        for (int t = 0; t < nt; ++t)
-            for (int64_t w = 0; w < V; ++w) {
-                const int64_t cnt = whist[t][w];
-                whist[t][w] = (int32_t)base[w];
-                base[w] += cnt;
-            }
-        parallel_chunks(nt, N, [&](int t, int64_t b, int64_t e) {
-            auto& fill = whist[t];
-            for (int64_t p = b; p < e; ++p) perm[p] = fill[doc_word[p]]++;
-        });
-        std::vector<std::vector<int32_t>>().swap(whist);
-    }
-    // multi-pass ranges: four per SM, so that blocks that finish early take more
-    // dense rows live in shared memory: one range per block slot suffices.
-    // Sparse rows live in global memory: ranges of ~4K tokens taken in
-    // order keep the rows that the resident blocks touch at once few enough
-    // to stay in L2.
-    const int ranges_target = c->sparse ? (1 << 30) : 4 * c->sms;
-    build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->region, c->chunk, ranges_target, &c->docs);
-    build_tier(word_off, V, K, c->dense, 0, c->bmax, c->region, c->chunk, ranges_target, &c->words);
-
-    // document batches list their tokens in word-major order, with each
-    // token's segment slot and position (document order) in the batch: a
-    // counting pass over the word-major order grouped by batch
-    std::vector<int32_t> sperm((size_t)N + 4, 0);
-    std::vector<uint32_t> sinfo((size_t)N + 4, 0u);
-    {
-        std::vector<int32_t> bod((size_t)std::max<int64_t>(D, 1), -1);
-        std::vector<int32_t> bfirst, bfill;
-        for (int k = 0; k < 2; ++k)
-            for (const int4& br : c->docs.batches[k]) {
-                for (int d = br.x; d < br.y; ++d) bod[d] = (int32_t)bfirst.size();
-                bfirst.push_back(br.x);
-                bfill.push_back(doc_off[br.x]);
-            }
-        std::vector<int32_t> inv((size_t)std::max<int64_t>(N, 1)), dop((size_t)std::max<int64_t>(N, 1));
-        const int nt = host_threads(N);
-        parallel_chunks(nt, N, [&](int, int64_t b, int64_t e) {
-            for (int64_t p = b; p < e; ++p) inv[perm[p]] = (int32_t)p;
-        });
-        parallel_chunks(nt, D, [&](int, int64_t b, int64_t e) {
-            for (int64_t d = b; d < e; ++d)
-                for (int32_t p = doc_off[d]; p < doc_off[d + 1]; ++p) dop[p] = (int32_t)d;
-        });
-        // word-major order grouped by batch, stable: per-thread counts per
-        // batch over contiguous ranges of t, then each thread's slots follow
-        // those of the threads before it
-        const int64_t nb = (int64_t)bfirst.size();
-        std::vector<std::vector<int32_t>> bcnt((size_t)nt, std::vector<int32_t>((size_t)std::max<int64_t>(nb, 1), 0));
-        parallel_chunks(nt, N, [&](int th, int64_t b, int64_t e) {
-            auto& cnt = bcnt[th];
-            for (int64_t t = b; t < e; ++t) {
-                const int32_t bb = bod[dop[inv[t]]];
-                if (bb >= 0) cnt[bb] += 1;
-            }
-        });
-        for (int64_t bb = 0; bb < nb; ++bb) {
-            int32_t at = bfill[bb];
-            for (int th = 0; th < nt; ++th) {
-                const int32_t cnt = bcnt[th][bb];
-                bcnt[th][bb] = at;
-                at += cnt;
-            }
-        }
-        parallel_chunks(nt, N, [&](int th, int64_t b, int64_t e) {
-            auto& fill = bcnt[th];
-            for (int64_t t = b; t < e; ++t) {
-                const int32_t p = inv[t], d = dop[p], bb = bod[d];
-                if (bb < 0) continue;
-                const int32_t q = fill[bb]++;
-                sperm[q] = (int32_t)t;
-                sinfo[q] = ((uint32_t)(d - bfirst[bb]) << 16) | (uint32_t)(p - doc_off[bfirst[bb]]);
-            }
-        });
-    }
-
+    // token arrays first: the word-major order is built on the device in them
     int rc;
     if ((rc = dalloc(c, &c->z, N + 4, "alloc z"))) return bail(rc);
     if ((rc = dalloc(c, &c->sperm, N + 4, "alloc sorted perm"))) return bail(rc);
@@ -1056,11 +924,50 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     if ((rc = dalloc(c, &c->perm, N + 4, "alloc perm"))) return bail(rc);
     if ((rc = dalloc(c, &c->doc_off, D + 1, "alloc doc offsets"))) return bail(rc);
     if ((rc = dalloc(c, &c->word_off, V + 1, "alloc word offsets"))) return bail(rc);
+    if ((rc = dalloc(c, &c->d_bad, 2, "alloc flag"))) return bail(rc);
+    // word ids go where pass 0 of the word sort reads them, so that the last
+    // pass leaves the positions in prop (z and prop are rewritten at the end)
+    const bool odd = token_sort_passes(V) % 2 == 1;
+    int32_t* ka = odd ? c->sperm : c->z;
+    int32_t* va = odd ? reinterpret_cast<int32_t*>(c->sinfo) : c->prop;
+    int32_t* kb = odd ? c->z : c->sperm;
+    int32_t* vb = odd ? c->prop : reinterpret_cast<int32_t*>(c->sinfo);
+    std::vector<int32_t> doc_off(D + 1), word_off(V + 1);
+    for (int64_t d = 0; d <= D; ++d) doc_off[d] = (int32_t)doc_ptr[d];
+    std::vector<int32_t> wcount((size_t)V, 0);
+    {
+        const int32_t init_bad[2] = {0x7FFFFFFF, 0x7FFFFFFF};
+        int32_t bad[2];
+        if (N > 0 && (e = cudaMemcpyAsync(ka, doc_word, (size_t)N * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+            return bail(cuda_fail(e, "upload word ids"));
+        if ((e = cudaMemcpyAsync(c->d_bad, init_bad, sizeof(init_bad), cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+            return bail(cuda_fail(e, "upload flag"));
+        if ((e = launch_word_hist(ka, N, (int32_t)V, c->word_off, c->d_bad, c->st)) != cudaSuccess)
+            return bail(cuda_fail(e, "word histogram"));
+        if ((e = cudaMemcpyAsync(wcount.data(), c->word_off, (size_t)V * 4, cudaMemcpyDeviceToHost, c->st)) != cudaSuccess)
+            return bail(cuda_fail(e, "copy word lengths"));
+        if ((e = cudaMemcpyAsync(bad, c->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->st)) != cudaSuccess)
+            return bail(cuda_fail(e, "copy flag"));
+        if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return bail(cuda_fail(e, "word histogram"));
+        if (bad[0] != 0x7FFFFFFF)
+            return bail(fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", doc_word[bad[0]], (long long)bad[0]));
+    }
+    c->word_ptr_h.assign(V + 1, 0);
+    for (int64_t w = 0; w < V; ++w) c->word_ptr_h[w + 1] = c->word_ptr_h[w] + wcount[w];
+    for (int64_t w = 0; w <= V; ++w) word_off[w] = (int32_t)c->word_ptr_h[w];
+    std::vector<int32_t>().swap(wcount);
+    // dense rows live in shared memory: one range per block slot suffices.
+    // Sparse rows live in global memory: ranges of ~4K tokens taken in
+    // order keep the rows that the resident blocks touch at once few enough
+    // to stay in L2.
+    const int ranges_target = c->sparse ? (1 << 30) : 4 * c->sms;
+    build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->region, c->chunk, ranges_target, &c->docs);
+    build_tier(word_off, V, K, c->dense, 0, c->bmax, c->region, c->chunk, ranges_target, &c->words);
+
     if ((rc = dalloc(c, &c->ck, K, "alloc c_k"))) return bail(rc);
     if ((rc = dalloc(c, &c->ckb, K, "alloc c_k float"))) return bail(rc);
     if ((rc = dalloc(c, &c->counters, kCounters, "alloc counters"))) return bail(rc);
     if ((rc = dalloc(c, &c->d_ll, 1, "alloc loglik"))) return bail(rc);
-    if ((rc = dalloc(c, &c->d_bad, 1, "alloc flag"))) return bail(rc);
     if ((rc = dalloc(c, &c->d_fault, 4, "alloc check record"))) return bail(rc);
     // count rows of the multi-pass tier; each row set starts 16-byte aligned
     // and is zeroed in whole int4 units
@@ -1119,16 +1026,32 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
                                      cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
                 return bail(cuda_fail(e, "upload ranges"));
     }
-    if ((e = cudaMemcpyAsync(c->perm, perm.data(), ((size_t)N + 4) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
-        return bail(cuda_fail(e, "upload perm"));
-    if ((e = cudaMemcpyAsync(c->sperm, sperm.data(), ((size_t)N + 4) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
-        return bail(cuda_fail(e, "upload sorted perm"));
-    if ((e = cudaMemcpyAsync(c->sinfo, sinfo.data(), ((size_t)N + 4) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
-        return bail(cuda_fail(e, "upload sorted info"));
     if ((e = cudaMemcpyAsync(c->doc_off, doc_off.data(), (D + 1) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
         return bail(cuda_fail(e, "upload doc offsets"));
     if ((e = cudaMemcpyAsync(c->word_off, word_off.data(), (V + 1) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
         return bail(cuda_fail(e, "upload word offsets"));
+    // word-major order (Sec. 5.2): stable sort of the tokens by word, perm
+    // from it, then each document batch's tokens in word-major order
+    {
+        int32_t* scratch = nullptr;
+        const int64_t sw = token_sort_scratch(N);
+        if ((e = cudaMalloc((void**)&scratch, (size_t)sw * 4)) != cudaSuccess) return bail(cuda_fail(e, "alloc sort scratch"));
+        int32_t* pos = nullptr;
+        e = launch_token_sort(ka, va, kb, vb, N, (int32_t)V, scratch, &pos, c->st);
+        if (e == cudaSuccess && N > 0 && pos != c->prop) e = cudaErrorInvalidValue;   // by the parity above
+        if (e == cudaSuccess) e = launch_perm(pos, N, c->perm, c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->sperm, 0, ((size_t)N + 4) * 4, c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->sinfo, 0, ((size_t)N + 4) * 4, c->st);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+            e = launch_batch_lists(c->docs.d_batches[k], (int)c->docs.batches[k].size(), c->doc_off, c->perm, pos, N,
+                                   c->sperm, c->sinfo, c->d_bad + 1, c->st);
+        int32_t bad2 = 0x7FFFFFFF;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad2, c->d_bad + 1, 4, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        cudaFree(scratch);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "token order build"));
+        if (bad2 != 0x7FFFFFFF) return bail(fail(WARPLDA_EINVAL, "document batch %d malformed", bad2));
+    }
 
     // grids: persistent blocks, as many as fit
     auto fit = [&](int per_sm) { return std::max(1, per_sm) * c->sms; };
