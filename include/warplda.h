@@ -158,6 +158,24 @@ int warplda_set_state(warplda_ctx* ctx, const int32_t* z_wordmajor, const int32_
 int warplda_token_order(warplda_ctx* ctx, int64_t* word_ptr, int32_t* perm);
 
 /*
+ * warplda_doc_batches -- the document batches of the on-chip tier and their
+ * tokens in word-major order (the gather lists of the document phase,
+ * Sec. 5.2), for tests and tracing.  Host buffers, each may be NULL:
+ *   n_batches  receives the number of batches;
+ *   batches  int32[4 * n_batches]: {first document, end document, table
+ *            words, 0} per batch (both size classes, the 8- or 4-token class
+ *            first);
+ *   sperm    int32[N]: over the doc-major positions of each batch, that
+ *            batch's word-major token indices in ascending order; 0 outside
+ *            the batches;
+ *   sinfo    uint32[N]: beside each sperm entry, (document slot in the batch
+ *            << 16) | (doc-major position - the batch's first position).
+ * Synchronises.  Errors: EINVAL, ECUDA.
+ */
+int warplda_doc_batches(warplda_ctx* ctx, int64_t* n_batches, int32_t* batches, int32_t* sperm,
+                        uint32_t* sinfo);
+
+/*
  * warplda_loglik -- joint log-likelihood log p(W, Z | alpha, beta) of Sec. 6.1
  * in FP64 (zero counts contribute zero; alpha_bar = K alpha and
  * beta_bar = V beta in double).  Synchronises.  Errors: ECUDA, ESTATE.

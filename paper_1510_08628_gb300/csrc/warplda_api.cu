@@ -1040,6 +1040,8 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         e = launch_token_sort(ka, va, kb, vb, N, (int32_t)V, scratch, &pos, c->st);
         if (e == cudaSuccess && N > 0 && pos != c->prop) e = cudaErrorInvalidValue;   // by the parity above
         if (e == cudaSuccess) e = launch_perm(pos, N, c->perm, c->st);
+        // padding past N is zero, as every array's tail is
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->perm + N, 0, 4 * 4, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->sperm, 0, ((size_t)N + 4) * 4, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->sinfo, 0, ((size_t)N + 4) * 4, c->st);
         for (int k = 0; k < 2 && e == cudaSuccess; ++k)
@@ -1080,7 +1082,11 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     }
     c->grid_topic = (int)std::min<int64_t>(fit(topic_hist_blocks_per_sm(K)), std::max<int64_t>(1, (N + 8191) / 8192));
 
-    // z = Dice(K), proposals = z (Alg. 2); c_k = histogram of z
+    // z = Dice(K), proposals = z (Alg. 2); c_k = histogram of z.  The sort
+    // left its values in z and prop: their padding past N is cleared
+    if ((e = cudaMemsetAsync(c->z + N, 0, 4 * 4, c->st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->prop + N * M, 0, (size_t)4 * M * 4, c->st)) != cudaSuccess)
+        return bail(cuda_fail(e, "clear padding"));
     if ((e = launch_init_z(c->z, c->prop, N, K, M, c->seed, c->st)) != cudaSuccess)
         return bail(cuda_fail(e, "init z"));
     if ((rc = recount(c))) return bail(rc);
@@ -1180,6 +1186,27 @@ int warplda_set_state(warplda_ctx* c, const int32_t* z, const int32_t* prop, uin
     int rc = recount(c);
     if (rc) return rc;
     c->iter = sweeps;
+    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    return WARPLDA_OK;
+}
+
+int warplda_doc_batches(warplda_ctx* c, int64_t* n_batches, int32_t* batches, int32_t* sperm,
+                        uint32_t* sinfo) {
+    if (!c) return fail(WARPLDA_EINVAL, "null context");
+    WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
+    if (n_batches) *n_batches = (int64_t)(c->docs.batches[0].size() + c->docs.batches[1].size());
+    if (batches) {
+        size_t o = 0;
+        for (int k = 0; k < 2; ++k) {
+            const auto& b = c->docs.batches[k];
+            if (!b.empty()) std::memcpy(batches + o, b.data(), b.size() * sizeof(int4));
+            o += 4 * b.size();
+        }
+    }
+    if (c->N > 0 && sperm)
+        WL_CU(cudaMemcpyAsync(sperm, c->sperm, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->st), "copy lists");
+    if (c->N > 0 && sinfo)
+        WL_CU(cudaMemcpyAsync(sinfo, c->sinfo, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->st), "copy lists");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     return WARPLDA_OK;
 }

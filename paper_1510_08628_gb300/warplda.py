@@ -60,6 +60,7 @@ _SIGS = {
     "warplda_get_state": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "warplda_set_state": (ctypes.c_int, [_P, _P, _P, ctypes.c_uint32]),
     "warplda_token_order": (ctypes.c_int, [_P, _P, _P]),
+    "warplda_doc_batches": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "warplda_loglik": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "warplda_save": (ctypes.c_int, [_P, ctypes.c_char_p]),
     "warplda_load": (ctypes.c_int, [_P, ctypes.c_char_p]),
@@ -206,6 +207,17 @@ class WarpLDA:
         perm = np.empty(max(self.N, 1), dtype=np.int32)
         _check(load().warplda_token_order(self._h, _ptr(wp), _ptr(perm)))
         return wp, perm[: self.N]
+
+    def doc_batches(self):
+        """(batches [n, 4], sperm [N], sinfo [N]) of the document batch tier."""
+        nb = ctypes.c_int64()
+        _check(load().warplda_doc_batches(self._h, ctypes.byref(nb), None, None, None))
+        n = int(nb.value)
+        b = np.empty((max(n, 1), 4), dtype=np.int32)
+        sp = np.empty(max(self.N, 1), dtype=np.int32)
+        si = np.empty(max(self.N, 1), dtype=np.uint32)
+        _check(load().warplda_doc_batches(self._h, None, _ptr(b), _ptr(sp), _ptr(si)))
+        return b[:n], sp[: self.N], si[: self.N]
 
     def loglik(self) -> float:
         out = ctypes.c_double()

@@ -255,3 +255,49 @@ def test_large_K_dense_model_calls_rejected():
         g.word_counts()
     with pytest.raises(WarpLDAError, match="16384"):
         g.foldin(c.doc_ptr, c.doc_word, 2, 1)
+
+
+def _expected_batch_lists(doc_ptr, perm, batches):
+    """sperm / sinfo of the document batches from their definition: each
+    batch's tokens (a contiguous doc-major range) listed by ascending
+    word-major index, with (document slot << 16 | position in the batch)."""
+    N = len(perm)
+    sperm = np.zeros(N, np.int64)
+    sinfo = np.zeros(N, np.int64)
+    bid = np.full(N, -1, np.int64)
+    b0 = doc_ptr[batches[:, 0]]
+    b1 = doc_ptr[batches[:, 1]]
+    for i in range(len(batches)):
+        bid[b0[i]:b1[i]] = i
+    pos = np.flatnonzero(bid >= 0)
+    order = np.lexsort((perm[pos], bid[pos]))
+    p = pos[order]
+    g = bid[p]
+    start = np.searchsorted(g, np.arange(len(batches)))
+    dest = b0[g] + (np.arange(len(p)) - start[g])
+    doc = np.searchsorted(doc_ptr, p, side="right") - 1
+    sperm[dest] = perm[p]
+    sinfo[dest] = ((doc - batches[g, 0]) << 16) | (p - b0[g])
+    return sperm, sinfo
+
+
+@pytest.mark.parametrize("kind,K,tuning", [("mixed", 7, None), ("mixed", 5000, None),
+                                           ("giant_doc", 16, None), ("empty_segments", 3, None),
+                                           ("mixed", 50, {"batch_max_tokens": 64}),
+                                           ("mixed", 3000, {"doc_warp_max": 20})])
+def test_device_token_order_build(kind, K, tuning):
+    """The token store built on the device (Sec. 5.2): word offsets and perm
+    equal the stable sort of the tokens by word, and the document batches'
+    word-major lists equal their definition."""
+    c = _edge_corpus(kind)
+    g = _gpu(c, c.V, K, 0.3, 0.02, 2, 99, tuning=tuning)
+    wp, perm = g.token_order()
+    assert np.array_equal(wp, np.concatenate([[0], np.cumsum(np.bincount(c.doc_word, minlength=c.V))]))
+    order = np.argsort(c.doc_word, kind="stable")
+    want = np.empty(c.N, np.int64)
+    want[order] = np.arange(c.N)
+    assert np.array_equal(perm, want)
+    batches, sperm, sinfo = g.doc_batches()
+    es, ei = _expected_batch_lists(c.doc_ptr.astype(np.int64), perm.astype(np.int64), batches.astype(np.int64))
+    assert np.array_equal(sperm, es)
+    assert np.array_equal(sinfo.astype(np.int64), ei)
