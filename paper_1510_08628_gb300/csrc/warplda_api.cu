@@ -934,28 +934,37 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     int32_t* vb = odd ? c->prop : reinterpret_cast<int32_t*>(c->sinfo);
     std::vector<int32_t> doc_off(D + 1), word_off(V + 1);
     for (int64_t d = 0; d <= D; ++d) doc_off[d] = (int32_t)doc_ptr[d];
-    std::vector<int32_t> wcount((size_t)V, 0);
+    // word-major order (Sec. 5.2): the word ids are checked, then a stable
+    // sort of the tokens by word leaves the doc-major positions in prop and
+    // the sorted ids in z; each word's first index gives the word offsets
+    int32_t* pos = nullptr;
     {
+        std::vector<int32_t> wstart((size_t)V, -1);
         const int32_t init_bad[2] = {0x7FFFFFFF, 0x7FFFFFFF};
         int32_t bad[2];
+        int32_t* scratch = nullptr;
+        int32_t* keys = nullptr;
         if (N > 0 && (e = cudaMemcpyAsync(ka, doc_word, (size_t)N * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
             return bail(cuda_fail(e, "upload word ids"));
         if ((e = cudaMemcpyAsync(c->d_bad, init_bad, sizeof(init_bad), cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
             return bail(cuda_fail(e, "upload flag"));
-        if ((e = launch_word_hist(ka, N, (int32_t)V, c->word_off, c->d_bad, c->st)) != cudaSuccess)
-            return bail(cuda_fail(e, "word histogram"));
-        if ((e = cudaMemcpyAsync(wcount.data(), c->word_off, (size_t)V * 4, cudaMemcpyDeviceToHost, c->st)) != cudaSuccess)
-            return bail(cuda_fail(e, "copy word lengths"));
-        if ((e = cudaMemcpyAsync(bad, c->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->st)) != cudaSuccess)
-            return bail(cuda_fail(e, "copy flag"));
-        if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return bail(cuda_fail(e, "word histogram"));
+        e = launch_word_check(ka, N, (int32_t)V, c->d_bad, c->st);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&scratch, (size_t)token_sort_scratch(N) * 4);
+        if (e == cudaSuccess) e = launch_token_sort(ka, va, kb, vb, N, (int32_t)V, scratch, &pos, &keys, c->st);
+        if (e == cudaSuccess && N > 0 && (pos != c->prop || keys != c->z)) e = cudaErrorInvalidValue;   // by the parity above
+        if (e == cudaSuccess) e = launch_word_starts(keys, N, (int32_t)V, c->word_off, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(wstart.data(), c->word_off, (size_t)V * 4, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bad, c->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (scratch) cudaFree(scratch);
+        if (e != cudaSuccess) return bail(cuda_fail(e, "token order sort"));
         if (bad[0] != 0x7FFFFFFF)
             return bail(fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", doc_word[bad[0]], (long long)bad[0]));
+        // words without tokens start where the next word does
+        c->word_ptr_h.assign(V + 1, N);
+        for (int64_t w = V - 1; w >= 0; --w) c->word_ptr_h[w] = wstart[w] >= 0 ? wstart[w] : c->word_ptr_h[w + 1];
     }
-    c->word_ptr_h.assign(V + 1, 0);
-    for (int64_t w = 0; w < V; ++w) c->word_ptr_h[w + 1] = c->word_ptr_h[w] + wcount[w];
     for (int64_t w = 0; w <= V; ++w) word_off[w] = (int32_t)c->word_ptr_h[w];
-    std::vector<int32_t>().swap(wcount);
     // dense rows live in shared memory: one range per block slot suffices.
     // Sparse rows live in global memory: ranges of ~4K tokens taken in
     // order keep the rows that the resident blocks touch at once few enough
@@ -1030,16 +1039,10 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         return bail(cuda_fail(e, "upload doc offsets"));
     if ((e = cudaMemcpyAsync(c->word_off, word_off.data(), (V + 1) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
         return bail(cuda_fail(e, "upload word offsets"));
-    // word-major order (Sec. 5.2): stable sort of the tokens by word, perm
-    // from it, then each document batch's tokens in word-major order
+    // perm from the sorted positions, then each document batch's tokens in
+    // word-major order
     {
-        int32_t* scratch = nullptr;
-        const int64_t sw = token_sort_scratch(N);
-        if ((e = cudaMalloc((void**)&scratch, (size_t)sw * 4)) != cudaSuccess) return bail(cuda_fail(e, "alloc sort scratch"));
-        int32_t* pos = nullptr;
-        e = launch_token_sort(ka, va, kb, vb, N, (int32_t)V, scratch, &pos, c->st);
-        if (e == cudaSuccess && N > 0 && pos != c->prop) e = cudaErrorInvalidValue;   // by the parity above
-        if (e == cudaSuccess) e = launch_perm(pos, N, c->perm, c->st);
+        e = launch_perm(pos, N, c->perm, c->st);
         // padding past N is zero, as every array's tail is
         if (e == cudaSuccess) e = cudaMemsetAsync(c->perm + N, 0, 4 * 4, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->sperm, 0, ((size_t)N + 4) * 4, c->st);
@@ -1050,7 +1053,6 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         int32_t bad2 = 0x7FFFFFFF;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&bad2, c->d_bad + 1, 4, cudaMemcpyDeviceToHost, c->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-        cudaFree(scratch);
         if (e != cudaSuccess) return bail(cuda_fail(e, "token order build"));
         if (bad2 != 0x7FFFFFFF) return bail(fail(WARPLDA_EINVAL, "document batch %d malformed", bad2));
     }

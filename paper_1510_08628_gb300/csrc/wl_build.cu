@@ -2,8 +2,7 @@
 // tokens and the pointer array P between the two orders, and the document
 // batches' lists of their tokens in word-major order.
 //
-//   word_hist_kernel      L_w per word (and the first token whose word id is
-//                         outside [0, V)).
+//   word_check_kernel     the first token whose word id is outside [0, V).
 //   radix_count_kernel /  one pass of a stable LSD radix sort (8-bit digits)
 //   radix_scatter_kernel  of (word id, doc-major position) pairs: per-tile
 //                         digit counts, a device-wide exclusive scan in
@@ -11,6 +10,8 @@
 //                         at their digit's offset plus their stable rank.
 //                         After the passes the positions are in word-major
 //                         order, ties (same word) in doc-major order.
+//   word_starts_kernel    the first word-major index of each word present
+//                         (the word offsets, read off the sorted word ids).
 //   perm_kernel           perm[p] = word-major index of doc-major position p.
 //   batch_lists_kernel    one block per document batch: the batch's word-major
 //                         indices sorted ascending (block radix sort) with
@@ -26,17 +27,20 @@ constexpr int kSortItems = 16;                      // items per thread of a til
 constexpr int kSortTile = kThreads * kSortItems;    // 4096 pairs per tile
 constexpr int kScanChunk = kThreads * 16;           // entries per block of the scan
 
-// Word lengths; invalid word ids are skipped and the first such position is
-// kept in *bad (initialised to INT_MAX by the caller).
-__global__ void word_hist_kernel(const int32_t* __restrict__ w, int64_t N, int32_t V, int32_t* __restrict__ cnt,
-                                 int32_t* __restrict__ bad) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t x = w[t];
-        const bool ok = (uint32_t)x < (uint32_t)V;
-        if (!ok) atomicMin(bad, (int32_t)t);
-        // Zipf-heavy words repeat within a warp: one add per distinct word
-        const unsigned m = __match_any_sync(__activemask(), ok ? x : -1);
-        if (ok && (threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&cnt[x], __popc(m));
+// The first position whose word id is outside [0, V) goes to *bad
+// (initialised to INT_MAX by the caller).
+__global__ void word_check_kernel(const int32_t* __restrict__ w, int64_t N, int32_t V, int32_t* __restrict__ bad) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x)
+        if ((uint32_t)w[t] >= (uint32_t)V) atomicMin(bad, (int32_t)t);
+}
+
+// start[w] = first index of word w in the sorted word ids (start is -1 for
+// words without tokens; set by the caller).
+__global__ void word_starts_kernel(const int32_t* __restrict__ keys, int64_t N, int32_t V,
+                                   int32_t* __restrict__ start) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t w = keys[i];
+        if ((i == 0 || keys[i - 1] != w) && (uint32_t)w < (uint32_t)V) start[w] = (int32_t)i;
     }
 }
 
@@ -222,11 +226,18 @@ int64_t token_sort_scratch(int64_t N) {
     return 256 * ntiles + scan_scratch(256 * ntiles) + 4;
 }
 
-cudaError_t launch_word_hist(const int32_t* w, int64_t N, int32_t V, int32_t* cnt, int32_t* bad, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)V, st);
+cudaError_t launch_word_check(const int32_t* w, int64_t N, int32_t V, int32_t* bad, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    const int64_t g = std::min<int64_t>((N + kThreads - 1) / kThreads, 152 * 16);
+    word_check_kernel<<<(unsigned)g, kThreads, 0, st>>>(w, N, V, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_word_starts(const int32_t* keys_sorted, int64_t N, int32_t V, int32_t* start, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(start, 0xFF, sizeof(int32_t) * (size_t)V, st);
     if (e != cudaSuccess || N <= 0) return e;
     const int64_t g = std::min<int64_t>((N + kThreads - 1) / kThreads, 152 * 16);
-    word_hist_kernel<<<(unsigned)g, kThreads, 0, st>>>(w, N, V, cnt, bad);
+    word_starts_kernel<<<(unsigned)g, kThreads, 0, st>>>(keys_sorted, N, V, start);
     return cudaGetLastError();
 }
 
@@ -237,8 +248,10 @@ int token_sort_passes(int64_t V) {
 }
 
 cudaError_t launch_token_sort(int32_t* keys_a, int32_t* vals_a, int32_t* keys_b, int32_t* vals_b, int64_t N,
-                              int32_t V, int32_t* scratch, int32_t** pos_sorted, cudaStream_t st) {
+                              int32_t V, int32_t* scratch, int32_t** pos_sorted, int32_t** keys_sorted,
+                              cudaStream_t st) {
     *pos_sorted = nullptr;
+    *keys_sorted = nullptr;
     if (N <= 0) return cudaSuccess;
     const int64_t ntiles = (N + kSortTile - 1) / kSortTile;
     const int passes = token_sort_passes(V);
@@ -256,6 +269,7 @@ cudaError_t launch_token_sort(int32_t* keys_a, int32_t* vals_a, int32_t* keys_b,
         radix_scatter_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(kin, vin, N, 8 * p, tile, ntiles, kout, vout);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *pos_sorted = vout;
+        *keys_sorted = kout;
         // next pass reads what this one wrote
         int32_t* nk = (kout == keys_b) ? keys_a : keys_b;
         int32_t* nv = (vout == vals_b) ? vals_a : vals_b;

@@ -173,14 +173,17 @@ int record_error(int code, const char* msg);
 // Token store build (wl_build.cu).  launch_token_sort: stable LSD sort of
 // (word id, doc-major position) pairs; pass 0 reads keys_a (word ids, values
 // implicit), passes alternate between the (a) and (b) buffers, and
-// *pos_sorted receives the buffer holding the positions in word-major order
-// ((b) after an odd number of passes, token_sort_passes(V)).  scratch holds
+// *pos_sorted / *keys_sorted receive the buffers holding the positions and
+// the word ids in word-major order ((b) after an odd number of passes,
+// token_sort_passes(V)).  scratch holds
 // token_sort_scratch(N) words.
-cudaError_t launch_word_hist(const int32_t* w, int64_t N, int32_t V, int32_t* cnt, int32_t* bad, cudaStream_t st);
+cudaError_t launch_word_check(const int32_t* w, int64_t N, int32_t V, int32_t* bad, cudaStream_t st);
+cudaError_t launch_word_starts(const int32_t* keys_sorted, int64_t N, int32_t V, int32_t* start, cudaStream_t st);
 int token_sort_passes(int64_t V);
 int64_t token_sort_scratch(int64_t N);
 cudaError_t launch_token_sort(int32_t* keys_a, int32_t* vals_a, int32_t* keys_b, int32_t* vals_b, int64_t N,
-                              int32_t V, int32_t* scratch, int32_t** pos_sorted, cudaStream_t st);
+                              int32_t V, int32_t* scratch, int32_t** pos_sorted, int32_t** keys_sorted,
+                              cudaStream_t st);
 cudaError_t launch_perm(const int32_t* pos_sorted, int64_t N, int32_t* perm, cudaStream_t st);
 cudaError_t launch_batch_lists(const int4* batches, int nb, const int32_t* doc_off, const int32_t* perm,
                                const int32_t* pos_sorted, int64_t N, int32_t* sperm, uint32_t* sinfo, int32_t* bad,

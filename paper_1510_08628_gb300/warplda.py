@@ -180,11 +180,20 @@ class WarpLDA:
         _check(load().warplda_phase(self._h, int(which)))
 
     # -- results --------------------------------------------------------------
-    def counts(self, want_z: bool = True, want_ck: bool = True):
-        z = np.empty(max(self.N, 1), dtype=np.int32) if want_z else None
-        ck = np.empty(self.K, dtype=np.int32) if want_ck else None
+    def counts(self, want_z: bool = True, want_ck: bool = True, z_out=None, ck_out=None):
+        """z in document order and c_k on the host.  z_out / ck_out: optional
+        caller-held int32 arrays (e.g. views of pinned memory, which the copy
+        reaches at full speed) of N and K entries to fill instead."""
+        def buf(out, n, want):
+            if out is not None:
+                if out.dtype != np.int32 or not out.flags["C_CONTIGUOUS"] or out.size < n:
+                    raise ValueError(f"output buffer must be contiguous int32 with >= {n} entries")
+                return out
+            return np.empty(max(n, 1), dtype=np.int32) if want else None
+        z = buf(z_out, self.N, want_z)
+        ck = buf(ck_out, self.K, want_ck)
         _check(load().warplda_counts(self._h, _ptr(z), _ptr(ck)))
-        return (z[: self.N] if z is not None else None), ck
+        return (z[: self.N] if z is not None else None), (ck[: self.K] if ck is not None else None)
 
     def counts_dev(self, z_dev=None, ck_dev=None) -> None:
         _check(load().warplda_counts_dev(self._h, _dev_ptr(z_dev), _dev_ptr(ck_dev)))
