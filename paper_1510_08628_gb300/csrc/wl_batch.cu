@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) bat
                 }
                 if (tk[j] >= 0) {
                     store_props<M>(a.prop, tk[j], pp[j].v);
-                    a.z[tk[j]] = zz[j];
+                    if (zz[j] != zo[j]) a.z[tk[j]] = zz[j];   // rejected chains leave z as it was
                 }
             }
         } else {
