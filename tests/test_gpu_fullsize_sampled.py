@@ -1,0 +1,77 @@
+"""Full-size parity on the PubMed-shaped (736M tokens, K=10^4, M=2) and
+ClueWeb-shaped (1.5B tokens, K=10^6, M=1, sparse count rows) workloads, in
+the launch configuration the benchmark times, on sampled outputs.
+
+From the GPU's own state at the start of a phase, the oracle recomputes that
+phase for a sample of documents (the longest ones, which the multi-pass tier
+takes, and random ones from the batch tier) or of words (the heaviest ones
+and random ones), one segment at a time; the GPU's topics and proposals for
+those tokens must match bit for bit.  c_k after each phase must equal the
+histogram of z (a property that holds at any size).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1510_08628_gb300 import corpus
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def _sample(lengths, n_random, n_top, rng):
+    nz = np.flatnonzero(lengths > 0)
+    top = nz[np.argsort(-lengths[nz], kind="stable")[:n_top]]
+    rnd = rng.choice(nz, size=min(n_random, len(nz)), replace=False)
+    return np.unique(np.concatenate([top, rnd]))
+
+
+@pytest.mark.parametrize("name", ["pubmed", "clueweb"])
+def test_full_size_sampled_phase_parity(name):
+    from paper_1510_08628_gb300.warplda import WarpLDA
+    c, wl = corpus.generate(name, seed=1)
+    gpu = WarpLDA(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, 7)
+    gpu.sweep(2)
+    z, p, ck, it = gpu.get_state()
+    # K above 16,384 uses storage-order word positioning
+    ref = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, 7,
+                        word_rule=1 if wl.K > 16384 else 0)
+    N, M = ref.N, ref.M
+    rng = np.random.default_rng(3)
+
+    # document phase of sweep it + 1
+    ref.z[:N] = z
+    ref.prop[: N * M] = p
+    ref.ck[:] = ck
+    gpu.phase(1)
+    z1, p1, ck1, _ = gpu.get_state()
+    assert np.array_equal(ck1, np.bincount(z1, minlength=wl.K)), "c_k after the document phase"
+    docs = _sample(np.diff(c.doc_ptr), 3000, 20, rng)
+    for d in docs:
+        ref.doc_phase(it + 1, int(d), int(d) + 1)
+    t = ref.perm[np.concatenate([np.arange(c.doc_ptr[d], c.doc_ptr[d + 1]) for d in docs])]
+    assert np.array_equal(z1[t], ref.z[t]), "document phase: z"
+    pt = (t[:, None] * M + np.arange(M)).reshape(-1)
+    assert np.array_equal(p1[pt], ref.prop[pt]), "document phase: proposals"
+
+    # word phase of the same sweep
+    ref.z[:N] = z1
+    ref.prop[: N * M] = p1
+    ref.ck[:] = ck1
+    gpu.phase(2)
+    z2, p2, ck2, _ = gpu.get_state()
+    assert np.array_equal(ck2, np.bincount(z2, minlength=wl.K)), "c_k after the word phase"
+    words = _sample(np.diff(ref.word_ptr), 3000, 5, rng)
+    for w in words:
+        ref.word_phase(it + 1, int(w), int(w) + 1)
+    t = np.concatenate([np.arange(ref.word_ptr[w], ref.word_ptr[w + 1]) for w in words])
+    assert np.array_equal(z2[t], ref.z[t]), "word phase: z"
+    pt = (t[:, None] * M + np.arange(M)).reshape(-1)
+    assert np.array_equal(p2[pt], ref.prop[pt]), "word phase: proposals"
+    gpu.sync()
