@@ -949,14 +949,18 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         if ((e = cudaMemcpyAsync(c->d_bad, init_bad, sizeof(init_bad), cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
             return bail(cuda_fail(e, "upload flag"));
         e = launch_word_check(ka, N, (int32_t)V, c->d_bad, c->st);
-        if (e == cudaSuccess) e = cudaMalloc((void**)&scratch, (size_t)token_sort_scratch(N) * 4);
+        // the sort's tile counters (~N/16 words) live in perm, which is only
+        // written from the sorted positions afterwards; tiny corpora allocate
+        const bool own_scratch = token_sort_scratch(N) > N + 4;
+        if (!own_scratch) scratch = c->perm;
+        else if (e == cudaSuccess) e = cudaMalloc((void**)&scratch, (size_t)token_sort_scratch(N) * 4);
         if (e == cudaSuccess) e = launch_token_sort(ka, va, kb, vb, N, (int32_t)V, scratch, &pos, &keys, c->st);
         if (e == cudaSuccess && N > 0 && (pos != c->prop || keys != c->z)) e = cudaErrorInvalidValue;   // by the parity above
         if (e == cudaSuccess) e = launch_word_starts(keys, N, (int32_t)V, c->word_off, c->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(wstart.data(), c->word_off, (size_t)V * 4, cudaMemcpyDeviceToHost, c->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(bad, c->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
-        if (scratch) cudaFree(scratch);
+        if (own_scratch && scratch) cudaFree(scratch);
         if (e != cudaSuccess) return bail(cuda_fail(e, "token order sort"));
         if (bad[0] != 0x7FFFFFFF)
             return bail(fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", doc_word[bad[0]], (long long)bad[0]));
