@@ -129,6 +129,9 @@ int warplda_phase(warplda_ctx* ctx, int32_t phase);
 /*
  * warplda_counts -- copy results to host buffers (each may be NULL):
  *   z_docmajor  int32[N], topic of each token in the caller's doc_ptr order.
+ *               Pinned (page-locked) host memory is written directly by the
+ *               gather kernel; pageable memory goes through a device buffer
+ *               of N int32 allocated on first use.
  *   ck          int32[K], global topic counts c_k (Sec. 2.1).
  * Synchronises the stream.  Errors: ECUDA.
  */

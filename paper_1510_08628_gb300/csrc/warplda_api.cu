@@ -1145,10 +1145,23 @@ int warplda_counts(warplda_ctx* c, int32_t* z_docmajor, int32_t* ck) {
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
     if (z_docmajor && c->N > 0) {
-        int rc = ensure_scratch(c);
-        if (rc) return rc;
-        WL_CU(launch_gather_docmajor(c->z, c->perm, c->N, c->scratch, c->st), "gather z");
-        WL_CU(cudaMemcpyAsync(z_docmajor, c->scratch, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->st), "copy z");
+        // pinned host buffer: the gather writes into it through its device
+        // alias (no device scratch, no separate copy); otherwise gather on
+        // the device and copy
+        cudaPointerAttributes pa{};
+        const cudaError_t pe = cudaPointerGetAttributes(&pa, z_docmajor);
+        if (pe != cudaSuccess) cudaGetLastError();   // clear the query's own error only
+        const bool pinned = pe == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer != nullptr;
+        if (pinned) {
+            WL_CU(launch_gather_docmajor(c->z, c->perm, c->N, static_cast<int32_t*>(pa.devicePointer), c->st),
+                  "gather z");
+        } else {
+            int rc = ensure_scratch(c);
+            if (rc) return rc;
+            WL_CU(launch_gather_docmajor(c->z, c->perm, c->N, c->scratch, c->st), "gather z");
+            WL_CU(cudaMemcpyAsync(z_docmajor, c->scratch, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->st),
+                  "copy z");
+        }
     }
     if (ck) WL_CU(cudaMemcpyAsync(ck, c->ck, (size_t)c->K * 4, cudaMemcpyDeviceToHost, c->st), "copy c_k");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");

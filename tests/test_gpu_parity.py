@@ -174,6 +174,11 @@ def test_counts_dev_and_bad_state(tiny_corpus):
     torch.cuda.synchronize()
     z, ck = g.counts()
     assert np.array_equal(zt.cpu().numpy(), z) and np.array_equal(ckt.cpu().numpy(), ck)
+    # pinned host buffers take the direct gather; same values as the copy path
+    zp = torch.full((c.N,), -1, dtype=torch.int32, pin_memory=True).numpy()
+    ckp = torch.full((wl.K,), -1, dtype=torch.int32, pin_memory=True).numpy()
+    z2, ck2 = g.counts(z_out=zp, ck_out=ckp)
+    assert np.array_equal(z2, z) and np.array_equal(ck2, ck) and np.array_equal(zp, z)
     zs, ps, _, it = g.get_state()
     bad = zs.copy()
     bad[5] = wl.K
