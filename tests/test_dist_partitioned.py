@@ -84,3 +84,60 @@ def test_partitions_cover_and_balance():
         assert load.sum() == o.N
         # greedy by descending size: no set exceeds the mean by more than the largest word
         assert load.max() - o.N / P <= np.diff(o.word_ptr).max()
+
+
+def _rank_planted(rank, P, port, mistake, q):
+    """As _rank, with one mistake planted in the exchange (oracle side, CPU)."""
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from oracle.partitioned import PartitionedOracle
+
+    class Planted(PartitionedOracle):
+        def _reduce_ck(self, owned):
+            if mistake == "local_ck":          # c_k from this rank's tokens only
+                self.ck = np.bincount(self.o.z[owned], minlength=self.o.K).astype(np.int32)
+            else:
+                super()._reduce_ck(owned)
+
+        def _exchange(self, to_words):
+            if mistake == "drop_block" and to_words:
+                saved = self.block[(0, 1)]
+                self.block[(0, 1)] = saved[: len(saved) // 2]   # half a block never arrives
+                super()._exchange(to_words)
+                self.block[(0, 1)] = saved
+            else:
+                super()._exchange(to_words)
+
+    dist.init_process_group("gloo", rank=rank, world_size=P)
+    c = _corpus()
+    po = Planted(c.doc_ptr, c.doc_word, c.V, 24, 0.3, 0.02, 2, 5, rank, P)
+    po.sweep(2)
+    z, p, ck = po.gather()
+    if rank == 0:
+        q.put((z, p, ck))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("mistake", ["local_ck", "drop_block"])
+def test_planted_exchange_mistakes_are_caught(mistake):
+    mp = pytest.importorskip("torch.multiprocessing")
+    sys.path.insert(0, ROOT)
+    import oracle
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank_planted, args=(r, 2, port, mistake, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    z, prop, ck = q.get(timeout=300)
+    for p in ps:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    c = _corpus()
+    ref = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, 24, 0.3, 0.02, 2, 5)
+    ref.sweep(2)
+    same = (np.array_equal(z, ref.z[: ref.N]) and np.array_equal(prop, ref.prop[: ref.N * 2])
+            and np.array_equal(ck, ref.ck))
+    assert not same, f"planted mistake {mistake} went unnoticed"
