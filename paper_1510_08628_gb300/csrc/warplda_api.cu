@@ -310,8 +310,15 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
 // record means a kernel met a bad index and skipped the access.
 int check_record(warplda_ctx* c, const char* where) {
     int32_t f[4] = {0, 0, 0, 0};
-    WL_CU(cudaMemcpyAsync(f, c->d_fault, sizeof(f), cudaMemcpyDeviceToHost, c->st), "read check record");
-    WL_CU(cudaStreamSynchronize(c->st), "synchronize");
+    cudaError_t e = cudaMemcpyAsync(f, c->d_fault, sizeof(f), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        // a fault of an earlier launch surfaces here: name the call that read
+        // the record (with WARPLDA_SYNC_CHECK=1, the launch just made)
+        char what[96];
+        std::snprintf(what, sizeof(what), "read check record after %s", where);
+        return cuda_fail(e, what);
+    }
     if (f[0] == 0 && f[3] == 0) return WARPLDA_OK;
     WL_CU(cudaMemsetAsync(c->d_fault, 0, sizeof(f), c->st), "clear check record");
     if (f[0] == 0) return fail(WARPLDA_ETIMEDOUT, "a tensor-core wait ran out (reported at %s)", where);
