@@ -135,3 +135,22 @@ def test_empty_documents_and_words_are_skipped():
     o.sweep(3)
     assert np.array_equal(o.ck, np.bincount(o.z[: o.N], minlength=4))
     assert np.isfinite(o.loglik())
+
+
+def test_results_do_not_depend_on_thread_count():
+    """The oracle's OpenMP loops over documents and words give the same state
+    with 1 and with several threads: every random number is keyed by the
+    token, and documents (words) of one phase touch disjoint tokens."""
+    c, _ = corpus.generate("tiny", seed=3)
+    prev = oracle.num_threads()
+    try:
+        out = []
+        for n in (1, max(2, prev)):
+            oracle.set_threads(n)
+            o = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, 16, 3.125, 0.01, 2, 11)
+            o.sweep(3)
+            out.append((o.z.copy(), o.prop.copy(), o.ck.copy()))
+        for a, b in zip(out[0], out[1]):
+            assert np.array_equal(a, b)
+    finally:
+        oracle.set_threads(prev)
