@@ -4,7 +4,8 @@ word phase) on a synthetic LDA corpus shaped like NYTimes (D=300K, V=100K,
 of the whole sweep, the CPU oracle as the reported baseline, and the
 end-to-end throughput through the C ABI from host buffers.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload nytimes|pubmed|tiny]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload nytimes|pubmed|clueweb|tiny]
+                  [--docs D] [--tuning key=value,...] [--m-sweep] [--foldin-docs N]
   python bench.py --impl reference ...   (the CPU oracle on the same workload)
 
 One "step" is one sweep.  Prints one JSON line (rank 0).  With N > 1
@@ -455,7 +456,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="nytimes")
+    ap.add_argument("--workload", default="nytimes", help="nytimes | pubmed | clueweb | tiny")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--corpus-seed", type=int, default=1)
