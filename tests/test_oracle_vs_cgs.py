@@ -52,3 +52,25 @@ def test_more_mh_steps_converge_no_slower(runs):
     a, b = runs["w1_early"], runs["w2_early"]
     se = np.sqrt(a.var(ddof=1) / len(a) + b.var(ddof=1) / len(b))
     assert b.mean() >= a.mean() - 3 * se, (a, b)
+
+
+def test_topic_recovery_against_the_generator():
+    """Soft check: after 150 sweeps on the tiny workload (K_true = K = 16) the
+    oracle's topics phi_k = (C_kw + beta) / (C_k + V beta) (Eq. 4) match the
+    generator's true rows after Hungarian matching on the Hellinger distance
+    far better than an arbitrary pairing does."""
+    from scipy.optimize import linear_sum_assignment
+    wl = corpus.WORKLOADS["tiny"]
+    model = corpus.TopicModel(wl.V, wl.K_true, wl.zipf_s, wl.conc_c, 1, keep_phi=True)
+    lens = corpus.lengths(wl.D, wl.len_kind, wl.len_mean, wl.len_sigma, 1)
+    c = corpus.generate_docs(model, lens, wl.doc_alpha, 1)
+    phi = model.phi.reshape(wl.K_true, wl.V)
+    o = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, 7)
+    o.sweep(150)
+    cw = oracle.word_topic_counts(o.z[: o.N], o.word_ptr, c.V, wl.K).astype(np.float64)
+    est = (cw.T + wl.beta) / (cw.sum(axis=0)[:, None] + c.V * wl.beta)
+    H = np.sqrt(0.5 * ((np.sqrt(est)[:, None, :] - np.sqrt(phi)[None, :, :]) ** 2).sum(-1))
+    r, k = linear_sum_assignment(H)
+    matched = H[r, k].mean()
+    arbitrary = H[np.arange(wl.K), np.random.default_rng(0).permutation(wl.K_true)].mean()
+    assert matched < 0.5 and arbitrary > 0.7 and matched < 0.7 * arbitrary, (matched, arbitrary)
