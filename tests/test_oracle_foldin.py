@@ -18,7 +18,6 @@ frozen model (the trained C_w and c_k).
 import functools
 
 import numpy as np
-import pytest
 from scipy import stats
 
 import oracle

@@ -18,7 +18,6 @@ least one of the distribution pins (test_oracle_law.py) or the Philox pin
  12  fold-in: theta normalised by L_d + alpha instead of L_d + alpha_bar
  13  learned fold-in: q(s) and q(t) swapped in the independence-sampler rate
 """
-import numpy as np
 import pytest
 
 import oracle
