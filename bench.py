@@ -334,7 +334,8 @@ def serving_bench(gpu, c, wl, args, learned: bool, rate: float, n: int = 6000, n
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "steps": steps}
 
 
-TUNING_KEYS = ("batch_max_tokens", "huge_chunk", "region_budget", "doc_warp_max", "word_positioning")
+TUNING_KEYS = ("batch_max_tokens", "huge_chunk", "region_budget", "doc_warp_max", "word_positioning",
+               "doc_batch_kernel")
 
 
 def parse_tuning(text: str) -> dict | None:
@@ -473,7 +474,8 @@ def main():
                     help="also record log-likelihood against iterations for M = 1, 2, 4 (Fig. 7)")
     ap.add_argument("--tuning", default="",
                     help="launch tuning of the sampler as key=value pairs separated by commas "
-                         "(batch_max_tokens, huge_chunk, region_budget, doc_warp_max, word_positioning)")
+                         "(batch_max_tokens, huge_chunk, region_budget, doc_warp_max, word_positioning, "
+                         "doc_batch_kernel)")
     ap.add_argument("--docs", type=int, default=0,
                     help="use only the first DOCS documents of the workload (small profiling cases)")
     args = ap.parse_args()

@@ -64,6 +64,14 @@ typedef struct warplda_server warplda_server;
  *   doc_warp_max      documents with at most this many tokens (capped at 512
  *                     with dense count tables, 256 with hash tables) are
  *                     sampled one warp per document; 0 (default) or -1: off.
+ *   doc_batch_kernel  which kernel samples the document batches of up to
+ *                     2045 tokens: 2 = the pipelined document kernel
+ *                     (batches of up to 1021 tokens and 128 documents; the
+ *                     next batch's tokens are gathered into shared memory
+ *                     while the current one is sampled; region_budget
+ *                     defaults to 4096 words for them); 1 = the block batch
+ *                     kernel; 0 (default) = pipelined with hash count
+ *                     tables and 2048 < K <= 16384, else block batch.
  * One field changes the sampler (a different, equally valid chain):
  *   word_positioning  the word proposal's p_A branch (Eq. 6): 0 (default) =
  *                     the j-th smallest post-acceptance topic of the word;
@@ -76,7 +84,8 @@ typedef struct warplda_tuning {
     int32_t region_budget;
     int32_t doc_warp_max;
     int32_t word_positioning;
-    int32_t reserved[3];
+    int32_t doc_batch_kernel;
+    int32_t reserved[2];
 } warplda_tuning;
 
 /*

@@ -59,6 +59,13 @@ const char* kClassNames[kcCount] = {
     "count_ck", "finalize_ck", "zero_rows"};
 // topics: packed hash entries hold (topic + 1) << 12 in 32 bits
 constexpr int kMaxTopics = (1 << 20) - 1;
+// tokens of a pipelined document batch (at most 4 * 256 - 3; at most 509
+// gives the kernel's 2-tokens-per-thread form)
+#ifndef WL_PIPE_TOKENS
+#define WL_PIPE_TOKENS 1021
+#endif
+constexpr int kPipeTokens = WL_PIPE_TOKENS;
+static_assert(kPipeTokens >= 1 && kPipeTokens <= 4 * kThreads - 3, "pipelined batch size");
 // above this K the multi-pass tier's count rows are sparse (global hash)
 constexpr int kDenseRowMaxK = 16384;
 // work counters: 0-3 batches [class][phase], 4 doc warp tier, 5-8 the
@@ -106,6 +113,12 @@ struct warplda_ctx {
     // latency-bound gather and probe loops), else 8
     int tpt0[2] = {8, 8};
     int dbmax[2] = {0, 0};
+    int dregion[2] = {0, 0};   // table budget of the document batches [class]
+    // document batches of the small class run in the pipelined kernel
+    // (wl_docpipe.cu): by default with hash tables, or as tuning says
+    bool doc_pipe = true;
+    int4* d_pipe_desc = nullptr;
+    int grid_pipe = 1;
     bool dense = true;   // 16-bit dense count tables (K <= kDenseMaxK), else hash tables
     int warp_tpl = 16;   // tokens per lane of the document warp tier
     int grid_doc_warp = 1;
@@ -194,7 +207,7 @@ int table_words(int L, int K, bool dense) {
 // Split segments [0, S) with offsets off[] into the kernel tiers: segments
 // with 1..warp_max tokens go to the warp tier (warp_max = 0: none); small
 // segments to block batches of the 8-tokens-per-thread kernel (at most
-// bmax[0] tokens, kSegsMax segments, region[0] table words per batch), large
+// bmax[0] tokens, segs0 segments, region[0] table words per batch), large
 // ones to batches of the 16-tokens-per-thread kernel (bmax[1], region[1]);
 // longer segments get a count row, and their tokens are cut into ranges of
 // about equal size (ranges_target of them), each a list of pieces of at
@@ -204,7 +217,9 @@ int table_words(int L, int K, bool dense) {
 // log-likelihood batches cover every segment that is not chunked, with the
 // paper's table rule.
 void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, int warp_max,
-                const int bmax[2], const int region[2], int chunk, int ranges_target, Tier* t) {
+                const int bmax[2], const int region[2], int chunk, int ranges_target, Tier* t,
+                int segs0 = kSegsMax) {
+    const int segs_max[2] = {segs0, kSegsMax};
     for (auto& b : t->batches) b.clear();
     t->warp_list.clear();
     t->chunks.clear();
@@ -229,7 +244,7 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
     for (int64_t s = 0; s < S; ++s) {
         const int L = off[s + 1] - off[s];
         if (L == 0) {
-            if (cur0 >= 0 && nseg + 1 <= kSegsMax) {
+            if (cur0 >= 0 && nseg + 1 <= segs_max[cls]) {
                 t->region[s] = nw;
                 nseg += 1;
             } else {
@@ -270,7 +285,7 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
             continue;
         }
         if (c == 1) t->large_tokens += L;
-        if (cur0 >= 0 && (c != cls || ntok + L > bmax[c] || nseg + 1 > kSegsMax || nw + w > region[c]))
+        if (cur0 >= 0 && (c != cls || ntok + L > bmax[c] || nseg + 1 > segs_max[c] || nw + w > region[c]))
             close((int)s);
         if (cur0 < 0) {
             cur0 = (int)s;
@@ -444,11 +459,14 @@ int run_phase(warplda_ctx* c, bool doc) {
             PhaseCall* q = (PhaseCall*)p;
             Tier& TT = q->doc ? cc->docs : cc->words;
             const int k = q->cls;
+            if (q->doc && k == 0 && cc->doc_pipe)
+                return launch_doc_pipe(cc->dense, cc->tpt0[0], q->a, cc->d_pipe_desc, (int)TT.batches[0].size(),
+                                       cc->counters, TT.d_region, cc->dregion[0], cc->grid_pipe, cc->st);
             return launch_batch_phase(q->doc, cc->dense, k ? 16 : cc->tpt0[q->doc ? 0 : 1], q->a, TT.d_batches[k],
                                       (int)TT.batches[k].size(),
                                       cc->counters + 2 * k + (q->doc ? 0 : 1), TT.d_region,
-                                      cc->region[k], cc->kbits, cc->grid_batch[q->doc ? 0 : 1][k],
-                                      cc->st);
+                                      q->doc ? cc->dregion[k] : cc->region[k], cc->kbits,
+                                      cc->grid_batch[q->doc ? 0 : 1][k], cc->st);
         }, &pc);
         if (rc) return rc;
     }
@@ -892,6 +910,26 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     c->dbmax[1] = c->bmax[1];
     c->region[0] = rb ? rb : 8192;
     c->region[1] = rb ? rb : 8192;
+    // the pipelined document kernel takes batches of up to 1021 tokens and
+    // 128 documents; their hash tables need at most 4 words per token
+    if (tuning && (tuning->doc_batch_kernel < 0 || tuning->doc_batch_kernel > 2)) {
+        delete c;
+        return fail(WARPLDA_EINVAL, "doc_batch_kernel must be 0, 1 or 2");
+    }
+    {
+        // measured: pipelined batches of 1021 tokens beat the block kernel
+        // with hash tables and K up to 16384; with dense tables the block
+        // kernel's 2045-token batches share more gather sectors, and with
+        // sparse rows (c_k in L2) its grouped operand loads, and it wins
+        const int dk = tuning ? tuning->doc_batch_kernel : 0;
+        c->doc_pipe = dk == 2 || (dk == 0 && !c->dense && K <= kDenseRowMaxK);
+    }
+    if (c->doc_pipe) {
+        c->dbmax[0] = std::min(bmax, kPipeTokens);
+        c->tpt0[0] = c->dbmax[0] + 3 <= 2 * kThreads ? 2 : 4;
+    }
+    c->dregion[0] = rb ? rb : (c->doc_pipe ? (c->tpt0[0] == 2 ? 2048 : 4096) : 8192);
+    c->dregion[1] = c->region[1];
     // documents of up to 32 * warp_tpl tokens go to the warp tier; the
     // block tier takes the rest (its small class is not used for documents)
     c->warp_tpl = c->dense ? 16 : 8;
@@ -981,7 +1019,8 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     // order keep the rows that the resident blocks touch at once few enough
     // to stay in L2.
     const int ranges_target = c->sparse ? (1 << 30) : 4 * c->sms;
-    build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->region, c->chunk, ranges_target, &c->docs);
+    build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->dregion, c->chunk, ranges_target, &c->docs,
+               c->doc_pipe ? kDocSegs : kSegsMax);
     build_tier(word_off, V, K, c->dense, 0, c->bmax, c->region, c->chunk, ranges_target, &c->words);
 
     if ((rc = dalloc(c, &c->ck, K, "alloc c_k"))) return bail(rc);
@@ -1046,6 +1085,22 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
                                      cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
                 return bail(cuda_fail(e, "upload ranges"));
     }
+    {
+        // descriptors of the pipelined document batches: {first document,
+        // documents | table words << 16, first token, tokens}
+        const auto& B = c->docs.batches[0];
+        std::vector<int4> desc(B.size());
+        for (size_t i = 0; i < B.size(); ++i)
+            desc[i] = make_int4(B[i].x, (B[i].y - B[i].x) | (B[i].z << 16), doc_off[B[i].x],
+                                doc_off[B[i].y] - doc_off[B[i].x]);
+        if ((rc = dalloc(c, &c->d_pipe_desc, (int64_t)desc.size(), "alloc batch descriptors"))) return bail(rc);
+        if (!desc.empty()) {
+            if ((e = cudaMemcpyAsync(c->d_pipe_desc, desc.data(), desc.size() * sizeof(int4),
+                                     cudaMemcpyHostToDevice, c->st)) != cudaSuccess ||
+                (e = cudaStreamSynchronize(c->st)) != cudaSuccess)   // `desc` goes out of scope
+                return bail(cuda_fail(e, "upload batch descriptors"));
+        }
+    }
     if ((e = cudaMemcpyAsync(c->doc_off, doc_off.data(), (D + 1) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
         return bail(cuda_fail(e, "upload doc offsets"));
     if ((e = cudaMemcpyAsync(c->word_off, word_off.data(), (V + 1) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
@@ -1072,10 +1127,18 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     auto fit = [&](int per_sm) { return std::max(1, per_sm) * c->sms; };
     for (int w = 0; w < 2; ++w)
         for (int k = 0; k < 2; ++k) {
-            const int per_sm = batch_blocks_per_sm(K, c->stage_ck, c->region[k], k ? 16 : c->tpt0[w], w, M, c->dense);
+            const int64_t nb = (int64_t)(w ? c->words : c->docs).batches[k].size();
+            const int rw = w ? c->region[k] : c->dregion[k];
+            if (w == 0 && k == 0 && c->doc_pipe) {
+                const int per_sm = docpipe_blocks_per_sm(K, c->dense ? 1 : 0, rw, c->tpt0[0], M);
+                if (per_sm < 1)
+                    return bail(fail(WARPLDA_EINVAL, "document batch kernel does not fit (region_budget too large?)"));
+                c->grid_pipe = (int)std::min<int64_t>(fit(per_sm), std::max<int64_t>(1, nb));
+                continue;
+            }
+            const int per_sm = batch_blocks_per_sm(K, c->stage_ck, rw, k ? 16 : c->tpt0[w], w, M, c->dense);
             if (per_sm < 1)
                 return bail(fail(WARPLDA_EINVAL, "batch kernel does not fit (region_budget too large?)"));
-            const int64_t nb = (int64_t)(w ? c->words : c->docs).batches[k].size();
             c->grid_batch[w][k] = (int)std::min<int64_t>(fit(per_sm), std::max<int64_t>(1, nb));
         }
     {

@@ -10,6 +10,7 @@ namespace wl {
 constexpr int kThreads = 256;          // threads of every sampler block
 constexpr int kWarps = kThreads / 32;
 constexpr int kSegsMax = 512;          // segments (documents / words) per block batch
+constexpr int kDocSegs = 128;          // documents per batch of the pipelined document kernel
 constexpr int kHashCountBits = 12;     // packed hash entry: (topic + 1) << 12 | count
 constexpr int kMaxBatchTokens = 4093;  // count of a packed entry stays below 2^12
 constexpr int kDenseMaxK = 2048;       // dense 16-bit count tables up to this K, hash above

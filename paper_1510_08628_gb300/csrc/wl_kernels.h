@@ -19,6 +19,14 @@ cudaError_t launch_batch_phase(bool doc, bool dense, int tpt, const PhaseArgs& a
                                const int32_t* seg_region, int region_words, int kbits, int grid,
                                cudaStream_t st);
 
+// Pipelined document batches (wl_docpipe.cu): desc[b] = {first document,
+// documents | table words << 16, first token, tokens}.
+int docpipe_smem_bytes(int K, int dense, int region_words, int tpt, int M);
+int docpipe_blocks_per_sm(int K, int dense, int region_words, int tpt, int M);
+cudaError_t launch_doc_pipe(bool dense, int tpt, const PhaseArgs& a, const int4* desc, int nbatch,
+                            int* counter, const int32_t* seg_region, int region_words, int grid,
+                            cudaStream_t st);
+
 // Warp tier of the document phase (wl_docwarp.cu): docs = ids of documents
 // with 1..32*tpl tokens.
 int docwarp_table_words(int K, int tpl, int dense);

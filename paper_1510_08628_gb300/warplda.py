@@ -31,7 +31,8 @@ class WarpLDAError(RuntimeError):
 class Tuning(ctypes.Structure):
     _fields_ = [("batch_max_tokens", ctypes.c_int32), ("huge_chunk", ctypes.c_int32),
                 ("region_budget", ctypes.c_int32), ("doc_warp_max", ctypes.c_int32),
-                ("word_positioning", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("word_positioning", ctypes.c_int32), ("doc_batch_kernel", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Info(ctypes.Structure):

@@ -105,13 +105,18 @@ def _edge_corpus(kind, seed=5):
     if kind == "mixed":
         lens = np.concatenate([rng.integers(0, 30, size=400), [5000, 4093, 4094, 1]])
         return corpus.from_lengths(lens, V=500, seed=seed, zipf_s=1.2)
+    if kind == "short_docs":
+        # thousands of 0-3 token documents: batches end at their document cap
+        lens = rng.integers(0, 4, size=3000)
+        lens[::97] = 200
+        return corpus.from_lengths(lens, V=300, seed=seed)
     raise ValueError(kind)
 
 
 EDGE_CASES = [
     ("empty_segments", 3, 1), ("empty_segments", 1, 2), ("giant_doc", 2, 2), ("giant_doc", 16, 4),
     ("giant_word", 30, 2), ("giant_word", 1, 1), ("mixed", 7, 3), ("mixed", 5000, 2),
-    ("mixed", 4097, 1), ("giant_word", 200, 4),
+    ("mixed", 4097, 1), ("giant_word", 200, 4), ("short_docs", 50, 2), ("short_docs", 2049, 2),
 ]
 
 
@@ -130,7 +135,33 @@ def test_edge_corpora_bit_exact(kind, K, M):
 
 TUNINGS = [None, {"batch_max_tokens": 64}, {"batch_max_tokens": 2000, "region_budget": 1024},
            {"huge_chunk": 300, "batch_max_tokens": 500}, {"batch_max_tokens": 4095},
-           {"doc_warp_max": 512}, {"doc_warp_max": 20, "batch_max_tokens": 3000}]
+           {"doc_warp_max": 512}, {"doc_warp_max": 20, "batch_max_tokens": 3000},
+           {"doc_batch_kernel": 2}, {"doc_batch_kernel": 2, "batch_max_tokens": 64},
+           {"doc_batch_kernel": 2, "region_budget": 600}]
+
+
+@pytest.mark.parametrize("kind,K,M,dk", [("mixed", 7, 3, 2), ("mixed", 5000, 2, 1), ("giant_doc", 16, 4, 2),
+                                         ("short_docs", 2049, 2, 1), ("empty_segments", 3, 1, 2),
+                                         ("short_docs", 50, 1, 2), ("mixed", 300, 4, 2),
+                                         ("mixed", 5000, 3, 1), ("giant_word", 30, 2, 2)])
+def test_other_document_kernel_bit_exact(kind, K, M, dk):
+    """The document kernel the default does not pick for K (tuning
+    doc_batch_kernel: 1 = block batch kernel with hash tables, 2 = pipelined
+    kernel with dense tables) against the oracle."""
+    c = _edge_corpus(kind)
+    gpu = _gpu(c, c.V, K, 0.3, 0.02, M, 99, tuning={"doc_batch_kernel": dk})
+    ref = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, K, 0.3, 0.02, M, 99)
+    for s in (1, 2):
+        gpu.sweep(s)
+        ref.sweep(s)
+        _same_state(gpu, ref, f"document kernel {dk}: {kind} K={K} M={M}")
+
+
+def test_pipelined_document_kernel_rejects_bad_tuning():
+    from paper_1510_08628_gb300.warplda import WarpLDAError
+    c = _edge_corpus("mixed")
+    with pytest.raises(WarpLDAError, match="doc_batch_kernel"):
+        _gpu(c, c.V, 50, 0.1, 0.01, 2, 5, tuning={"doc_batch_kernel": 3})
 
 
 def test_schedule_independence():
@@ -234,7 +265,10 @@ def test_storage_order_word_positioning_bit_exact(kind, K, M, tuning):
 @pytest.mark.parametrize("kind,K,M,tuning", [("giant_word", 100000, 2, None),
                                              ("mixed", 20000, 3, {"batch_max_tokens": 64}),
                                              ("giant_doc", (1 << 20) - 1, 1, None),
-                                             ("giant_word", 16385, 4, {"huge_chunk": 300})])
+                                             ("giant_word", 16385, 4, {"huge_chunk": 300}),
+                                             ("short_docs", 70000, 1, None),
+                                             ("mixed", 40000, 2, {"doc_batch_kernel": 2}),
+                                             ("short_docs", 70000, 1, {"doc_batch_kernel": 2})])
 def test_large_K_sparse_rows_bit_exact(kind, K, M, tuning):
     """K above 16384: long segments count into hash rows in device memory and
     word proposals use storage-order positioning (forced), so the oracle runs
