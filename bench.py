@@ -1,11 +1,14 @@
 """Benchmark: tokens per second of one full WarpLDA MH sweep (document phase +
-word phase) on a synthetic LDA corpus shaped like NYTimes (D=300K, V=100K,
-~99M tokens, K=1,000, M=2), with the HBM roofline of the dominant kernel and
+word phase) on a synthetic LDA corpus shaped like PubMed (D=8M, V=140K,
+~736M tokens, K=10,000, M=2), with the HBM roofline of the dominant kernel and
 of the whole sweep, the CPU oracle as the reported baseline, and the
-end-to-end throughput through the C ABI from host buffers.
+end-to-end throughput through the C ABI from host buffers; then fold-in,
+the learned document proposal and the serving loop on a model of the
+NYTimes-shaped corpus (D=300K, V=100K, ~99M tokens, K=1,000).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload nytimes|pubmed|clueweb|tiny]
-                  [--docs D] [--tuning key=value,...] [--m-sweep] [--foldin-docs N]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload pubmed|nytimes|clueweb|tiny]
+                  [--foldin-workload nytimes|...] [--docs D] [--tuning key=value,...]
+                  [--m-sweep] [--foldin-docs N]
   python bench.py --impl reference ...   (the CPU oracle on the same workload)
 
 One "step" is one sweep.  Prints one JSON line (rank 0).  With N > 1
@@ -41,6 +44,7 @@ FALLBACK_HBM_GBS = 6800.0
 def alg_bytes_per_token(kind: str, M: int) -> float:
     return {
         "doc_batch": 4 + 8 * (M + 1),
+        "doc_pipe": 4 + 8 * (M + 1),
         "word_batch": 8 * (M + 1),
         "word_mega_hist": 4,
         "word_mega_accept": 4 * (M + 1) + 4,
@@ -68,6 +72,7 @@ def measured_peaks() -> tuple[float, str]:
 # valid while these files are unchanged)
 KERNEL_SOURCES = {
     "doc_batch": ["wl_batch.cu", "wl_common.cuh", "wl_block.cuh"],
+    "doc_pipe": ["wl_docpipe.cu", "wl_common.cuh", "wl_block.cuh"],
     "word_batch": ["wl_batch.cu", "wl_common.cuh", "wl_block.cuh"],
     "word_mega_accept": ["wl_huge.cu", "wl_common.cuh", "wl_block.cuh"],
     "word_mega_draw": ["wl_huge.cu", "wl_common.cuh", "wl_block.cuh"],
@@ -457,7 +462,10 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="nytimes", help="nytimes | pubmed | clueweb | tiny")
+    ap.add_argument("--workload", default="pubmed", help="pubmed | nytimes | clueweb | tiny")
+    ap.add_argument("--foldin-workload", default="nytimes",
+                    help="corpus whose trained model the fold-in, learned-proposal and serving "
+                         "measurements use")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--corpus-seed", type=int, default=1)
@@ -550,7 +558,8 @@ def main():
     gpu.profile(False)
     peak, peak_kind = measured_peaks()
     tier_tokens = {
-        "doc_batch": c.N - info["huge_doc_tokens"], "word_batch": c.N - info["mega_word_tokens"],
+        "doc_batch": c.N - info["huge_doc_tokens"] - info["pipe_doc_tokens"],
+        "doc_pipe": info["pipe_doc_tokens"], "word_batch": c.N - info["mega_word_tokens"],
         "word_mega_hist": info["mega_word_tokens"], "word_mega_accept": info["mega_word_tokens"],
         "word_mega_draw": info["mega_word_tokens"], "doc_huge_hist": info["huge_doc_tokens"],
         "doc_huge_accept": info["huge_doc_tokens"], "doc_huge_draw": info["huge_doc_tokens"],
@@ -577,20 +586,7 @@ def main():
             "traffic": recorded_traffic(dom, args.workload),
             "alg_bytes_per_launch": d["alg_bytes"]}
 
-    foldin = None
-    if args.foldin_docs > 0 and rank == 0:
-        gpu.sweep(max(0, args.model_sweeps - (args.warmup + 2 * args.steps)))   # train the model
-        foldin = foldin_bench(gpu, c, wl, args, torch, stream)
-        foldin["model_sweeps"] = max(args.model_sweeps, args.warmup + 2 * args.steps)
-        if args.encoder_epochs > 0:
-            foldin["learned"] = learned_bench(gpu, c, wl, args)
-        # serving at equal load for both proposals: half the plain fold-in's
-        # measured throughput, capped
-        rate = min(0.5 * foldin["docs_per_s"], 100_000.0)
-        foldin["serving"] = [serving_bench(gpu, c, wl, args, False, rate)]
-        if args.encoder_epochs > 0:
-            foldin["serving"].append(serving_bench(gpu, c, wl, args, True, rate))
-
+    gpu.close()
     msweep = m_sweep(c, wl, args, stream) if (args.m_sweep and rank == 0) else None
 
     # end to end through the C ABI from pinned host buffers: init (H2D of the
@@ -617,6 +613,32 @@ def main():
                "seconds": e2e_s, "includes": "init (H2D of the corpus, device token-order build) + sweeps + "
                                              "D2H of z and c_k into pinned host buffers"}
 
+    # fold-in, the learned proposal and serving: a model of the fold-in
+    # workload, trained first (its own context; the sweep's is closed)
+    foldin = None
+    if args.foldin_docs > 0 and rank == 0:
+        import copy
+        fa = copy.copy(args)
+        fa.workload = args.foldin_workload
+        if fa.workload == args.workload:
+            cf, wf = c, wl
+        else:
+            cf, wf = corpus.generate(fa.workload, seed=args.corpus_seed)
+        model = WarpLDA(cf.doc_ptr, cf.doc_word, cf.V, wf.K, wf.alpha, wf.beta, wf.M, seed, stream=stream)
+        model.sweep(args.model_sweeps)   # train the model
+        foldin = foldin_bench(model, cf, wf, fa, torch, stream)
+        foldin["workload"] = fa.workload
+        foldin["model_sweeps"] = args.model_sweeps
+        if args.encoder_epochs > 0:
+            foldin["learned"] = learned_bench(model, cf, wf, fa)
+        # serving at equal load for both proposals: half the plain fold-in's
+        # measured throughput, capped
+        rate = min(0.5 * foldin["docs_per_s"], 100_000.0)
+        foldin["serving"] = [serving_bench(model, cf, wf, fa, False, rate)]
+        if args.encoder_epochs > 0:
+            foldin["serving"].append(serving_bench(model, cf, wf, fa, True, rate))
+        model.close()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -641,7 +663,6 @@ def main():
                               "hardware": "2x Xeon E5-2692v2 (24 cores), NYTimes/PubMed, M=2"},
         }
         print(json.dumps(line), flush=True)
-    gpu.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -212,7 +212,8 @@ typedef struct warplda_info {
     int64_t huge_docs, huge_doc_tokens;
     int64_t mega_words, mega_word_tokens;
     int64_t device_bytes;             /* device memory held by the context */
-    int32_t reserved[8];
+    int64_t pipe_doc_tokens;          /* tokens of the pipelined document batches */
+    int32_t reserved[6];
 } warplda_info;
 int warplda_get_info(warplda_ctx* ctx, warplda_info* out);
 

@@ -51,12 +51,12 @@ int cuda_fail(cudaError_t e, const char* what) {
 enum KernelClass {
     kcDocWarp, kcDocBatch, kcDocHugeHist, kcDocHugeAccept, kcDocHugeDraw,
     kcWordBatch, kcWordMegaHist, kcWordMegaAccept, kcWordMegaHistPost, kcWordMegaDraw,
-    kcCountCk, kcFinalize, kcZero, kcCount
+    kcCountCk, kcFinalize, kcZero, kcDocPipe, kcCount
 };
 const char* kClassNames[kcCount] = {
     "doc_warp", "doc_batch", "doc_huge_hist", "doc_huge_accept", "doc_huge_draw",
     "word_batch", "word_mega_hist", "word_mega_accept", "word_mega_hist_post", "word_mega_draw",
-    "count_ck", "finalize_ck", "zero_rows"};
+    "count_ck", "finalize_ck", "zero_rows", "doc_pipe"};
 // topics: packed hash entries hold (topic + 1) << 12 in 32 bits
 constexpr int kMaxTopics = (1 << 20) - 1;
 // tokens of a pipelined document batch (at most 4 * 256 - 3; at most 509
@@ -455,7 +455,8 @@ int run_phase(warplda_ctx* c, bool doc) {
     for (int cls = 1; cls >= 0; --cls) {
         if (T.batches[cls].empty()) continue;
         pc.cls = cls;
-        rc = launch_rec(c, doc ? kcDocBatch : kcWordBatch, [](warplda_ctx* cc, void* p) {
+        rc = launch_rec(c, doc ? (cls == 0 && c->doc_pipe ? kcDocPipe : kcDocBatch) : kcWordBatch,
+                        [](warplda_ctx* cc, void* p) {
             PhaseCall* q = (PhaseCall*)p;
             Tier& TT = q->doc ? cc->docs : cc->words;
             const int k = q->cls;
@@ -1413,6 +1414,9 @@ int warplda_get_info(warplda_ctx* c, warplda_info* o) {
     o->mega_words = c->words.nrows;
     o->mega_word_tokens = c->words.row_tokens;
     o->device_bytes = c->device_bytes;
+    // the small document class: every batched token outside the large
+    // class and the warp tier
+    o->pipe_doc_tokens = c->doc_pipe ? c->N - c->docs.row_tokens - c->docs.large_tokens - c->docs.warp_tokens : 0;
     return WARPLDA_OK;
 }
 

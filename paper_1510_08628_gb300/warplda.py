@@ -42,7 +42,8 @@ class Info(ctypes.Structure):
                 ("doc_batches", ctypes.c_int64), ("word_batches", ctypes.c_int64),
                 ("huge_docs", ctypes.c_int64), ("huge_doc_tokens", ctypes.c_int64),
                 ("mega_words", ctypes.c_int64), ("mega_word_tokens", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
+                ("device_bytes", ctypes.c_int64), ("pipe_doc_tokens", ctypes.c_int64),
+                ("reserved", ctypes.c_int32 * 6)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
