@@ -15,6 +15,7 @@
 #include <vector>
 #include <chrono>
 #include <map>
+#include <mutex>
 
 #include "../../include/warplda.h"
 #include "wl_kernels.h"
@@ -24,6 +25,41 @@ using namespace wl;
 namespace {
 
 thread_local std::string g_err;
+
+// Fault injection (see launch_gate in wl_kernels.h): the count of calls that
+// saw the variable's current value.
+struct InjectState {
+    std::string value;
+    long count = 0;
+};
+std::mutex g_inject_mu;
+InjectState g_inject_launch, g_inject_alloc;
+
+bool inject_fires(const char* var, InjectState& st) {
+    const char* v = std::getenv(var);
+    std::lock_guard<std::mutex> lock(g_inject_mu);
+    if (!v || !*v) {
+        st.value.clear();
+        st.count = 0;
+        return false;
+    }
+    if (st.value != v) {
+        st.value = v;
+        st.count = 0;
+    }
+    const long k = std::strtol(v, nullptr, 10);
+    return k > 0 && ++st.count == k;
+}
+
+// Every device and pinned host allocation of the library goes through these.
+cudaError_t dev_malloc(void** p, size_t bytes) {
+    if (const cudaError_t e = alloc_gate()) return e;
+    return cudaMalloc(p, bytes);
+}
+cudaError_t host_malloc(void** p, size_t bytes) {
+    if (const cudaError_t e = alloc_gate()) return e;
+    return cudaMallocHost(p, bytes);
+}
 
 int64_t r4(int64_t x) { return (x + 3) & ~(int64_t)3; }
 
@@ -176,7 +212,7 @@ template <typename T>
 int dalloc(warplda_ctx* c, T** p, int64_t n, const char* what) {
     size_t bytes = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
     bytes = (bytes + 255) & ~(size_t)255;
-    cudaError_t e = cudaMalloc((void**)p, bytes);
+    cudaError_t e = dev_malloc((void**)p, bytes);
     if (e != cudaSuccess) return cuda_fail(e, what);
     c->allocs.push_back(*p);
     c->device_bytes += (int64_t)bytes;
@@ -537,12 +573,19 @@ int recount(warplda_ctx* c) {
 
 int wl::record_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
+cudaError_t wl::launch_gate() {
+    return inject_fires("WARPLDA_FAIL_LAUNCH", g_inject_launch) ? cudaErrorLaunchOutOfResources : cudaSuccess;
+}
+cudaError_t wl::alloc_gate() {
+    return inject_fires("WARPLDA_FAIL_ALLOC", g_inject_alloc) ? cudaErrorMemoryAllocation : cudaSuccess;
+}
+
 // Device buffers of one fold-in call, freed on every return path.
 struct FoldBuffers {
     std::vector<void*> p;
     template <typename T>
     cudaError_t get(T** out, int64_t n) {
-        cudaError_t e = cudaMalloc((void**)out, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
+        cudaError_t e = dev_malloc((void**)out, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
         if (e == cudaSuccess) p.push_back(*out);
         return e;
     }
@@ -748,7 +791,7 @@ void pool_give(warplda_server* s, int64_t start, int64_t n) {
 
 template <typename T>
 int salloc(warplda_server* s, T** p, int64_t n) {
-    cudaError_t e = cudaMalloc((void**)p, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
+    cudaError_t e = dev_malloc((void**)p, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
     if (e != cudaSuccess) return cuda_fail(e, "alloc server");
     s->allocs.push_back(*p);
     return WARPLDA_OK;
@@ -791,7 +834,7 @@ int stage_room(warplda_server* s, int64_t n) {
     if (s->h_stage) cudaFreeHost(s->h_stage);
     s->h_stage = nullptr;
     const int64_t cap = std::max<int64_t>(n, 2 * s->h_stage_cap);
-    if (cudaMallocHost((void**)&s->h_stage, (size_t)cap * 4) != cudaSuccess) {
+    if (host_malloc((void**)&s->h_stage, (size_t)cap * 4) != cudaSuccess) {
         s->h_stage_cap = 0;
         return fail(WARPLDA_ENOMEM, "pinned staging");
     }
@@ -816,7 +859,7 @@ int server_admit(warplda_server* s, const std::vector<int32_t>& active, int64_t*
     if (total + 4 > s->staged_cap) {
         int64_t cap = std::max<int64_t>(total + 4, 2 * s->staged_cap);
         int32_t* p = nullptr;
-        WL_CU(cudaMalloc((void**)&p, (size_t)cap * 4), "alloc staging");
+        WL_CU(dev_malloc((void**)&p, (size_t)cap * 4), "alloc staging");
         s->allocs.push_back(p);
         s->d_staged = p;
         s->staged_cap = cap;
@@ -999,7 +1042,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         // written from the sorted positions afterwards; tiny corpora allocate
         const bool own_scratch = token_sort_scratch(N) > N + 4;
         if (!own_scratch) scratch = c->perm;
-        else if (e == cudaSuccess) e = cudaMalloc((void**)&scratch, (size_t)token_sort_scratch(N) * 4);
+        else if (e == cudaSuccess) e = dev_malloc((void**)&scratch, (size_t)token_sort_scratch(N) * 4);
         if (e == cudaSuccess) e = launch_token_sort(ka, va, kb, vb, N, (int32_t)V, scratch, &pos, &keys, c->st);
         if (e == cudaSuccess && N > 0 && (pos != c->prop || keys != c->z)) e = cudaErrorInvalidValue;   // by the parity above
         if (e == cudaSuccess) e = launch_word_starts(keys, N, (int32_t)V, c->word_off, c->st);
@@ -1793,7 +1836,7 @@ int warplda_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, const 
         return fail(WARPLDA_EINVAL, "GEMM operands must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int32_t* status = nullptr;
-    WL_CU(cudaMalloc((void**)&status, sizeof(int32_t)), "alloc GEMM status");
+    WL_CU(dev_malloc((void**)&status, sizeof(int32_t)), "alloc GEMM status");
     int32_t h = 0;
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
     if (e == cudaSuccess)
@@ -1851,8 +1894,8 @@ int warplda_server_create(warplda_ctx* c, int32_t slots, int64_t pool_tokens, in
          (rc = salloc(s, &s->d_aprob, (int64_t)slots * K)) || (rc = salloc(s, &s->d_aalias, (int64_t)slots * K)) ||
          (rc = salloc(s, &s->d_astack, (int64_t)slots * K))))
         return bail(rc);
-    if (cudaMallocHost((void**)&s->h_theta, (size_t)slots * K * 4) != cudaSuccess ||
-        cudaMallocHost((void**)&s->h_fin_slot, (size_t)slots * 4) != cudaSuccess)
+    if (host_malloc((void**)&s->h_theta, (size_t)slots * K * 4) != cudaSuccess ||
+        host_malloc((void**)&s->h_fin_slot, (size_t)slots * 4) != cudaSuccess)
         return bail(fail(WARPLDA_ENOMEM, "pinned staging"));
     if (cudaEventCreateWithFlags(&s->tick, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(WARPLDA_ECUDA, "event"));

@@ -524,6 +524,7 @@ cudaError_t launch_batch_phase(bool doc, bool dense, int tpt, const PhaseArgs& a
                                const int4* batches, int nbatch, int* counter,
                                const int32_t* seg_region, int region_words, int kbits, int grid,
                                cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (nbatch <= 0) return cudaSuccess;
     const int smem = batch_smem_bytes(a.K, a.stage_ck, region_words, tpt, doc ? 0 : 1, dense ? 1 : 0);
     const void* f = pick_kernel(doc, dense, tpt, a.M);

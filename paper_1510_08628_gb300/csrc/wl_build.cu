@@ -227,6 +227,7 @@ int64_t token_sort_scratch(int64_t N) {
 }
 
 cudaError_t launch_word_check(const int32_t* w, int64_t N, int32_t V, int32_t* bad, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (N <= 0) return cudaSuccess;
     const int64_t g = std::min<int64_t>((N + kThreads - 1) / kThreads, 152 * 16);
     word_check_kernel<<<(unsigned)g, kThreads, 0, st>>>(w, N, V, bad);
@@ -234,6 +235,7 @@ cudaError_t launch_word_check(const int32_t* w, int64_t N, int32_t V, int32_t* b
 }
 
 cudaError_t launch_word_starts(const int32_t* keys_sorted, int64_t N, int32_t V, int32_t* start, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     cudaError_t e = cudaMemsetAsync(start, 0xFF, sizeof(int32_t) * (size_t)V, st);
     if (e != cudaSuccess || N <= 0) return e;
     const int64_t g = std::min<int64_t>((N + kThreads - 1) / kThreads, 152 * 16);
@@ -250,6 +252,7 @@ int token_sort_passes(int64_t V) {
 cudaError_t launch_token_sort(int32_t* keys_a, int32_t* vals_a, int32_t* keys_b, int32_t* vals_b, int64_t N,
                               int32_t V, int32_t* scratch, int32_t** pos_sorted, int32_t** keys_sorted,
                               cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     *pos_sorted = nullptr;
     *keys_sorted = nullptr;
     if (N <= 0) return cudaSuccess;
@@ -282,6 +285,7 @@ cudaError_t launch_token_sort(int32_t* keys_a, int32_t* vals_a, int32_t* keys_b,
 }
 
 cudaError_t launch_perm(const int32_t* pos_sorted, int64_t N, int32_t* perm, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (N <= 0) return cudaSuccess;
     const int64_t g = std::min<int64_t>((N + kThreads - 1) / kThreads, 152 * 16);
     perm_kernel<<<(unsigned)g, kThreads, 0, st>>>(pos_sorted, N, perm);
@@ -291,6 +295,7 @@ cudaError_t launch_perm(const int32_t* pos_sorted, int64_t N, int32_t* perm, cud
 cudaError_t launch_batch_lists(const int4* batches, int nb, const int32_t* doc_off, const int32_t* perm,
                                const int32_t* pos_sorted, int64_t N, int32_t* sperm, uint32_t* sinfo, int32_t* bad,
                                cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (nb <= 0) return cudaSuccess;
     int nbits = 1;
     while (nbits < 32 && ((int64_t)1 << nbits) <= N) ++nbits;   // 2^nbits - 1 >= N > every key

@@ -506,6 +506,7 @@ int docpipe_blocks_per_sm(int K, int dense, int region_words, int tpt, int M) {
 cudaError_t launch_doc_pipe(bool dense, int tpt, const PhaseArgs& a, const int4* desc, int nbatch,
                             int* counter, const int32_t* seg_region, int region_words, int grid,
                             cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (nbatch <= 0) return cudaSuccess;
     const void* f = docpipe_pick(dense, tpt, a.M);
     if (!f) return cudaErrorInvalidValue;

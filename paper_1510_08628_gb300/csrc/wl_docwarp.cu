@@ -217,6 +217,7 @@ int docwarp_blocks_per_sm(int K, int stage_ck, int tpl, int M, int dense) {
 
 cudaError_t launch_doc_warp(int tpl, bool dense, const PhaseArgs& a, const int32_t* docs, int ndocs,
                             int* counter, int grid, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (ndocs <= 0) return cudaSuccess;
     const int smem = docwarp_smem_bytes(a.K, a.stage_ck, tpl, dense ? 1 : 0);
     const void* f = docwarp_pick(tpl, a.M, dense);

@@ -265,6 +265,7 @@ static int grid_n(int64_t n) { return (int)std::min<int64_t>(4096, std::max<int6
 
 cudaError_t launch_enc_docword(const int32_t* perm, const int32_t* word_off, int64_t N, int64_t V,
                                int32_t* out, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (N <= 0) return cudaSuccess;
     enc_docword_kernel<<<grid_n(N), 256, 0, st>>>(perm, word_off, N, V, out);
     return cudaGetLastError();
@@ -272,6 +273,7 @@ cudaError_t launch_enc_docword(const int32_t* perm, const int32_t* word_off, int
 
 cudaError_t launch_enc_l1_fwd(const EncBatch& b, int B, const uint16_t* W1b, const float* b1, int H, int log2F,
                               float* h_pre, uint16_t* hb, uint16_t* hbT, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     enc_l1_fwd_kernel<<<B, kEncThreads, 0, st>>>(b, W1b, b1, H, log2F, h_pre, hb, hbT);
     return cudaGetLastError();
 }
@@ -280,6 +282,7 @@ cudaError_t launch_enc_softmax(const EncBatch& b, int B, const float* logits, in
                                const float* tgt, const int32_t* z, const int32_t* perm, float alpha, float abar,
                                uint16_t* dl, uint16_t* dlT, float* gb2, double* loss, int32_t* cnt,
                                cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     enc_softmax_kernel<<<B, kEncThreads, 0, st>>>(b, logits, K, Kp, q_out, tgt, z, perm, alpha, abar, dl, dlT,
                                                   gb2, loss, cnt);
     return cudaGetLastError();
@@ -287,12 +290,14 @@ cudaError_t launch_enc_softmax(const EncBatch& b, int B, const float* logits, in
 
 cudaError_t launch_enc_l1_bwd(const EncBatch& b, int B, const float* dH, const float* h_pre, int H, int log2F,
                               float* gW1, float* gb1, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     enc_l1_bwd_kernel<<<B, kEncThreads, 0, st>>>(b, dH, h_pre, H, log2F, gW1, gb1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_enc_adam(float* w, float* m, float* v, const float* g, int64_t n, float lr, int step,
                             uint16_t* wb, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     const float c1 = (float)(1.0 - std::pow(0.9, step)), c2 = (float)(1.0 - std::pow(0.999, step));
     enc_adam_kernel<<<grid_n(n), 256, 0, st>>>(w, m, v, g, n, lr, c1, c2, wb);
     return cudaGetLastError();
@@ -300,17 +305,20 @@ cudaError_t launch_enc_adam(float* w, float* m, float* v, const float* g, int64_
 
 cudaError_t launch_enc_w2_copies(const float* W2t, int Kp, int H, uint16_t* W2tb, uint16_t* W2nb,
                                  cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     enc_w2_copies_kernel<<<grid_n((int64_t)Kp * H), 256, 0, st>>>(W2t, Kp, H, W2tb, W2nb);
     return cudaGetLastError();
 }
 
 cudaError_t launch_enc_to_bf16(const float* x, int64_t n, uint16_t* y, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     enc_to_bf16_kernel<<<grid_n(n), 256, 0, st>>>(x, n, y);
     return cudaGetLastError();
 }
 
 cudaError_t launch_enc_alias(const float* q, int64_t Dn, int K, float* prob, int32_t* alias, int32_t* stack,
                              cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (Dn <= 0) return cudaSuccess;
     enc_alias_kernel<<<(int)((Dn + 63) / 64), 64, 0, st>>>(q, Dn, K, prob, alias, stack);
     return cudaGetLastError();

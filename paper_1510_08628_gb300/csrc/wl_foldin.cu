@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(kThreads) model_sort_kernel(const int32_t* __r
 
 cudaError_t launch_model_build(const int32_t* z, const int32_t* word_off, int64_t V, int K,
                                int32_t* Cw, int32_t* Zs, int32_t* fault, int grid, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     cudaError_t e = cudaMemsetAsync(Cw, 0, (size_t)V * K * sizeof(int32_t), st);
     if (e != cudaSuccess || V <= 0) return e;
     model_counts_kernel<<<grid, kThreads, 0, st>>>(z, word_off, V, K, Cw, fault);
@@ -354,6 +355,7 @@ int foldin_warps(int tab_words) {
 }
 
 cudaError_t launch_foldin(const FoldArgs& f, int tab_words, int grid, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (f.Dn <= 0) return cudaSuccess;
     const bool dense = f.K <= kDenseMaxK;
     const void* fn = fold_pick(f.M, dense, f.q != nullptr);
@@ -393,6 +395,7 @@ __global__ void serve_rows_kernel(const uint32_t* __restrict__ src, const int32_
 
 cudaError_t launch_serve_admit(const int32_t* staged, const int4* req, const int32_t* src, int n, int nslots,
                                int64_t pool_tokens, int32_t* pool_words, int4* info, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (n <= 0) return cudaSuccess;
     serve_admit_kernel<<<std::min(n, 4096), 256, 0, st>>>(staged, req, src, n, nslots, pool_tokens, pool_words, info);
     return cudaGetLastError();
@@ -400,12 +403,14 @@ cudaError_t launch_serve_admit(const int32_t* staged, const int4* req, const int
 
 cudaError_t launch_serve_rows(const void* src, const int32_t* slots, int n, int K, int nslots, void* dst,
                               cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (n <= 0) return cudaSuccess;
     serve_rows_kernel<<<std::min(n, 4096), 256, 0, st>>>((const uint32_t*)src, slots, n, K, nslots, (uint32_t*)dst);
     return cudaGetLastError();
 }
 
 cudaError_t launch_serve(const FoldArgs& f, const ServeSlots& sl, int tab_words, int grid, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (sl.nactive <= 0) return cudaSuccess;
     const bool dense = f.K <= kDenseMaxK;
     const void* fn = fold_pick(f.M, dense, sl.q != nullptr, true);

@@ -191,6 +191,7 @@ int gemm_smem_bytes() { return 4 * kStageBytes; }
 
 cudaError_t launch_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, const float* bias,
                              int M, int N, int K, int32_t* status, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if (M % kGemmTile || N % kGemmTile || K % kGemmChunk) return cudaErrorInvalidValue;
     const int smem = gemm_smem_bytes();

@@ -442,6 +442,7 @@ static cudaError_t set_smem(F f, int smem) {
 
 cudaError_t launch_huge_hist(bool doc, const PhaseArgs& a, const HugeWork& w, int32_t* rows,
                              int grid, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (w.npieces <= 0) return cudaSuccess;
     const int smem = huge_smem_bytes(a.K, a.stage_ck, 0, doc);
     if (doc) {
@@ -467,6 +468,7 @@ cudaError_t launch_huge_hist(bool doc, const PhaseArgs& a, const HugeWork& w, in
 
 cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const HugeWork& w,
                                const int32_t* rows_pre, int grid, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (w.npieces <= 0) return cudaSuccess;
     const int smem = huge_smem_bytes(a.K, a.stage_ck, 1, doc);
     cudaError_t e = cudaSuccess;
@@ -488,6 +490,7 @@ cudaError_t launch_huge_accept(bool doc, const PhaseArgs& a, const HugeWork& w,
 
 cudaError_t launch_huge_draw(bool doc, const PhaseArgs& a, const HugeWork& w,
                              const int32_t* rows_post, int grid, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (w.npieces <= 0) return cudaSuccess;
     // storage-order word positioning reads z directly: no prefix, no guide
     const int smem = a.word_storage ? 0 : huge_smem_bytes(a.K, a.stage_ck, 2, doc);
@@ -645,6 +648,7 @@ __global__ void __launch_bounds__(kThreads) sparse_accept_kernel(PhaseArgs a, Hu
 
 cudaError_t launch_sparse_hist(bool doc, const PhaseArgs& a, const HugeWork& w, const SparseRows& r, int grid,
                                cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (w.npieces <= 0) return cudaSuccess;
     if (doc) sparse_hist_kernel<true><<<grid, kThreads, 0, st>>>(a, w, r);
     else sparse_hist_kernel<false><<<grid, kThreads, 0, st>>>(a, w, r);
@@ -653,6 +657,7 @@ cudaError_t launch_sparse_hist(bool doc, const PhaseArgs& a, const HugeWork& w, 
 
 cudaError_t launch_sparse_accept(bool doc, const PhaseArgs& a, const HugeWork& w, const SparseRows& r, int grid,
                                  cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (w.npieces <= 0) return cudaSuccess;
     if (doc) {
         WL_M_SWITCH({ sparse_accept_kernel<true, MM><<<grid, kThreads, 0, st>>>(a, w, r); })
@@ -685,6 +690,7 @@ __global__ void sparse_loglik_kernel(const unsigned long long* __restrict__ slot
 
 cudaError_t launch_sparse_loglik(const unsigned long long* slots, int64_t n, double g, double* out,
                                  cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (n <= 0) return cudaSuccess;
     const int grid = (int)std::min<int64_t>(4096, (n + kThreads - 1) / kThreads);
     sparse_loglik_kernel<<<grid, kThreads, 0, st>>>(slots, n, g, out);

@@ -8,6 +8,16 @@
 
 namespace wl {
 
+// Host-side fault injection, for tests of the error paths (nothing is run
+// on the GPU to fail): with WARPLDA_FAIL_LAUNCH=k in the environment the
+// k-th kernel launcher called from then on returns a launch error instead of
+// launching, and with WARPLDA_FAIL_ALLOC=k the k-th device or pinned host
+// allocation the library asks for fails as out of memory.  "From then on"
+// counts from the first call that sees the variable with its current value;
+// unset, empty or 0 disables it.  Every launcher starts with launch_gate().
+cudaError_t launch_gate();
+cudaError_t alloc_gate();
+
 // On-chip batch tier (wl_batch.cu).  A batch is {first segment, end
 // segment, table words, 0}; seg_region[s] is segment s's table offset in its
 // batch; dense selects 16-bit dense tables (else hash tables).

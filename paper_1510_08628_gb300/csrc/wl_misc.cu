@@ -25,6 +25,7 @@ __global__ void init_z_kernel(int32_t* z, int32_t* prop, int64_t N, int K, int M
 
 cudaError_t launch_init_z(int32_t* z, int32_t* prop, int64_t N, int K, int M, uint64_t seed,
                           cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (N <= 0) return cudaSuccess;
     init_z_kernel<<<grid_for(N), kThreads, 0, st>>>(z, prop, N, K, M, round_keys(seed));
     return cudaGetLastError();
@@ -83,6 +84,7 @@ __global__ void topic_hist_global_kernel(const int32_t* __restrict__ z, int64_t 
 }
 
 cudaError_t launch_topic_hist(const int32_t* z, int64_t N, int32_t* ck, int K, int grid, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     cudaError_t e = cudaMemsetAsync(ck, 0, sizeof(int32_t) * K, st);
     if (e != cudaSuccess || N <= 0) return e;
     if (K > kTopicHistSmemMaxK) {
@@ -107,6 +109,7 @@ __global__ void finalize_ck_kernel(const int32_t* ck, float* ckb, int K, float b
 
 cudaError_t launch_finalize_ck(const int32_t* ck, float* ckb, int K, float beta_bar,
                                int32_t* counters, int ncounters, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     const int n = K > ncounters ? K : ncounters;
     finalize_ck_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, st>>>(ck, ckb, K, beta_bar,
                                                                            counters, ncounters);
@@ -121,6 +124,7 @@ __global__ void zero_kernel(int4* p, int64_t n4) {
 
 // n must be a multiple of 4 and p 16-byte aligned (row arrays are padded).
 cudaError_t launch_zero(int32_t* p, int64_t n, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (n <= 0) return cudaSuccess;
     zero_kernel<<<grid_for(n / 4), kThreads, 0, st>>>(reinterpret_cast<int4*>(p), n / 4);
     return cudaGetLastError();
@@ -134,6 +138,7 @@ __global__ void gather_kernel(const int32_t* z, const int32_t* perm, int64_t N, 
 
 cudaError_t launch_gather_docmajor(const int32_t* z, const int32_t* perm, int64_t N, int32_t* out,
                                    cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (N <= 0) return cudaSuccess;
     gather_kernel<<<grid_for(N), kThreads, 0, st>>>(z, perm, N, out);
     return cudaGetLastError();
@@ -146,6 +151,7 @@ __global__ void check_range_kernel(const int32_t* v, int64_t n, int K, int32_t* 
 }
 
 cudaError_t launch_check_range(const int32_t* v, int64_t n, int K, int32_t* bad, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (n <= 0) return cudaSuccess;
     check_range_kernel<<<grid_for(n), kThreads, 0, st>>>(v, n, K, bad);
     return cudaGetLastError();
@@ -252,6 +258,7 @@ cudaError_t launch_loglik_batches(bool doc, const int32_t* z, const int32_t* per
                                   const int32_t* seg_off, const int4* batches, int nbatch, int K,
                                   double g, int region_words, int64_t N, int64_t nseg_total,
                                   int32_t* fault, double* out, int grid, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (nbatch <= 0) return cudaSuccess;
     const int smem = loglik_smem_bytes(region_words);
     cudaError_t e = cudaFuncSetAttribute(loglik_batch_kernel,
@@ -277,6 +284,7 @@ __global__ void loglik_rows_kernel(const int32_t* rows, int64_t n, double g, dou
 
 cudaError_t launch_loglik_rows(const int32_t* rows, int64_t nrows, int K, double g, double* out,
                                cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     const int64_t n = nrows * K;
     if (n <= 0) return cudaSuccess;
     loglik_rows_kernel<<<grid_for(n), kThreads, 0, st>>>(rows, n, g, out);
@@ -297,6 +305,7 @@ __global__ void loglik_lengths_kernel(const int32_t* seg_off, int64_t nseg, doub
 
 cudaError_t launch_loglik_lengths(const int32_t* seg_off, int64_t nseg, double abar, double* out,
                                   cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     if (nseg <= 0) return cudaSuccess;
     loglik_lengths_kernel<<<grid_for(nseg), kThreads, 0, st>>>(seg_off, nseg, abar, out);
     return cudaGetLastError();
@@ -314,6 +323,7 @@ __global__ void loglik_topics_kernel(const int32_t* ck, int K, double bbar, doub
 
 cudaError_t launch_loglik_topics(const int32_t* ck, int K, double bbar, double* out,
                                  cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
     loglik_topics_kernel<<<grid_for(K), kThreads, 0, st>>>(ck, K, bbar, out);
     return cudaGetLastError();
 }
