@@ -397,17 +397,22 @@ const char* warplda_last_error(void);
  *   word_ptr_dev    device int64[V+1], token offsets of the words.
  *   z_wordmajor_dev device int32[N], the same topics grouped by word.
  *               A value outside [0, K) is not counted and makes the
- *               result NaN; the offsets must be valid (not checked).
+ *               result NaN.  N must equal doc_ptr[D] and word_ptr[V] (the
+ *               tokens counted on either side); if it does not, the result
+ *               is NaN.  The offsets must otherwise be valid: monotone and
+ *               within the z arrays (not checked).
  *   out_dev     device double, receives the log-likelihood.
  *   cuda_stream cudaStream_t or NULL; the call is asynchronous on it.
  * It calls no cudaMalloc, cudaFree or allocating library routine.  Its
  * scratch is a static device array of about 66 KB that every GPU loading
- * this library holds until the process exits; the first call on a device
- * looks up that array's device address (make that first call before any
- * stream capture).  All calls share the array and each call clears it
- * first, so calls whose kernels overlap on a GPU (different streams,
- * threads) race and must be serialised by the caller.  Errors: EINVAL
- * (sizes, K above 16384, null pointer), ECUDA.
+ * this library holds until the process exits; every call looks up that
+ * array's device address on the current device (cudaGetSymbolAddress,
+ * which allocates nothing).  All calls share the array and each call clears
+ * it first, so calls whose kernels overlap on a GPU (different streams,
+ * threads) race and must be serialised by the caller.  Cost: every document
+ * and word clears and scans K shared-memory counters, O((D + V) K) work
+ * besides reading the N topics twice.  Errors: EINVAL (sizes, K above
+ * 16384, null pointer), ECUDA.
  */
 int warplda_loglik_noalloc(int64_t D, int64_t V, int64_t N, int32_t K, float alpha, float beta,
                            const int64_t* doc_ptr_dev, const int32_t* z_docmajor_dev,

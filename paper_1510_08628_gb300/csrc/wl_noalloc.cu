@@ -6,13 +6,17 @@
 // fail or stall the device.  It needs no context (creating a context
 // allocates) and calls no allocating routine.
 //
-// Its scratch -- the topic-count vector c_k and one FP64 partial sum per block
-// -- lives in the file-scope array below, which every GPU that loads this
-// library holds until the process exits (kNaScratchBytes, about 66 KB).
+// Its scratch -- the topic-count vector c_k, one FP64 partial sum per block
+// and a token counter -- lives in the file-scope array below, which every GPU
+// that loads this library holds until the process exits (kNaScratchBytes,
+// about 66 KB).
+//
+// Cost: every document and word clears and scans a K-entry histogram in
+// shared memory, so a call does O((D + V) K) shared-memory work besides its
+// O(N) reads -- at K = 16384 on a 400K-segment corpus about 6.5G operations.
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "../../include/warplda.h"
@@ -23,34 +27,25 @@ namespace {
 
 constexpr int kNaMaxK = 16384;         // largest K this entry point accepts
 constexpr int kNaBlocks = 256;         // blocks, one FP64 partial sum each
-constexpr size_t kNaScratchBytes = (size_t)kNaMaxK * sizeof(int32_t) + (size_t)kNaBlocks * sizeof(double);
-constexpr int kNaMaxDevices = 64;
+constexpr size_t kNaScratchBytes =
+    (size_t)kNaMaxK * sizeof(int32_t) + (size_t)kNaBlocks * sizeof(double) + 2 * sizeof(unsigned long long);
 
-// [c_k: kNaMaxK int32][partial sums: kNaBlocks double]
+// [c_k: kNaMaxK int32][partial sums: kNaBlocks double][word tokens: uint64, pad]
 static __device__ __align__(256) unsigned char g_na_scratch[kNaScratchBytes];
-
-std::mutex g_na_mu;
-void* g_na_ptr[kNaMaxDevices] = {};
 
 // failures are reported through warplda_last_error()
 int na_fail(int code, const std::string& msg) { return wl::record_error(code, msg.c_str()); }
 
-// Device address of g_na_scratch on the current device, looked up once per
-// device (the host-side symbol is only a stand-in, not a device address).
+// Device address of g_na_scratch on the current device (the host-side
+// symbol is only a stand-in, not a device address).  Looked up on every call:
+// it allocates nothing, and a cached address would go stale if the device's
+// context were reset and the module loaded again elsewhere.
 int na_scratch(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return na_fail(WARPLDA_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kNaMaxDevices) return na_fail(WARPLDA_EINVAL, "device index out of range");
-    std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_na_scratch);
-        if (e != cudaSuccess || !p)
-            return na_fail(WARPLDA_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_na_ptr[dev] = p;
-    }
-    *out = g_na_ptr[dev];
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
+    if (e != cudaSuccess || !p)
+        return na_fail(WARPLDA_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    *out = p;
     return WARPLDA_OK;
 }
 
@@ -66,28 +61,32 @@ __device__ __forceinline__ double na_block_sum(double v, double* red) {
     return s;
 }
 
-// Clears the scratch c_k and partial sums of this call.
-__global__ void na_clear_kernel(int32_t* ck, double* part, int K) {
+// Clears the scratch c_k, partial sums and word-token counter of this call.
+__global__ void na_clear_kernel(int32_t* ck, double* part, unsigned long long* wtok, int K) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < K; i += gridDim.x * blockDim.x) ck[i] = 0;
-    if (blockIdx.x == 0)
+    if (blockIdx.x == 0) {
         for (int i = threadIdx.x; i < kNaBlocks; i += blockDim.x) part[i] = 0.0;
+        if (threadIdx.x == 0) *wtok = 0ull;
+    }
 }
 
 // One block per segment at a time (documents 0..D-1, then words): the
 // segment's topic histogram in shared memory, then
 //   documents: lnG(abar) - lnG(abar + L_d) + sum_k [lnG(alpha + C_dk) - lnG(alpha)]
 //   words:     sum_k [lnG(beta + C_wk) - lnG(beta)]
-// Document tokens also add into the scratch c_k.  Each block writes its own
-// partial sum; nothing is accumulated across blocks in floating point.
+// Document tokens also add into the scratch c_k, and the words' token counts
+// into the word-token counter.  Each block writes its own partial sum;
+// nothing is accumulated across blocks in floating point.
 __global__ void __launch_bounds__(wl::kThreads) na_segments_kernel(
     int64_t D, int64_t V, int K, double alpha, double beta, double abar,
     const int64_t* __restrict__ doc_ptr, const int32_t* __restrict__ z_doc,
     const int64_t* __restrict__ word_ptr, const int32_t* __restrict__ z_word,
-    int32_t* __restrict__ ck, double* __restrict__ part) {
+    int32_t* __restrict__ ck, double* __restrict__ part, unsigned long long* __restrict__ wtok) {
     extern __shared__ int hist[];
     __shared__ double red[wl::kWarps];
     const double la = lgamma(alpha), lb = lgamma(beta), lab = lgamma(abar);
     double acc = 0.0;
+    unsigned long long words = 0;
     for (int64_t s = blockIdx.x; s < D + V; s += gridDim.x) {
         const bool doc = s < D;
         const int64_t b = doc ? doc_ptr[s] : word_ptr[s - D];
@@ -111,23 +110,34 @@ __global__ void __launch_bounds__(wl::kThreads) na_segments_kernel(
             if (c) acc += lgamma(g + c) - lg;
         }
         if (doc && threadIdx.x == 0) acc += lab - lgamma(abar + (double)(e - b));
+        if (!doc && threadIdx.x == 0) words += (unsigned long long)(e - b);
         __syncthreads();
     }
     const double tot = na_block_sum(acc, red);
-    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = tot;
+        if (words) atomicAdd(wtok, words);
+    }
 }
 
 // Topic terms sum_k [lnG(bbar) - lnG(bbar + C_k)] plus the block partials, in
-// a fixed order; one block.
+// a fixed order; one block.  The document tokens (sum of c_k) and the word
+// tokens must both equal N, else the result is NaN.
 __global__ void na_final_kernel(const int32_t* __restrict__ ck, const double* __restrict__ part,
-                                int K, double bbar, double* __restrict__ out) {
+                                const unsigned long long* __restrict__ wtok, int K, int64_t N,
+                                double bbar, double* __restrict__ out) {
     __shared__ double red[wl::kWarps];
     const double lbb = lgamma(bbar);
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) acc += lbb - lgamma(bbar + (double)ck[k]);
+    double acc = 0.0, ntok = 0.0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        acc += lbb - lgamma(bbar + (double)ck[k]);
+        ntok += (double)ck[k];   // exact: integers below 2^53
+    }
     for (int i = threadIdx.x; i < kNaBlocks; i += blockDim.x) acc += part[i];
     const double tot = na_block_sum(acc, red);
-    if (threadIdx.x == 0) *out = tot;
+    const double n = na_block_sum(ntok, red);
+    if (threadIdx.x == 0)
+        *out = (n == (double)N && *wtok == (unsigned long long)N) ? tot : __longlong_as_double(0x7FF8000000000000ll);
 }
 
 }  // namespace
@@ -152,16 +162,17 @@ extern "C" int warplda_loglik_noalloc(int64_t D, int64_t V, int64_t N, int32_t K
     int32_t* ck = reinterpret_cast<int32_t*>(scratch);
     double* part = reinterpret_cast<double*>(static_cast<unsigned char*>(scratch) +
                                              (size_t)kNaMaxK * sizeof(int32_t));
+    unsigned long long* wtok = reinterpret_cast<unsigned long long*>(part + kNaBlocks);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const double a = alpha, b = beta;
     const int smem = K * (int)sizeof(int);
     cudaError_t e = cudaFuncSetAttribute(na_segments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) {
-        na_clear_kernel<<<16, wl::kThreads, 0, st>>>(ck, part, K);
+        na_clear_kernel<<<16, wl::kThreads, 0, st>>>(ck, part, wtok, K);
         na_segments_kernel<<<kNaBlocks, wl::kThreads, smem, st>>>(D, V, K, a, b, (double)K * a, doc_ptr_dev,
                                                                   z_docmajor_dev, word_ptr_dev,
-                                                                  z_wordmajor_dev, ck, part);
-        na_final_kernel<<<1, wl::kThreads, 0, st>>>(ck, part, K, (double)V * b, out_dev);
+                                                                  z_wordmajor_dev, ck, part, wtok);
+        na_final_kernel<<<1, wl::kThreads, 0, st>>>(ck, part, wtok, K, N, (double)V * b, out_dev);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return na_fail(WARPLDA_ECUDA, std::string("warplda_loglik_noalloc: ") + cudaGetErrorString(e));
