@@ -227,45 +227,135 @@ def heldout_ll(theta, hptr, hwords, cw, ck, beta, bbar):
     return tot / max(n, 1)
 
 
-def learned_curve(gpu, c, wl, name, seed, corpus_seed, n_req, sweeps):
-    """Held-out log-likelihood (document completion) after S fold-in sweeps,
-    plain vs learned, and the sweeps each needs to come within 0.5% of plain
-    fold-in's value at the largest S."""
+def theta_entropy(gpu, c, wl) -> float:
+    """Mean entropy (nats) of the encoder's training targets -- theta of
+    Eq. 4 from the context's current z, one per document: the floor of the
+    encoder's cross-entropy loss (loss = entropy + KL)."""
+    z, _ = gpu.counts(want_ck=False)
+    D, K, a = c.D, wl.K, float(wl.alpha)
+    L = np.diff(c.doc_ptr).astype(np.float64)
+    doc = np.repeat(np.arange(D, dtype=np.int64), np.diff(c.doc_ptr))
+    u, cnt = np.unique(doc * K + z, return_counts=True)
+    ud = u // K
+    den = L + K * a
+    th = (cnt + a) / den[ud]
+    H = np.zeros(D)
+    np.add.at(H, ud, -th * np.log(th))
+    th0 = a / den
+    H += (K - np.bincount(ud, minlength=D)) * (-th0 * np.log(th0))
+    return float(H[L > 0].mean())
+
+
+def foldin_objective(z, optr, owords, cw, ck, K, alpha, beta, bbar) -> float:
+    """Mean per token of log p(w, z | frozen model) of folded-in documents:
+    the Dirichlet-multinomial term of each document's counts (alpha) plus
+    log phi_hat[z, w] of Eq. 4 -- the target the fold-in chain samples
+    (Eq. 5 with the word side frozen), which rises as the chain converges."""
+    from scipy.special import gammaln
+    L = np.diff(optr)
+    D, N = len(L), int(optr[-1])
+    doc = np.repeat(np.arange(D, dtype=np.int64), L)
+    z = np.asarray(z[:N], dtype=np.int64)
+    _, cnt = np.unique(doc * K + z, return_counts=True)
+    a, abar = float(alpha), float(K) * float(alpha)
+    td = float(np.sum(gammaln(abar) - gammaln(abar + L.astype(np.float64))))
+    td += float(np.sum(gammaln(a + cnt) - gammaln(a)))
+    w = np.asarray(owords[:N], dtype=np.int64)
+    tw = float(np.sum(np.log((cw[w, z].astype(np.float64) + beta) / (ck[z].astype(np.float64) + bbar))))
+    return (td + tw) / max(N, 1)
+
+
+def signal_bounds(c, wl, name, corpus_seed, rq, doc_offset):
+    """Held-out log-likelihood per token (odd positions of the requests) of
+    two reference predictors: the unigram model of the training corpus, and
+    the generator itself -- its true topic rows, with each document's topic
+    mixture predicted by the Polya urn of its true even-position topics
+    (the generator's own sequential law): the ceiling of any topic model."""
     from paper_1510_08628_gb300 import corpus
-    rq = corpus.requests(name, seed=corpus_seed, n=n_req, doc_offset=c.D + 700_000)
+    wlw = corpus.WORKLOADS[name]
+    out = {}
+    wc = np.bincount(c.doc_word, minlength=c.V).astype(np.float64)
+    pw = (wc + wl.beta) / (c.N + c.V * wl.beta)
+    ho = np.concatenate([rq.doc_word[rq.doc_ptr[d] + 1: rq.doc_ptr[d + 1]: 2] for d in range(rq.D)])
+    out["unigram"] = float(np.log(pw[ho]).mean())
+    if wlw.K_true * wlw.V <= 50_000_000:
+        tm = corpus.TopicModel(wlw.V, wlw.K_true, wlw.zipf_s, wlw.conc_c, corpus_seed, keep_phi=True)
+        r2 = corpus.generate_docs(tm, np.diff(rq.doc_ptr), wlw.doc_alpha, corpus_seed, doc_offset,
+                                  keep_z=True)
+        phi = tm.phi.reshape(wlw.K_true, wlw.V)
+        tot, n = 0.0, 0
+        for d in range(rq.D):
+            w = r2.doc_word[r2.doc_ptr[d]: r2.doc_ptr[d + 1]]
+            tz = r2.true_z[r2.doc_ptr[d]: r2.doc_ptr[d + 1]]
+            if len(w) < 2:
+                continue
+            post = (np.bincount(tz[0::2], minlength=wlw.K_true) + wlw.doc_alpha) / (
+                len(tz[0::2]) + wlw.K_true * wlw.doc_alpha)
+            tot += float(np.log(post @ phi[:, w[1::2]]).sum())
+            n += len(w[1::2])
+        out["true_model_ceiling"] = tot / max(n, 1)
+    return out
+
+
+def learned_curve(gpu, c, wl, name, seed, corpus_seed, n_req, sweeps):
+    """Fold-in of the requests' even positions, plain vs learned proposal,
+    after S sweeps: held-out log-likelihood of the odd positions (document
+    completion) and the fold-in objective (the chain's target); for each,
+    the sweeps each proposal needs to come within 0.5% of plain fold-in's
+    value at the largest S."""
+    from paper_1510_08628_gb300 import corpus
+    off = c.D + 700_000
+    rq = corpus.requests(name, seed=corpus_seed, n=n_req, doc_offset=off)
     optr, owords, hptr, hwords = heldout_split(rq)
     cw = gpu.word_counts()
     _, ck = gpu.counts(want_z=False)
     bbar = float(np.float32(c.V) * np.float32(wl.beta))
     curve = {"plain": {}, "learned": {}}
+    obj = {"plain": {}, "learned": {}}
     for S in sweeps:
         for kind in ("plain", "learned"):
-            th, _ = gpu.foldin(optr, owords, sweeps=S, seed=seed + 29, z=False,
+            th, z = gpu.foldin(optr, owords, sweeps=S, seed=seed + 29, z=True,
                                learned=(kind == "learned"))
             curve[kind][S] = heldout_ll(th, hptr, hwords, cw, ck, wl.beta, bbar)
-    target = curve["plain"][sweeps[-1]]
-    tol = 0.005 * abs(target)
-    need = {k: next((S for S in sweeps if curve[k][S] >= target - tol), None) for k in curve}
+            obj[kind][S] = foldin_objective(z, optr, owords, cw, ck, wl.K, wl.alpha, wl.beta, bbar)
+
+    def need(cv):
+        target = cv["plain"][sweeps[-1]]
+        tol = 0.005 * abs(target)
+        return {k: next((S for S in sweeps if cv[k][S] >= target - tol), None) for k in cv}
+
     return {"docs": rq.D, "split": "even positions folded in, odd held out",
             "ll_per_token": {k: {str(S): v for S, v in curve[k].items()} for k in curve},
             "target": "plain fold-in after %d sweeps, within 0.5%%" % sweeps[-1],
-            "sweeps_to_target": need}
+            "sweeps_to_target": need(curve),
+            "objective_per_token": {k: {str(S): v for S, v in obj[k].items()} for k in obj},
+            "sweeps_to_target_objective": need(obj),
+            "signal": signal_bounds(c, wl, name, corpus_seed, rq, off)}
 
 
 def learned_bench(gpu, c, wl, args):
     """The learned document proposal for fold-in: encoder training on the
-    corpus's own (document, theta) pairs, then held-out log-likelihood after
-    S fold-in sweeps, plain vs learned, and fold-in throughput; the same
-    curve on the tiny workload (16 strongly separated topics), where the
-    generator leaves more topic signal in the words."""
+    corpus's own (document, theta) pairs (loss beside its entropy floor),
+    then held-out log-likelihood and the fold-in objective after S fold-in
+    sweeps, plain vs learned, serving at equal load with the sweeps each
+    needs, and fold-in throughput; the same on the tiny workload (16
+    strongly separated topics)."""
     from paper_1510_08628_gb300 import corpus
     from paper_1510_08628_gb300.warplda import WarpLDA
+    floor = theta_entropy(gpu, c, wl)
     gpu.encoder_init(log2_features=16, hidden=512, batch_rows=256, seed=args.seed)
     t = time.perf_counter()
-    losses = gpu.encoder_train(epochs=args.encoder_epochs, lr=1e-3, seed=args.seed)
+    losses = gpu.encoder_train(epochs=args.encoder_epochs, lr=args.encoder_lr, seed=args.seed)
     train_s = time.perf_counter() - t
     heldout = learned_curve(gpu, c, wl, args.workload, args.seed, args.corpus_seed, 1000,
                             [1, 2, 3, 4, 6, 8, 12, 16, 24, 30])
+    need = heldout["sweeps_to_target_objective"]
+    # the offered load of the main serving comparison (half the plain
+    # fold-in's throughput, capped)
+    rate = min(0.5 * getattr(args, "_plain_docs_per_s", 200_000.0), 100_000.0)
+    heldout["serving_at_objective_target"] = [
+        serving_bench(gpu, c, wl, args, kind == "learned", rate, sweeps=need[kind] or args.foldin_sweeps)
+        for kind in ("plain", "learned")]
     ct, wt = corpus.generate("tiny", seed=1)
     gt = WarpLDA(ct.doc_ptr, ct.doc_word, ct.V, wt.K, wt.alpha, wt.beta, 2, 7)
     gt.sweep(200)
@@ -290,7 +380,9 @@ def learned_bench(gpu, c, wl, args):
                learned=True)
     wall = time.perf_counter() - t
     return {"encoder": {"features": 1 << 16, "hidden": 512, "K": wl.K, "epochs": args.encoder_epochs,
-                        "train_seconds": train_s, "epoch_loss": [float(x) for x in losses],
+                        "lr": args.encoder_lr, "train_seconds": train_s,
+                        "epoch_loss": [float(x) for x in losses],
+                        "theta_target_entropy": floor,
                         "pairs": "the corpus's own documents with theta of Eq. 4 of the current z"},
             "heldout": heldout, "heldout_tiny": tiny,
             "docs_per_s": big.D / wall, "docs": big.D, "sweeps": args.foldin_sweeps,
@@ -476,8 +568,9 @@ def main():
     ap.add_argument("--foldin-sweeps", type=int, default=30)
     ap.add_argument("--model-sweeps", type=int, default=100,
                     help="sweeps the model has when the fold-in measurements start")
-    ap.add_argument("--encoder-epochs", type=int, default=4,
+    ap.add_argument("--encoder-epochs", type=int, default=16,
                     help="epochs of encoder training for the learned fold-in proposal (0: skip)")
+    ap.add_argument("--encoder-lr", type=float, default=3e-3, help="Adam step size of encoder training")
     ap.add_argument("--m-sweep", action="store_true",
                     help="also record log-likelihood against iterations for M = 1, 2, 4 (Fig. 7)")
     ap.add_argument("--tuning", default="",
@@ -627,6 +720,7 @@ def main():
         model = WarpLDA(cf.doc_ptr, cf.doc_word, cf.V, wf.K, wf.alpha, wf.beta, wf.M, seed, stream=stream)
         model.sweep(args.model_sweeps)   # train the model
         foldin = foldin_bench(model, cf, wf, fa, torch, stream)
+        fa._plain_docs_per_s = foldin["docs_per_s"]
         foldin["workload"] = fa.workload
         foldin["model_sweeps"] = args.model_sweeps
         if args.encoder_epochs > 0:

@@ -332,9 +332,12 @@ int warplda_encoder_proposal(warplda_ctx* ctx, int64_t Dn, const int64_t* doc_pt
  * warplda_server_step -- upload the requests admitted since the last step,
  *   then launch one sweep for every admitted, unfinished request (new ones
  *   are initialised first; a request's last sweep writes its theta);
- *   asynchronous.  *active_out (or NULL) = requests advanced.  Requests
- *   submitted while a step runs join the next step.  The previous step's
- *   results must have been polled (else ESTATE).
+ *   asynchronous.  With the learned proposal a new request's encoder
+ *   forward and alias table are made on a second stream while the step's
+ *   sweep runs, and it joins the sweeps from the next step on (its results
+ *   are unchanged).  *active_out (or NULL) = requests advanced or being
+ *   admitted.  Requests submitted while a step runs join the next step.
+ *   The previous step's results must have been polled (else ESTATE).
  * warplda_server_poll -- wait at most timeout_ms for the last step (else
  *   ETIMEDOUT), then hand over the requests it finished: ids[n] and
  *   theta[n*K] (Eq. 4), *n_out = n <= max_results (else EINVAL; max_results

@@ -727,8 +727,9 @@ struct warplda_server {
     uint64_t seed = 0;
     int4* d_info = nullptr;
     int32_t *d_active = nullptr, *d_z = nullptr, *d_prop = nullptr, *d_words = nullptr, *d_counter = nullptr;
-    float *d_fin_theta = nullptr, *d_q = nullptr, *d_prob = nullptr;
-    int32_t *d_fin_slot = nullptr, *d_alias = nullptr;
+    float *d_fin_theta = nullptr, *d_q = nullptr;
+    int32_t* d_fin_slot = nullptr;
+    int2* d_atab = nullptr;         // learned proposal: each slot's alias table
     int32_t* d_staged = nullptr;   // words of requests admitted since the last step
     int4* d_req = nullptr;          // their {slot, pool offset, L, id}
     int32_t* d_src = nullptr;       // their offsets in the staged words
@@ -738,13 +739,18 @@ struct warplda_server {
     int32_t* h_stage = nullptr;     // pinned upload staging: words, then requests, sources, active list
     int64_t h_stage_cap = 0;
     // learned proposal: admission scratch for up to nslots new requests
-    int32_t *d_aoff = nullptr, *d_aids = nullptr, *d_aslots = nullptr, *d_astack = nullptr;
-    float *d_aq = nullptr, *d_aprob = nullptr;
-    int32_t* d_aalias = nullptr;
+    float* d_aq = nullptr;
+    int2* d_aatab = nullptr;
     int n_fin_staged = 0;
     cudaEvent_t tick = nullptr;
+    // learned proposal: the admission work (encoder, alias tables, rows) of
+    // a step runs on a second stream while the step's sweep runs; its
+    // requests join the next step
+    cudaStream_t side = nullptr;
+    cudaEvent_t uploaded = nullptr, admitted = nullptr;
     struct Slot {
         bool used = false;
+        bool ready = false;     // proposal rows in place: the slot joins the sweeps
         int64_t id = 0;
         int32_t off = 0, L = 0, done = 0;
     };
@@ -804,6 +810,9 @@ void server_free(warplda_server* s) {
     if (s->h_fin_slot) cudaFreeHost(s->h_fin_slot);
     if (s->h_stage) cudaFreeHost(s->h_stage);
     if (s->tick) cudaEventDestroy(s->tick);
+    if (s->uploaded) cudaEventDestroy(s->uploaded);
+    if (s->admitted) cudaEventDestroy(s->admitted);
+    if (s->side) cudaStreamDestroy(s->side);
 }
 
 FoldArgs server_args(warplda_server* s) {
@@ -881,16 +890,24 @@ int server_admit(warplda_server* s, const std::vector<int32_t>& active, int64_t*
         WL_CU(launch_serve_admit(d, reinterpret_cast<const int4*>(d + o_req), d + o_src, n, s->nslots, s->pool_tokens,
                                  s->d_words, s->d_info, c->st), "admit requests");
     if (n > 0 && s->proposal == WARPLDA_PROPOSAL_LEARNED) {
+        // on the side stream, once the upload is done; the caller makes the
+        // main stream wait for `admitted` after the step's sweep is queued
         const int K = c->K;
         auto& e = c->enc;
-        for (int b0 = 0; b0 < n; b0 += e.B) {
+        WL_CU(cudaEventRecord(s->uploaded, c->st), "record upload");
+        WL_CU(cudaStreamWaitEvent(s->side, s->uploaded, 0), "wait upload");
+        cudaStream_t main_st = c->st;
+        c->st = s->side;   // enc_forward queues on the context's stream
+        for (int b0 = 0; b0 < n && !rc; b0 += e.B) {
             EncBatch b{d + o_ids + b0, d + o_off, d, std::min(e.B, n - b0)};
-            if ((rc = enc_forward(c, b, s->d_aq + (int64_t)b0 * K, false, nullptr))) return rc;
+            rc = enc_forward(c, b, s->d_aq + (int64_t)b0 * K, false, nullptr);
         }
-        WL_CU(launch_enc_alias(s->d_aq, n, K, s->d_aprob, s->d_aalias, s->d_astack, c->st), "alias tables");
-        WL_CU(launch_serve_rows(s->d_aq, d + o_sl, n, K, s->nslots, s->d_q, c->st), "proposal rows");
-        WL_CU(launch_serve_rows(s->d_aprob, d + o_sl, n, K, s->nslots, s->d_prob, c->st), "alias rows");
-        WL_CU(launch_serve_rows(s->d_aalias, d + o_sl, n, K, s->nslots, s->d_alias, c->st), "alias rows");
+        c->st = main_st;
+        if (rc) return rc;
+        WL_CU(launch_enc_alias(s->d_aq, n, K, s->d_aatab, s->side), "alias tables");
+        WL_CU(launch_serve_rows(s->d_aq, d + o_sl, n, K, s->nslots, s->d_q, s->side), "proposal rows");
+        WL_CU(launch_serve_rows(s->d_aatab, d + o_sl, n, 2 * K, s->nslots, s->d_atab, s->side), "alias rows");
+        WL_CU(cudaEventRecord(s->admitted, s->side), "record admission");
     }
     s->new_words.clear();
     s->new_src.clear();
@@ -1594,25 +1611,23 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
     if (proposal == WARPLDA_PROPOSAL_LEARNED && Dn > 0) {
         // the encoder's proposal rows and their alias tables
         HostDocs hd;
-        float *q, *prob;
-        int32_t *alias, *stack, *ident;
+        float* q;
+        int2* atab;
+        int32_t* ident;
         std::vector<int32_t> idv((size_t)Dn);
         for (int64_t d = 0; d < Dn; ++d) idv[d] = (int32_t)d;
         WL_CU(buf.get(&ident, Dn), "alloc ids");
         WL_CU(buf.get(&q, Dn * (int64_t)K), "alloc proposals");
-        WL_CU(buf.get(&prob, Dn * (int64_t)K), "alloc alias tables");
-        WL_CU(buf.get(&alias, Dn * (int64_t)K), "alloc alias tables");
-        WL_CU(buf.get(&stack, Dn * (int64_t)K), "alloc alias scratch");
+        WL_CU(buf.get(&atab, Dn * (int64_t)K), "alloc alias tables");
         WL_CU(cudaMemcpyAsync(ident, idv.data(), (size_t)Dn * 4, cudaMemcpyHostToDevice, c->st), "upload ids");
         hd.off = d_off;
         hd.words = d_words;
         hd.ids = ident;
         int rc2 = enc_proposal_dev(c, Dn, hd, q);   // synchronises
         if (rc2) return rc2;
-        WL_CU(launch_enc_alias(q, Dn, K, prob, alias, stack, c->st), "alias tables");
+        WL_CU(launch_enc_alias(q, Dn, K, atab, c->st), "alias tables");
         f.q = q;
-        f.aprob = prob;
-        f.alias = alias;
+        f.atab = atab;
     }
     const int tab_words = foldin_table_words(K, (int)Lmax);
     const int per_sm = foldin_blocks_per_sm(K, M, tab_words);
@@ -1889,16 +1904,19 @@ int warplda_server_create(warplda_ctx* c, int32_t slots, int64_t pool_tokens, in
         (rc = salloc(s, &s->d_req, slots)) || (rc = salloc(s, &s->d_src, slots)))
         return bail(rc);
     if (proposal == WARPLDA_PROPOSAL_LEARNED &&
-        ((rc = salloc(s, &s->d_q, (int64_t)slots * K)) || (rc = salloc(s, &s->d_prob, (int64_t)slots * K)) ||
-         (rc = salloc(s, &s->d_alias, (int64_t)slots * K)) || (rc = salloc(s, &s->d_aq, (int64_t)slots * K)) ||
-         (rc = salloc(s, &s->d_aprob, (int64_t)slots * K)) || (rc = salloc(s, &s->d_aalias, (int64_t)slots * K)) ||
-         (rc = salloc(s, &s->d_astack, (int64_t)slots * K))))
+        ((rc = salloc(s, &s->d_q, (int64_t)slots * K)) || (rc = salloc(s, &s->d_atab, (int64_t)slots * K)) ||
+         (rc = salloc(s, &s->d_aq, (int64_t)slots * K)) || (rc = salloc(s, &s->d_aatab, (int64_t)slots * K))))
         return bail(rc);
     if (host_malloc((void**)&s->h_theta, (size_t)slots * K * 4) != cudaSuccess ||
         host_malloc((void**)&s->h_fin_slot, (size_t)slots * 4) != cudaSuccess)
         return bail(fail(WARPLDA_ENOMEM, "pinned staging"));
     if (cudaEventCreateWithFlags(&s->tick, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(WARPLDA_ECUDA, "event"));
+    if (proposal == WARPLDA_PROPOSAL_LEARNED &&
+        (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+         cudaEventCreateWithFlags(&s->uploaded, cudaEventDisableTiming) != cudaSuccess ||
+         cudaEventCreateWithFlags(&s->admitted, cudaEventDisableTiming) != cudaSuccess))
+        return bail(fail(WARPLDA_ECUDA, "side stream"));
     s->slots.resize(slots);
     for (int i = slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     s->free_ranges[0] = pool_tokens;
@@ -1942,19 +1960,39 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     if (s->n_fin_staged > 0) return fail(WARPLDA_ESTATE, "poll the previous step's results first");
     // the pinned staging is reused: the previous step's upload must be done
     WL_CU(cudaEventSynchronize(s->tick), "previous step");
+    // the previous step (and its admission work) is complete: its learned
+    // requests have their proposal rows
+    const bool learned = s->proposal == WARPLDA_PROPOSAL_LEARNED;
+    for (auto& S : s->slots)
+        if (S.used) S.ready = true;
+    // requests staged since the last step: with the plain proposal they join
+    // this step's sweep; with the learned one the next step's
+    for (const int4& r : s->new_req) s->slots[r.x].ready = !learned;
     std::vector<int32_t> active;
-    int nfin = 0;
+    int nfin = 0, pending = 0;
     for (int i = 0; i < s->nslots; ++i) {
         const auto& S = s->slots[i];
         if (!S.used || S.done >= s->sweeps) continue;
+        if (!S.ready) {
+            ++pending;
+            continue;
+        }
         active.push_back(i);
         if (S.done + 1 >= s->sweeps) ++nfin;
     }
-    if (active_out) *active_out = (int32_t)active.size();
-    if (active.empty()) return WARPLDA_OK;
+    if (active_out) *active_out = (int32_t)(active.size() + pending);
+    if (active.empty() && pending == 0) return WARPLDA_OK;
     int64_t act_off = 0;
+    const bool admit_learned = learned && !s->new_req.empty();
     int rc = server_admit(s, active, &act_off);
     if (rc) return rc;
+    if (active.empty()) {
+        // only fresh learned requests: their admission is the step
+        if (admit_learned) WL_CU(cudaStreamWaitEvent(c->st, s->admitted, 0), "wait admission");
+        s->n_fin_staged = 0;
+        WL_CU(cudaEventRecord(s->tick, c->st), "record tick");
+        return WARPLDA_OK;
+    }
     WL_CU(cudaMemsetAsync(s->d_counter, 0, 8, c->st), "reset counters");
     FoldArgs f = server_args(s);
     ServeSlots sl{};
@@ -1970,10 +2008,10 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     sl.fin_slot = s->d_fin_slot;
     sl.fin_count = s->d_counter + 1;
     sl.q = s->d_q;
-    sl.prob = s->d_prob;
-    sl.alias = s->d_alias;
+    sl.atab = s->d_atab;
     const int grid = (int)std::min<int64_t>(s->grid, ((int64_t)active.size() + kWarps - 1) / kWarps + 1);
     WL_CU(launch_serve(f, sl, s->tab_words, grid, c->st), "serve");
+    if (admit_learned) WL_CU(cudaStreamWaitEvent(c->st, s->admitted, 0), "wait admission");
     for (int32_t i : active) s->slots[i].done += 1;
     if (nfin > 0) {
         WL_CU(cudaMemcpyAsync(s->h_fin_slot, s->d_fin_slot, (size_t)nfin * 4, cudaMemcpyDeviceToHost, c->st), "copy finished");

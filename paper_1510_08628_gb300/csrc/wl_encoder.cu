@@ -51,14 +51,23 @@ __global__ void enc_docword_kernel(const int32_t* __restrict__ perm, const int32
 }
 
 // Layer 1 for a batch: row r of the batch is document docs[r] (r < nreal),
-// else padding (h = 0).  Each thread owns hidden units 4*tid .. 4*tid + 3 of
-// each 4*kEncThreads-wide slice.
-__global__ void __launch_bounds__(kEncThreads) enc_l1_fwd_kernel(EncBatch b, const uint16_t* __restrict__ W1b,
-                                                                 const float* __restrict__ b1, int H, int log2F,
-                                                                 float* __restrict__ h_pre, uint16_t* __restrict__ hb,
-                                                                 uint16_t* __restrict__ hbT) {
+// else padding (h = 0).  One block per row: the document's tokens are dealt
+// to the block's warps (token t to warp t mod 8), each warp reading whole
+// W1 rows (a lane's 8 columns of each 256-column slice, one 16-byte load)
+// with four rows in flight; the warps' partial sums are added in warp
+// order.  The order of every sum depends only on the document, not on the
+// batch it is in.
+constexpr int kL1Threads = 256;
+constexpr int kL1Warps = kL1Threads / 32;
+
+__global__ void __launch_bounds__(kL1Threads) enc_l1_fwd_kernel(EncBatch b, const uint16_t* __restrict__ W1b,
+                                                                const float* __restrict__ b1, int H, int log2F,
+                                                                float* __restrict__ h_pre, uint16_t* __restrict__ hb,
+                                                                uint16_t* __restrict__ hbT) {
+    __shared__ float part[kL1Warps][256];
     const int r = blockIdx.x;
     const int B = gridDim.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int d0 = 0, d1 = 0;
     if (r < b.nreal) {
         const int d = b.docs[r];
@@ -66,26 +75,57 @@ __global__ void __launch_bounds__(kEncThreads) enc_l1_fwd_kernel(EncBatch b, con
         d1 = b.doc_off[d + 1];
     }
     const float invL = d1 > d0 ? 1.0f / (float)(d1 - d0) : 0.0f;
-    for (int j0 = 4 * threadIdx.x; j0 < H; j0 += 4 * kEncThreads) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        for (int t = d0; t < d1; ++t) {
-            const int f = enc_feature(b.words[t], log2F);
-            const uint2 w = *reinterpret_cast<const uint2*>(W1b + (int64_t)f * H + j0);
-            a0 += __uint_as_float(w.x << 16);
-            a1 += __uint_as_float(w.x & 0xFFFF0000u);
-            a2 += __uint_as_float(w.y << 16);
-            a3 += __uint_as_float(w.y & 0xFFFF0000u);
-        }
-        const float acc[4] = {a0, a1, a2, a3};
+    for (int c0 = 0; c0 < H; c0 += 256) {
+        float acc[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int j = j0 + u;
-            const float hp = r < b.nreal ? b1[j] + acc[u] * invL : 0.0f;
+        for (int u = 0; u < 8; ++u) acc[u] = 0.0f;
+        // a slice may be half used (H a multiple of 128): lanes past H idle
+        const bool cols = c0 + lane * 8 < H;
+        const uint16_t* Wc = W1b + c0 + (cols ? lane * 8 : 0);
+        int t = cols ? d0 + w : d1;
+        for (; t + 3 * kL1Warps < d1; t += 4 * kL1Warps) {
+            uint4 x[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int f = enc_feature(b.words[t + v * kL1Warps], log2F);
+                x[v] = *reinterpret_cast<const uint4*>(Wc + (int64_t)f * H);
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const uint32_t e[4] = {x[v].x, x[v].y, x[v].z, x[v].w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    acc[2 * u] += __uint_as_float(e[u] << 16);
+                    acc[2 * u + 1] += __uint_as_float(e[u] & 0xFFFF0000u);
+                }
+            }
+        }
+        for (; t < d1; t += kL1Warps) {
+            const int f = enc_feature(b.words[t], log2F);
+            const uint4 x = *reinterpret_cast<const uint4*>(Wc + (int64_t)f * H);
+            const uint32_t e[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                acc[2 * u] += __uint_as_float(e[u] << 16);
+                acc[2 * u + 1] += __uint_as_float(e[u] & 0xFFFF0000u);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) part[w][lane * 8 + u] = acc[u];
+        __syncthreads();
+        if (c0 + (int)threadIdx.x < H) {
+            const int jj = threadIdx.x;   // one column of the slice per thread
+            float sum = 0.0f;
+#pragma unroll
+            for (int v = 0; v < kL1Warps; ++v) sum += part[v][jj];
+            const int j = c0 + jj;
+            const float hp = r < b.nreal ? b1[j] + sum * invL : 0.0f;
             h_pre[(int64_t)r * H + j] = hp;
             const uint16_t hv = to_bf16(hp > 0.0f ? hp : 0.0f);
             hb[(int64_t)r * H + j] = hv;
             hbT[(int64_t)j * B + r] = hv;
         }
+        __syncthreads();
     }
 }
 
@@ -226,38 +266,91 @@ __global__ void enc_to_bf16_kernel(const float* __restrict__ x, int64_t n, uint1
 }
 
 // Walker alias tables of the proposal rows q[d, 0..K) (Vose's construction,
-// in the oracle's order and FP32 operations): one thread per document; the
-// two stacks share one scratch row (small from the front, large from the back).
-__global__ void enc_alias_kernel(const float* __restrict__ q, int64_t Dn, int K, float* __restrict__ prob,
-                                 int32_t* __restrict__ alias, int32_t* __restrict__ stack) {
-    const int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (d >= Dn) return;
-    const float* qd = q + d * K;
-    float* p = prob + d * K;
-    int32_t* al = alias + d * K;
-    int32_t* stk = stack + d * K;
-    int ns = 0, nl = 0;
+// in the oracle's order and FP32 operations): one block per document, its
+// scaled row p, the two stacks (small from the front, large from the back)
+// and the aliases in shared memory; out: {bits of the cut p, alias} per
+// topic, so that a draw reads one 8-byte entry.  The block scales the row and fills the stacks in
+// parallel -- a block scan gives each topic its place, in increasing topic
+// order as the serial construction pushes them -- then one thread pairs
+// them, a chain of dependent steps that only shared-memory latency keeps
+// short.
+constexpr int kAliasThreads = 256;
+
+__global__ void __launch_bounds__(kAliasThreads) enc_alias_kernel(const float* __restrict__ q, int64_t Dn, int K,
+                                                                  int2* __restrict__ atab) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    float* p = reinterpret_cast<float*>(sm);
+    int32_t* stk = reinterpret_cast<int32_t*>(p + K);
+    int32_t* al = stk + K;
+    __shared__ int warp_s[kAliasThreads / 32], warp_l[kAliasThreads / 32];
+    __shared__ int s_ns, s_nl;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const float Kf = (float)K;
-    for (int k = 0; k < K; ++k) {
-        p[k] = __fmul_rn(qd[k], Kf);
-        if (p[k] < 1.0f) stk[ns++] = k; else stk[K - 1 - nl++] = k;
-    }
-    while (ns > 0 && nl > 0) {
-        const int l = stk[--ns];
-        const int g = stk[K - nl--];
-        al[l] = g;
-        p[g] = __fsub_rn(__fadd_rn(p[g], p[l]), 1.0f);
-        if (p[g] < 1.0f) stk[ns++] = g; else stk[K - 1 - nl++] = g;
-    }
-    while (nl > 0) {
-        const int g = stk[K - nl--];
-        p[g] = 1.0f;
-        al[g] = g;
-    }
-    while (ns > 0) {
-        const int l = stk[--ns];
-        p[l] = 1.0f;
-        al[l] = l;
+    for (int64_t d = blockIdx.x; d < Dn; d += gridDim.x) {
+        const float* qd = q + d * K;
+        if (tid == 0) {
+            s_ns = 0;
+            s_nl = 0;
+        }
+        __syncthreads();
+        for (int base = 0; base < K; base += kAliasThreads) {
+            const int k = base + tid;
+            float pk = 0.0f;
+            if (k < K) {
+                pk = __fmul_rn(qd[k], Kf);
+                p[k] = pk;
+            }
+            const bool small = k < K && pk < 1.0f, large = k < K && !(pk < 1.0f);
+            const unsigned bs = __ballot_sync(0xFFFFFFFFu, small), bl = __ballot_sync(0xFFFFFFFFu, large);
+            if (lane == 0) {
+                warp_s[w] = __popc(bs);
+                warp_l[w] = __popc(bl);
+            }
+            __syncthreads();
+            int os = s_ns, ol = s_nl;
+            for (int i = 0; i < w; ++i) {
+                os += warp_s[i];
+                ol += warp_l[i];
+            }
+            const unsigned below = (1u << lane) - 1u;
+            if (small) stk[os + __popc(bs & below)] = k;
+            if (large) stk[K - 1 - (ol + __popc(bl & below))] = k;
+            __syncthreads();
+            if (tid == 0) {
+                int ts = 0, tl = 0;
+                for (int i = 0; i < kAliasThreads / 32; ++i) {
+                    ts += warp_s[i];
+                    tl += warp_l[i];
+                }
+                s_ns += ts;
+                s_nl += tl;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            int ns = s_ns, nl = s_nl;
+            while (ns > 0 && nl > 0) {
+                const int l = stk[--ns];
+                const int g = stk[K - nl--];
+                al[l] = g;
+                p[g] = __fsub_rn(__fadd_rn(p[g], p[l]), 1.0f);
+                if (p[g] < 1.0f) stk[ns++] = g; else stk[K - 1 - nl++] = g;
+            }
+            while (nl > 0) {
+                const int g = stk[K - nl--];
+                p[g] = 1.0f;
+                al[g] = g;
+            }
+            while (ns > 0) {
+                const int l = stk[--ns];
+                p[l] = 1.0f;
+                al[l] = l;
+            }
+        }
+        __syncthreads();
+        int2* td = atab + d * K;
+        for (int k = tid; k < K; k += kAliasThreads) td[k] = make_int2(__float_as_int(p[k]), al[k]);
+        __syncthreads();
     }
 }
 
@@ -274,7 +367,8 @@ cudaError_t launch_enc_docword(const int32_t* perm, const int32_t* word_off, int
 cudaError_t launch_enc_l1_fwd(const EncBatch& b, int B, const uint16_t* W1b, const float* b1, int H, int log2F,
                               float* h_pre, uint16_t* hb, uint16_t* hbT, cudaStream_t st) {
     if (const cudaError_t g_ = launch_gate()) return g_;
-    enc_l1_fwd_kernel<<<B, kEncThreads, 0, st>>>(b, W1b, b1, H, log2F, h_pre, hb, hbT);
+    if (H % 128 != 0) return cudaErrorInvalidValue;
+    enc_l1_fwd_kernel<<<B, kL1Threads, 0, st>>>(b, W1b, b1, H, log2F, h_pre, hb, hbT);
     return cudaGetLastError();
 }
 
@@ -316,11 +410,14 @@ cudaError_t launch_enc_to_bf16(const float* x, int64_t n, uint16_t* y, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_enc_alias(const float* q, int64_t Dn, int K, float* prob, int32_t* alias, int32_t* stack,
-                             cudaStream_t st) {
+cudaError_t launch_enc_alias(const float* q, int64_t Dn, int K, int2* atab, cudaStream_t st) {
     if (const cudaError_t g_ = launch_gate()) return g_;
     if (Dn <= 0) return cudaSuccess;
-    enc_alias_kernel<<<(int)((Dn + 63) / 64), 64, 0, st>>>(q, Dn, K, prob, alias, stack);
+    const int smem = K * 12;
+    cudaError_t e = cudaFuncSetAttribute(enc_alias_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<int64_t>(Dn, 152 * 8);
+    enc_alias_kernel<<<grid, kAliasThreads, smem, st>>>(q, Dn, K, atab);
     return cudaGetLastError();
 }
 

@@ -96,8 +96,7 @@ struct FoldDoc {
     int L;
     uint32_t id;
     const float* q;
-    const float* prob;
-    const int32_t* alias;
+    const int2* atab;
 };
 
 // The warp's count table of the document's current z (dense, or a hash of
@@ -174,7 +173,8 @@ __device__ void fold_sweep(const FoldArgs& f, const FoldDoc& doc, int it, uint32
             const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldDoc, (uint32_t)(i + 1), doc.id, f.rk);
             if (kLearned) {
                 const int k = (int)dice(r.z, (uint32_t)K);
-                prop[j * M + i] = u24(r.y) < __ldg(doc.prob + k) ? k : (int)min((uint32_t)__ldg(doc.alias + k), km);
+                const int2 e = __ldg(doc.atab + k);
+                prop[j * M + i] = u24(r.y) < __int_as_float(e.x) ? k : (int)min((uint32_t)e.y, km);
             } else {
                 prop[j * M + i] = coin(r.y, Lf, LG) ? z[dice(r.z, (uint32_t)L)] : (int)dice(r.z, (uint32_t)K);
             }
@@ -195,6 +195,7 @@ __device__ void fold_sweep(const FoldArgs& f, const FoldDoc& doc, int it, uint32
         int s = min((uint32_t)z[j], km);
         int cs = __ldg(row + s);
         float ks = __ldg(f.ckb + s);
+        float qs = kLearned ? __ldg(doc.q + s) : 0.0f;
         uint32_t r1[M], r2[M];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
@@ -205,16 +206,17 @@ __device__ void fold_sweep(const FoldArgs& f, const FoldDoc& doc, int it, uint32
             if (t != s) {
                 const int ct = __ldg(row + t);
                 const float kt = __ldg(f.ckb + t);
+                const float qt = kLearned ? __ldg(doc.q + t) : 0.0f;
                 bool acc;
                 if (kLearned) {
                     const float cds = __int2float_rn(fold_count(tab, cap, kDense, s));
                     const float cdt = __int2float_rn(fold_count(tab, cap, kDense, t));
                     const float num = __fmul_rn(__fmul_rn(__fmul_rn(__fadd_rn(cdt, f.alpha),
                                                                     __fadd_rn(__int2float_rn(ct), f.beta)),
-                                                          ks), __ldg(doc.q + s));
+                                                          ks), qs);
                     const float den = __fmul_rn(__fmul_rn(__fmul_rn(__fadd_rn(cds, f.alpha),
                                                                     __fadd_rn(__int2float_rn(cs), f.beta)),
-                                                          kt), __ldg(doc.q + t));
+                                                          kt), qt);
                     acc = __fmul_rn(u24(r.x), den) < num;
                 } else {
                     acc = accept(r.x, cs, ct, f.beta, ks, kt);
@@ -223,6 +225,7 @@ __device__ void fold_sweep(const FoldArgs& f, const FoldDoc& doc, int it, uint32
                     s = t;
                     cs = ct;
                     ks = kt;
+                    qs = qt;
                 }
             }
         }
@@ -271,8 +274,7 @@ __global__ void __launch_bounds__(kThreads) foldin_kernel(FoldArgs f, int tab_wo
         doc.L = L;
         doc.id = (uint32_t)f.ids[d];
         doc.q = kLearned ? f.q + (int64_t)d * K : nullptr;
-        doc.prob = kLearned ? f.aprob + (int64_t)d * K : nullptr;
-        doc.alias = kLearned ? f.alias + (int64_t)d * K : nullptr;
+        doc.atab = kLearned ? f.atab + (int64_t)d * K : nullptr;
         const uint32_t cap = kDense ? 0u : pow2_above((uint32_t)min(2 * max(L, 1), K));
         const int words = kDense ? tab_words : (int)cap;
         fold_init<M>(f, doc, lane);
@@ -309,8 +311,7 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(FoldArgs f, ServeSlots 
         doc.L = L;
         doc.id = (uint32_t)info.w;
         doc.q = kLearned ? sl.q + (int64_t)s * K : nullptr;
-        doc.prob = kLearned ? sl.prob + (int64_t)s * K : nullptr;
-        doc.alias = kLearned ? sl.alias + (int64_t)s * K : nullptr;
+        doc.atab = kLearned ? sl.atab + (int64_t)s * K : nullptr;
         const uint32_t cap = kDense ? 0u : pow2_above((uint32_t)min(2 * max(L, 1), K));
         const int words = kDense ? tab_words : (int)cap;
         const int done = info.z;

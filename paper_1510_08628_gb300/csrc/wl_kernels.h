@@ -84,8 +84,7 @@ struct FoldArgs {
     const float* ckb;        // [K] frozen (float)c_k + beta_bar
     float* theta;            // [Dn * K] or null
     const float* q;          // learned proposal [Dn * K] or null (plain fold-in)
-    const float* aprob;      // its alias tables [Dn * K]
-    const int32_t* alias;
+    const int2* atab;        // its alias tables [Dn * K]: {bits of the FP32 cut, alias}
     int32_t* counter;        // work counter (zero on entry)
     int32_t* fault;          // index-check record
     int Dn, K, M, V, sweeps, Lmax;
@@ -118,8 +117,7 @@ struct ServeSlots {
     int32_t* fin_slot;       // their slots
     int32_t* fin_count;      // rows written (zero on entry)
     const float* q;
-    const float* prob;
-    const int32_t* alias;
+    const int2* atab;        // {bits of the FP32 cut, alias} per topic
 };
 cudaError_t launch_serve_admit(const int32_t* staged, const int4* req, const int32_t* src, int n, int nslots,
                                int64_t pool_tokens, int32_t* pool_words, int4* info, cudaStream_t st);
@@ -158,7 +156,7 @@ cudaError_t launch_enc_adam(float* w, float* m, float* v, const float* g, int64_
 cudaError_t launch_enc_w2_copies(const float* W2t, int Kp, int H, uint16_t* W2tb, uint16_t* W2nb,
                                  cudaStream_t st);
 cudaError_t launch_enc_to_bf16(const float* x, int64_t n, uint16_t* y, cudaStream_t st);
-cudaError_t launch_enc_alias(const float* q, int64_t Dn, int K, float* prob, int32_t* alias, int32_t* stack,
+cudaError_t launch_enc_alias(const float* q, int64_t Dn, int K, int2* atab,
                              cudaStream_t st);
 
 // Initialisation, c_k, export, log-likelihood (wl_misc.cu).

@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -332,6 +333,10 @@ class WarpLDA:
         return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(min(n, cap))}
 
     def close(self) -> None:
+        """Destroys the context; its servers (which hold pointers into it)
+        are destroyed first."""
+        for srv in list(getattr(self, "_servers", {}).values()):
+            srv.close()
         if getattr(self, "_h", None):
             load().warplda_destroy(self._h)
             self._h = None
@@ -372,10 +377,15 @@ class Server:
                  sweeps: int, seed: int, learned: bool = False):
         self.K = model.K
         self._model = model
+        if not getattr(model, "_h", None):
+            raise WarpLDAError(ESTATE, "the model context is closed")
         h = ctypes.c_void_p()
         _check(load().warplda_server_create(model._h, slots, pool_tokens, max_doc_tokens, sweeps,
                                             int(seed), 1 if learned else 0, ctypes.byref(h)))
         self._h = h
+        if not hasattr(model, "_servers"):
+            model._servers = weakref.WeakValueDictionary()
+        model._servers[id(self)] = self
         self._slots = slots
 
     def submit(self, rid: int, words) -> bool:
@@ -403,6 +413,9 @@ class Server:
         if getattr(self, "_h", None):
             load().warplda_server_destroy(self._h)
             self._h = None
+            srvs = getattr(getattr(self, "_model", None), "_servers", None)
+            if srvs is not None:
+                srvs.pop(id(self), None)
 
     def __del__(self):
         try:

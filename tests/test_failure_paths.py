@@ -139,10 +139,12 @@ def test_server_create_allocation_failures(gpu, learned):
     assert _sweep_failures("ALLOC", ENOMEM, make) >= 8
     s = make()
     assert s.submit(7, c.doc_word[:50])
-    s.step()
-    s.step()
-    ids, th = s.poll()
-    assert list(ids) == [7] and np.isfinite(th).all()
+    got = []
+    for _ in range(4):   # 2 sweeps; a learned request joins one step after admission
+        s.step()
+        ids, th = s.poll()
+        got += [(int(i), t) for i, t in zip(ids, th)]
+    assert [i for i, _ in got] == [7] and np.isfinite(got[0][1]).all()
     s.close()
 
 
@@ -186,3 +188,25 @@ def test_poll_times_out_while_a_step_runs():
         break
     g.close()
     assert timed_out, "no step outlasted a zero-limit poll"
+
+
+@pytest.mark.gpu
+def test_closing_a_context_closes_its_servers():
+    """A server holds pointers into its model context: closing the context
+    first destroys the servers still open, so nothing touches freed memory."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1510_08628_gb300.warplda import Server, WarpLDA, WarpLDAError
+    c, wl = corpus.generate("tiny", seed=5, D=100)
+    g = WarpLDA(c.doc_ptr, c.doc_word, c.V, 40, wl.alpha, wl.beta, 2, 5)
+    g.sweep(1)
+    s = Server(g, slots=4, pool_tokens=1000, max_doc_tokens=200, sweeps=3, seed=1)
+    assert s.submit(1, c.doc_word[:20])
+    s.step()
+    g.close()
+    assert s._h is None          # destroyed with its context
+    s.close()                    # and closing it again is harmless
+    with pytest.raises(WarpLDAError):
+        Server(g, slots=4, pool_tokens=1000, max_doc_tokens=200, sweeps=3, seed=1)
+
