@@ -45,6 +45,7 @@ def alg_bytes_per_token(kind: str, M: int) -> float:
     return {
         "doc_batch": 4 + 8 * (M + 1),
         "doc_pipe": 4 + 8 * (M + 1),
+        "word_cluster": 8 * (M + 1),
         "word_batch": 8 * (M + 1),
         "word_mega_hist": 4,
         "word_mega_accept": 4 * (M + 1) + 4,
@@ -73,6 +74,7 @@ def measured_peaks() -> tuple[float, str]:
 KERNEL_SOURCES = {
     "doc_batch": ["wl_batch.cu", "wl_common.cuh", "wl_block.cuh"],
     "doc_pipe": ["wl_docpipe.cu", "wl_common.cuh", "wl_block.cuh"],
+    "word_cluster": ["wl_cluster.cu", "wl_common.cuh", "wl_block.cuh"],
     "word_batch": ["wl_batch.cu", "wl_common.cuh", "wl_block.cuh"],
     "word_mega_accept": ["wl_huge.cu", "wl_common.cuh", "wl_block.cuh"],
     "word_mega_draw": ["wl_huge.cu", "wl_common.cuh", "wl_block.cuh"],
@@ -432,7 +434,7 @@ def serving_bench(gpu, c, wl, args, learned: bool, rate: float, n: int = 6000, n
 
 
 TUNING_KEYS = ("batch_max_tokens", "huge_chunk", "region_budget", "doc_warp_max", "word_positioning",
-               "doc_batch_kernel")
+               "doc_batch_kernel", "cluster_max_tokens")
 
 
 def parse_tuning(text: str) -> dict | None:
@@ -576,7 +578,7 @@ def main():
     ap.add_argument("--tuning", default="",
                     help="launch tuning of the sampler as key=value pairs separated by commas "
                          "(batch_max_tokens, huge_chunk, region_budget, doc_warp_max, word_positioning, "
-                         "doc_batch_kernel)")
+                         "doc_batch_kernel, cluster_max_tokens)")
     ap.add_argument("--docs", type=int, default=0,
                     help="use only the first DOCS documents of the workload (small profiling cases)")
     args = ap.parse_args()
@@ -652,7 +654,9 @@ def main():
     peak, peak_kind = measured_peaks()
     tier_tokens = {
         "doc_batch": c.N - info["huge_doc_tokens"] - info["pipe_doc_tokens"],
-        "doc_pipe": info["pipe_doc_tokens"], "word_batch": c.N - info["mega_word_tokens"],
+        "doc_pipe": info["pipe_doc_tokens"],
+        "word_batch": c.N - info["mega_word_tokens"] - info["cluster_word_tokens"],
+        "word_cluster": info["cluster_word_tokens"],
         "word_mega_hist": info["mega_word_tokens"], "word_mega_accept": info["mega_word_tokens"],
         "word_mega_draw": info["mega_word_tokens"], "doc_huge_hist": info["huge_doc_tokens"],
         "doc_huge_accept": info["huge_doc_tokens"], "doc_huge_draw": info["huge_doc_tokens"],

@@ -72,6 +72,15 @@ typedef struct warplda_server warplda_server;
  *                     defaults to 4096 words for them); 1 = the block batch
  *                     kernel; 0 (default) = pipelined with hash count
  *                     tables and 2048 < K <= 16384, else block batch.
+ *   cluster_max_tokens  words longer than a block batch and at most this
+ *                     long are sampled on a thread-block cluster of 1 to 16
+ *                     blocks (their tokens held in the cluster's shared
+ *                     memory, the count rows reduced over distributed shared
+ *                     memory); longer words take the multi-pass tier.  -1:
+ *                     as long as the cluster's shared memory allows; 0
+ *                     (default): no cluster tier (the multi-pass tier is
+ *                     faster on the workloads measured).  K above 16384 has
+ *                     no cluster tier.
  * One field changes the sampler (a different, equally valid chain):
  *   word_positioning  the word proposal's p_A branch (Eq. 6): 0 (default) =
  *                     the j-th smallest post-acceptance topic of the word;
@@ -85,7 +94,8 @@ typedef struct warplda_tuning {
     int32_t doc_warp_max;
     int32_t word_positioning;
     int32_t doc_batch_kernel;
-    int32_t reserved[2];
+    int32_t cluster_max_tokens;
+    int32_t reserved[1];
 } warplda_tuning;
 
 /*
@@ -210,10 +220,11 @@ typedef struct warplda_info {
     int32_t batch_max_tokens;
     int64_t doc_batches, word_batches;
     int64_t huge_docs, huge_doc_tokens;
-    int64_t mega_words, mega_word_tokens;
+    int64_t mega_words, mega_word_tokens;   /* words of the multi-pass tier */
     int64_t device_bytes;             /* device memory held by the context */
     int64_t pipe_doc_tokens;          /* tokens of the pipelined document batches */
-    int32_t reserved[6];
+    int64_t cluster_words, cluster_word_tokens;   /* words sampled on a thread-block cluster */
+    int32_t reserved[2];
 } warplda_info;
 int warplda_get_info(warplda_ctx* ctx, warplda_info* out);
 

@@ -87,12 +87,12 @@ int cuda_fail(cudaError_t e, const char* what) {
 enum KernelClass {
     kcDocWarp, kcDocBatch, kcDocHugeHist, kcDocHugeAccept, kcDocHugeDraw,
     kcWordBatch, kcWordMegaHist, kcWordMegaAccept, kcWordMegaHistPost, kcWordMegaDraw,
-    kcCountCk, kcFinalize, kcZero, kcDocPipe, kcCount
+    kcCountCk, kcFinalize, kcZero, kcDocPipe, kcWordCluster, kcCount
 };
 const char* kClassNames[kcCount] = {
     "doc_warp", "doc_batch", "doc_huge_hist", "doc_huge_accept", "doc_huge_draw",
     "word_batch", "word_mega_hist", "word_mega_accept", "word_mega_hist_post", "word_mega_draw",
-    "count_ck", "finalize_ck", "zero_rows", "doc_pipe"};
+    "count_ck", "finalize_ck", "zero_rows", "doc_pipe", "word_cluster"};
 // topics: packed hash entries hold (topic + 1) << 12 in 32 bits
 constexpr int kMaxTopics = (1 << 20) - 1;
 // tokens of a pipelined document batch (at most 4 * 256 - 3; at most 509
@@ -102,6 +102,8 @@ constexpr int kMaxTopics = (1 << 20) - 1;
 #endif
 constexpr int kPipeTokens = WL_PIPE_TOKENS;
 static_assert(kPipeTokens >= 1 && kPipeTokens <= 4 * kThreads - 3, "pipelined batch size");
+// cluster sizes of the cluster tier: 1, 2, 4, 8, 16 blocks
+constexpr int kClusterClasses = 5;
 // above this K the multi-pass tier's count rows are sparse (global hash)
 constexpr int kDenseRowMaxK = 16384;
 // work counters: 0-3 batches [class][phase], 4 doc warp tier, 5-8 the
@@ -122,6 +124,18 @@ struct Tier {
     std::vector<int32_t> range_off;  // range r = pieces [range_off[r], range_off[r+1])
     std::vector<int32_t> region;     // table offset of each batched segment in its batch
     std::vector<int4> ll_batches;    // log-likelihood batches over all non-chunked segments
+    // long segments sampled on a thread-block cluster (words only); they keep
+    // their rows and pieces above for the log-likelihood, and the multi-pass
+    // sampling passes take the pieces s_chunks / ranges s_range_off of the
+    // other long segments
+    std::vector<int32_t> cluster_list;   // grouped by cluster size: class c holds
+    std::vector<int32_t> cluster_cls;    // cluster_list[cluster_cls[c] .. cluster_cls[c+1])
+    std::vector<int4> s_chunks;
+    std::vector<int32_t> s_range_off;
+    int64_t cluster_tokens = 0, s_row_tokens = 0;
+    int32_t* d_cluster_list = nullptr;
+    int4* d_s_chunks = nullptr;
+    int32_t* d_s_range_off = nullptr;
     int64_t nrows = 0, row_tokens = 0, large_tokens = 0, warp_tokens = 0;
     int4* d_batches[2] = {nullptr, nullptr};
     int32_t* d_warp_list = nullptr;
@@ -155,6 +169,9 @@ struct warplda_ctx {
     bool doc_pipe = true;
     int4* d_pipe_desc = nullptr;
     int grid_pipe = 1;
+    // words sampled on a thread-block cluster: cluster size, tokens per block
+    // (slice capacity), dynamic shared memory per block
+    int cluster_C = 0, cluster_T = 0, cluster_smem = 0;
     bool dense = true;   // 16-bit dense count tables (K <= kDenseMaxK), else hash tables
     int warp_tpl = 16;   // tokens per lane of the document warp tier
     int grid_doc_warp = 1;
@@ -254,7 +271,7 @@ int table_words(int L, int K, bool dense) {
 // paper's table rule.
 void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, int warp_max,
                 const int bmax[2], const int region[2], int chunk, int ranges_target, Tier* t,
-                int segs0 = kSegsMax) {
+                int segs0 = kSegsMax, int64_t cluster_max = 0, int64_t cluster_slice = 1) {
     const int segs_max[2] = {segs0, kSegsMax};
     for (auto& b : t->batches) b.clear();
     t->warp_list.clear();
@@ -262,6 +279,12 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
     t->row_len.clear();
     t->range_off.clear();
     t->ll_batches.clear();
+    t->cluster_list.clear();
+    t->s_chunks.clear();
+    t->s_range_off.clear();
+    t->cluster_tokens = t->s_row_tokens = 0;
+    std::vector<int4> s_longs;   // long segments of the multi-pass sampling passes
+    std::vector<int2> cl_words;  // {tokens, segment} of the cluster tier
     std::vector<int4> longs;   // {row, segment, first position, length}
     t->region.assign((size_t)std::max<int64_t>(S, 1), 0);
     t->nrows = t->row_tokens = t->large_tokens = t->warp_tokens = 0;
@@ -301,6 +324,13 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
             t->row_tokens += L;
             t->row_len.push_back(L);
             longs.push_back(make_int4(row, (int)s, off[s], L));
+            if (cluster_max > 0 && L <= cluster_max) {
+                cl_words.push_back(make_int2(L, (int)s));
+                t->cluster_tokens += L;
+            } else {
+                s_longs.push_back(make_int4(row, (int)s, off[s], L));
+                t->s_row_tokens += L;
+            }
             continue;
         }
         // log-likelihood batches (paper's table rule)
@@ -334,27 +364,49 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
     }
     close((int)S);
     lclose((int)S);
-    if (t->row_tokens > 0) {
-        const int64_t R = std::max<int64_t>(1, std::min<int64_t>(ranges_target, (t->row_tokens + 4095) / 4096));
-        const int64_t per = (t->row_tokens + R - 1) / R;
+    // ranges of about equal size over the long segments' tokens, each a list
+    // of pieces of at most `chunk` tokens of one segment
+    auto make_ranges = [&](const std::vector<int4>& ls, int64_t tokens, std::vector<int4>* chunks,
+                           std::vector<int32_t>* range_off) {
+        if (tokens <= 0) return;
+        const int64_t R = std::max<int64_t>(1, std::min<int64_t>(ranges_target, (tokens + 4095) / 4096));
+        const int64_t per = (tokens + R - 1) / R;
         int64_t fill = 0;
-        t->range_off.push_back(0);
-        for (const int4& h : longs) {
+        range_off->push_back(0);
+        for (const int4& h : ls) {
             int p = h.z, left = h.w;
             while (left > 0) {
                 const int take = (int)std::min<int64_t>(std::min<int64_t>(left, per - fill), chunk);
-                t->chunks.push_back(make_int4(h.x, h.y, p, take));
+                chunks->push_back(make_int4(h.x, h.y, p, take));
                 p += take;
                 left -= take;
                 fill += take;
                 if (fill == per) {
-                    t->range_off.push_back((int32_t)t->chunks.size());
+                    range_off->push_back((int32_t)chunks->size());
                     fill = 0;
                 }
             }
         }
-        if (fill > 0) t->range_off.push_back((int32_t)t->chunks.size());
+        if (fill > 0) range_off->push_back((int32_t)chunks->size());
+    };
+    make_ranges(longs, t->row_tokens, &t->chunks, &t->range_off);
+    make_ranges(s_longs, t->s_row_tokens, &t->s_chunks, &t->s_range_off);
+    // cluster-tier words by cluster size: class c (size 2^c) takes the words
+    // whose slices fit with 2^c blocks but not with 2^(c-1)
+    t->cluster_cls.assign(kClusterClasses + 1, 0);
+    if (!cl_words.empty()) {
+        std::vector<std::vector<int32_t>> by(kClusterClasses);
+        for (const int2& w : cl_words) {
+            int c = 0;
+            while (c + 1 < kClusterClasses && (int64_t)(1 << c) * cluster_slice < w.x) ++c;
+            by[c].push_back(w.y);
+        }
+        for (int c = 0; c < kClusterClasses; ++c) {
+            t->cluster_cls[c] = (int32_t)t->cluster_list.size();
+            t->cluster_list.insert(t->cluster_list.end(), by[c].begin(), by[c].end());
+        }
     }
+    t->cluster_cls[kClusterClasses] = (int32_t)t->cluster_list.size();
 }
 
 // Reads the index-check record of the kernels (synchronises); a non-zero
@@ -375,8 +427,8 @@ int check_record(warplda_ctx* c, const char* where) {
     if (f[0] == 0) return fail(WARPLDA_ETIMEDOUT, "a tensor-core wait ran out (reported at %s)", where);
     static const char* kSites[] = {"?", "doc batch", "word batch", "multi-pass hist",
                                    "multi-pass accept", "multi-pass draw", "doc warp", "loglik",
-                                   "fold-in"};
-    const char* site = (f[0] >= 1 && f[0] <= 8) ? kSites[f[0]] : "?";
+                                   "fold-in", "word cluster"};
+    const char* site = (f[0] >= 1 && f[0] <= 9) ? kSites[f[0]] : "?";
     return fail(WARPLDA_ECUDA, "index check failed (reported at %s): first in the %s kernel, checks 0x%x",
                 where, site, (unsigned)f[2]);
 }
@@ -434,12 +486,14 @@ struct PhaseCall {
     int cls;
 };
 
-HugeWork huge_work(warplda_ctx* c, const Tier& T, int counter) {
+// Work of the multi-pass passes: the sampling pieces (long segments not on a
+// cluster), or with `all` every long segment's pieces (log-likelihood).
+HugeWork huge_work(warplda_ctx* c, const Tier& T, int counter, bool all = false) {
     HugeWork w;
-    w.pieces = T.d_chunks;
-    w.range_off = T.d_range_off;
-    w.nranges = (int)T.range_off.size() - 1;
-    w.npieces = (int)T.chunks.size();
+    w.pieces = all ? T.d_chunks : T.d_s_chunks;
+    w.range_off = all ? T.d_range_off : T.d_s_range_off;
+    w.nranges = (int)(all ? T.range_off.size() : T.s_range_off.size()) - 1;
+    w.npieces = (int)(all ? T.chunks.size() : T.s_chunks.size());
     w.nrows = (int)T.nrows;
     w.guide_bits = huge_guide_bits(c->K);
     w.counter = c->counters + counter;
@@ -450,7 +504,7 @@ int run_phase(warplda_ctx* c, bool doc) {
     const uint32_t it = c->iter + 1;
     PhaseCall pc{phase_args(c, doc, it), doc, 0};
     Tier& T = doc ? c->docs : c->words;
-    const int nch = (int)T.chunks.size();
+    const int nch = (int)T.s_chunks.size();
     int rc;
     if (nch > 0 && c->sparse) {
         rc = launch_rec(c, kcZero, [](warplda_ctx* cc, void* p) {
@@ -507,6 +561,18 @@ int run_phase(warplda_ctx* c, bool doc) {
         }, &pc);
         if (rc) return rc;
     }
+    for (int cls = 0; !doc && cls < kClusterClasses && !T.cluster_list.empty(); ++cls) {
+        if (T.cluster_cls[cls + 1] == T.cluster_cls[cls]) continue;
+        pc.cls = cls;
+        rc = launch_rec(c, kcWordCluster, [](warplda_ctx* cc, void* p) {
+            PhaseCall* q = (PhaseCall*)p;
+            const Tier& W = cc->words;
+            const int b0 = W.cluster_cls[q->cls], b1 = W.cluster_cls[q->cls + 1];
+            return launch_cluster_word(q->a, W.d_cluster_list + b0, b1 - b0, 1 << q->cls, cc->cluster_T,
+                                       cc->cluster_smem, cc->st);
+        }, &pc);
+        if (rc) return rc;
+    }
     if (nch > 0) {
         rc = launch_rec(c, doc ? kcDocHugeAccept : kcWordMegaAccept, [](warplda_ctx* cc, void* p) {
             PhaseCall* q = (PhaseCall*)p;
@@ -559,7 +625,11 @@ int run_phase(warplda_ctx* c, bool doc) {
 
 int launches_per_phase(const warplda_ctx* c, bool doc) {
     const Tier& T = doc ? c->docs : c->words;
-    return (T.chunks.empty() ? 0 : ((doc || c->word_storage) ? 4 : 5)) + (T.batches[0].empty() ? 0 : 1) +
+    int cl = 0;
+    for (int k = 0; !doc && k < kClusterClasses && !T.cluster_list.empty(); ++k)
+        cl += T.cluster_cls[k + 1] > T.cluster_cls[k] ? 1 : 0;
+    return (T.s_chunks.empty() ? 0 : ((doc || c->word_storage) ? 4 : 5)) + cl +
+           (T.batches[0].empty() ? 0 : 1) +
            (T.batches[1].empty() ? 0 : 1) + (T.warp_list.empty() ? 0 : 1) + ((c->stage_ck || c->ck_delta) ? 1 : 2);
 }
 
@@ -973,6 +1043,10 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     c->region[1] = rb ? rb : 8192;
     // the pipelined document kernel takes batches of up to 1021 tokens and
     // 128 documents; their hash tables need at most 4 words per token
+    if (tuning && tuning->cluster_max_tokens < -1) {
+        delete c;
+        return fail(WARPLDA_EINVAL, "cluster_max_tokens must be -1, 0 or positive");
+    }
     if (tuning && (tuning->doc_batch_kernel < 0 || tuning->doc_batch_kernel > 2)) {
         delete c;
         return fail(WARPLDA_EINVAL, "doc_batch_kernel must be 0, 1 or 2");
@@ -1082,7 +1156,35 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     const int ranges_target = c->sparse ? (1 << 30) : 4 * c->sms;
     build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->dregion, c->chunk, ranges_target, &c->docs,
                c->doc_pipe ? kDocSegs : kSegsMax);
-    build_tier(word_off, V, K, c->dense, 0, c->bmax, c->region, c->chunk, ranges_target, &c->words);
+    // with tuning cluster_max_tokens, words too long for a block batch but
+    // within a cluster's shared memory (or the cap) are sampled on a
+    // thread-block cluster (up to 16 blocks where the device allows, else 8).
+    // Off by default: measured slower than the multi-pass tier on the
+    // PubMed- and NYTimes-shaped workloads (8.4 vs 7.3 ms and 1.1 vs 0.7 ms
+    // per sweep for the same words)
+    int64_t cluster_max = 0;
+    {
+        const int ct = tuning ? tuning->cluster_max_tokens : 0;
+        int optin = 0;
+        if (!c->sparse && ct != 0 &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev) == cudaSuccess) {
+            const int smem = (optin - 1024) & ~15;   // room for the kernel's static shared memory
+            for (int C : {16, 8}) {
+                if (cluster_size_supported(K, M, c->stage_ck, C, smem) >= 1) {
+                    c->cluster_C = C;
+                    c->cluster_smem = smem;
+                    c->cluster_T = cluster_slice_capacity(K, M, c->stage_ck, smem);
+                    break;
+                }
+            }
+            if (c->cluster_C > 0 && c->cluster_T > 0) {
+                cluster_max = (int64_t)c->cluster_C * c->cluster_T;
+                if (ct > 0) cluster_max = std::min<int64_t>(cluster_max, ct);
+            }
+        }
+    }
+    build_tier(word_off, V, K, c->dense, 0, c->bmax, c->region, c->chunk, ranges_target, &c->words, kSegsMax,
+               cluster_max, std::max(1, c->cluster_T));
 
     if ((rc = dalloc(c, &c->ck, K, "alloc c_k"))) return bail(rc);
     if ((rc = dalloc(c, &c->ckb, K, "alloc c_k float"))) return bail(rc);
@@ -1145,6 +1247,21 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
             if ((e = cudaMemcpyAsync(t->d_range_off, t->range_off.data(), t->range_off.size() * sizeof(int32_t),
                                      cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
                 return bail(cuda_fail(e, "upload ranges"));
+        if ((rc = dalloc(c, &t->d_s_chunks, (int64_t)t->s_chunks.size(), "alloc chunks"))) return bail(rc);
+        if (!t->s_chunks.empty())
+            if ((e = cudaMemcpyAsync(t->d_s_chunks, t->s_chunks.data(), t->s_chunks.size() * sizeof(int4),
+                                     cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+                return bail(cuda_fail(e, "upload chunks"));
+        if ((rc = dalloc(c, &t->d_s_range_off, (int64_t)t->s_range_off.size(), "alloc ranges"))) return bail(rc);
+        if (!t->s_range_off.empty())
+            if ((e = cudaMemcpyAsync(t->d_s_range_off, t->s_range_off.data(), t->s_range_off.size() * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+                return bail(cuda_fail(e, "upload ranges"));
+        if ((rc = dalloc(c, &t->d_cluster_list, (int64_t)t->cluster_list.size(), "alloc cluster words"))) return bail(rc);
+        if (!t->cluster_list.empty())
+            if ((e = cudaMemcpyAsync(t->d_cluster_list, t->cluster_list.data(), t->cluster_list.size() * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
+                return bail(cuda_fail(e, "upload cluster words"));
     }
     {
         // descriptors of the pipelined document batches: {first document,
@@ -1387,14 +1504,14 @@ int warplda_loglik(warplda_ctx* c, double* out) {
             const int k = doc ? 0 : 1;
             WL_CU(cudaMemsetAsync(c->sslots[k], 0, (size_t)c->sn[k] * 8, c->st), "zero rows");
             WL_CU(cudaMemsetAsync(c->counters + kCtrLoglik, 0, sizeof(int32_t), c->st), "reset counter");
-            WL_CU(launch_sparse_hist(doc, pa, huge_work(c, T, kCtrLoglik), SparseRows{c->d_soff[k], c->sslots[k]},
+            WL_CU(launch_sparse_hist(doc, pa, huge_work(c, T, kCtrLoglik, true), SparseRows{c->d_soff[k], c->sslots[k]},
                                      c->grid_hist, c->st), "loglik rows");
             WL_CU(cudaMemsetAsync(c->counters + kCtrLoglik, 0, sizeof(int32_t), c->st), "reset counter");
             WL_CU(launch_sparse_loglik(c->sslots[k], c->sn[k], doc ? a : b, c->d_ll, c->st), "loglik rows");
         } else if (!T.chunks.empty()) {
             WL_CU(launch_zero(rows, r4(T.nrows * (int64_t)c->K), c->st), "zero rows");
             WL_CU(cudaMemsetAsync(c->counters + kCtrLoglik, 0, sizeof(int32_t), c->st), "reset counter");
-            WL_CU(launch_huge_hist(doc, pa, huge_work(c, T, kCtrLoglik), rows, c->grid_hist, c->st),
+            WL_CU(launch_huge_hist(doc, pa, huge_work(c, T, kCtrLoglik, true), rows, c->grid_hist, c->st),
                   "loglik rows");
             WL_CU(launch_loglik_rows(rows, T.nrows, c->K, doc ? a : b, c->d_ll, c->st), "loglik rows");
         }
@@ -1471,8 +1588,10 @@ int warplda_get_info(warplda_ctx* c, warplda_info* o) {
     o->word_batches = (int64_t)(c->words.batches[0].size() + c->words.batches[1].size());
     o->huge_docs = c->docs.nrows;
     o->huge_doc_tokens = c->docs.row_tokens;
-    o->mega_words = c->words.nrows;
-    o->mega_word_tokens = c->words.row_tokens;
+    o->mega_words = c->words.nrows - (int64_t)c->words.cluster_list.size();
+    o->mega_word_tokens = c->words.s_row_tokens;
+    o->cluster_words = (int64_t)c->words.cluster_list.size();
+    o->cluster_word_tokens = c->words.cluster_tokens;
     o->device_bytes = c->device_bytes;
     // the small document class: every batched token outside the large
     // class and the warp tier

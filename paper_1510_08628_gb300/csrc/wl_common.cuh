@@ -217,7 +217,7 @@ struct Checks {
 // Kernel sites of the check record.
 enum : int {
     kSiteDocBatch = 1, kSiteWordBatch = 2, kSiteHugeHist = 3, kSiteHugeAccept = 4,
-    kSiteHugeDraw = 5, kSiteDocWarp = 6, kSiteLoglik = 7, kSiteFoldin = 8
+    kSiteHugeDraw = 5, kSiteDocWarp = 6, kSiteLoglik = 7, kSiteFoldin = 8, kSiteWordCluster = 9
 };
 
 }  // namespace wl

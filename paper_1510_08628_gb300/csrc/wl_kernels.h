@@ -37,6 +37,14 @@ cudaError_t launch_doc_pipe(bool dense, int tpt, const PhaseArgs& a, const int4*
                             int* counter, const int32_t* seg_region, int region_words, int grid,
                             cudaStream_t st);
 
+// Heavy words on a thread-block cluster (wl_cluster.cu): one cluster of C
+// blocks per word of words[0..nwords), T tokens per block at most, smem
+// bytes of dynamic shared memory per block.
+int cluster_slice_capacity(int K, int M, int stage_ck, int smem_max);
+int cluster_size_supported(int K, int M, int stage_ck, int C, int smem);
+cudaError_t launch_cluster_word(const PhaseArgs& a, const int32_t* words, int nwords, int C, int T, int smem,
+                                cudaStream_t st);
+
 // Warp tier of the document phase (wl_docwarp.cu): docs = ids of documents
 // with 1..32*tpl tokens.
 int docwarp_table_words(int K, int tpl, int dense);

@@ -33,7 +33,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("batch_max_tokens", ctypes.c_int32), ("huge_chunk", ctypes.c_int32),
                 ("region_budget", ctypes.c_int32), ("doc_warp_max", ctypes.c_int32),
                 ("word_positioning", ctypes.c_int32), ("doc_batch_kernel", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("cluster_max_tokens", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -44,7 +44,8 @@ class Info(ctypes.Structure):
                 ("huge_docs", ctypes.c_int64), ("huge_doc_tokens", ctypes.c_int64),
                 ("mega_words", ctypes.c_int64), ("mega_word_tokens", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("pipe_doc_tokens", ctypes.c_int64),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("cluster_words", ctypes.c_int64), ("cluster_word_tokens", ctypes.c_int64),
+                ("reserved", ctypes.c_int32 * 2)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

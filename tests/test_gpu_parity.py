@@ -137,7 +137,44 @@ TUNINGS = [None, {"batch_max_tokens": 64}, {"batch_max_tokens": 2000, "region_bu
            {"huge_chunk": 300, "batch_max_tokens": 500}, {"batch_max_tokens": 4095},
            {"doc_warp_max": 512}, {"doc_warp_max": 20, "batch_max_tokens": 3000},
            {"doc_batch_kernel": 2}, {"doc_batch_kernel": 2, "batch_max_tokens": 64},
-           {"doc_batch_kernel": 2, "region_budget": 600}]
+           {"doc_batch_kernel": 2, "region_budget": 600},
+           {"batch_max_tokens": 64, "cluster_max_tokens": -1},
+           {"batch_max_tokens": 64, "cluster_max_tokens": 300}]
+
+CL = {"cluster_max_tokens": -1}   # the cluster tier as far as shared memory allows
+
+
+@pytest.mark.parametrize("kind,K,M,tun,rule,on_cluster", [
+    ("giant_word", 30, 2, CL, 0, True),
+    ("giant_word", 3000, 1, CL, 0, True),
+    ("giant_word", 1, 3, CL, 0, True),
+    ("giant_word", 200, 4, {"cluster_max_tokens": 5000}, 0, False),
+    ("mixed", 5000, 3, {"batch_max_tokens": 64, "cluster_max_tokens": 400}, 0, True),
+    ("mixed", 16384, 2, {"batch_max_tokens": 100, "cluster_max_tokens": -1}, 0, True),
+    ("giant_word", 40, 2, CL, 1, True),
+    ("mixed", 3000, 2, {"batch_max_tokens": 64, "cluster_max_tokens": -1}, 1, True),
+    ("giant_word", 30, 2, None, 0, False),
+])
+def test_cluster_tier_bit_exact(kind, K, M, tun, rule, on_cluster):
+    """Words between a block batch and a cluster's shared memory, sampled on
+    a thread-block cluster with the count rows reduced over distributed
+    shared memory, against the oracle -- both word-positioning rules, dense
+    and hash K, and caps that put some long words on the cluster and the
+    others in the multi-pass tier."""
+    c = _edge_corpus(kind)
+    t = dict(tun or {})
+    t["word_positioning"] = rule
+    gpu = _gpu(c, c.V, K, 0.3, 0.02, M, 99, tuning=t)
+    info = gpu.info()
+    assert (info["cluster_words"] > 0) == on_cluster, info
+    ref = oracle.Oracle(c.doc_ptr, c.doc_word, c.V, K, 0.3, 0.02, M, 99, word_rule=rule)
+    for s in (1, 2):
+        gpu.sweep(s)
+        ref.sweep(s)
+        _same_state(gpu, ref, f"cluster tier {kind} K={K} M={M} rule={rule}")
+    gpu.sync()
+    ll, want = gpu.loglik(), ref.loglik()
+    assert abs(ll - want) <= 1e-9 * abs(want)
 
 
 @pytest.mark.parametrize("kind,K,M,dk", [("mixed", 7, 3, 2), ("mixed", 5000, 2, 1), ("giant_doc", 16, 4, 2),
