@@ -434,7 +434,7 @@ def serving_bench(gpu, c, wl, args, learned: bool, rate: float, n: int = 6000, n
 
 
 TUNING_KEYS = ("batch_max_tokens", "huge_chunk", "region_budget", "doc_warp_max", "word_positioning",
-               "doc_batch_kernel", "cluster_max_tokens")
+               "doc_batch_kernel", "cluster_max_tokens", "foldin_kernel")
 
 
 def parse_tuning(text: str) -> dict | None:
@@ -499,7 +499,10 @@ def foldin_bench(gpu, c, wl, args, torch, stream):
            "docs_per_s": rq.D / wall, "tokens_sweeps_per_s": rq.N * S / wall, "seconds": wall,
            "device_seconds": dev_s, "includes": "host checks + H2D of the CSR + fold-in kernel + "
                                                  "D2H of theta (synchronous C ABI call)",
-           "proposal": "plain", "lengths": "lognormal of the workload, clipped to [20, 5000]"}
+           "proposal": "plain", "lengths": "lognormal of the workload, clipped to [20, 5000]",
+           "kernel": ("one warp per document, all sweeps in one launch"
+                      if (getattr(args, "_tuning", None) or {}).get("foldin_kernel") == 1 else
+                      "word-major phases (document phase per document, word phase per word)")}
     if not args.no_cpu_baseline:
         import oracle
         n = min(400, rq.D)
@@ -578,7 +581,7 @@ def main():
     ap.add_argument("--tuning", default="",
                     help="launch tuning of the sampler as key=value pairs separated by commas "
                          "(batch_max_tokens, huge_chunk, region_budget, doc_warp_max, word_positioning, "
-                         "doc_batch_kernel, cluster_max_tokens)")
+                         "doc_batch_kernel, cluster_max_tokens, foldin_kernel)")
     ap.add_argument("--docs", type=int, default=0,
                     help="use only the first DOCS documents of the workload (small profiling cases)")
     args = ap.parse_args()
@@ -624,6 +627,7 @@ def main():
     seed = args.seed + 1000 * rank
     stream = torch.cuda.current_stream()
     tun = parse_tuning(args.tuning)
+    args._tuning = tun
     gpu = WarpLDA(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, seed, stream=stream,
                   tuning=tun)
     info = gpu.info()
@@ -721,7 +725,8 @@ def main():
             cf, wf = c, wl
         else:
             cf, wf = corpus.generate(fa.workload, seed=args.corpus_seed)
-        model = WarpLDA(cf.doc_ptr, cf.doc_word, cf.V, wf.K, wf.alpha, wf.beta, wf.M, seed, stream=stream)
+        model = WarpLDA(cf.doc_ptr, cf.doc_word, cf.V, wf.K, wf.alpha, wf.beta, wf.M, seed, stream=stream,
+                        tuning=tun)
         model.sweep(args.model_sweeps)   # train the model
         foldin = foldin_bench(model, cf, wf, fa, torch, stream)
         fa._plain_docs_per_s = foldin["docs_per_s"]

@@ -81,6 +81,15 @@ typedef struct warplda_server warplda_server;
  *                     (default): no cluster tier (the multi-pass tier is
  *                     faster on the workloads measured).  K above 16384 has
  *                     no cluster tier.
+ *   foldin_kernel     fold-in with the plain proposal: 0 (default) or 2 =
+ *                     word-major phases (per sweep one launch for the
+ *                     document phase, one warp per document, and one for
+ *                     the word phase over the requests' tokens grouped by
+ *                     word, a frequent word's frozen row read once per
+ *                     piece of its tokens into shared memory); 1 = one warp
+ *                     per document for all sweeps in one launch.  The
+ *                     learned proposal and serving always take the
+ *                     per-document kernel.
  * One field changes the sampler (a different, equally valid chain):
  *   word_positioning  the word proposal's p_A branch (Eq. 6): 0 (default) =
  *                     the j-th smallest post-acceptance topic of the word;
@@ -95,7 +104,7 @@ typedef struct warplda_tuning {
     int32_t word_positioning;
     int32_t doc_batch_kernel;
     int32_t cluster_max_tokens;
-    int32_t reserved[1];
+    int32_t foldin_kernel;
 } warplda_tuning;
 
 /*
@@ -343,11 +352,11 @@ int warplda_encoder_proposal(warplda_ctx* ctx, int64_t Dn, const int64_t* doc_pt
  * warplda_server_step -- upload the requests admitted since the last step,
  *   then launch one sweep for every admitted, unfinished request (new ones
  *   are initialised first; a request's last sweep writes its theta);
- *   asynchronous.  With the learned proposal a new request's encoder
- *   forward and alias table are made on a second stream while the step's
- *   sweep runs, and it joins the sweeps from the next step on (its results
- *   are unchanged).  *active_out (or NULL) = requests advanced or being
- *   admitted.  Requests submitted while a step runs join the next step.
+ *   asynchronous.  With the learned proposal the new requests' encoder
+ *   forward, alias tables and first sweep run on a second stream beside the
+ *   sweep of the requests already running (the step ends when both have).
+ *   *active_out (or NULL) = requests advanced.  Requests submitted while a
+ *   step runs join the next step.
  *   The previous step's results must have been polled (else ESTATE).
  * warplda_server_poll -- wait at most timeout_ms for the last step (else
  *   ETIMEDOUT), then hand over the requests it finished: ids[n] and

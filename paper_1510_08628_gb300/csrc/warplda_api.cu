@@ -104,6 +104,13 @@ constexpr int kPipeTokens = WL_PIPE_TOKENS;
 static_assert(kPipeTokens >= 1 && kPipeTokens <= 4 * kThreads - 3, "pipelined batch size");
 // cluster sizes of the cluster tier: 1, 2, 4, 8, 16 blocks
 constexpr int kClusterClasses = 5;
+// word-major fold-in: words with at least this many request tokens have
+// their frozen row staged in shared memory, the others keep direct loads
+#ifndef WL_FOLD_STAGE_MIN
+#define WL_FOLD_STAGE_MIN 64
+#endif
+constexpr int kFoldStageMin = WL_FOLD_STAGE_MIN;
+static_assert(kFoldStageMin >= 1, "staging threshold");
 // above this K the multi-pass tier's count rows are sparse (global hash)
 constexpr int kDenseRowMaxK = 16384;
 // work counters: 0-3 batches [class][phase], 4 doc warp tier, 5-8 the
@@ -172,6 +179,9 @@ struct warplda_ctx {
     // words sampled on a thread-block cluster: cluster size, tokens per block
     // (slice capacity), dynamic shared memory per block
     int cluster_C = 0, cluster_T = 0, cluster_smem = 0;
+    // plain-proposal fold-in: word-major phases (default) or one warp per
+    // document for all sweeps (tuning foldin_kernel = 1)
+    bool foldin_word_major = true;
     bool dense = true;   // 16-bit dense count tables (K <= kDenseMaxK), else hash tables
     int warp_tpl = 16;   // tokens per lane of the document warp tier
     int grid_doc_warp = 1;
@@ -814,13 +824,12 @@ struct warplda_server {
     int n_fin_staged = 0;
     cudaEvent_t tick = nullptr;
     // learned proposal: the admission work (encoder, alias tables, rows) of
-    // a step runs on a second stream while the step's sweep runs; its
-    // requests join the next step
+    // a step and its new requests' first sweep run on a second stream while
+    // the step's sweep of the running requests runs
     cudaStream_t side = nullptr;
     cudaEvent_t uploaded = nullptr, admitted = nullptr;
     struct Slot {
         bool used = false;
-        bool ready = false;     // proposal rows in place: the slot joins the sweeps
         int64_t id = 0;
         int32_t off = 0, L = 0, done = 0;
     };
@@ -925,7 +934,7 @@ int stage_room(warplda_server* s, int64_t n) {
 // staging, one admission kernel) and, with the learned proposal, makes their
 // proposal rows and alias tables -- all queued on the stream, no host wait.
 // The staging also carries the step's active list (written at `act_off`).
-int server_admit(warplda_server* s, const std::vector<int32_t>& active, int64_t* act_off) {
+int server_admit(warplda_server* s, const std::vector<int32_t>& active, int64_t* act_off, int64_t* sl_off) {
     warplda_ctx* c = s->c;
     const int n = (int)s->new_req.size();
     const int64_t nw = (int64_t)s->new_words.size();
@@ -955,13 +964,15 @@ int server_admit(warplda_server* s, const std::vector<int32_t>& active, int64_t*
     if (!active.empty()) std::memcpy(h + o_act, active.data(), active.size() * 4);
     WL_CU(cudaMemcpyAsync(s->d_staged, h, (size_t)total * 4, cudaMemcpyHostToDevice, c->st), "upload requests");
     *act_off = o_act;
+    *sl_off = o_sl;
     const int32_t* d = s->d_staged;
     if (n > 0)
         WL_CU(launch_serve_admit(d, reinterpret_cast<const int4*>(d + o_req), d + o_src, n, s->nslots, s->pool_tokens,
                                  s->d_words, s->d_info, c->st), "admit requests");
     if (n > 0 && s->proposal == WARPLDA_PROPOSAL_LEARNED) {
-        // on the side stream, once the upload is done; the caller makes the
-        // main stream wait for `admitted` after the step's sweep is queued
+        // on the side stream, once the upload is done; the caller queues the
+        // new requests' first sweep behind it there and makes the main stream
+        // wait for `admitted` after the running requests' sweep is queued
         const int K = c->K;
         auto& e = c->enc;
         WL_CU(cudaEventRecord(s->uploaded, c->st), "record upload");
@@ -977,7 +988,6 @@ int server_admit(warplda_server* s, const std::vector<int32_t>& active, int64_t*
         WL_CU(launch_enc_alias(s->d_aq, n, K, s->d_aatab, s->side), "alias tables");
         WL_CU(launch_serve_rows(s->d_aq, d + o_sl, n, K, s->nslots, s->d_q, s->side), "proposal rows");
         WL_CU(launch_serve_rows(s->d_aatab, d + o_sl, n, 2 * K, s->nslots, s->d_atab, s->side), "alias rows");
-        WL_CU(cudaEventRecord(s->admitted, s->side), "record admission");
     }
     s->new_words.clear();
     s->new_src.clear();
@@ -1051,6 +1061,11 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         delete c;
         return fail(WARPLDA_EINVAL, "doc_batch_kernel must be 0, 1 or 2");
     }
+    if (tuning && (tuning->foldin_kernel < 0 || tuning->foldin_kernel > 2)) {
+        delete c;
+        return fail(WARPLDA_EINVAL, "foldin_kernel must be 0, 1 or 2");
+    }
+    c->foldin_word_major = !tuning || tuning->foldin_kernel != 1;
     {
         // measured: pipelined batches of 1021 tokens beat the block kernel
         // with hash tables and K up to 16384; with dense tables the block
@@ -1749,11 +1764,57 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
         f.atab = atab;
     }
     const int tab_words = foldin_table_words(K, (int)Lmax);
-    const int per_sm = foldin_blocks_per_sm(K, M, tab_words);
-    if (per_sm < 1) return fail(WARPLDA_EINVAL, "fold-in tables do not fit in shared memory");
     const int warps = foldin_warps(tab_words);
-    const int grid = (int)std::min<int64_t>((int64_t)per_sm * c->sms, (Dn + warps - 1) / warps + 1);
-    WL_CU(launch_foldin(f, tab_words, grid, c->st), "fold-in");
+    if (proposal == WARPLDA_PROPOSAL_PLAIN && c->foldin_word_major && Dn > 0) {
+        // word-major phases: the requests' tokens grouped by word once, then
+        // per sweep a document-phase and a word-phase launch
+        const int64_t V = c->V;
+        const bool stage = K <= kFoldStageMaxK;
+        const int stage_min = stage ? kFoldStageMin : 0x7FFFFFFF;
+        int32_t *cnt, *hc, *lc, *pc, *cur, *tmp, *npieces, *counters;
+        int4 *rec, *pieces;
+        WL_CU(buf.get(&cnt, V + 1), "alloc fold-in word counts");
+        WL_CU(buf.get(&hc, V + 1), "alloc fold-in word offsets");
+        WL_CU(buf.get(&lc, V + 1), "alloc fold-in word offsets");
+        WL_CU(buf.get(&pc, V + 1), "alloc fold-in piece offsets");
+        WL_CU(buf.get(&cur, V + 1), "alloc fold-in cursors");
+        WL_CU(buf.get(&tmp, scan_scratch_words(V + 1)), "alloc fold-in scan scratch");
+        WL_CU(buf.get(&rec, Nn), "alloc fold-in records");
+        WL_CU(buf.get(&pieces, fold_pieces_bound(Nn, stage_min)), "alloc fold-in pieces");
+        WL_CU(buf.get(&npieces, 1), "alloc fold-in piece count");
+        WL_CU(buf.get(&counters, (int64_t)sweeps + 2), "alloc fold-in counters");
+        WL_CU(cudaMemsetAsync(counters, 0, ((size_t)sweeps + 2) * 4, c->st), "reset counters");
+        FoldWords fw{};
+        fw.rec = rec;
+        fw.pieces = pieces;
+        fw.npieces = npieces;
+        fw.Nn = Nn;
+        fw.pstride = stage ? ((K + 1 + 3) & ~3) : 0;
+        fw.per = ((K + 31) / 32) | 1;
+        WL_CU(launch_fold_words_build(f, Nn, stage_min, cnt, hc, lc, pc, cur, tmp, rec, pieces, npieces,
+                                      4 * c->sms, c->st),
+              "fold-in word order");
+        const int dper = fold_doc_blocks_per_sm(K, M, tab_words);
+        const int wper = fold_word_blocks_per_sm(M, fw);
+        if (dper < 1 || wper < 1) return fail(WARPLDA_EINVAL, "fold-in tables do not fit in shared memory");
+        const int dgrid = (int)std::min<int64_t>((int64_t)dper * c->sms, (Dn + warps - 1) / warps + 1);
+        const int wgrid = wper * c->sms;
+        if (sweeps == 0) {
+            WL_CU(launch_fold_doc(f, tab_words, 1, 1 | 4, counters, dgrid, c->st), "fold-in");
+        } else {
+            for (int it = 1; it <= sweeps; ++it) {
+                WL_CU(launch_fold_doc(f, tab_words, it, (it == 1 ? 1 : 0) | 2, counters + it - 1, dgrid, c->st),
+                      "fold-in document phase");
+                WL_CU(launch_fold_word(f, fw, it, wgrid, c->st), "fold-in word phase");
+            }
+            if (theta_out) WL_CU(launch_fold_doc(f, tab_words, sweeps + 1, 4, counters + sweeps, dgrid, c->st), "fold-in theta");
+        }
+    } else {
+        const int per_sm = foldin_blocks_per_sm(K, M, tab_words);
+        if (per_sm < 1) return fail(WARPLDA_EINVAL, "fold-in tables do not fit in shared memory");
+        const int grid = (int)std::min<int64_t>((int64_t)per_sm * c->sms, (Dn + warps - 1) / warps + 1);
+        WL_CU(launch_foldin(f, tab_words, grid, c->st), "fold-in");
+    }
     if (z_out && Nn > 0)
         WL_CU(cudaMemcpyAsync(z_out, d_z, (size_t)Nn * 4, cudaMemcpyDeviceToHost, c->st), "copy z");
     if (theta_out && Dn > 0)
@@ -2018,7 +2079,7 @@ int warplda_server_create(warplda_ctx* c, int32_t slots, int64_t pool_tokens, in
     };
     if ((rc = salloc(s, &s->d_info, slots)) || (rc = salloc(s, &s->d_active, slots)) ||
         (rc = salloc(s, &s->d_z, pool_tokens + 4)) || (rc = salloc(s, &s->d_prop, (pool_tokens + 4) * M)) ||
-        (rc = salloc(s, &s->d_words, pool_tokens + 4)) || (rc = salloc(s, &s->d_counter, 2)) ||
+        (rc = salloc(s, &s->d_words, pool_tokens + 4)) || (rc = salloc(s, &s->d_counter, 4)) ||
         (rc = salloc(s, &s->d_fin_theta, (int64_t)slots * K)) || (rc = salloc(s, &s->d_fin_slot, slots)) ||
         (rc = salloc(s, &s->d_req, slots)) || (rc = salloc(s, &s->d_src, slots)))
         return bail(rc);
@@ -2079,45 +2140,38 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     if (s->n_fin_staged > 0) return fail(WARPLDA_ESTATE, "poll the previous step's results first");
     // the pinned staging is reused: the previous step's upload must be done
     WL_CU(cudaEventSynchronize(s->tick), "previous step");
-    // the previous step (and its admission work) is complete: its learned
-    // requests have their proposal rows
+    // requests staged since the last step join this step: with the plain
+    // proposal in the step's sweep; with the learned one their first sweep
+    // runs on the side stream behind their encoder forward and alias tables,
+    // beside the sweep of the requests already running
     const bool learned = s->proposal == WARPLDA_PROPOSAL_LEARNED;
-    for (auto& S : s->slots)
-        if (S.used) S.ready = true;
-    // requests staged since the last step: with the plain proposal they join
-    // this step's sweep; with the learned one the next step's
-    for (const int4& r : s->new_req) s->slots[r.x].ready = !learned;
-    std::vector<int32_t> active;
-    int nfin = 0, pending = 0;
+    std::vector<int32_t> active, fresh;
+    if (learned)
+        for (const int4& r : s->new_req) fresh.push_back(r.x);
+    std::vector<char> is_fresh((size_t)s->nslots, 0);
+    for (int32_t i : fresh) is_fresh[i] = 1;
+    int nfin = 0;
     for (int i = 0; i < s->nslots; ++i) {
         const auto& S = s->slots[i];
         if (!S.used || S.done >= s->sweeps) continue;
-        if (!S.ready) {
-            ++pending;
+        if (is_fresh[i]) {
+            if (S.done + 1 >= s->sweeps) ++nfin;
             continue;
         }
         active.push_back(i);
         if (S.done + 1 >= s->sweeps) ++nfin;
     }
-    if (active_out) *active_out = (int32_t)(active.size() + pending);
-    if (active.empty() && pending == 0) return WARPLDA_OK;
-    int64_t act_off = 0;
-    const bool admit_learned = learned && !s->new_req.empty();
-    int rc = server_admit(s, active, &act_off);
+    if (active_out) *active_out = (int32_t)(active.size() + fresh.size());
+    if (active.empty() && fresh.empty()) return WARPLDA_OK;
+    // work counters of the two launches [0], [2] and the shared count of
+    // finished rows [1]; zeroed before the side stream is released
+    WL_CU(cudaMemsetAsync(s->d_counter, 0, 16, c->st), "reset counters");
+    int64_t act_off = 0, sl_off = 0;
+    int rc = server_admit(s, active, &act_off, &sl_off);
     if (rc) return rc;
-    if (active.empty()) {
-        // only fresh learned requests: their admission is the step
-        if (admit_learned) WL_CU(cudaStreamWaitEvent(c->st, s->admitted, 0), "wait admission");
-        s->n_fin_staged = 0;
-        WL_CU(cudaEventRecord(s->tick, c->st), "record tick");
-        return WARPLDA_OK;
-    }
-    WL_CU(cudaMemsetAsync(s->d_counter, 0, 8, c->st), "reset counters");
     FoldArgs f = server_args(s);
     ServeSlots sl{};
     sl.info = s->d_info;
-    sl.active = s->d_staged + act_off;
-    sl.nactive = (int)active.size();
     sl.nslots = s->nslots;
     sl.pool_tokens = s->pool_tokens;
     sl.z = s->d_z;
@@ -2128,10 +2182,24 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     sl.fin_count = s->d_counter + 1;
     sl.q = s->d_q;
     sl.atab = s->d_atab;
-    const int grid = (int)std::min<int64_t>(s->grid, ((int64_t)active.size() + kWarps - 1) / kWarps + 1);
-    WL_CU(launch_serve(f, sl, s->tab_words, grid, c->st), "serve");
-    if (admit_learned) WL_CU(cudaStreamWaitEvent(c->st, s->admitted, 0), "wait admission");
+    if (!active.empty()) {
+        sl.active = s->d_staged + act_off;
+        sl.nactive = (int)active.size();
+        const int grid = (int)std::min<int64_t>(s->grid, ((int64_t)active.size() + kWarps - 1) / kWarps + 1);
+        WL_CU(launch_serve(f, sl, s->tab_words, grid, c->st), "serve");
+    }
+    if (!fresh.empty()) {
+        FoldArgs fs = f;
+        fs.counter = s->d_counter + 2;
+        sl.active = s->d_staged + sl_off;
+        sl.nactive = (int)fresh.size();
+        const int grid = (int)std::min<int64_t>(s->grid, ((int64_t)fresh.size() + kWarps - 1) / kWarps + 1);
+        WL_CU(launch_serve(fs, sl, s->tab_words, grid, s->side), "serve new requests");
+        WL_CU(cudaEventRecord(s->admitted, s->side), "record admission");
+        WL_CU(cudaStreamWaitEvent(c->st, s->admitted, 0), "wait admission");
+    }
     for (int32_t i : active) s->slots[i].done += 1;
+    for (int32_t i : fresh) s->slots[i].done += 1;
     if (nfin > 0) {
         WL_CU(cudaMemcpyAsync(s->h_fin_slot, s->d_fin_slot, (size_t)nfin * 4, cudaMemcpyDeviceToHost, c->st), "copy finished");
         WL_CU(cudaMemcpyAsync(s->h_theta, s->d_fin_theta, (size_t)nfin * c->K * 4, cudaMemcpyDeviceToHost, c->st),

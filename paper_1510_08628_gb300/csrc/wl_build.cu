@@ -226,6 +226,12 @@ int64_t token_sort_scratch(int64_t N) {
     return 256 * ntiles + scan_scratch(256 * ntiles) + 4;
 }
 
+cudaError_t launch_scan_exclusive(int32_t* d, int64_t n, int32_t* tmp, cudaStream_t st) {
+    return scan_exclusive(d, n, tmp, st);
+}
+
+int64_t scan_scratch_words(int64_t n) { return scan_scratch(n); }
+
 cudaError_t launch_word_check(const int32_t* w, int64_t N, int32_t V, int32_t* bad, cudaStream_t st) {
     if (const cudaError_t g_ = launch_gate()) return g_;
     if (N <= 0) return cudaSuccess;

@@ -127,15 +127,12 @@ __device__ __forceinline__ void fold_init(const FoldArgs& f, const FoldDoc& doc,
     __syncwarp();
 }
 
-// Sweep `it` of one document: the document phase, then the word phase
-// against the frozen rows.  kLearned: the learned document proposal (the
-// encoder's q through its alias table) replaces positioning, and the word
-// phase accepts it with the independence-sampler rate min{1, p(t) q(s) /
-// (p(s) q(t))} of Alg. 1, p(k) = (C_dk + alpha)(C_wk + beta)/(c_k + beta_bar)
-// with the word phase's phase-start c_d (the oracle's readings L6-L7).
+// The document phase of sweep `it` of one document.  kLearned: the learned
+// document proposal (the encoder's q through its alias table) replaces
+// positioning.
 template <int M, bool kDense, bool kLearned>
-__device__ void fold_sweep(const FoldArgs& f, const FoldDoc& doc, int it, uint32_t* tab, int words,
-                           uint32_t cap, Checks& chk, int lane) {
+__device__ void fold_doc_phase(const FoldArgs& f, const FoldDoc& doc, int it, uint32_t* tab, int words,
+                               uint32_t cap, int lane) {
     const int K = f.K, L = doc.L;
     const uint32_t km = (uint32_t)K - 1u;
     int32_t* z = doc.z;
@@ -181,6 +178,21 @@ __device__ void fold_sweep(const FoldArgs& f, const FoldDoc& doc, int it, uint32
         }
     }
     __syncwarp();
+}
+
+// Sweep `it` of one document: the document phase, then the word phase
+// against the frozen rows.  kLearned: the word phase accepts the learned
+// proposal with the independence-sampler rate min{1, p(t) q(s) / (p(s) q(t))}
+// of Alg. 1, p(k) = (C_dk + alpha)(C_wk + beta)/(c_k + beta_bar) with the word
+// phase's phase-start c_d (the oracle's readings L6-L7).
+template <int M, bool kDense, bool kLearned>
+__device__ void fold_sweep(const FoldArgs& f, const FoldDoc& doc, int it, uint32_t* tab, int words,
+                           uint32_t cap, Checks& chk, int lane) {
+    const int K = f.K, L = doc.L;
+    const uint32_t km = (uint32_t)K - 1u;
+    int32_t* z = doc.z;
+    int32_t* prop = doc.prop;
+    fold_doc_phase<M, kDense, kLearned>(f, doc, it, tab, words, cap, lane);
     if (kLearned) fold_table<kDense>(tab, words, cap, doc, km, lane);   // the word phase's phase-start c_d
     // word phase against the frozen rows: accept, then a proposal from the
     // token's frozen row (one Philox block per step)
@@ -330,6 +342,372 @@ __global__ void __launch_bounds__(kThreads) serve_kernel(FoldArgs f, ServeSlots 
         if (lane == 0) sl.info[s].z = done + 1;
     }
     chk.publish(f.fault, kSiteFoldin);
+}
+
+// ---------------------------------------------------------------------------
+// Word-major fold-in (plain proposal).  In the kernel above a token's word
+// phase reads its word's frozen row at random: C_wz and C_wt of M proposals
+// and M entries of the word's sorted topics, one 32-byte sector each, out of
+// a model several times the size of L2.  Here each sweep is two launches:
+// the document phase, one warp per document as above (the requests' z and
+// proposals stay in document order), then the word phase over the requests'
+// tokens regrouped by word.  A warp takes pieces of up to kFoldPiece
+// tokens of one word; for a word with at least `stage_min` tokens in the
+// request set it loads the word's frozen row once into shared memory as
+// prefix sums P (C_wk = P[k+1] - P[k], and the j-th smallest trained topic
+// is the k with P[k] <= j < P[k+1], the value the sorted topics hold at j),
+// so its tokens touch the model only there.  The other words keep the direct
+// loads.  Every token draws the same Philox blocks and takes the same FP32
+// decisions as in the per-document kernel: theta and z are identical.
+// ---------------------------------------------------------------------------
+constexpr int kFoldPiece = 256;
+
+// Request tokens per word (warp-aggregated atomics: a warp's tokens of one
+// word add once).
+__global__ void fw_count_kernel(const int32_t* __restrict__ words, int64_t Nn, int32_t* __restrict__ cnt) {
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < Nn; b += step) {
+        const int64_t g = b + threadIdx.x;
+        const int w = g < Nn ? words[g] : -1;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, w);
+        if (w >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[w], __popc(peers));
+    }
+}
+
+// Per word (and one zero entry at V, which the exclusive scans turn into
+// totals): records in the staged region, records in the direct region,
+// staged pieces.
+__global__ void fw_class_kernel(const int32_t* __restrict__ cnt, int64_t V, int stage_min,
+                                int32_t* __restrict__ hc, int32_t* __restrict__ lc, int32_t* __restrict__ pc) {
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w <= V; w += step) {
+        const int n = w < V ? cnt[w] : 0;
+        const bool st = n >= stage_min;
+        hc[w] = st ? n : 0;
+        lc[w] = st ? 0 : n;
+        pc[w] = st ? (n + kFoldPiece - 1) / kFoldPiece : 0;
+    }
+}
+
+// Write cursor of each word's records: the staged region first, then the
+// direct region.
+__global__ void fw_cursor_kernel(const int32_t* __restrict__ cnt, const int32_t* __restrict__ hc,
+                                 const int32_t* __restrict__ lc, int64_t V, int stage_min,
+                                 int32_t* __restrict__ cur) {
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    const int htot = hc[V];
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < V; w += step)
+        cur[w] = cnt[w] >= stage_min ? hc[w] : htot + lc[w];
+}
+
+// One warp per document: each token's record {token index, position in the
+// document, stream id, word} at its word's cursor.
+__global__ void fw_scatter_kernel(const int32_t* __restrict__ doc_off, const int64_t* __restrict__ ids,
+                                  const int32_t* __restrict__ words, int Dn, int64_t Nn, int V,
+                                  int32_t* __restrict__ cur, int4* __restrict__ rec, int32_t* fault) {
+    Checks chk;
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int d = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); d < Dn; d += nw) {
+        const int b = doc_off[d], L = doc_off[d + 1] - b;
+        const int id = (int)(uint32_t)ids[d];
+        for (int jb = 0; jb < L; jb += 32) {
+            const int j = jb + lane;
+            int w = j < L ? words[b + j] : -1;
+            if (w >= V) w = -1;
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, w);
+            const int leader = __ffs(peers) - 1;
+            int pos = 0;
+            if (lane == leader && w >= 0) pos = atomicAdd(&cur[w], __popc(peers));
+            pos = __shfl_sync(0xFFFFFFFFu, pos, leader) + __popc(peers & ((1u << lane) - 1u));
+            if (w >= 0 && chk(pos >= 0 && (int64_t)pos < Nn, 2)) rec[pos] = make_int4(b + j, j, id, w);
+        }
+    }
+    chk.publish(fault, kSiteFoldin);
+}
+
+// The pieces: staged words' records in pieces of up to kFoldPiece, then the
+// direct region cut the same way.
+__global__ void fw_pieces_kernel(const int32_t* __restrict__ cnt, const int32_t* __restrict__ hc,
+                                 const int32_t* __restrict__ lc, const int32_t* __restrict__ pc, int64_t V,
+                                 int stage_min, int4* __restrict__ pieces, int32_t* __restrict__ npieces) {
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ptot = pc[V], htot = hc[V], ltot = lc[V];
+    const int nlight = (ltot + kFoldPiece - 1) / kFoldPiece;
+    for (int64_t w = tid; w < V; w += step) {
+        const int n = cnt[w];
+        if (n < stage_min) continue;
+        int p = pc[w];
+        for (int q = 0; q < n; q += kFoldPiece) pieces[p++] = make_int4((int)w, hc[w] + q, min(kFoldPiece, n - q), 1);
+    }
+    for (int64_t q = tid; q < nlight; q += step) {
+        const int first = (int)q * kFoldPiece;
+        pieces[ptot + q] = make_int4(-1, htot + first, min(kFoldPiece, ltot - first), 0);
+    }
+    if (tid == 0) *npieces = ptot + nlight;
+}
+
+// The j-th smallest trained topic of a staged word: the k with
+// P[k] <= j < P[k+1] (P[0] = 0 <= j < P[K] = L_w).
+__device__ __forceinline__ int fold_rank(const int32_t* P, int K, int j) {
+    int lo = 0, hi = K;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (P[mid] <= j) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The word phase of one token (the plain-proposal branch of fold_sweep):
+// accept against the frozen row, then M proposals from it.  kStaged: the row
+// is the warp's prefix array P; else direct loads of C_w and the sorted
+// topics.
+template <int M, bool kStaged>
+__device__ __forceinline__ void fold_word_token(const FoldArgs& f, const FoldWords& fw, const int4 rc, int it,
+                                                const int32_t* P, Checks& chk) {
+    const int K = f.K;
+    const uint32_t km = (uint32_t)K - 1u;
+    const int g = rc.x, j = rc.y, w = rc.w;
+    const uint32_t id = (uint32_t)rc.z;
+    if (!chk((int64_t)(uint32_t)g < fw.Nn && (uint32_t)w < (uint32_t)f.V, 1)) return;
+    const int32_t* row = f.Cw + (int64_t)w * K;
+    int wb = 0, Lw;
+    if (kStaged) {
+        Lw = P[K];
+    } else {
+        wb = __ldg(f.word_off + w);
+        Lw = __ldg(f.word_off + w + 1) - wb;
+    }
+    auto cw = [&](int k) { return kStaged ? P[k + 1] - P[k] : __ldg(row + k); };
+    const float Lwf = __int2float_rn(Lw);
+    const float LwG = __fadd_rn(Lwf, f.kbeta);
+    int32_t* prop = f.prop + (int64_t)g * M;
+    int s = min((uint32_t)f.z[g], km);
+    int cs = cw(s);
+    float ks = __ldg(f.ckb + s);
+    uint32_t r1[M], r2[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldWord, (uint32_t)(i + 1), id, f.rk);
+        r1[i] = r.y;
+        r2[i] = r.z;
+        const int t = (int)min((uint32_t)prop[i], km);
+        if (t != s) {
+            const int ct = cw(t);
+            const float kt = __ldg(f.ckb + t);
+            if (accept(r.x, cs, ct, f.beta, ks, kt)) {
+                s = t;
+                cs = ct;
+                ks = kt;
+            }
+        }
+    }
+    f.z[g] = s;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        int v;
+        if (Lw > 0 && coin(r1[i], Lwf, LwG)) {
+            const int jj = (int)dice(r2[i], (uint32_t)Lw);
+            v = kStaged ? fold_rank(P, K, jj) : __ldg(f.Zs + wb + jj);
+        } else {
+            v = (int)dice(r2[i], (uint32_t)K);
+        }
+        prop[i] = v;
+    }
+}
+
+// The word phase of sweep `it`: warp w takes a contiguous range of the
+// pieces (so consecutive pieces of one word are staged once).
+template <int M>
+__global__ void __launch_bounds__(kThreads) fold_word_kernel(FoldArgs f, FoldWords fw, int it) {
+    extern __shared__ __align__(16) int32_t wsm[];
+    const int lane = threadIdx.x & 31;
+    const int K = f.K;
+    int32_t* P = wsm + (threadIdx.x >> 5) * fw.pstride;
+    Checks chk;
+    const int np = *fw.npieces;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int p0 = (int)(np * gw / nw), p1 = (int)(np * (gw + 1) / nw);
+    int staged = -1;
+    for (int p = p0; p < p1; ++p) {
+        const int4 pc = fw.pieces[p];   // {word, first record, records, staged}
+        if (!chk(pc.y >= 0 && pc.z >= 0 && (int64_t)pc.y + pc.z <= fw.Nn, 2)) continue;
+        if (pc.w != 0 && fw.pstride > 0 && (uint32_t)pc.x < (uint32_t)f.V) {
+            if (pc.x != staged) {
+                // P[k + 1] = C_wk, then prefix sums: lane l sums its chunk of
+                // `per` entries (odd, so the lanes' chunks fall in distinct
+                // banks), a warp scan of the chunk sums, then the chunk.
+                const int32_t* row = f.Cw + (int64_t)pc.x * K;
+                __syncwarp();
+                for (int k = lane; k < K; k += 32) P[k + 1] = __ldg(row + k);
+                __syncwarp();
+                const int k0 = min(K, lane * fw.per), k1 = min(K, k0 + fw.per);
+                int sum = 0;
+                for (int k = k0; k < k1; ++k) sum += P[k + 1];
+                int x = sum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                    if (lane >= o) x += y;
+                }
+                int run = x - sum;
+                for (int k = k0; k < k1; ++k) {
+                    run += P[k + 1];
+                    P[k + 1] = run;
+                }
+                if (lane == 0) P[0] = 0;
+                __syncwarp();
+                staged = pc.x;
+            }
+            for (int i = lane; i < pc.z; i += 32) fold_word_token<M, true>(f, fw, fw.rec[pc.y + i], it, P, chk);
+        } else {
+            for (int i = lane; i < pc.z; i += 32) fold_word_token<M, false>(f, fw, fw.rec[pc.y + i], it, P, chk);
+        }
+    }
+    chk.publish(f.fault, kSiteFoldin);
+}
+
+// One launch per phase of the document side: mode bit 1 initialises z and
+// the proposals, bit 2 runs the document phase of sweep `it`, bit 4 writes
+// theta.  `counter` is this launch's own work counter (zero on entry).
+template <int M, bool kDense>
+__global__ void __launch_bounds__(kThreads) fold_doc_kernel(FoldArgs f, int tab_words, int it, int mode,
+                                                            int32_t* counter) {
+    extern __shared__ __align__(16) uint32_t fsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* tab = fsm + warp * tab_words;
+    Checks chk;
+    for (;;) {
+        int di = 0;
+        if (lane == 0) di = atomicAdd(counter, 1);
+        di = __shfl_sync(0xFFFFFFFFu, di, 0);
+        if (di >= f.Dn) break;
+        int d = f.order[di];
+        if (!chk(d >= 0 && d < f.Dn, 0)) d = 0;
+        const int b = f.doc_off[d];
+        int L = f.doc_off[d + 1] - b;
+        if (!chk(L >= 0 && L <= f.Lmax, 0)) L = 0;
+        FoldDoc doc;
+        doc.z = f.z + b;
+        doc.prop = f.prop + (int64_t)b * M;
+        doc.words = f.words + b;
+        doc.L = L;
+        doc.id = (uint32_t)f.ids[d];
+        doc.q = nullptr;
+        doc.atab = nullptr;
+        const uint32_t cap = kDense ? 0u : pow2_above((uint32_t)min(2 * max(L, 1), f.K));
+        const int words = kDense ? tab_words : (int)cap;
+        if (mode & 1) fold_init<M>(f, doc, lane);
+        if (mode & 2) fold_doc_phase<M, kDense, false>(f, doc, it, tab, words, cap, lane);
+        if ((mode & 4) && f.theta) fold_theta<kDense>(f, doc, f.theta + (int64_t)d * f.K, tab, words, cap, lane);
+    }
+    chk.publish(f.fault, kSiteFoldin);
+}
+
+int64_t fold_pieces_bound(int64_t Nn, int stage_min) {
+    return 2 * (Nn / kFoldPiece + 1) + Nn / std::max(stage_min, 1) + 2;
+}
+
+cudaError_t launch_fold_words_build(const FoldArgs& f, int64_t Nn, int stage_min, int32_t* cnt, int32_t* hc,
+                                    int32_t* lc, int32_t* pc, int32_t* cur, int32_t* scan_tmp, int4* rec,
+                                    int4* pieces, int32_t* npieces, int grid, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
+    const int64_t V = f.V;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)(V + 1) * 4, st);
+    if (e != cudaSuccess) return e;
+    if (Nn > 0) fw_count_kernel<<<grid, kThreads, 0, st>>>(f.words, Nn, cnt);
+    fw_class_kernel<<<grid, kThreads, 0, st>>>(cnt, V, stage_min, hc, lc, pc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_scan_exclusive(hc, V + 1, scan_tmp, st)) != cudaSuccess) return e;
+    if ((e = launch_scan_exclusive(lc, V + 1, scan_tmp, st)) != cudaSuccess) return e;
+    if ((e = launch_scan_exclusive(pc, V + 1, scan_tmp, st)) != cudaSuccess) return e;
+    fw_cursor_kernel<<<grid, kThreads, 0, st>>>(cnt, hc, lc, V, stage_min, cur);
+    if (f.Dn > 0) fw_scatter_kernel<<<grid, kThreads, 0, st>>>(f.doc_off, f.ids, f.words, f.Dn, Nn, f.V, cur, rec, f.fault);
+    fw_pieces_kernel<<<grid, kThreads, 0, st>>>(cnt, hc, lc, pc, V, stage_min, pieces, npieces);
+    return cudaGetLastError();
+}
+
+template <int M>
+static const void* fold_doc_ptr(bool dense) {
+    return dense ? (const void*)fold_doc_kernel<M, true> : (const void*)fold_doc_kernel<M, false>;
+}
+
+static const void* fold_doc_pick(int M, bool dense) {
+    switch (M) {
+        case 1: return fold_doc_ptr<1>(dense);
+        case 2: return fold_doc_ptr<2>(dense);
+        case 3: return fold_doc_ptr<3>(dense);
+        case 4: return fold_doc_ptr<4>(dense);
+        default: return nullptr;
+    }
+}
+
+static const void* fold_word_pick(int M) {
+    switch (M) {
+        case 1: return (const void*)fold_word_kernel<1>;
+        case 2: return (const void*)fold_word_kernel<2>;
+        case 3: return (const void*)fold_word_kernel<3>;
+        case 4: return (const void*)fold_word_kernel<4>;
+        default: return nullptr;
+    }
+}
+
+cudaError_t launch_fold_doc(const FoldArgs& f, int tab_words, int it, int mode, int32_t* counter, int grid,
+                            cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
+    if (f.Dn <= 0) return cudaSuccess;
+    const void* fn = fold_doc_pick(f.M, f.K <= kDenseMaxK);
+    const int warps = foldin_warps(tab_words);
+    if (!fn || warps < 1) return cudaErrorInvalidValue;
+    const int smem = warps * tab_words * 4;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    FoldArgs args = f;
+    int tw = tab_words, i = it, m = mode;
+    int32_t* cnt = counter;
+    void* params[] = {&args, &tw, &i, &m, &cnt};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(32 * warps), params, (size_t)smem, st);
+}
+
+int fold_word_smem(const FoldWords& fw) { return kWarps * fw.pstride * 4; }
+
+cudaError_t launch_fold_word(const FoldArgs& f, const FoldWords& fw, int it, int grid, cudaStream_t st) {
+    if (const cudaError_t g_ = launch_gate()) return g_;
+    if (fw.Nn <= 0) return cudaSuccess;
+    const void* fn = fold_word_pick(f.M);
+    if (!fn) return cudaErrorInvalidValue;
+    const int smem = fold_word_smem(fw);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    FoldArgs args = f;
+    FoldWords w = fw;
+    int i = it;
+    void* params[] = {&args, &w, &i};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), params, (size_t)smem, st);
+}
+
+int fold_doc_blocks_per_sm(int K, int M, int tab_words) {
+    const void* fn = fold_doc_pick(M, K <= kDenseMaxK);
+    const int warps = foldin_warps(tab_words);
+    if (!fn || warps < 1) return 0;
+    const int smem = warps * tab_words * 4;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, 32 * warps, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+int fold_word_blocks_per_sm(int M, const FoldWords& fw) {
+    const void* fn = fold_word_pick(M);
+    if (!fn) return 0;
+    const int smem = fold_word_smem(fw);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kThreads, smem) != cudaSuccess) return 0;
+    return n;
 }
 
 template <int M, bool kDense>

@@ -109,6 +109,29 @@ int foldin_warps(int tab_words);
 int foldin_blocks_per_sm(int K, int M, int tab_words);
 cudaError_t launch_foldin(const FoldArgs& f, int tab_words, int grid, cudaStream_t st);
 
+// Word-major fold-in (plain proposal; wl_foldin.cu): the requests' tokens
+// regrouped by word, in pieces of up to 256 tokens of one word (staged: the
+// word's frozen row is loaded once into the warp's shared memory) or of the
+// words with few tokens (direct loads).
+struct FoldWords {
+    const int4* rec;          // [Nn] {token index, position in its document, stream id, word}
+    const int4* pieces;       // {word or -1, first record, records, staged}
+    const int32_t* npieces;   // number of pieces (device)
+    int64_t Nn;
+    int pstride;              // ints of shared memory per warp for a staged row (0: no staging)
+    int per;                  // prefix-sum chunk per lane (odd)
+};
+constexpr int kFoldStageMaxK = 2048;   // staged rows above this K would cost too many resident warps
+int64_t fold_pieces_bound(int64_t Nn, int stage_min);
+cudaError_t launch_fold_words_build(const FoldArgs& f, int64_t Nn, int stage_min, int32_t* cnt, int32_t* hc,
+                                    int32_t* lc, int32_t* pc, int32_t* cur, int32_t* scan_tmp, int4* rec,
+                                    int4* pieces, int32_t* npieces, int grid, cudaStream_t st);
+cudaError_t launch_fold_doc(const FoldArgs& f, int tab_words, int it, int mode, int32_t* counter, int grid,
+                            cudaStream_t st);
+cudaError_t launch_fold_word(const FoldArgs& f, const FoldWords& fw, int it, int grid, cudaStream_t st);
+int fold_doc_blocks_per_sm(int K, int M, int tab_words);
+int fold_word_blocks_per_sm(int M, const FoldWords& fw);
+
 // Serving slots (continuous batching of fold-in requests): per slot
 // info = {token offset in the pool, L, sweeps done, stream id}; the pool holds
 // the active requests' word ids, z and proposals; theta (and, with the
@@ -201,6 +224,9 @@ int record_error(int code, const char* msg);
 // the word ids in word-major order ((b) after an odd number of passes,
 // token_sort_passes(V)).  scratch holds
 // token_sort_scratch(N) words.
+// In-place exclusive scan of n int32 entries; tmp holds scan_scratch_words(n).
+cudaError_t launch_scan_exclusive(int32_t* d, int64_t n, int32_t* tmp, cudaStream_t st);
+int64_t scan_scratch_words(int64_t n);
 cudaError_t launch_word_check(const int32_t* w, int64_t N, int32_t V, int32_t* bad, cudaStream_t st);
 cudaError_t launch_word_starts(const int32_t* keys_sorted, int64_t N, int32_t V, int32_t* start, cudaStream_t st);
 int token_sort_passes(int64_t V);

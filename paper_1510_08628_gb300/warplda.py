@@ -33,7 +33,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("batch_max_tokens", ctypes.c_int32), ("huge_chunk", ctypes.c_int32),
                 ("region_budget", ctypes.c_int32), ("doc_warp_max", ctypes.c_int32),
                 ("word_positioning", ctypes.c_int32), ("doc_batch_kernel", ctypes.c_int32),
-                ("cluster_max_tokens", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("cluster_max_tokens", ctypes.c_int32), ("foldin_kernel", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -140,7 +140,7 @@ def test_server_create_allocation_failures(gpu, learned):
     s = make()
     assert s.submit(7, c.doc_word[:50])
     got = []
-    for _ in range(4):   # 2 sweeps; a learned request joins one step after admission
+    for _ in range(2):   # 2 sweeps: the result comes with the second step
         s.step()
         ids, th = s.poll()
         got += [(int(i), t) for i, t in zip(ids, th)]
