@@ -486,19 +486,38 @@ def foldin_bench(gpu, c, wl, args, torch, stream):
     S = args.foldin_sweeps
     small = int(rq.doc_ptr[min(64, rq.D)])
     gpu.foldin(rq.doc_ptr[: min(64, rq.D) + 1], rq.doc_word[:small], sweeps=2, seed=1)  # model build
+    # the request CSR and theta in pinned host memory, as a server would hold them
+    dp = torch.from_numpy(rq.doc_ptr).pin_memory().numpy()
+    dw = torch.from_numpy(rq.doc_word).pin_memory().numpy()
+    th_buf = torch.empty((rq.D, wl.K), dtype=torch.float32, pin_memory=True).numpy()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gpu.profile(True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     start.record(stream)
-    th, _ = gpu.foldin(rq.doc_ptr, rq.doc_word, sweeps=S, seed=args.seed + 17, z=False)
+    th, _ = gpu.foldin(dp, dw, sweeps=S, seed=args.seed + 17, z=False, theta_out=th_buf)
     stop.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     dev_s = start.elapsed_time(stop) / 1000.0
+    kt = gpu.kernel_times()
+    gpu.profile(False)
+    # algorithmic bytes per token and sweep of the word-major phases: the
+    # document phase reads and writes z and the proposals (4 + 4M each way),
+    # the word phase streams a 16-byte record and reads and writes the same
+    alg = {"foldin_doc": 2 * (4 + 4 * wl.M), "foldin_word": 16 + 2 * (4 + 4 * wl.M)}
+    kernels = {}
+    for name, (n, ms) in kt.items():
+        e = {"launches": n, "total_ms": ms}
+        if name in alg and n > 0:
+            e["alg_bytes_per_token"] = alg[name]
+            e["gbs"] = alg[name] * rq.N * min(n, S) / (ms / 1e3) / 1e9
+        kernels[name] = e
     out = {"docs": rq.D, "tokens": rq.N, "sweeps": S, "K": wl.K, "M": wl.M,
            "docs_per_s": rq.D / wall, "tokens_sweeps_per_s": rq.N * S / wall, "seconds": wall,
-           "device_seconds": dev_s, "includes": "host checks + H2D of the CSR + fold-in kernel + "
-                                                 "D2H of theta (synchronous C ABI call)",
+           "device_seconds": dev_s, "includes": "host checks + H2D of the CSR + fold-in kernels + "
+                                                 "D2H of theta into pinned memory (synchronous C ABI call)",
+           "kernels": kernels,
            "proposal": "plain", "lengths": "lognormal of the workload, clipped to [20, 5000]",
            "kernel": ("one warp per document, all sweeps in one launch"
                       if (getattr(args, "_tuning", None) or {}).get("foldin_kernel") == 1 else

@@ -87,12 +87,14 @@ int cuda_fail(cudaError_t e, const char* what) {
 enum KernelClass {
     kcDocWarp, kcDocBatch, kcDocHugeHist, kcDocHugeAccept, kcDocHugeDraw,
     kcWordBatch, kcWordMegaHist, kcWordMegaAccept, kcWordMegaHistPost, kcWordMegaDraw,
-    kcCountCk, kcFinalize, kcZero, kcDocPipe, kcWordCluster, kcCount
+    kcCountCk, kcFinalize, kcZero, kcDocPipe, kcWordCluster,
+    kcFoldBuild, kcFoldDoc, kcFoldWord, kcFoldin, kcCount
 };
 const char* kClassNames[kcCount] = {
     "doc_warp", "doc_batch", "doc_huge_hist", "doc_huge_accept", "doc_huge_draw",
     "word_batch", "word_mega_hist", "word_mega_accept", "word_mega_hist_post", "word_mega_draw",
-    "count_ck", "finalize_ck", "zero_rows", "doc_pipe", "word_cluster"};
+    "count_ck", "finalize_ck", "zero_rows", "doc_pipe", "word_cluster",
+    "foldin_build", "foldin_doc", "foldin_word", "foldin_kernel"};
 // topics: packed hash entries hold (topic + 1) << 12 in 32 bits
 constexpr int kMaxTopics = (1 << 20) - 1;
 // tokens of a pipelined document batch (at most 4 * 256 - 3; at most 509
@@ -104,6 +106,15 @@ constexpr int kPipeTokens = WL_PIPE_TOKENS;
 static_assert(kPipeTokens >= 1 && kPipeTokens <= 4 * kThreads - 3, "pipelined batch size");
 // cluster sizes of the cluster tier: 1, 2, 4, 8, 16 blocks
 constexpr int kClusterClasses = 5;
+// ranges of the multi-pass tier with dense rows, per SM: enough that the
+// last wave of blocks is short (4 per SM left a 1.33-wave tail with three
+// resident blocks per SM: 7.7 against 5.8 ms for the PubMed-shaped accept)
+#ifndef WL_RANGES_PER_SM
+#define WL_RANGES_PER_SM 32
+#endif
+constexpr int kRangesPerSm = WL_RANGES_PER_SM;
+// serving: documents of at least this many tokens are swept by a block
+constexpr int kServeBlockMin = 512;
 // word-major fold-in: words with at least this many request tokens have
 // their frozen row staged in shared memory, the others keep direct loads
 #ifndef WL_FOLD_STAGE_MIN
@@ -465,6 +476,28 @@ int launch_rec(warplda_ctx* c, int cls, cudaError_t (*fn)(warplda_ctx*, void*), 
     return WARPLDA_OK;
 }
 
+// A launch outside the sweep (fold-in), timed like launch_rec.
+template <class F>
+int launch_timed(warplda_ctx* c, int cls, F&& fn) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->prof) {
+        WL_CU(cudaEventCreate(&a), "cudaEventCreate");
+        WL_CU(cudaEventCreate(&b), "cudaEventCreate");
+        WL_CU(cudaEventRecord(a, c->st), "cudaEventRecord");
+    }
+    const cudaError_t e = fn();
+    if (e != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        return cuda_fail(e, kClassNames[cls]);
+    }
+    if (c->prof) {
+        WL_CU(cudaEventRecord(b, c->st), "cudaEventRecord");
+        c->recs.push_back(Rec{cls, a, b});
+    }
+    return WARPLDA_OK;
+}
+
 PhaseArgs phase_args(warplda_ctx* c, bool doc, uint32_t iter) {
     PhaseArgs a;
     a.z = c->z;
@@ -754,6 +787,23 @@ int upload_docs(warplda_ctx* c, FoldBuffers& buf, int64_t Dn, const int64_t* doc
     return WARPLDA_OK;
 }
 
+// First position of a word id outside [0, V), or -1.  The scan is a
+// branch-free OR over blocks of ids (one unsigned compare each, which the
+// compiler vectorises); the position is searched only in a bad block.
+int64_t first_bad_word(const int32_t* w, int64_t n, int64_t V) {
+    const uint32_t v = (uint32_t)std::min<int64_t>(V, 0x7FFFFFFF);
+    constexpr int64_t kBlock = 4096;
+    for (int64_t b = 0; b < n; b += kBlock) {
+        const int64_t e = std::min(n, b + kBlock);
+        uint32_t bad = 0;
+        for (int64_t p = b; p < e; ++p) bad |= (uint32_t)((uint32_t)w[p] >= v);
+        if (bad)
+            for (int64_t p = b; p < e; ++p)
+                if ((uint32_t)w[p] >= v) return p;
+    }
+    return -1;
+}
+
 int check_docs(const warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word) {
     if (Dn < 0 || !doc_ptr || doc_ptr[0] != 0) return fail(WARPLDA_EINVAL, "bad document CSR");
     for (int64_t d = 0; d < Dn; ++d)
@@ -761,9 +811,8 @@ int check_docs(const warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const i
     const int64_t Nn = doc_ptr[Dn];
     if (Nn > (int64_t)0x7FFFFFF0) return fail(WARPLDA_EINVAL, "too many tokens");
     if (Nn > 0 && !doc_word) return fail(WARPLDA_EINVAL, "null doc_word");
-    for (int64_t p = 0; p < Nn; ++p)
-        if (doc_word[p] < 0 || (int64_t)doc_word[p] >= c->V)
-            return fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", doc_word[p], (long long)p);
+    const int64_t p = first_bad_word(doc_word, Nn, c->V);
+    if (p >= 0) return fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", doc_word[p], (long long)p);
     return WARPLDA_OK;
 }
 
@@ -1164,11 +1213,12 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         for (int64_t w = V - 1; w >= 0; --w) c->word_ptr_h[w] = wstart[w] >= 0 ? wstart[w] : c->word_ptr_h[w + 1];
     }
     for (int64_t w = 0; w <= V; ++w) word_off[w] = (int32_t)c->word_ptr_h[w];
-    // dense rows live in shared memory: one range per block slot suffices.
+    // dense rows live in shared memory: a few ranges per block slot, each
+    // long enough that its row load is a small part of it.
     // Sparse rows live in global memory: ranges of ~4K tokens taken in
     // order keep the rows that the resident blocks touch at once few enough
     // to stay in L2.
-    const int ranges_target = c->sparse ? (1 << 30) : 4 * c->sms;
+    const int ranges_target = c->sparse ? (1 << 30) : kRangesPerSm * c->sms;
     build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->dregion, c->chunk, ranges_target, &c->docs,
                c->doc_pipe ? kDocSegs : kSegsMax);
     // with tuning cluster_max_tokens, words too long for a block batch but
@@ -1674,9 +1724,10 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
     const int64_t Nn = doc_ptr[Dn];
     if (Nn > (int64_t)0x7FFFFFF0) return fail(WARPLDA_EINVAL, "too many fold-in tokens");
     if (Nn > 0 && !doc_word) return fail(WARPLDA_EINVAL, "null doc_word");
-    for (int64_t p = 0; p < Nn; ++p)
-        if (doc_word[p] < 0 || (int64_t)doc_word[p] >= c->V)
-            return fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", doc_word[p], (long long)p);
+    {
+        const int64_t p = first_bad_word(doc_word, Nn, c->V);
+        if (p >= 0) return fail(WARPLDA_EINVAL, "word id %d at %lld outside [0, V)", doc_word[p], (long long)p);
+    }
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
 
     // the frozen model: C_w prefix rows and c_k of the current state
@@ -1791,29 +1842,37 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
         fw.Nn = Nn;
         fw.pstride = stage ? ((K + 1 + 3) & ~3) : 0;
         fw.per = ((K + 31) / 32) | 1;
-        WL_CU(launch_fold_words_build(f, Nn, stage_min, cnt, hc, lc, pc, cur, tmp, rec, pieces, npieces,
-                                      4 * c->sms, c->st),
-              "fold-in word order");
+        int rc = launch_timed(c, kcFoldBuild, [&] {
+            return launch_fold_words_build(f, Nn, stage_min, cnt, hc, lc, pc, cur, tmp, rec, pieces, npieces,
+                                           4 * c->sms, c->st);
+        });
+        if (rc) return rc;
         const int dper = fold_doc_blocks_per_sm(K, M, tab_words);
         const int wper = fold_word_blocks_per_sm(M, fw);
         if (dper < 1 || wper < 1) return fail(WARPLDA_EINVAL, "fold-in tables do not fit in shared memory");
         const int dgrid = (int)std::min<int64_t>((int64_t)dper * c->sms, (Dn + warps - 1) / warps + 1);
         const int wgrid = wper * c->sms;
+        auto doc_launch = [&](int it, int mode) {
+            return launch_timed(c, kcFoldDoc, [&] {
+                return launch_fold_doc(f, tab_words, it, mode, counters + it - 1, dgrid, c->st);
+            });
+        };
         if (sweeps == 0) {
-            WL_CU(launch_fold_doc(f, tab_words, 1, 1 | 4, counters, dgrid, c->st), "fold-in");
+            if ((rc = doc_launch(1, 1 | 4))) return rc;
         } else {
             for (int it = 1; it <= sweeps; ++it) {
-                WL_CU(launch_fold_doc(f, tab_words, it, (it == 1 ? 1 : 0) | 2, counters + it - 1, dgrid, c->st),
-                      "fold-in document phase");
-                WL_CU(launch_fold_word(f, fw, it, wgrid, c->st), "fold-in word phase");
+                if ((rc = doc_launch(it, (it == 1 ? 1 : 0) | 2))) return rc;
+                rc = launch_timed(c, kcFoldWord, [&] { return launch_fold_word(f, fw, it, wgrid, c->st); });
+                if (rc) return rc;
             }
-            if (theta_out) WL_CU(launch_fold_doc(f, tab_words, sweeps + 1, 4, counters + sweeps, dgrid, c->st), "fold-in theta");
+            if (theta_out && (rc = doc_launch(sweeps + 1, 4))) return rc;
         }
     } else {
         const int per_sm = foldin_blocks_per_sm(K, M, tab_words);
         if (per_sm < 1) return fail(WARPLDA_EINVAL, "fold-in tables do not fit in shared memory");
         const int grid = (int)std::min<int64_t>((int64_t)per_sm * c->sms, (Dn + warps - 1) / warps + 1);
-        WL_CU(launch_foldin(f, tab_words, grid, c->st), "fold-in");
+        const int rc = launch_timed(c, kcFoldin, [&] { return launch_foldin(f, tab_words, grid, c->st); });
+        if (rc) return rc;
     }
     if (z_out && Nn > 0)
         WL_CU(cudaMemcpyAsync(z_out, d_z, (size_t)Nn * 4, cudaMemcpyDeviceToHost, c->st), "copy z");
@@ -2079,7 +2138,7 @@ int warplda_server_create(warplda_ctx* c, int32_t slots, int64_t pool_tokens, in
     };
     if ((rc = salloc(s, &s->d_info, slots)) || (rc = salloc(s, &s->d_active, slots)) ||
         (rc = salloc(s, &s->d_z, pool_tokens + 4)) || (rc = salloc(s, &s->d_prop, (pool_tokens + 4) * M)) ||
-        (rc = salloc(s, &s->d_words, pool_tokens + 4)) || (rc = salloc(s, &s->d_counter, 4)) ||
+        (rc = salloc(s, &s->d_words, pool_tokens + 4)) || (rc = salloc(s, &s->d_counter, 8)) ||
         (rc = salloc(s, &s->d_fin_theta, (int64_t)slots * K)) || (rc = salloc(s, &s->d_fin_slot, slots)) ||
         (rc = salloc(s, &s->d_req, slots)) || (rc = salloc(s, &s->d_src, slots)))
         return bail(rc);
@@ -2163,11 +2222,21 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     }
     if (active_out) *active_out = (int32_t)(active.size() + fresh.size());
     if (active.empty() && fresh.empty()) return WARPLDA_OK;
-    // work counters of the two launches [0], [2] and the shared count of
-    // finished rows [1]; zeroed before the side stream is released
-    WL_CU(cudaMemsetAsync(s->d_counter, 0, 16, c->st), "reset counters");
+    // a step lasts as long as its longest document: documents of at least
+    // kServeBlockMin tokens are swept by a whole block each.  Upload order:
+    // running short, running long, new short, new long.
+    const bool blocks = foldin_warps(s->tab_words) >= 4;
+    std::vector<int32_t> lists[4];
+    for (int32_t i : active) lists[blocks && s->slots[i].L >= kServeBlockMin ? 1 : 0].push_back(i);
+    for (int32_t i : fresh) lists[blocks && s->slots[i].L >= kServeBlockMin ? 3 : 2].push_back(i);
+    std::vector<int32_t> upload;
+    for (const auto& l : lists) upload.insert(upload.end(), l.begin(), l.end());
+    // counters: short-document work [0] (running) and [2] (new), long
+    // [3] and [4], and the shared count of finished rows [1]; zeroed
+    // before the side stream is released
+    WL_CU(cudaMemsetAsync(s->d_counter, 0, 32, c->st), "reset counters");
     int64_t act_off = 0, sl_off = 0;
-    int rc = server_admit(s, active, &act_off, &sl_off);
+    int rc = server_admit(s, upload, &act_off, &sl_off);
     if (rc) return rc;
     FoldArgs f = server_args(s);
     ServeSlots sl{};
@@ -2182,19 +2251,27 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     sl.fin_count = s->d_counter + 1;
     sl.q = s->d_q;
     sl.atab = s->d_atab;
-    if (!active.empty()) {
-        sl.active = s->d_staged + act_off;
-        sl.nactive = (int)active.size();
-        const int grid = (int)std::min<int64_t>(s->grid, ((int64_t)active.size() + kWarps - 1) / kWarps + 1);
-        WL_CU(launch_serve(f, sl, s->tab_words, grid, c->st), "serve");
-    }
+    const int warps = foldin_warps(s->tab_words);
+    // one launch over a short and a long list starting at `off` in the upload
+    auto serve = [&](int which, int64_t off, cudaStream_t st) -> int {
+        const int ns = (int)lists[which].size(), nl = (int)lists[which + 1].size();
+        if (ns + nl == 0) return WARPLDA_OK;
+        FoldArgs fa = f;
+        fa.counter = s->d_counter + (which == 0 ? 0 : 2);
+        ServeSlots a = sl;
+        a.active = s->d_staged + off;
+        a.nactive = ns;
+        a.long_active = s->d_staged + off + ns;
+        a.nlong = nl;
+        a.long_counter = s->d_counter + (which == 0 ? 3 : 4);
+        a.long_blocks = nl > 0 ? (int)std::min<int64_t>(nl, std::max(1, s->grid / 2)) : 0;
+        const int short_blocks = ns > 0 ? (int)std::min<int64_t>(s->grid, ((int64_t)ns + warps - 1) / warps) : 0;
+        WL_CU(launch_serve(fa, a, s->tab_words, a.long_blocks + short_blocks, st), "serve");
+        return WARPLDA_OK;
+    };
+    if ((rc = serve(0, act_off, c->st))) return rc;
     if (!fresh.empty()) {
-        FoldArgs fs = f;
-        fs.counter = s->d_counter + 2;
-        sl.active = s->d_staged + sl_off;
-        sl.nactive = (int)fresh.size();
-        const int grid = (int)std::min<int64_t>(s->grid, ((int64_t)fresh.size() + kWarps - 1) / kWarps + 1);
-        WL_CU(launch_serve(fs, sl, s->tab_words, grid, s->side), "serve new requests");
+        if ((rc = serve(2, act_off + (int64_t)(lists[0].size() + lists[1].size()), s->side))) return rc;
         WL_CU(cudaEventRecord(s->admitted, s->side), "record admission");
         WL_CU(cudaStreamWaitEvent(c->st, s->admitted, 0), "wait admission");
     }

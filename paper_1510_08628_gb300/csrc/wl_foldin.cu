@@ -86,6 +86,29 @@ __device__ __forceinline__ int fold_count(const uint32_t* tab, uint32_t cap, boo
                  : table_get(tab, cap, (uint32_t)k);
 }
 
+// The threads that sweep one document together: one warp, or (long
+// documents in serving) the whole block.
+struct WarpGroup {
+    int lane;
+    __device__ __forceinline__ int rank() const { return lane; }
+    __device__ __forceinline__ int size() const { return 32; }
+    __device__ __forceinline__ void sync() const { __syncwarp(); }
+    __device__ __forceinline__ int bcast(int v) const { return __shfl_sync(0xFFFFFFFFu, v, 0); }
+};
+struct BlockGroup {
+    __device__ __forceinline__ int rank() const { return (int)threadIdx.x; }
+    __device__ __forceinline__ int size() const { return (int)blockDim.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+    __device__ __forceinline__ int bcast(int v) const {
+        __shared__ int s_v;
+        if (threadIdx.x == 0) s_v = v;
+        __syncthreads();
+        const int r = s_v;
+        __syncthreads();
+        return r;
+    }
+};
+
 // One document's state: its tokens' word ids, z and proposals (document
 // order), its stream id, and (learned proposal) its proposal row and alias
 // table.
@@ -99,40 +122,40 @@ struct FoldDoc {
     const int2* atab;
 };
 
-// The warp's count table of the document's current z (dense, or a hash of
+// The group's count table of the document's current z (dense, or a hash of
 // capacity cap).
-template <bool kDense>
+template <bool kDense, class G>
 __device__ __forceinline__ void fold_table(uint32_t* tab, int words, uint32_t cap, const FoldDoc& doc,
-                                           uint32_t km, int lane) {
-    for (int i = lane; i < words; i += 32) tab[i] = 0u;
-    __syncwarp();
-    for (int j = lane; j < doc.L; j += 32) {
+                                           uint32_t km, const G& g) {
+    for (int i = g.rank(); i < words; i += g.size()) tab[i] = 0u;
+    g.sync();
+    for (int j = g.rank(); j < doc.L; j += g.size()) {
         const uint32_t k = min((uint32_t)doc.z[j], km);
         if (kDense) atomicAdd(&tab[k >> 1], (k & 1) ? 65536u : 1u);
         else table_add(tab, cap, k);
     }
-    __syncwarp();
+    g.sync();
 }
 
 // Initialisation: z = Dice(K), proposals = z.
-template <int M>
-__device__ __forceinline__ void fold_init(const FoldArgs& f, const FoldDoc& doc, int lane) {
-    for (int j = lane; j < doc.L; j += 32) {
+template <int M, class G>
+__device__ __forceinline__ void fold_init(const FoldArgs& f, const FoldDoc& doc, const G& g) {
+    for (int j = g.rank(); j < doc.L; j += g.size()) {
         const uint4 r = draw((uint32_t)j, 0u, kPhaseFoldInit, 0u, doc.id, f.rk);
         const int z0 = (int)dice(r.x, (uint32_t)f.K);
 #pragma unroll
         for (int i = 0; i < M; ++i) doc.prop[j * M + i] = z0;
         doc.z[j] = z0;
     }
-    __syncwarp();
+    g.sync();
 }
 
 // The document phase of sweep `it` of one document.  kLearned: the learned
 // document proposal (the encoder's q through its alias table) replaces
 // positioning.
-template <int M, bool kDense, bool kLearned>
+template <int M, bool kDense, bool kLearned, class G>
 __device__ void fold_doc_phase(const FoldArgs& f, const FoldDoc& doc, int it, uint32_t* tab, int words,
-                               uint32_t cap, int lane) {
+                               uint32_t cap, const G& g) {
     const int K = f.K, L = doc.L;
     const uint32_t km = (uint32_t)K - 1u;
     int32_t* z = doc.z;
@@ -140,8 +163,8 @@ __device__ void fold_doc_phase(const FoldArgs& f, const FoldDoc& doc, int it, ui
     const float Lf = __int2float_rn(L);
     const float LG = __fadd_rn(Lf, f.abar);
     // document phase: accept with the phase-start c_d ...
-    fold_table<kDense>(tab, words, cap, doc, km, lane);
-    for (int j = lane; j < L; j += 32) {
+    fold_table<kDense>(tab, words, cap, doc, km, g);
+    for (int j = g.rank(); j < L; j += g.size()) {
         int s = min((uint32_t)z[j], km);
         int cs = fold_count(tab, cap, kDense, s);
         float ks = __ldg(f.ckb + s);
@@ -161,10 +184,10 @@ __device__ void fold_doc_phase(const FoldArgs& f, const FoldDoc& doc, int it, ui
         }
         z[j] = s;
     }
-    __syncwarp();
+    g.sync();
     // ... then positioning over the post-acceptance z_d (or draws from the
     // learned proposal's alias table)
-    for (int j = lane; j < L; j += 32) {
+    for (int j = g.rank(); j < L; j += g.size()) {
 #pragma unroll
         for (int i = 0; i < M; ++i) {
             const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldDoc, (uint32_t)(i + 1), doc.id, f.rk);
@@ -177,7 +200,7 @@ __device__ void fold_doc_phase(const FoldArgs& f, const FoldDoc& doc, int it, ui
             }
         }
     }
-    __syncwarp();
+    g.sync();
 }
 
 // Sweep `it` of one document: the document phase, then the word phase
@@ -185,18 +208,18 @@ __device__ void fold_doc_phase(const FoldArgs& f, const FoldDoc& doc, int it, ui
 // proposal with the independence-sampler rate min{1, p(t) q(s) / (p(s) q(t))}
 // of Alg. 1, p(k) = (C_dk + alpha)(C_wk + beta)/(c_k + beta_bar) with the word
 // phase's phase-start c_d (the oracle's readings L6-L7).
-template <int M, bool kDense, bool kLearned>
+template <int M, bool kDense, bool kLearned, class G>
 __device__ void fold_sweep(const FoldArgs& f, const FoldDoc& doc, int it, uint32_t* tab, int words,
-                           uint32_t cap, Checks& chk, int lane) {
+                           uint32_t cap, Checks& chk, const G& g) {
     const int K = f.K, L = doc.L;
     const uint32_t km = (uint32_t)K - 1u;
     int32_t* z = doc.z;
     int32_t* prop = doc.prop;
-    fold_doc_phase<M, kDense, kLearned>(f, doc, it, tab, words, cap, lane);
-    if (kLearned) fold_table<kDense>(tab, words, cap, doc, km, lane);   // the word phase's phase-start c_d
+    fold_doc_phase<M, kDense, kLearned>(f, doc, it, tab, words, cap, g);
+    if (kLearned) fold_table<kDense>(tab, words, cap, doc, km, g);   // the word phase's phase-start c_d
     // word phase against the frozen rows: accept, then a proposal from the
     // token's frozen row (one Philox block per step)
-    for (int j = lane; j < L; j += 32) {
+    for (int j = g.rank(); j < L; j += g.size()) {
         int w = doc.words[j];
         if (!chk((uint32_t)w < (uint32_t)f.V, 1)) w = 0;
         const int32_t* row = f.Cw + (int64_t)w * K;
@@ -248,18 +271,18 @@ __device__ void fold_sweep(const FoldArgs& f, const FoldDoc& doc, int it, uint32
                                   ? __ldg(f.Zs + wb + (int)dice(r2[i], (uint32_t)Lw))
                                   : (int)dice(r2[i], (uint32_t)K);
     }
-    __syncwarp();
+    g.sync();
 }
 
 // theta (Eq. 4) of the document's current z.
-template <bool kDense>
+template <bool kDense, class G>
 __device__ __forceinline__ void fold_theta(const FoldArgs& f, const FoldDoc& doc, float* th, uint32_t* tab,
-                                           int words, uint32_t cap, int lane) {
-    fold_table<kDense>(tab, words, cap, doc, (uint32_t)f.K - 1u, lane);
+                                           int words, uint32_t cap, const G& g) {
+    fold_table<kDense>(tab, words, cap, doc, (uint32_t)f.K - 1u, g);
     const float den = __fadd_rn(__int2float_rn(doc.L), f.abar);
-    for (int k = lane; k < f.K; k += 32)
+    for (int k = g.rank(); k < f.K; k += g.size())
         th[k] = __fdiv_rn(__fadd_rn(__int2float_rn(fold_count(tab, cap, kDense, k)), f.alpha), den);
-    __syncwarp();
+    g.sync();
 }
 
 template <int M, bool kDense, bool kLearned>
@@ -289,57 +312,79 @@ __global__ void __launch_bounds__(kThreads) foldin_kernel(FoldArgs f, int tab_wo
         doc.atab = kLearned ? f.atab + (int64_t)d * K : nullptr;
         const uint32_t cap = kDense ? 0u : pow2_above((uint32_t)min(2 * max(L, 1), K));
         const int words = kDense ? tab_words : (int)cap;
-        fold_init<M>(f, doc, lane);
-        for (int it = 1; it <= f.sweeps; ++it) fold_sweep<M, kDense, kLearned>(f, doc, it, tab, words, cap, chk, lane);
-        if (f.theta) fold_theta<kDense>(f, doc, f.theta + (int64_t)d * K, tab, words, cap, lane);
+        const WarpGroup wg{lane};
+        fold_init<M>(f, doc, wg);
+        for (int it = 1; it <= f.sweeps; ++it) fold_sweep<M, kDense, kLearned>(f, doc, it, tab, words, cap, chk, wg);
+        if (f.theta) fold_theta<kDense>(f, doc, f.theta + (int64_t)d * K, tab, words, cap, wg);
     }
     chk.publish(f.fault, kSiteFoldin);
 }
 
 // Serving: one launch advances every active slot by one sweep (a slot's
-// first launch initialises it; its last writes theta).  Slots are taken by
-// warps from a work counter.
+// first launch initialises it; its last writes theta).  The step lasts as
+// long as its longest document takes, so long documents (sl.long_active)
+// are swept by a whole block each, from the first sl.long_blocks blocks;
+// the other blocks' warps take one short document each.  Slots are handed
+// out by work counters.
+template <int M, bool kDense, bool kLearned, class G>
+__device__ __forceinline__ void serve_slot(const FoldArgs& f, const ServeSlots& sl, int s, uint32_t* tab,
+                                           int tab_words, Checks& chk, const G& g) {
+    const int K = f.K;
+    if (!chk(s >= 0 && s < sl.nslots, 0)) return;
+    const int4 info = sl.info[s];   // {token offset, L, sweeps done, stream id}
+    const int L = info.y;
+    if (!chk(info.x >= 0 && L >= 0 && L <= f.Lmax && (int64_t)info.x + L <= sl.pool_tokens, 0)) return;
+    FoldDoc doc;
+    doc.z = sl.z + info.x;
+    doc.prop = sl.prop + (int64_t)info.x * M;
+    doc.words = sl.words + info.x;
+    doc.L = L;
+    doc.id = (uint32_t)info.w;
+    doc.q = kLearned ? sl.q + (int64_t)s * K : nullptr;
+    doc.atab = kLearned ? sl.atab + (int64_t)s * K : nullptr;
+    const uint32_t cap = kDense ? 0u : pow2_above((uint32_t)min(2 * max(L, 1), K));
+    const int words = kDense ? tab_words : (int)cap;
+    const int done = info.z;
+    if (done == 0) fold_init<M>(f, doc, g);
+    fold_sweep<M, kDense, kLearned>(f, doc, done + 1, tab, words, cap, chk, g);
+    if (done + 1 >= f.sweeps) {
+        // finished: theta into the next row of the step's output
+        int oi = 0;
+        if (g.rank() == 0) oi = atomicAdd(sl.fin_count, 1);
+        oi = g.bcast(oi);
+        if (chk(oi < sl.nslots, 0)) {
+            fold_theta<kDense>(f, doc, sl.fin_theta + (int64_t)oi * K, tab, words, cap, g);
+            if (g.rank() == 0) sl.fin_slot[oi] = s;
+        }
+    }
+    if (g.rank() == 0) sl.info[s].z = done + 1;
+}
+
 template <int M, bool kDense, bool kLearned>
 __global__ void __launch_bounds__(kThreads) serve_kernel(FoldArgs f, ServeSlots sl, int tab_words) {
     extern __shared__ __align__(16) uint32_t fsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* tab = fsm + warp * tab_words;
-    const int K = f.K;
     Checks chk;
-    for (;;) {
-        int si = 0;
-        if (lane == 0) si = atomicAdd(f.counter, 1);
-        si = __shfl_sync(0xFFFFFFFFu, si, 0);
-        if (si >= sl.nactive) break;
-        int s = sl.active[si];
-        if (!chk(s >= 0 && s < sl.nslots, 0)) continue;
-        const int4 info = sl.info[s];   // {token offset, L, sweeps done, stream id}
-        int L = info.y;
-        if (!chk(info.x >= 0 && L >= 0 && L <= f.Lmax && (int64_t)info.x + L <= sl.pool_tokens, 0)) continue;
-        FoldDoc doc;
-        doc.z = sl.z + info.x;
-        doc.prop = sl.prop + (int64_t)info.x * M;
-        doc.words = sl.words + info.x;
-        doc.L = L;
-        doc.id = (uint32_t)info.w;
-        doc.q = kLearned ? sl.q + (int64_t)s * K : nullptr;
-        doc.atab = kLearned ? sl.atab + (int64_t)s * K : nullptr;
-        const uint32_t cap = kDense ? 0u : pow2_above((uint32_t)min(2 * max(L, 1), K));
-        const int words = kDense ? tab_words : (int)cap;
-        const int done = info.z;
-        if (done == 0) fold_init<M>(f, doc, lane);
-        fold_sweep<M, kDense, kLearned>(f, doc, done + 1, tab, words, cap, chk, lane);
-        if (done + 1 >= f.sweeps) {
-            // finished: theta into the next row of the step's output
-            int oi = 0;
-            if (lane == 0) oi = atomicAdd(sl.fin_count, 1);
-            oi = __shfl_sync(0xFFFFFFFFu, oi, 0);
-            if (chk(oi < sl.nslots, 0)) {
-                fold_theta<kDense>(f, doc, sl.fin_theta + (int64_t)oi * K, tab, words, cap, lane);
-                if (lane == 0) sl.fin_slot[oi] = s;
-            }
+    if ((int)blockIdx.x < sl.long_blocks) {
+        const BlockGroup bg;
+        for (;;) {
+            int si = 0;
+            if (threadIdx.x == 0) si = atomicAdd(sl.long_counter, 1);
+            si = bg.bcast(si);
+            if (si >= sl.nlong) break;
+            serve_slot<M, kDense, kLearned>(f, sl, sl.long_active[si], fsm, tab_words, chk, bg);
+            __syncthreads();   // the table is the next document's
         }
-        if (lane == 0) sl.info[s].z = done + 1;
+    } else {
+        const WarpGroup wg{lane};
+        uint32_t* tab = fsm + warp * tab_words;
+        for (;;) {
+            int si = 0;
+            if (lane == 0) si = atomicAdd(f.counter, 1);
+            si = __shfl_sync(0xFFFFFFFFu, si, 0);
+            if (si >= sl.nactive) break;
+            serve_slot<M, kDense, kLearned>(f, sl, sl.active[si], tab, tab_words, chk, wg);
+        }
     }
     chk.publish(f.fault, kSiteFoldin);
 }
@@ -460,18 +505,53 @@ __device__ __forceinline__ int fold_rank(const int32_t* P, int K, int j) {
     return lo;
 }
 
+// A token of the word phase with its state loaded: record {token index,
+// position in its document, stream id, word}, z and proposals.
+template <int M>
+struct WordTok {
+    int4 rc;
+    int z;
+    int p[M];
+    bool ok;
+};
+
+template <int M>
+__device__ __forceinline__ WordTok<M> fold_word_load(const FoldArgs& f, const FoldWords& fw, const int4 rc,
+                                                     Checks& chk) {
+    WordTok<M> t;
+    t.rc = rc;
+    t.ok = chk((int64_t)(uint32_t)rc.x < fw.Nn && (uint32_t)rc.w < (uint32_t)f.V, 1);
+    const int64_t g = t.ok ? rc.x : 0;
+    t.z = f.z[g];
+    if (M == 2) {
+        const int2 v = *reinterpret_cast<const int2*>(f.prop + g * 2);
+        t.p[0] = v.x;
+        t.p[M - 1] = v.y;
+    } else if (M == 4) {
+        const int4 v = *reinterpret_cast<const int4*>(f.prop + g * 4);
+        t.p[0] = v.x;
+        t.p[1 % M] = v.y;
+        t.p[2 % M] = v.z;
+        t.p[M - 1] = v.w;
+    } else {
+#pragma unroll
+        for (int i = 0; i < M; ++i) t.p[i] = f.prop[g * M + i];
+    }
+    return t;
+}
+
 // The word phase of one token (the plain-proposal branch of fold_sweep):
 // accept against the frozen row, then M proposals from it.  kStaged: the row
 // is the warp's prefix array P; else direct loads of C_w and the sorted
 // topics.
 template <int M, bool kStaged>
-__device__ __forceinline__ void fold_word_token(const FoldArgs& f, const FoldWords& fw, const int4 rc, int it,
-                                                const int32_t* P, Checks& chk) {
+__device__ __forceinline__ void fold_word_apply(const FoldArgs& f, const WordTok<M>& tk, int it,
+                                                const int32_t* P) {
+    if (!tk.ok) return;
     const int K = f.K;
     const uint32_t km = (uint32_t)K - 1u;
-    const int g = rc.x, j = rc.y, w = rc.w;
-    const uint32_t id = (uint32_t)rc.z;
-    if (!chk((int64_t)(uint32_t)g < fw.Nn && (uint32_t)w < (uint32_t)f.V, 1)) return;
+    const int g = tk.rc.x, j = tk.rc.y, w = tk.rc.w;
+    const uint32_t id = (uint32_t)tk.rc.z;
     const int32_t* row = f.Cw + (int64_t)w * K;
     int wb = 0, Lw;
     if (kStaged) {
@@ -483,8 +563,7 @@ __device__ __forceinline__ void fold_word_token(const FoldArgs& f, const FoldWor
     auto cw = [&](int k) { return kStaged ? P[k + 1] - P[k] : __ldg(row + k); };
     const float Lwf = __int2float_rn(Lw);
     const float LwG = __fadd_rn(Lwf, f.kbeta);
-    int32_t* prop = f.prop + (int64_t)g * M;
-    int s = min((uint32_t)f.z[g], km);
+    int s = min((uint32_t)tk.z, km);
     int cs = cw(s);
     float ks = __ldg(f.ckb + s);
     uint32_t r1[M], r2[M];
@@ -493,7 +572,7 @@ __device__ __forceinline__ void fold_word_token(const FoldArgs& f, const FoldWor
         const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldWord, (uint32_t)(i + 1), id, f.rk);
         r1[i] = r.y;
         r2[i] = r.z;
-        const int t = (int)min((uint32_t)prop[i], km);
+        const int t = (int)min((uint32_t)tk.p[i], km);
         if (t != s) {
             const int ct = cw(t);
             const float kt = __ldg(f.ckb + t);
@@ -505,21 +584,55 @@ __device__ __forceinline__ void fold_word_token(const FoldArgs& f, const FoldWor
         }
     }
     f.z[g] = s;
+    int out[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-        int v;
         if (Lw > 0 && coin(r1[i], Lwf, LwG)) {
             const int jj = (int)dice(r2[i], (uint32_t)Lw);
-            v = kStaged ? fold_rank(P, K, jj) : __ldg(f.Zs + wb + jj);
+            out[i] = kStaged ? fold_rank(P, K, jj) : __ldg(f.Zs + wb + jj);
         } else {
-            v = (int)dice(r2[i], (uint32_t)K);
+            out[i] = (int)dice(r2[i], (uint32_t)K);
         }
-        prop[i] = v;
+    }
+    int32_t* prop = f.prop + (int64_t)g * M;
+    if (M == 2) {
+        *reinterpret_cast<int2*>(prop) = make_int2(out[0], out[M - 1]);
+    } else if (M == 4) {
+        *reinterpret_cast<int4*>(prop) = make_int4(out[0], out[1 % M], out[2 % M], out[M - 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < M; ++i) prop[i] = out[i];
+    }
+}
+
+// The tokens of one piece, lane-strided, software-pipelined: the record two
+// tokens ahead and the z and proposals of the next token are in flight
+// while a token is sampled.
+template <int M, bool kStaged>
+__device__ __forceinline__ void fold_word_piece(const FoldArgs& f, const FoldWords& fw, const int4 pc, int it,
+                                                const int32_t* P, Checks& chk, int lane) {
+    const int n = pc.z;
+    const int4* rp = fw.rec + pc.y;
+    if (lane >= n) return;
+    int4 rn = __ldcs(rp + lane);
+    WordTok<M> cur = fold_word_load<M>(f, fw, rn, chk);
+    if (lane + 32 < n) rn = __ldcs(rp + lane + 32);
+    for (int i = lane; i < n; i += 32) {
+        const bool more = i + 32 < n;
+        WordTok<M> nxt = cur;
+        if (more) {
+            nxt = fold_word_load<M>(f, fw, rn, chk);
+            if (i + 64 < n) rn = __ldcs(rp + i + 64);
+        }
+        fold_word_apply<M, kStaged>(f, cur, it, P);
+        cur = nxt;
     }
 }
 
 // The word phase of sweep `it`: warp w takes a contiguous range of the
-// pieces (so consecutive pieces of one word are staged once).
+// pieces (so consecutive pieces of one word are staged once).  The records
+// are streamed with the evict-first hint, so that L2 keeps the requests' z
+// and proposals, which the word order reads and writes at random.
 template <int M>
 __global__ void __launch_bounds__(kThreads) fold_word_kernel(FoldArgs f, FoldWords fw, int it) {
     extern __shared__ __align__(16) int32_t wsm[];
@@ -562,9 +675,9 @@ __global__ void __launch_bounds__(kThreads) fold_word_kernel(FoldArgs f, FoldWor
                 __syncwarp();
                 staged = pc.x;
             }
-            for (int i = lane; i < pc.z; i += 32) fold_word_token<M, true>(f, fw, fw.rec[pc.y + i], it, P, chk);
+            fold_word_piece<M, true>(f, fw, pc, it, P, chk, lane);
         } else {
-            for (int i = lane; i < pc.z; i += 32) fold_word_token<M, false>(f, fw, fw.rec[pc.y + i], it, P, chk);
+            fold_word_piece<M, false>(f, fw, pc, it, P, chk, lane);
         }
     }
     chk.publish(f.fault, kSiteFoldin);
@@ -600,9 +713,10 @@ __global__ void __launch_bounds__(kThreads) fold_doc_kernel(FoldArgs f, int tab_
         doc.atab = nullptr;
         const uint32_t cap = kDense ? 0u : pow2_above((uint32_t)min(2 * max(L, 1), f.K));
         const int words = kDense ? tab_words : (int)cap;
-        if (mode & 1) fold_init<M>(f, doc, lane);
-        if (mode & 2) fold_doc_phase<M, kDense, false>(f, doc, it, tab, words, cap, lane);
-        if ((mode & 4) && f.theta) fold_theta<kDense>(f, doc, f.theta + (int64_t)d * f.K, tab, words, cap, lane);
+        const WarpGroup wg{lane};
+        if (mode & 1) fold_init<M>(f, doc, wg);
+        if (mode & 2) fold_doc_phase<M, kDense, false>(f, doc, it, tab, words, cap, wg);
+        if ((mode & 4) && f.theta) fold_theta<kDense>(f, doc, f.theta + (int64_t)d * f.K, tab, words, cap, wg);
     }
     chk.publish(f.fault, kSiteFoldin);
 }
@@ -790,7 +904,7 @@ cudaError_t launch_serve_rows(const void* src, const int32_t* slots, int n, int 
 
 cudaError_t launch_serve(const FoldArgs& f, const ServeSlots& sl, int tab_words, int grid, cudaStream_t st) {
     if (const cudaError_t g_ = launch_gate()) return g_;
-    if (sl.nactive <= 0) return cudaSuccess;
+    if (sl.nactive <= 0 && sl.nlong <= 0) return cudaSuccess;
     const bool dense = f.K <= kDenseMaxK;
     const void* fn = fold_pick(f.M, dense, sl.q != nullptr, true);
     const int warps = foldin_warps(tab_words);

@@ -138,8 +138,11 @@ int fold_word_blocks_per_sm(int M, const FoldWords& fw);
 // learned proposal, q and its alias table) per slot.
 struct ServeSlots {
     int4* info;
-    const int32_t* active;   // [nactive] slots advanced by this launch
+    const int32_t* active;   // [nactive] slots advanced by this launch, one warp each
     int nactive, nslots;
+    const int32_t* long_active;   // [nlong] slots advanced by a whole block each
+    int nlong, long_blocks;       // ... by the launch's first long_blocks blocks
+    int32_t* long_counter;        // their work counter (zero on entry)
     int64_t pool_tokens;
     int32_t* z;
     int32_t* prop;

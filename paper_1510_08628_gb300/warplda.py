@@ -244,15 +244,23 @@ class WarpLDA:
         _check(load().warplda_load(self._h, path.encode()))
 
     def foldin(self, doc_ptr, doc_word, sweeps: int, seed: int, doc_ids=None,
-               theta: bool = True, z: bool = True, learned: bool = False):
+               theta: bool = True, z: bool = True, learned: bool = False, theta_out=None, z_out=None):
         """Fold in new documents against the current model: (theta[Dn, K], z[Nn]);
-        learned=True uses the encoder's proposal."""
+        learned=True uses the encoder's proposal.  theta_out / z_out: the
+        caller's float32 [Dn, K] / int32 [Nn] arrays to fill (e.g. pinned)."""
         dp = np.ascontiguousarray(doc_ptr, dtype=np.int64)
         dw = np.ascontiguousarray(doc_word, dtype=np.int32)
         Dn, Nn = len(dp) - 1, int(dp[-1])
         ids = None if doc_ids is None else np.ascontiguousarray(doc_ids, dtype=np.int64)
-        th = np.empty((Dn, self.K), dtype=np.float32) if theta else None
-        zo = np.empty(Nn, dtype=np.int32) if z else None
+        th = zo = None
+        if theta:
+            th = theta_out if theta_out is not None else np.empty((Dn, self.K), dtype=np.float32)
+            if th.dtype != np.float32 or th.shape != (Dn, self.K) or not th.flags.c_contiguous:
+                raise ValueError("theta_out must be a C-contiguous float32 [Dn, K] array")
+        if z:
+            zo = z_out if z_out is not None else np.empty(Nn, dtype=np.int32)
+            if zo.dtype != np.int32 or zo.shape != (Nn,) or not zo.flags.c_contiguous:
+                raise ValueError("z_out must be a C-contiguous int32 [Nn] array")
         ptr = lambda a: a.ctypes.data if a is not None and a.size else None
         _check(load().warplda_foldin(self._h, Dn, ptr(dp), ptr(dw), ptr(ids), int(sweeps),
                                      int(seed), 1 if learned else 0, ptr(th), ptr(zo)))

@@ -163,18 +163,18 @@ def test_poll_times_out_while_a_step_runs():
     rng = np.random.default_rng(2)
     L = 20000
     timed_out = False
-    for n_docs in (256, 1024, 2048):
+    for n_docs in (256, 1024, 4096):
         docs = [rng.integers(0, c.V, size=L).astype(np.int32) for _ in range(n_docs)]
         s = Server(g, slots=n_docs, pool_tokens=n_docs * L, max_doc_tokens=L, sweeps=1, seed=4)
         for i, d in enumerate(docs):
             assert s.submit(i, d)
         s.step()
         try:
-            s.poll(timeout_ms=0)
+            ids, th = s.poll(timeout_ms=0)
         except WarpLDAError as e:
             assert e.code == ETIMEDOUT, e
             timed_out = True
-        ids, th = s.poll(timeout_ms=120000)
+            ids, th = s.poll(timeout_ms=120000)
         if not timed_out:
             assert len(ids) == n_docs      # finished within the poll: try a longer step
             s.close()
