@@ -279,9 +279,13 @@ int warplda_kernel_times(warplda_ctx* ctx, int32_t cap, const char** names, int6
  *               NULL.
  * The frozen model (C_w as V*K int32 and each word's topics in ascending
  * order, N int32, held by the context until warplda_destroy) is rebuilt when
- * the context has swept since the last fold-in.  Documents may have at most 65535 tokens when K <= 2048,
- * 4095 above.  Synchronous.  Errors: EINVAL (CSR, word id, length, proposal),
- * ESTATE (a word phase is pending), ENOMEM, ECUDA.
+ * the context has swept since the last fold-in.  The call's device scratch
+ * (the documents' words, z, proposals, theta and the word-major records,
+ * about 40 + 12 M bytes per token plus 4 K bytes per document) is kept by
+ * the context for the next call and grown when a call needs more; it is
+ * freed by warplda_destroy.  Documents may have at most 65535 tokens when
+ * K <= 2048, 4095 above.  Synchronous.  Errors: EINVAL (CSR, word id,
+ * length, proposal), ESTATE (a word phase is pending), ENOMEM, ECUDA.
  */
 #define WARPLDA_PROPOSAL_PLAIN 0
 #define WARPLDA_PROPOSAL_LEARNED 1

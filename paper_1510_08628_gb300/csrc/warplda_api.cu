@@ -193,6 +193,13 @@ struct warplda_ctx {
     // plain-proposal fold-in: word-major phases (default) or one warp per
     // document for all sweeps (tuning foldin_kernel = 1)
     bool foldin_word_major = true;
+    // warplda_foldin's device scratch, kept between calls and grown on
+    // demand (slot i = the call's i-th buffer)
+    struct Scratch {
+        void* p = nullptr;
+        size_t bytes = 0;
+    };
+    std::vector<Scratch> fold_ws;
     bool dense = true;   // 16-bit dense count tables (K <= kDenseMaxK), else hash tables
     int warp_tpl = 16;   // tokens per lane of the document warp tier
     int grid_doc_warp = 1;
@@ -267,6 +274,9 @@ void free_all(warplda_ctx* c) {
     c->recs.clear();
     for (void* p : c->allocs) cudaFree(p);
     c->allocs.clear();
+    for (auto& w : c->fold_ws)
+        if (w.p) cudaFree(w.p);
+    c->fold_ws.clear();
 }
 
 // Table words of a segment of L tokens: dense ceil(K/2) words (two 16-bit
@@ -694,6 +704,31 @@ cudaError_t wl::alloc_gate() {
 }
 
 // Device buffers of one fold-in call, freed on every return path.
+// Buffers of one warplda_foldin call from the context's scratch: the call's
+// i-th request takes slot i, which is reallocated (a quarter larger) only
+// when too small, so repeated calls of similar size allocate nothing.
+struct FoldScratch {
+    warplda_ctx* c;
+    size_t next = 0;
+    template <typename T>
+    cudaError_t get(T** out, int64_t n) {
+        const size_t bytes = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
+        if (next >= c->fold_ws.size()) c->fold_ws.resize(next + 1);
+        auto& w = c->fold_ws[next++];
+        if (w.bytes < bytes) {
+            if (w.p) cudaFree(w.p);
+            w.p = nullptr;
+            w.bytes = 0;
+            const size_t want = bytes + bytes / 4;
+            const cudaError_t e = dev_malloc(&w.p, want);
+            if (e != cudaSuccess) return e;
+            w.bytes = want;
+        }
+        *out = static_cast<T*>(w.p);
+        return cudaSuccess;
+    }
+};
+
 struct FoldBuffers {
     std::vector<void*> p;
     template <typename T>
@@ -1748,7 +1783,7 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
         return off[a + 1] - off[a] > off[b + 1] - off[b];
     });
 
-    FoldBuffers buf;
+    FoldScratch buf{c};
     FoldArgs f{};
     int32_t *d_z, *d_prop, *d_words, *d_off, *d_order, *d_counter;
     int64_t* d_ids;

@@ -115,14 +115,28 @@ def test_init_allocation_and_launch_failures(gpu, K):
 
 @pytest.mark.gpu
 def test_foldin_allocation_and_launch_failures(gpu):
+    """Fold-in keeps its scratch in the context between calls, so the
+    allocation failures are swept on fresh contexts (their init's allocations
+    come first, then the fold-in's); launch failures on the warm context."""
+    from paper_1510_08628_gb300.warplda import WarpLDA
     c, wl, g = gpu
     rq = corpus.requests("tiny", seed=3, n=30, doc_offset=9000, lo=1, hi=300)
     want, _ = g.foldin(rq.doc_ptr, rq.doc_word, sweeps=4, seed=3)
-    call = lambda: g.foldin(rq.doc_ptr, rq.doc_word, sweeps=4, seed=3)
-    assert _sweep_failures("ALLOC", ENOMEM, call) >= 1
-    assert _sweep_failures("LAUNCH", ECUDA, call) >= 1
-    got, _ = call()
+
+    def cold():
+        m = WarpLDA(c.doc_ptr, c.doc_word, c.V, 40, wl.alpha, wl.beta, 2, 5)
+        try:
+            m.sweep(3)
+            return m.foldin(rq.doc_ptr, rq.doc_word, sweeps=4, seed=3)
+        finally:
+            m.close()
+
+    assert _sweep_failures("ALLOC", ENOMEM, cold) >= 12
+    warm = lambda: g.foldin(rq.doc_ptr, rq.doc_word, sweeps=4, seed=3)
+    assert _sweep_failures("LAUNCH", ECUDA, warm) >= 1
+    got, _ = warm()
     assert np.array_equal(got, want)
+    assert np.array_equal(cold()[0], want)
     g.sync()
 
 
