@@ -213,10 +213,7 @@ __host__ __device__ inline DocPipeSmem docpipe_layout(int K, int dense, int regi
 }
 
 template <bool kDense, int M, int TPT>
-#ifndef WL_DOCPIPE_MINB
-#define WL_DOCPIPE_MINB 3
-#endif
-__global__ void __launch_bounds__(kThreads, (TPT <= 2 ? 4 : WL_DOCPIPE_MINB)) doc_pipe_kernel(
+__global__ void __launch_bounds__(kThreads, (TPT <= 2 ? 4 : 3)) doc_pipe_kernel(
     PhaseArgs a, const int4* __restrict__ desc, int nbatch, int* __restrict__ counter,
     const int32_t* __restrict__ seg_region, int region_words) {
     constexpr int T = kThreads * TPT;
