@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -300,25 +301,18 @@ int table_words(int L, int K, bool dense) {
 // each batched segment records its table offset within the batch.  The
 // log-likelihood batches cover every segment that is not chunked, with the
 // paper's table rule.
-void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, int warp_max,
-                const int bmax[2], const int region[2], int chunk, int ranges_target, Tier* t,
-                int segs0 = kSegsMax, int64_t cluster_max = 0, int64_t cluster_slice = 1) {
-    const int segs_max[2] = {segs0, kSegsMax};
-    for (auto& b : t->batches) b.clear();
-    t->warp_list.clear();
-    t->chunks.clear();
-    t->row_len.clear();
-    t->range_off.clear();
-    t->ll_batches.clear();
-    t->cluster_list.clear();
-    t->s_chunks.clear();
-    t->s_range_off.clear();
-    t->cluster_tokens = t->s_row_tokens = 0;
-    std::vector<int4> s_longs;   // long segments of the multi-pass sampling passes
-    std::vector<int2> cl_words;  // {tokens, segment} of the cluster tier
-    std::vector<int4> longs;   // {row, segment, first position, length}
-    t->region.assign((size_t)std::max<int64_t>(S, 1), 0);
-    t->nrows = t->row_tokens = t->large_tokens = t->warp_tokens = 0;
+// The tier lists of segments [s0, s1): the greedy batching below, closed at
+// s1.  Rows of long segments are numbered from 0 within the part.
+struct TierPart {
+    std::vector<int4> batches[2], ll_batches, longs, s_longs;
+    std::vector<int32_t> warp_list, row_len;
+    std::vector<int2> cl_words;   // {tokens, segment} of the cluster tier
+    int64_t nrows = 0, row_tokens = 0, large_tokens = 0, warp_tokens = 0, cluster_tokens = 0, s_row_tokens = 0;
+};
+
+void scan_tier(const std::vector<int32_t>& off, int64_t s0, int64_t s1, int K, bool dense, int warp_max,
+               const int bmax[2], const int region[2], const int segs_max[2], int64_t cluster_max,
+               int32_t* seg_region, TierPart* t) {
     int cur0 = -1, cls = -1, ntok = 0, nseg = 0, nw = 0;
     auto close = [&](int end) {
         if (cur0 >= 0 && end > cur0) t->batches[cls].push_back(make_int4(cur0, end, nw, 0));
@@ -331,11 +325,11 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
         l0 = -1;
         lt = ls = lw = 0;
     };
-    for (int64_t s = 0; s < S; ++s) {
+    for (int64_t s = s0; s < s1; ++s) {
         const int L = off[s + 1] - off[s];
         if (L == 0) {
             if (cur0 >= 0 && nseg + 1 <= segs_max[cls]) {
-                t->region[s] = nw;
+                seg_region[s] = nw;
                 nseg += 1;
             } else {
                 close((int)s);
@@ -354,12 +348,12 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
             const int row = (int)t->nrows++;
             t->row_tokens += L;
             t->row_len.push_back(L);
-            longs.push_back(make_int4(row, (int)s, off[s], L));
+            t->longs.push_back(make_int4(row, (int)s, off[s], L));
             if (cluster_max > 0 && L <= cluster_max) {
-                cl_words.push_back(make_int2(L, (int)s));
+                t->cl_words.push_back(make_int2(L, (int)s));
                 t->cluster_tokens += L;
             } else {
-                s_longs.push_back(make_int4(row, (int)s, off[s], L));
+                t->s_longs.push_back(make_int4(row, (int)s, off[s], L));
                 t->s_row_tokens += L;
             }
             continue;
@@ -388,13 +382,78 @@ void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, i
             cur0 = (int)s;
             cls = c;
         }
-        t->region[s] = nw;
+        seg_region[s] = nw;
         ntok += L;
         nseg += 1;
         nw += w;
     }
-    close((int)S);
-    lclose((int)S);
+    close((int)s1);
+    lclose((int)s1);
+}
+
+// Segments per part of the tier scan.  Parts are scanned on host threads;
+// a batch never spans two parts, so the lists depend on this size only, not
+// on the number of host cores.
+constexpr int64_t kTierPart = 1 << 20;
+
+void build_tier(const std::vector<int32_t>& off, int64_t S, int K, bool dense, int warp_max,
+                const int bmax[2], const int region[2], int chunk, int ranges_target, Tier* t,
+                int segs0 = kSegsMax, int64_t cluster_max = 0, int64_t cluster_slice = 1) {
+    const int segs_max[2] = {segs0, kSegsMax};
+    for (auto& b : t->batches) b.clear();
+    t->warp_list.clear();
+    t->chunks.clear();
+    t->row_len.clear();
+    t->range_off.clear();
+    t->ll_batches.clear();
+    t->cluster_list.clear();
+    t->s_chunks.clear();
+    t->s_range_off.clear();
+    t->cluster_tokens = t->s_row_tokens = 0;
+    t->region.assign((size_t)std::max<int64_t>(S, 1), 0);
+    t->nrows = t->row_tokens = t->large_tokens = t->warp_tokens = 0;
+    const int64_t nparts = std::max<int64_t>(1, (S + kTierPart - 1) / kTierPart);
+    std::vector<TierPart> parts((size_t)nparts);
+    auto scan = [&](int64_t i) {
+        scan_tier(off, i * kTierPart, std::min(S, (i + 1) * kTierPart), K, dense, warp_max, bmax, region, segs_max,
+                  cluster_max, t->region.data(), &parts[(size_t)i]);
+    };
+    {
+        // parts taken from a counter by up to 15 helper threads and this one
+        // (which alone does the work if no thread can be started)
+        std::atomic<int64_t> next{0};
+        auto work = [&] {
+            for (int64_t i; (i = next.fetch_add(1)) < nparts;) scan(i);
+        };
+        std::vector<std::thread> th;
+        const int helpers = (int)std::min<int64_t>(nparts - 1, (int64_t)std::min(15u, std::thread::hardware_concurrency()));
+        try {
+            for (int k = 0; k < helpers; ++k) th.emplace_back(work);
+        } catch (...) {
+        }
+        work();
+        for (auto& x : th) x.join();
+    }
+    // the parts in segment order; rows renumbered
+    std::vector<int4> s_longs;   // long segments of the multi-pass sampling passes
+    std::vector<int2> cl_words;  // {tokens, segment} of the cluster tier
+    std::vector<int4> longs;     // {row, segment, first position, length}
+    for (auto& p : parts) {
+        const int base = (int)t->nrows;
+        for (int k = 0; k < 2; ++k) t->batches[k].insert(t->batches[k].end(), p.batches[k].begin(), p.batches[k].end());
+        t->ll_batches.insert(t->ll_batches.end(), p.ll_batches.begin(), p.ll_batches.end());
+        t->warp_list.insert(t->warp_list.end(), p.warp_list.begin(), p.warp_list.end());
+        t->row_len.insert(t->row_len.end(), p.row_len.begin(), p.row_len.end());
+        for (int4 h : p.longs) longs.push_back(make_int4(h.x + base, h.y, h.z, h.w));
+        for (int4 h : p.s_longs) s_longs.push_back(make_int4(h.x + base, h.y, h.z, h.w));
+        cl_words.insert(cl_words.end(), p.cl_words.begin(), p.cl_words.end());
+        t->nrows += p.nrows;
+        t->row_tokens += p.row_tokens;
+        t->large_tokens += p.large_tokens;
+        t->warp_tokens += p.warp_tokens;
+        t->cluster_tokens += p.cluster_tokens;
+        t->s_row_tokens += p.s_row_tokens;
+    }
     // ranges of about equal size over the long segments' tokens, each a list
     // of pieces of at most `chunk` tokens of one segment
     auto make_ranges = [&](const std::vector<int4>& ls, int64_t tokens, std::vector<int4>* chunks,
@@ -1392,7 +1451,8 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         if (e == cudaSuccess) e = cudaMemsetAsync(c->sperm, 0, ((size_t)N + 4) * 4, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->sinfo, 0, ((size_t)N + 4) * 4, c->st);
         for (int k = 0; k < 2 && e == cudaSuccess; ++k)
-            e = launch_batch_lists(c->docs.d_batches[k], (int)c->docs.batches[k].size(), c->doc_off, c->perm, pos, N,
+            e = launch_batch_lists(c->docs.d_batches[k], (int)c->docs.batches[k].size(), c->dbmax[k], c->doc_off,
+                                   c->perm, pos, N,
                                    c->sperm, c->sinfo, c->d_bad + 1, c->st);
         int32_t bad2 = 0x7FFFFFFF;
         if (e == cudaSuccess) e = cudaMemcpyAsync(&bad2, c->d_bad + 1, 4, cudaMemcpyDeviceToHost, c->st);

@@ -181,12 +181,12 @@ __global__ void perm_kernel(const int32_t* __restrict__ pos_sorted, int64_t N, i
 // One block per document batch {first doc, end doc, table words, 0}: its
 // tokens occupy doc-major positions [doc_off[x], doc_off[y]) and the same
 // range of sperm / sinfo.
+template <int kTPT>
 __global__ void __launch_bounds__(kThreads) batch_lists_kernel(
     const int4* __restrict__ batches, int nb, const int32_t* __restrict__ doc_off, const int32_t* __restrict__ perm,
     const int32_t* __restrict__ pos_sorted, int nbits, int32_t* __restrict__ sperm, uint32_t* __restrict__ sinfo,
     int32_t* __restrict__ bad) {
     extern __shared__ __align__(16) unsigned char bsm[];
-    constexpr int kTPT = 16;
     uint32_t* keys = reinterpret_cast<uint32_t*>(bsm);
     uint16_t* cnt = reinterpret_cast<uint16_t*>(bsm + (kThreads * kTPT + (kThreads * kTPT >> 5) + 4) * 4);
     __shared__ int warp_tot[kWarps];
@@ -298,19 +298,31 @@ cudaError_t launch_perm(const int32_t* pos_sorted, int64_t N, int32_t* perm, cud
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_lists(const int4* batches, int nb, const int32_t* doc_off, const int32_t* perm,
-                               const int32_t* pos_sorted, int64_t N, int32_t* sperm, uint32_t* sinfo, int32_t* bad,
-                               cudaStream_t st) {
+template <int kTPT>
+static cudaError_t batch_lists_tpt(const int4* batches, int nb, const int32_t* doc_off, const int32_t* perm,
+                                   const int32_t* pos_sorted, int nbits, int32_t* sperm, uint32_t* sinfo,
+                                   int32_t* bad, cudaStream_t st) {
+    const int smem = (kThreads * kTPT + ((kThreads * kTPT) >> 5) + 4) * 4 + 16 * kThreads * 2;
+    cudaError_t e = cudaFuncSetAttribute(batch_lists_kernel<kTPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    batch_lists_kernel<kTPT><<<(unsigned)std::min(nb, 152 * 8), kThreads, smem, st>>>(
+        batches, nb, doc_off, perm, pos_sorted, nbits, sperm, sinfo, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_lists(const int4* batches, int nb, int max_tokens, const int32_t* doc_off,
+                               const int32_t* perm, const int32_t* pos_sorted, int64_t N, int32_t* sperm,
+                               uint32_t* sinfo, int32_t* bad, cudaStream_t st) {
     if (const cudaError_t g_ = launch_gate()) return g_;
     if (nb <= 0) return cudaSuccess;
     int nbits = 1;
     while (nbits < 32 && ((int64_t)1 << nbits) <= N) ++nbits;   // 2^nbits - 1 >= N > every key
-    const int smem = (kThreads * 16 + ((kThreads * 16) >> 5) + 4) * 4 + 16 * kThreads * 2;
-    cudaError_t e = cudaFuncSetAttribute(batch_lists_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    batch_lists_kernel<<<(unsigned)std::min(nb, 152 * 8), kThreads, smem, st>>>(batches, nb, doc_off, perm, pos_sorted,
-                                                                             nbits, sperm, sinfo, bad);
-    return cudaGetLastError();
+    // the block sorts 256 * TPT keys: the smallest TPT that holds a batch
+    if (max_tokens <= kThreads * 4)
+        return batch_lists_tpt<4>(batches, nb, doc_off, perm, pos_sorted, nbits, sperm, sinfo, bad, st);
+    if (max_tokens <= kThreads * 8)
+        return batch_lists_tpt<8>(batches, nb, doc_off, perm, pos_sorted, nbits, sperm, sinfo, bad, st);
+    return batch_lists_tpt<16>(batches, nb, doc_off, perm, pos_sorted, nbits, sperm, sinfo, bad, st);
 }
 
 }  // namespace wl

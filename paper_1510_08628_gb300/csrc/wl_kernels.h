@@ -238,8 +238,8 @@ cudaError_t launch_token_sort(int32_t* keys_a, int32_t* vals_a, int32_t* keys_b,
                               int32_t V, int32_t* scratch, int32_t** pos_sorted, int32_t** keys_sorted,
                               cudaStream_t st);
 cudaError_t launch_perm(const int32_t* pos_sorted, int64_t N, int32_t* perm, cudaStream_t st);
-cudaError_t launch_batch_lists(const int4* batches, int nb, const int32_t* doc_off, const int32_t* perm,
-                               const int32_t* pos_sorted, int64_t N, int32_t* sperm, uint32_t* sinfo, int32_t* bad,
-                               cudaStream_t st);
+cudaError_t launch_batch_lists(const int4* batches, int nb, int max_tokens, const int32_t* doc_off,
+                               const int32_t* perm, const int32_t* pos_sorted, int64_t N, int32_t* sperm,
+                               uint32_t* sinfo, int32_t* bad, cudaStream_t st);
 
 }  // namespace wl
