@@ -357,10 +357,12 @@ int warplda_encoder_proposal(warplda_ctx* ctx, int64_t Dn, const int64_t* doc_pt
  *   then launch one sweep for every admitted, unfinished request (new ones
  *   are initialised first; a request's last sweep writes its theta);
  *   asynchronous.  With the learned proposal the new requests' encoder
- *   forward, alias tables and first sweep run on a second stream beside the
- *   sweep of the requests already running (the step ends when both have).
- *   *active_out (or NULL) = requests advanced.  Requests submitted while a
- *   step runs join the next step.
+ *   forward and alias tables run on a second stream beside the sweep of the
+ *   requests already running (the step ends when both have); with fewer
+ *   than 8 sweeps per request their first sweep follows there, in the same
+ *   step, else they join the sweeps from the next step on (results are the
+ *   same either way).  *active_out (or NULL) = requests advanced or being
+ *   admitted.  Requests submitted while a step runs join the next step.
  *   The previous step's results must have been polled (else ESTATE).
  * warplda_server_poll -- wait at most timeout_ms for the last step (else
  *   ETIMEDOUT), then hand over the requests it finished: ids[n] and

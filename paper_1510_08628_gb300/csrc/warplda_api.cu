@@ -116,6 +116,9 @@ constexpr int kClusterClasses = 5;
 constexpr int kRangesPerSm = WL_RANGES_PER_SM;
 // serving: documents of at least this many tokens are swept by a block
 constexpr int kServeBlockMin = 512;
+// serving with the learned proposal: requests of at least this many sweeps
+// join the step after their admission, shorter ones the step of it
+constexpr int kServeDeferMin = 8;
 // word-major fold-in: words with at least this many request tokens have
 // their frozen row staged in shared memory, the others keep direct loads
 #ifndef WL_FOLD_STAGE_MIN
@@ -967,8 +970,9 @@ struct warplda_server {
     int n_fin_staged = 0;
     cudaEvent_t tick = nullptr;
     // learned proposal: the admission work (encoder, alias tables, rows) of
-    // a step and its new requests' first sweep run on a second stream while
-    // the step's sweep of the running requests runs
+    // a step, and with few sweeps per request its new requests' first sweep,
+    // run on a second stream while the step's sweep of the running requests
+    // runs
     cudaStream_t side = nullptr;
     cudaEvent_t uploaded = nullptr, admitted = nullptr;
     struct Slot {
@@ -2294,11 +2298,15 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     if (s->n_fin_staged > 0) return fail(WARPLDA_ESTATE, "poll the previous step's results first");
     // the pinned staging is reused: the previous step's upload must be done
     WL_CU(cudaEventSynchronize(s->tick), "previous step");
-    // requests staged since the last step join this step: with the plain
-    // proposal in the step's sweep; with the learned one their first sweep
-    // runs on the side stream behind their encoder forward and alias tables,
-    // beside the sweep of the requests already running
+    // requests staged since the last step: with the plain proposal they join
+    // this step's sweep.  With the learned one their encoder forward and
+    // alias tables run on the side stream beside the running requests'
+    // sweep, and then either their first sweep follows there (few sweeps per
+    // request: a step of delay would be a large part of the latency) or
+    // they join the next step (many sweeps: one more step costs little,
+    // while a first sweep behind the encoder would lengthen every step)
     const bool learned = s->proposal == WARPLDA_PROPOSAL_LEARNED;
+    const bool defer = learned && s->sweeps >= kServeDeferMin;
     std::vector<int32_t> active, fresh;
     if (learned)
         for (const int4& r : s->new_req) fresh.push_back(r.x);
@@ -2309,7 +2317,7 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
         const auto& S = s->slots[i];
         if (!S.used || S.done >= s->sweeps) continue;
         if (is_fresh[i]) {
-            if (S.done + 1 >= s->sweeps) ++nfin;
+            if (!defer && S.done + 1 >= s->sweeps) ++nfin;
             continue;
         }
         active.push_back(i);
@@ -2323,7 +2331,8 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     const bool blocks = foldin_warps(s->tab_words) >= 4;
     std::vector<int32_t> lists[4];
     for (int32_t i : active) lists[blocks && s->slots[i].L >= kServeBlockMin ? 1 : 0].push_back(i);
-    for (int32_t i : fresh) lists[blocks && s->slots[i].L >= kServeBlockMin ? 3 : 2].push_back(i);
+    if (!defer)
+        for (int32_t i : fresh) lists[blocks && s->slots[i].L >= kServeBlockMin ? 3 : 2].push_back(i);
     std::vector<int32_t> upload;
     for (const auto& l : lists) upload.insert(upload.end(), l.begin(), l.end());
     // counters: short-document work [0] (running) and [2] (new), long
@@ -2371,7 +2380,8 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
         WL_CU(cudaStreamWaitEvent(c->st, s->admitted, 0), "wait admission");
     }
     for (int32_t i : active) s->slots[i].done += 1;
-    for (int32_t i : fresh) s->slots[i].done += 1;
+    if (!defer)
+        for (int32_t i : fresh) s->slots[i].done += 1;
     if (nfin > 0) {
         WL_CU(cudaMemcpyAsync(s->h_fin_slot, s->d_fin_slot, (size_t)nfin * 4, cudaMemcpyDeviceToHost, c->st), "copy finished");
         WL_CU(cudaMemcpyAsync(s->h_theta, s->d_fin_theta, (size_t)nfin * c->K * 4, cudaMemcpyDeviceToHost, c->st),

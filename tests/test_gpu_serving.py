@@ -62,9 +62,9 @@ def _oracle_theta(m, dp, dw, learned):
     return th
 
 
-def _serve(g, docs, order, batches, learned, max_doc=700, slots=64, pool=100000):
+def _serve(g, docs, order, batches, learned, max_doc=700, slots=64, pool=100000, sweeps=SWEEPS):
     from paper_1510_08628_gb300.warplda import Server
-    s = Server(g, slots=slots, pool_tokens=pool, max_doc_tokens=max_doc, sweeps=SWEEPS, seed=SEED,
+    s = Server(g, slots=slots, pool_tokens=pool, max_doc_tokens=max_doc, sweeps=sweeps, seed=SEED,
                learned=learned)
     out = {}
     pending = list(order)
@@ -117,6 +117,22 @@ def test_served_mix_of_empty_and_long_documents(model, learned):
                  max_doc=top, slots=8, pool=20000)
     for d in range(len(lens)):
         assert np.array_equal(got[d], want[d]), (d, lens[d])
+
+
+@pytest.mark.parametrize("learned", [False, True], ids=["plain", "learned"])
+def test_served_with_many_sweeps_equals_foldin(model, learned):
+    """12 sweeps per request: learned requests then join the step after
+    their admission (with fewer than 8 sweeps, as above, the step of it).
+    Rows equal warplda_foldin's (itself checked against the oracle), for
+    requests arriving all at once and trickled in."""
+    g, rq = model["g"], model["rq"]
+    n = rq.D
+    want, _ = g.foldin(rq.doc_ptr, rq.doc_word, sweeps=12, seed=SEED, doc_ids=np.arange(n), learned=learned)
+    docs = _docs(rq, range(n))
+    for order, batches in ((list(range(n)), [n]), (list(range(n))[::-1], [3, 0, 5, 1, 0, 0, 7, 2] * 20)):
+        got = _serve(g, docs, order, batches, learned, sweeps=12)
+        for d in range(n):
+            assert np.array_equal(got[d], want[d]), d
 
 
 def test_served_equals_context_foldin(model):
