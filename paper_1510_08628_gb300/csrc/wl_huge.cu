@@ -60,11 +60,14 @@ __device__ __forceinline__ int4 get_piece(const PhaseArgs& a, const HugeWork& w,
     return ch;
 }
 
-// Buckets of the rank guide table of the word draw: a power of two of at
-// least 2K (so that a bucket spans about half a topic or less), 4096 to 16384.
+// Buckets of the rank guide table of the word draw: the power of two of at
+// least 2K (so that a bucket spans about half a topic or less), 4096 to 8192.
+// Capped at 8192: with K = 10^4 a 16384-bucket guide took 64 KB and left two
+// blocks per SM, the 8192-bucket one three (draw 4.97 -> 4.50 ms per
+// PubMed-shaped sweep; 4096 buckets made the walks longer: 5.08 ms).
 int huge_guide_bits(int K) {
     int b = 12;
-    while (b < 14 && (1 << b) < 2 * K) ++b;
+    while (b < 13 && (1 << b) < 2 * K) ++b;
     return b;
 }
 
