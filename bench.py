@@ -406,6 +406,7 @@ def serving_bench(gpu, c, wl, args, learned: bool, rate: float, n: int = 6000, n
                  seed=args.seed + 41, learned=learned)
     lat = np.zeros(n)
     got, nxt, queue, steps = 0, 0, [], 0
+    gpu.profile(True)   # per-launch CUDA events by class, both streams
     t0 = time.perf_counter()
     while got < n:
         now = time.perf_counter() - t0
@@ -427,10 +428,16 @@ def serving_bench(gpu, c, wl, args, learned: bool, rate: float, n: int = 6000, n
         if active == 0 and not queue and nxt < n:
             time.sleep(max(0.0, min(0.001, arrive[nxt] - (time.perf_counter() - t0))))
     wall = time.perf_counter() - t0
+    kt = gpu.kernel_times()
+    gpu.profile(False)
     srv.close()
+    # device time per step of each kind of launch (the new requests' work is
+    # on a second stream, beside the running requests' sweep)
+    per_step = {k: round(ms / max(steps, 1), 4) for k, (_, ms) in kt.items() if k.startswith("serve")}
     return {"proposal": "learned" if learned else "plain", "offered_docs_per_s": rate, "docs": n,
             "sweeps": S, "docs_per_s": n / wall, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3), "steps": steps}
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "steps": steps,
+            "device_ms_per_step": per_step}
 
 
 TUNING_KEYS = ("batch_max_tokens", "huge_chunk", "region_budget", "doc_warp_max", "word_positioning",

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -89,13 +90,15 @@ enum KernelClass {
     kcDocWarp, kcDocBatch, kcDocHugeHist, kcDocHugeAccept, kcDocHugeDraw,
     kcWordBatch, kcWordMegaHist, kcWordMegaAccept, kcWordMegaHistPost, kcWordMegaDraw,
     kcCountCk, kcFinalize, kcZero, kcDocPipe, kcWordCluster,
-    kcFoldBuild, kcFoldDoc, kcFoldWord, kcFoldin, kcCount
+    kcFoldBuild, kcFoldDoc, kcFoldWord, kcFoldin,
+    kcServe, kcServeNew, kcServeAdmit, kcServeEncoder, kcServeAlias, kcServeRows, kcCount
 };
 const char* kClassNames[kcCount] = {
     "doc_warp", "doc_batch", "doc_huge_hist", "doc_huge_accept", "doc_huge_draw",
     "word_batch", "word_mega_hist", "word_mega_accept", "word_mega_hist_post", "word_mega_draw",
     "count_ck", "finalize_ck", "zero_rows", "doc_pipe", "word_cluster",
-    "foldin_build", "foldin_doc", "foldin_word", "foldin_kernel"};
+    "foldin_build", "foldin_doc", "foldin_word", "foldin_kernel",
+    "serve", "serve_new", "serve_admit", "serve_encoder", "serve_alias", "serve_rows"};
 // topics: packed hash entries hold (topic + 1) << 12 in 32 bits
 constexpr int kMaxTopics = (1 << 20) - 1;
 // tokens of a pipelined document batch (at most 4 * 256 - 3; at most 509
@@ -248,6 +251,8 @@ struct warplda_ctx {
         uint16_t *W1b, *W2tb, *W2nb;                                          // BF16 copies
         float *gW1, *gb1, *gW2t, *gb2;                                        // gradients
         float *h_pre, *logits, *dH;
+        float* gwork = nullptr;      // split-K partial tiles of the three GEMMs
+        int64_t gwork_floats = 0;
         uint16_t *hb, *hbT, *dl, *dlT;
         int32_t *cnt, *ids, *docword = nullptr;
         double* loss;
@@ -548,14 +553,16 @@ int launch_rec(warplda_ctx* c, int cls, cudaError_t (*fn)(warplda_ctx*, void*), 
     return WARPLDA_OK;
 }
 
-// A launch outside the sweep (fold-in), timed like launch_rec.
+// A launch outside the sweep (fold-in, serving), timed like launch_rec on
+// the stream it is queued on.
 template <class F>
-int launch_timed(warplda_ctx* c, int cls, F&& fn) {
+int launch_timed(warplda_ctx* c, int cls, F&& fn, cudaStream_t on = nullptr) {
+    if (!on) on = c->st;
     cudaEvent_t a = nullptr, b = nullptr;
     if (c->prof) {
         WL_CU(cudaEventCreate(&a), "cudaEventCreate");
         WL_CU(cudaEventCreate(&b), "cudaEventCreate");
-        WL_CU(cudaEventRecord(a, c->st), "cudaEventRecord");
+        WL_CU(cudaEventRecord(a, on), "cudaEventRecord");
     }
     const cudaError_t e = fn();
     if (e != cudaSuccess) {
@@ -564,7 +571,7 @@ int launch_timed(warplda_ctx* c, int cls, F&& fn) {
         return cuda_fail(e, kClassNames[cls]);
     }
     if (c->prof) {
-        WL_CU(cudaEventRecord(b, c->st), "cudaEventRecord");
+        WL_CU(cudaEventRecord(b, on), "cudaEventRecord");
         c->recs.push_back(Rec{cls, a, b});
     }
     return WARPLDA_OK;
@@ -816,7 +823,9 @@ int enc_forward(warplda_ctx* c, const EncBatch& b, float* q_out, bool grads, con
     auto& e = c->enc;
     WL_CU(launch_enc_l1_fwd(b, e.B, e.W1b, e.b1, e.H, e.log2F, e.h_pre, e.hb, e.hbT, c->st), "encoder layer 1");
     // the GEMM's status flag reuses the check record's last word
-    WL_CU(launch_gemm_bf16(e.hb, e.W2tb, e.logits, e.b2, e.B, e.Kp, e.H, c->d_fault + 3, c->st), "encoder layer 2");
+    WL_CU(launch_gemm_bf16(e.hb, e.W2tb, e.logits, e.b2, e.B, e.Kp, e.H, c->d_fault + 3, c->st, e.gwork,
+                           e.gwork_floats),
+          "encoder layer 2");
     WL_CU(launch_enc_softmax(b, e.B, e.logits, c->K, e.Kp, q_out, tgt, c->z, c->perm, c->alpha, c->abar,
                              grads ? e.dl : nullptr, e.dlT, e.gb2, e.loss, e.cnt, c->st), "encoder softmax");
     return WARPLDA_OK;
@@ -824,8 +833,12 @@ int enc_forward(warplda_ctx* c, const EncBatch& b, float* q_out, bool grads, con
 
 int enc_backward(warplda_ctx* c, const EncBatch& b) {
     auto& e = c->enc;
-    WL_CU(launch_gemm_bf16(e.dl, e.W2nb, e.dH, nullptr, e.B, e.H, e.Kp, c->d_fault + 3, c->st), "encoder dH");
-    WL_CU(launch_gemm_bf16(e.dlT, e.hbT, e.gW2t, nullptr, e.Kp, e.H, e.B, c->d_fault + 3, c->st), "encoder dW2");
+    WL_CU(launch_gemm_bf16(e.dl, e.W2nb, e.dH, nullptr, e.B, e.H, e.Kp, c->d_fault + 3, c->st, e.gwork,
+                           e.gwork_floats),
+          "encoder dH");
+    WL_CU(launch_gemm_bf16(e.dlT, e.hbT, e.gW2t, nullptr, e.Kp, e.H, e.B, c->d_fault + 3, c->st, e.gwork,
+                           e.gwork_floats),
+          "encoder dW2");
     WL_CU(launch_enc_l1_bwd(b, e.B, e.dH, e.h_pre, e.H, e.log2F, e.gW1, e.gb1, c->st), "encoder layer 1 backward");
     return WARPLDA_OK;
 }
@@ -1113,9 +1126,13 @@ int server_admit(warplda_server* s, const std::vector<int32_t>& active, int64_t*
     *act_off = o_act;
     *sl_off = o_sl;
     const int32_t* d = s->d_staged;
-    if (n > 0)
-        WL_CU(launch_serve_admit(d, reinterpret_cast<const int4*>(d + o_req), d + o_src, n, s->nslots, s->pool_tokens,
-                                 s->d_words, s->d_info, c->st), "admit requests");
+    if (n > 0) {
+        rc = launch_timed(c, kcServeAdmit, [&] {
+            return launch_serve_admit(d, reinterpret_cast<const int4*>(d + o_req), d + o_src, n, s->nslots,
+                                      s->pool_tokens, s->d_words, s->d_info, c->st);
+        });
+        if (rc) return rc;
+    }
     if (n > 0 && s->proposal == WARPLDA_PROPOSAL_LEARNED) {
         // on the side stream, once the upload is done; the caller queues the
         // new requests' first sweep behind it there and makes the main stream
@@ -1128,13 +1145,31 @@ int server_admit(warplda_server* s, const std::vector<int32_t>& active, int64_t*
         c->st = s->side;   // enc_forward queues on the context's stream
         for (int b0 = 0; b0 < n && !rc; b0 += e.B) {
             EncBatch b{d + o_ids + b0, d + o_off, d, std::min(e.B, n - b0)};
+            cudaEvent_t ea = nullptr, eb = nullptr;
+            if (c->prof) {
+                if (cudaEventCreate(&ea) != cudaSuccess) ea = nullptr;
+                if (ea && cudaEventCreate(&eb) != cudaSuccess) {
+                    cudaEventDestroy(ea);
+                    ea = eb = nullptr;
+                }
+                if (ea) cudaEventRecord(ea, c->st);
+            }
             rc = enc_forward(c, b, s->d_aq + (int64_t)b0 * K, false, nullptr);
+            if (ea) {
+                cudaEventRecord(eb, c->st);
+                c->recs.push_back(Rec{kcServeEncoder, ea, eb});
+            }
         }
         c->st = main_st;
         if (rc) return rc;
-        WL_CU(launch_enc_alias(s->d_aq, n, K, s->d_aatab, s->side), "alias tables");
-        WL_CU(launch_serve_rows(s->d_aq, d + o_sl, n, K, s->nslots, s->d_q, s->side), "proposal rows");
-        WL_CU(launch_serve_rows(s->d_aatab, d + o_sl, n, 2 * K, s->nslots, s->d_atab, s->side), "alias rows");
+        if ((rc = launch_timed(c, kcServeAlias, [&] { return launch_enc_alias(s->d_aq, n, K, s->d_aatab, s->side); },
+                               s->side)))
+            return rc;
+        rc = launch_timed(c, kcServeRows, [&] {
+            const cudaError_t e1 = launch_serve_rows(s->d_aq, d + o_sl, n, K, s->nslots, s->d_q, s->side);
+            return e1 != cudaSuccess ? e1 : launch_serve_rows(s->d_aatab, d + o_sl, n, 2 * K, s->nslots, s->d_atab, s->side);
+        }, s->side);
+        if (rc) return rc;
     }
     s->new_words.clear();
     s->new_src.clear();
@@ -2028,6 +2063,10 @@ int warplda_encoder_init(warplda_ctx* c, int32_t log2_features, int32_t hidden, 
     WL_A(e.h_pre, B * H); WL_A(e.logits, B * Kp); WL_A(e.dH, B * H);
     WL_A(e.hb, B * H); WL_A(e.hbT, B * H); WL_A(e.dl, B * Kp); WL_A(e.dlT, B * Kp);
     WL_A(e.cnt, B * (int64_t)c->K); WL_A(e.loss, 1); WL_A(e.ids, std::max<int64_t>(c->D, 1));
+    e.gwork_floats = std::max({gemm_splits((int)B, (int)Kp, (int)H, INT64_MAX) * B * Kp,
+                               gemm_splits((int)B, (int)H, (int)Kp, INT64_MAX) * B * H,
+                               gemm_splits((int)Kp, (int)H, (int)B, INT64_MAX) * Kp * H});
+    WL_A(e.gwork, e.gwork_floats);
 #undef WL_A
     // W1 ~ U(-1, 1); W2 ~ U(-a, a), a = sqrt(6 / (H + K)) (Glorot); biases 0
     std::vector<float> w1((size_t)(F * H)), w2((size_t)(Kp * H), 0.0f);
@@ -2189,14 +2228,24 @@ int warplda_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, const 
         return fail(WARPLDA_EINVAL, "GEMM operands must be 16-byte aligned");
     cudaStream_t st = (cudaStream_t)cuda_stream;
     int32_t* status = nullptr;
+    float* work = nullptr;
+    // the split-K workspace the encoder would use for this shape
+    const int64_t wf = M > 0 && N > 0 && K > 0 ? (int64_t)gemm_splits(M, N, K, INT64_MAX) * M * N : 0;
     WL_CU(dev_malloc((void**)&status, sizeof(int32_t)), "alloc GEMM status");
+    cudaError_t e = wf > (int64_t)M * N ? dev_malloc((void**)&work, (size_t)wf * 4) : cudaSuccess;
+    if (e != cudaSuccess) {
+        cudaFree(status);
+        return cuda_fail(e, "alloc GEMM workspace");
+    }
     int32_t h = 0;
-    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+    e = cudaMemsetAsync(status, 0, sizeof(int32_t), st);
     if (e == cudaSuccess)
-        e = launch_gemm_bf16((const uint16_t*)A_dev, (const uint16_t*)B_dev, C_dev, bias_dev, M, N, K, status, st);
+        e = launch_gemm_bf16((const uint16_t*)A_dev, (const uint16_t*)B_dev, C_dev, bias_dev, M, N, K, status, st,
+                             work, work ? wf : 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(status);
+    if (work) cudaFree(work);
     if (e != cudaSuccess) return cuda_fail(e, "GEMM");
     if (h) return fail(WARPLDA_ETIMEDOUT, "GEMM: a tensor-core wait ran out");
     return WARPLDA_OK;
@@ -2370,8 +2419,8 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
         a.long_counter = s->d_counter + (which == 0 ? 3 : 4);
         a.long_blocks = nl > 0 ? (int)std::min<int64_t>(nl, std::max(1, s->grid / 2)) : 0;
         const int short_blocks = ns > 0 ? (int)std::min<int64_t>(s->grid, ((int64_t)ns + warps - 1) / warps) : 0;
-        WL_CU(launch_serve(fa, a, s->tab_words, a.long_blocks + short_blocks, st), "serve");
-        return WARPLDA_OK;
+        return launch_timed(c, which == 0 ? kcServe : kcServeNew,
+                            [&] { return launch_serve(fa, a, s->tab_words, a.long_blocks + short_blocks, st); }, st);
     };
     if ((rc = serve(0, act_off, c->st))) return rc;
     if (!fresh.empty()) {

@@ -11,6 +11,13 @@
 // epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes
 // 32w..32w+31 = rows of the tile).  Every mbarrier wait is bounded; a wait
 // that runs out records an error and the CTA returns after freeing its TMEM.
+// Split K: the encoder's products have few 128 x 128 tiles (16 for a batch
+// of 256 rows against K = 1000 topics), so the K chunks are divided among
+// `splits` CTAs per tile (blockIdx.z), each writing its partial tile to a
+// workspace, and a second kernel adds the partials in split order (a fixed
+// order: the result does not depend on scheduling) plus the bias.
+#include <algorithm>
+
 #include "wl_kernels.h"
 
 namespace wl {
@@ -62,7 +69,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 
 __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(
     const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, float* __restrict__ C,
-    const float* __restrict__ bias, int M, int N, int K, int32_t* status) {
+    const float* __restrict__ bias, int M, int N, int K, int kc_per_split, int32_t* status) {
     extern __shared__ __align__(1024) uint8_t gsm[];
     __shared__ __align__(8) uint64_t bars[2];
     __shared__ uint32_t tmem_slot;
@@ -89,7 +96,12 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(
     const uint32_t tmem = tmem_slot;
     constexpr uint32_t idesc = umma_idesc_bf16(kGemmTile, kGemmTile);
 
-    const int nk = K / kGemmChunk;
+    // this CTA's K chunks; with splits, C is its slice of the workspace
+    const int kbeg = blockIdx.z * kc_per_split;
+    const int nk = min(K / kGemmChunk - kbeg, kc_per_split);
+    C += (int64_t)blockIdx.z * M * N;
+    A += (int64_t)kbeg * kGemmChunk;
+    B += (int64_t)kbeg * kGemmChunk;
     bool ok = true;
     for (int kc = 0; kc < nk; ++kc) {
         const int st = kc & 1;
@@ -187,18 +199,65 @@ __global__ void __launch_bounds__(kGemmThreads) gemm_bf16_kernel(
     }
 }
 
+// C = sum over splits s of part[s] (in order s = 0, 1, ...) + bias.
+__global__ void gemm_reduce_kernel(const float* __restrict__ part, int splits, int M, int N,
+                                   const float* __restrict__ bias, float* __restrict__ C) {
+    const int64_t n4 = (int64_t)M * N / 4;
+    const int64_t plane = (int64_t)M * N;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 a = reinterpret_cast<const float4*>(part)[i];
+        for (int s = 1; s < splits; ++s) {
+            const float4 b = reinterpret_cast<const float4*>(part + s * plane)[i];
+            a.x += b.x;
+            a.y += b.y;
+            a.z += b.z;
+            a.w += b.w;
+        }
+        if (bias) {
+            const int col = (int)((i * 4) % N);
+            a.x += bias[col];
+            a.y += bias[col + 1];
+            a.z += bias[col + 2];
+            a.w += bias[col + 3];
+        }
+        reinterpret_cast<float4*>(C)[i] = a;
+    }
+}
+
 int gemm_smem_bytes() { return 4 * kStageBytes; }
 
+// Splits of K for an M x N product: the smallest divisor of the chunk count
+// (up to 8) that gives 64 CTAs, else the largest, within the workspace.
+int gemm_splits(int M, int N, int K, int64_t work_floats) {
+    const int tiles = (M / kGemmTile) * (N / kGemmTile), nk = K / kGemmChunk;
+    int s = 1;
+    for (int d = 2; d <= 8 && d <= nk && tiles * s < 64; ++d)
+        if (nk % d == 0 && (int64_t)d * M * N <= work_floats) s = d;
+    return s;
+}
+
 cudaError_t launch_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, const float* bias,
-                             int M, int N, int K, int32_t* status, cudaStream_t st) {
+                             int M, int N, int K, int32_t* status, cudaStream_t st, float* work,
+                             int64_t work_floats) {
     if (const cudaError_t g_ = launch_gate()) return g_;
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
     if (M % kGemmTile || N % kGemmTile || K % kGemmChunk) return cudaErrorInvalidValue;
     const int smem = gemm_smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    gemm_bf16_kernel<<<dim3(N / kGemmTile, M / kGemmTile), kGemmThreads, smem, st>>>(A, B, C, bias, M, N,
-                                                                                     K, status);
+    const int splits = work ? gemm_splits(M, N, K, work_floats) : 1;
+    const int per = (K / kGemmChunk) / splits;
+    if (splits == 1) {
+        gemm_bf16_kernel<<<dim3(N / kGemmTile, M / kGemmTile, 1), kGemmThreads, smem, st>>>(A, B, C, bias, M, N, K,
+                                                                                            per, status);
+        return cudaGetLastError();
+    }
+    gemm_bf16_kernel<<<dim3(N / kGemmTile, M / kGemmTile, splits), kGemmThreads, smem, st>>>(A, B, work, nullptr, M,
+                                                                                            N, K, per, status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t n4 = (int64_t)M * N / 4;
+    gemm_reduce_kernel<<<(unsigned)std::min<int64_t>((n4 + 255) / 256, 152 * 8), 256, 0, st>>>(work, splits, M, N,
+                                                                                                bias, C);
     return cudaGetLastError();
 }
 

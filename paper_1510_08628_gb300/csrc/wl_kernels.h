@@ -163,8 +163,13 @@ cudaError_t launch_serve(const FoldArgs& f, const ServeSlots& sl, int tab_words,
 // FP32 C; M, N multiples of 128, K a multiple of 64; *status set to 1 if a
 // bounded wait ran out.
 int gemm_smem_bytes();
+// work: a float workspace of work_floats for split-K partial tiles (NULL:
+// one CTA per tile); the result is the same for every split count up to
+// FP32 rounding of the partial sums, and deterministic for a given one.
 cudaError_t launch_gemm_bf16(const uint16_t* A, const uint16_t* B, float* C, const float* bias,
-                             int M, int N, int K, int32_t* status, cudaStream_t st);
+                             int M, int N, int K, int32_t* status, cudaStream_t st, float* work = nullptr,
+                             int64_t work_floats = 0);
+int gemm_splits(int M, int N, int K, int64_t work_floats);
 
 // Fold-in encoder (wl_encoder.cu).  A batch is rows r = 0..B-1 of document
 // docs[r] (r < nreal; the other rows are padding), tokens at
