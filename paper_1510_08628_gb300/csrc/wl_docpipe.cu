@@ -64,6 +64,22 @@ __device__ __forceinline__ uint32_t bucket_match(const uint4& e, uint32_t tag) {
          : ((e.w & kTagMask) == tag) ? e.w : 0u;
 }
 
+// The count of topic k given its first bucket e (already loaded).
+__device__ __forceinline__ int bucket_resolve(const uint32_t* tab, uint32_t nbmask, uint32_t k, uint4 e) {
+    const uint32_t tag = (k + 1u) << kHashCountBits;
+    uint32_t b = k & nbmask;
+    uint32_t c = bucket_match(e, tag);
+    if (c == 0u && e.w != 0u) {
+        for (uint32_t n = 1; n <= nbmask; ++n) {
+            b = (b + 1u) & nbmask;
+            e = reinterpret_cast<const uint4*>(tab)[b];
+            c = bucket_match(e, tag);
+            if (c != 0u || e.w == 0u) break;
+        }
+    }
+    return (int)(c & kCountMask);
+}
+
 __device__ __forceinline__ int bucket_get(const uint32_t* tab, uint32_t nbmask, uint32_t k) {
     const uint32_t tag = (k + 1u) << kHashCountBits;
     uint32_t b = k & nbmask;
@@ -383,16 +399,32 @@ __global__ void __launch_bounds__(kThreads, (TPT <= 2 ? 4 : 3)) doc_pipe_kernel(
             const uint32_t* tab = region + sg.z;
             int cnt[M + 1];
             float ckv[M + 1];
+            uint4 rr[M];
+            if (kDense) {
 #pragma unroll
-            for (int i = 0; i <= M; ++i) {
-                const uint32_t k = (uint32_t)(i == 0 ? z0 : pr[i - 1]);
-                if (kDense) {
+                for (int i = 0; i <= M; ++i) {
+                    const uint32_t k = (uint32_t)(i == 0 ? z0 : pr[i - 1]);
                     cnt[i] = (int)((tab[k >> 1] >> ((k & 1u) * 16u)) & 0xFFFFu);
                     ckv[i] = ckb_s[k];
-                } else {
-                    cnt[i] = i == 0 ? (int)(region[ent[j]] & kCountMask) : bucket_get(tab, (uint32_t)sg.w, k);
-                    ckv[i] = __ldg(a.ckb + k);
                 }
+#pragma unroll
+                for (int i = 0; i < M; ++i) rr[i] = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
+            } else {
+                // the loads first (own entry, the proposals' first buckets,
+                // c_k), then the Philox blocks while they are in flight, then
+                // the bucket matches
+                uint4 eb[M];
+                cnt[0] = (int)(region[ent[j]] & kCountMask);
+                ckv[0] = __ldg(a.ckb + z0);
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    eb[i] = reinterpret_cast<const uint4*>(tab)[(uint32_t)pr[i] & (uint32_t)sg.w];
+                    ckv[i + 1] = __ldg(a.ckb + pr[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < M; ++i) rr[i] = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
+#pragma unroll
+                for (int i = 0; i < M; ++i) cnt[i + 1] = bucket_resolve(tab, (uint32_t)sg.w, (uint32_t)pr[i], eb[i]);
             }
             const float Lf = __int2float_rn(sg.y);
             const float LG = __fadd_rn(Lf, a.G);
@@ -400,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, (TPT <= 2 ? 4 : 3)) doc_pipe_kernel(
             float ks = ckv[0];
 #pragma unroll
             for (int i = 0; i < M; ++i) {
-                const uint4 r = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
+                const uint4 r = rr[i];
                 const int tp = pr[i];
                 const bool acc = (tp != sc) && accept(r.x, cs, cnt[i + 1], a.g, ks, ckv[i + 1]);
                 sc = acc ? tp : sc;
