@@ -256,18 +256,33 @@ __global__ void __launch_bounds__(kThreads, (M <= 2 ? 3 : 2)) huge_accept_kernel
                             for (int i = 0; i < M; ++i) pk[e * M + i] = 0;
                             if (q < p0 || q >= p1) { full = false; continue; }
                             const int z0 = chk.topic(out[e], K, 3);
-                            int s = z0;
+                            // the counts and c_k of z and of every proposal
+                            // are loaded first, then the Philox blocks are
+                            // drawn while the loads are in flight
+                            int tpv[M], rt[M];
+                            float kt[M];
+                            const int rz = row[z0];
+                            const float kz = a.stage_ck ? ckb_s[z0] : __ldg(a.ckb + z0);
 #pragma unroll
                             for (int i = 0; i < M; ++i) {
-                                const uint4 r = draw((uint32_t)q, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
-                                const int tp = chk.topic(elem(y[u][(e * M + i) / 4], (e * M + i) % 4), K, 4);
-                                if (tp != s) {
-                                    const float cs = a.stage_ck ? ckb_s[s] : __ldg(a.ckb + s);
-                                    const float ct = a.stage_ck ? ckb_s[tp] : __ldg(a.ckb + tp);
-                                    if (accept(r.x, row[s], row[tp], a.g, cs, ct)) s = tp;
+                                tpv[i] = chk.topic(elem(y[u][(e * M + i) / 4], (e * M + i) % 4), K, 4);
+                                rt[i] = row[tpv[i]];
+                                kt[i] = a.stage_ck ? ckb_s[tpv[i]] : __ldg(a.ckb + tpv[i]);
+                            }
+                            uint4 rr[M];
+#pragma unroll
+                            for (int i = 0; i < M; ++i) rr[i] = draw((uint32_t)q, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
+                            int s = z0, cs = rz;
+                            float ks = kz;
+#pragma unroll
+                            for (int i = 0; i < M; ++i) {
+                                if (tpv[i] != s && accept(rr[i].x, cs, rt[i], a.g, ks, kt[i])) {
+                                    s = tpv[i];
+                                    cs = rt[i];
+                                    ks = kt[i];
                                 }
-                                pk[e * M + i] = coin(r.y, Lf, LG) ? -(int)(dice(r.z, (uint32_t)Ls) + 1)
-                                                                  : (int)dice(r.z, (uint32_t)K);
+                                pk[e * M + i] = coin(rr[i].y, Lf, LG) ? -(int)(dice(rr[i].z, (uint32_t)Ls) + 1)
+                                                                      : (int)dice(rr[i].z, (uint32_t)K);
                             }
                             delta(z0, s);
                             out[e] = s;
