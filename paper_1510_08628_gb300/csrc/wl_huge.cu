@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, HugeWo
                 for (int u = 0; u < kVecUnroll; ++u) {
                     const int v = vb + u * kThreads;
                     if (v >= v1) continue;
-                    int out[4 * M];
+                    int out[4 * M], jv[4 * M], kg[4 * M], nx[4 * M];
 #pragma unroll
                     for (int n = 0; n < 4 * M; ++n) {
                         // only this piece's tokens: an edge vector's other
@@ -423,19 +423,29 @@ __global__ void __launch_bounds__(kThreads) huge_draw_kernel(PhaseArgs a, HugeWo
                         const int q = 4 * v + n / M;
                         int pk = elem(y[u][n / 4], n % 4);
                         if (q < p0 || q >= p1) pk = 0;
-                        if (pk < 0) {
-                            int j = -pk - 1;
-                            if (!chk.tok((uint32_t)j < (uint32_t)Ls, 5)) j = 0;
-                            if (storage) {
-                                // positioning: the j-th token's new topic
-                                pk = a.z[sb + min(j, Ls - 1)];
-                            } else {
-                                int k = guide[bucket_of(j)];
-                                while (k + 1 < K && P[k + 1] <= j) ++k;
-                                pk = chk.tok(P[k + 1] > j, 6) ? k : 0;
-                            }
-                        }
                         out[n] = pk;
+                        int j = pk < 0 ? -pk - 1 : -1;
+                        if (pk < 0 && !chk.tok((uint32_t)j < (uint32_t)Ls, 5)) j = 0;
+                        jv[n] = j;
+                    }
+                    if (storage) {
+#pragma unroll
+                        for (int n = 0; n < 4 * M; ++n)   // positioning: the j-th token's new topic
+                            if (jv[n] >= 0) out[n] = a.z[sb + min(jv[n], Ls - 1)];
+                    } else {
+                        // every pick's guide entry and the prefix after it
+                        // are loaded first, then the short walks
+#pragma unroll
+                        for (int n = 0; n < 4 * M; ++n) kg[n] = jv[n] >= 0 ? guide[bucket_of(jv[n])] : 0;
+#pragma unroll
+                        for (int n = 0; n < 4 * M; ++n) nx[n] = P[kg[n] + 1];
+#pragma unroll
+                        for (int n = 0; n < 4 * M; ++n) {
+                            if (jv[n] < 0) continue;
+                            int k = kg[n], next = nx[n];
+                            while (k + 1 < K && next <= jv[n]) next = P[++k + 1];
+                            out[n] = chk.tok(next > jv[n], 6) ? k : 0;
+                        }
                     }
                     const bool full = (4 * v >= p0) && (4 * v + 3 < p1);
                     if (full) {
@@ -583,6 +593,20 @@ __device__ __forceinline__ int sparse_get(const unsigned long long* slots, uint3
     return 0;
 }
 
+// sparse_get given the key's first slot v0 (already loaded).
+__device__ __forceinline__ int sparse_resolve(const unsigned long long* slots, uint32_t cap, uint32_t k,
+                                              unsigned long long v) {
+    const uint32_t mask = cap - 1u;
+    uint32_t h = sparse_slot(k, mask);
+    for (uint32_t probe = 0; probe < cap; ++probe) {
+        if ((v >> 32) == (k + 1u)) return (int)(uint32_t)v;
+        if (v == 0ull) return 0;
+        h = (h + 1) & mask;
+        v = __ldg(slots + h);
+    }
+    return 0;
+}
+
 template <bool kDoc>
 __global__ void __launch_bounds__(kThreads) sparse_hist_kernel(PhaseArgs a, HugeWork w, SparseRows r) {
     __shared__ int s_r;
@@ -631,17 +655,35 @@ __global__ void __launch_bounds__(kThreads) sparse_accept_kernel(PhaseArgs a, Hu
                 const int t = kDoc ? a.perm[p] : p;
                 if (!chk.tok((uint32_t)t < (uint32_t)a.N, 2)) continue;
                 const int z0 = chk.topic(a.z[t], K, 3);
+                // first slots and c_k of z and of every proposal loaded
+                // first, the Philox blocks drawn while they are in flight,
+                // then the probes resolved
+                const uint32_t mask = cap - 1u;
+                int tpv[M];
+                unsigned long long v0[M + 1];
+                float kv[M + 1];
+                v0[0] = __ldg(slots + sparse_slot((uint32_t)z0, mask));
+                kv[0] = __ldg(a.ckb + z0);
+#pragma unroll
+                for (int i = 0; i < M; ++i) {
+                    tpv[i] = chk.topic(a.prop[(int64_t)t * M + i], K, 4);
+                    v0[i + 1] = __ldg(slots + sparse_slot((uint32_t)tpv[i], mask));
+                    kv[i + 1] = __ldg(a.ckb + tpv[i]);
+                }
+                uint4 rv[M];
+#pragma unroll
+                for (int i = 0; i < M; ++i) rv[i] = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
                 int s = z0;
-                int cs = sparse_get(slots, cap, (uint32_t)s);
-                float ks = __ldg(a.ckb + s);
+                int cs = sparse_resolve(slots, cap, (uint32_t)z0, v0[0]);
+                float ks = kv[0];
                 int pk[M];
 #pragma unroll
                 for (int i = 0; i < M; ++i) {
-                    const uint4 rr = draw((uint32_t)t, a.iter, phase, (uint32_t)(i + 1), 0u, a.rk);
-                    const int tp = chk.topic(a.prop[(int64_t)t * M + i], K, 4);
+                    const uint4 rr = rv[i];
+                    const int tp = tpv[i];
                     if (tp != s) {
-                        const int ct = sparse_get(slots, cap, (uint32_t)tp);
-                        const float kt = __ldg(a.ckb + tp);
+                        const int ct = sparse_resolve(slots, cap, (uint32_t)tp, v0[i + 1]);
+                        const float kt = kv[i + 1];
                         if (accept(rr.x, cs, ct, a.g, ks, kt)) {
                             s = tp;
                             cs = ct;
