@@ -165,21 +165,28 @@ __device__ void fold_doc_phase(const FoldArgs& f, const FoldDoc& doc, int it, ui
     // document phase: accept with the phase-start c_d ...
     fold_table<kDense>(tab, words, cap, doc, km, g);
     for (int j = g.rank(); j < L; j += g.size()) {
+        // operands first, then the Philox blocks, then the chain
         int s = min((uint32_t)z[j], km);
         int cs = fold_count(tab, cap, kDense, s);
         float ks = __ldg(f.ckb + s);
+        int tv[M], ctv[M];
+        float ktv[M];
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-            const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldDoc, (uint32_t)(i + 1), doc.id, f.rk);
-            const int t = (int)min((uint32_t)prop[j * M + i], km);
-            if (t != s) {
-                const int ct = fold_count(tab, cap, kDense, t);
-                const float kt = __ldg(f.ckb + t);
-                if (accept(r.x, cs, ct, f.alpha, ks, kt)) {
-                    s = t;
-                    cs = ct;
-                    ks = kt;
-                }
+            tv[i] = (int)min((uint32_t)prop[j * M + i], km);
+            ctv[i] = fold_count(tab, cap, kDense, tv[i]);
+            ktv[i] = __ldg(f.ckb + tv[i]);
+        }
+        uint32_t r0[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i)
+            r0[i] = draw((uint32_t)j, (uint32_t)it, kPhaseFoldDoc, (uint32_t)(i + 1), doc.id, f.rk).x;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+            if (tv[i] != s && accept(r0[i], cs, ctv[i], f.alpha, ks, ktv[i])) {
+                s = tv[i];
+                cs = ctv[i];
+                ks = ktv[i];
             }
         }
         z[j] = s;
@@ -563,24 +570,33 @@ __device__ __forceinline__ void fold_word_apply(const FoldArgs& f, const WordTok
     auto cw = [&](int k) { return kStaged ? P[k + 1] - P[k] : __ldg(row + k); };
     const float Lwf = __int2float_rn(Lw);
     const float LwG = __fadd_rn(Lwf, f.kbeta);
+    // the counts and c_k of z and of every proposal first, then the Philox
+    // blocks while those loads are in flight, then the chain
     int s = min((uint32_t)tk.z, km);
     int cs = cw(s);
     float ks = __ldg(f.ckb + s);
-    uint32_t r1[M], r2[M];
+    int tv[M], ctv[M];
+    float ktv[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        tv[i] = (int)min((uint32_t)tk.p[i], km);
+        ctv[i] = cw(tv[i]);
+        ktv[i] = __ldg(f.ckb + tv[i]);
+    }
+    uint32_t r0[M], r1[M], r2[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) {
         const uint4 r = draw((uint32_t)j, (uint32_t)it, kPhaseFoldWord, (uint32_t)(i + 1), id, f.rk);
+        r0[i] = r.x;
         r1[i] = r.y;
         r2[i] = r.z;
-        const int t = (int)min((uint32_t)tk.p[i], km);
-        if (t != s) {
-            const int ct = cw(t);
-            const float kt = __ldg(f.ckb + t);
-            if (accept(r.x, cs, ct, f.beta, ks, kt)) {
-                s = t;
-                cs = ct;
-                ks = kt;
-            }
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        if (tv[i] != s && accept(r0[i], cs, ctv[i], f.beta, ks, ktv[i])) {
+            s = tv[i];
+            cs = ctv[i];
+            ks = ktv[i];
         }
     }
     f.z[g] = s;
