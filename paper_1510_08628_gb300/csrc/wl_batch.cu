@@ -95,9 +95,14 @@ __device__ __forceinline__ int tab_get(const uint32_t* tab, uint32_t cap, uint32
     return kDense ? dense_get(tab, k) : table_get(tab, cap, k);
 }
 
-// Resident blocks per SM the register allocation is held to.
+// Resident blocks per SM the register allocation is held to.  Word batches
+// of 8 tokens per thread: three (80 registers, a few spilled) measured
+// faster than two (126 registers): PubMed-shaped 3.99 -> 3.78 ms, NYTimes-
+// shaped 0.71 -> 0.69 ms per sweep; batches of 16 tokens per thread: two
+// (128 registers) rather than one (159): PubMed-shaped word batches 3.78 ->
+// 3.49 ms, its long documents 0.41 -> 0.32 ms.
 template <bool kDoc, int TPT>
-constexpr int batch_min_blocks() { return TPT == 4 ? 3 : (TPT == 8 ? 2 : 1); }
+constexpr int batch_min_blocks() { return TPT == 4 ? 3 : (TPT == 8 ? (kDoc ? 2 : 3) : 2); }
 
 template <bool kDoc, bool kDense, int TPT, int M>
 __global__ void __launch_bounds__(kThreads, (batch_min_blocks<kDoc, TPT>())) batch_phase_kernel(
