@@ -13,9 +13,13 @@
 // Random numbers: Philox keyed by the fold-in seed, counter = (position in
 // the document, iteration, phase << 8 | i, document id), phases 3/4/5, so a
 // document's result does not depend on the other documents of the call.
-// One warp per document, all sweeps in one launch: the document's count
-// table lives in the warp's slice of shared memory, its z and proposals in
-// global memory (document order, coalesced), the frozen rows in L2.
+// Two schedules with the same results.  One warp per document, all sweeps
+// in one launch (the learned proposal, serving, and tuning foldin_kernel =
+// 1): the document's count table lives in the warp's slice of shared
+// memory, its z and proposals in global memory (document order, coalesced),
+// the frozen rows read where the tokens need them.  Word-major phases (the
+// plain proposal's default, below): per sweep a document-phase launch and a
+// word-phase launch over the tokens grouped by word.
 #include <algorithm>
 
 #include "wl_block.cuh"
