@@ -4,11 +4,13 @@ word phase) on a synthetic LDA corpus shaped like PubMed (D=8M, V=140K,
 of the whole sweep, the CPU oracle as the reported baseline, and the
 end-to-end throughput through the C ABI from host buffers; then fold-in,
 the learned document proposal and the serving loop on a model of the
-NYTimes-shaped corpus (D=300K, V=100K, ~99M tokens, K=1,000).
+NYTimes-shaped corpus (D=300K, V=100K, ~99M tokens, K=1,000), and on that
+corpus the log-likelihood trajectories of M = 1, 2, 4 and of the paper's
+storage-order word positioning (Fig. 7).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload pubmed|nytimes|clueweb|tiny]
                   [--foldin-workload nytimes|...] [--docs D] [--tuning key=value,...]
-                  [--m-sweep] [--foldin-docs N]
+                  [--m-sweep | --no-m-sweep] [--foldin-docs N]
   python bench.py --impl reference ...   (the CPU oracle on the same workload)
 
 One "step" is one sweep.  Prints one JSON line (rank 0).  With N > 1
@@ -603,7 +605,9 @@ def main():
                     help="epochs of encoder training for the learned fold-in proposal (0: skip)")
     ap.add_argument("--encoder-lr", type=float, default=3e-3, help="Adam step size of encoder training")
     ap.add_argument("--m-sweep", action="store_true",
-                    help="also record log-likelihood against iterations for M = 1, 2, 4 (Fig. 7)")
+                    help="record log-likelihood against iterations for M = 1, 2, 4 (Fig. 7) on the timed "
+                         "workload (by default it is recorded on the fold-in workload's corpus)")
+    ap.add_argument("--no-m-sweep", action="store_true", help="skip the M comparison")
     ap.add_argument("--tuning", default="",
                     help="launch tuning of the sampler as key=value pairs separated by commas "
                          "(batch_max_tokens, huge_chunk, region_budget, doc_warp_max, word_positioning, "
@@ -714,7 +718,10 @@ def main():
             "alg_bytes_per_launch": d["alg_bytes"]}
 
     gpu.close()
-    msweep = m_sweep(c, wl, args, stream) if (args.m_sweep and rank == 0) else None
+    msweep = None
+    if args.m_sweep and not args.no_m_sweep and rank == 0:
+        msweep = m_sweep(c, wl, args, stream)
+        msweep["workload"] = args.workload
 
     # end to end through the C ABI from pinned host buffers: init (H2D of the
     # corpus, token-order build) + K sweeps + D2H of z and c_k
@@ -767,6 +774,10 @@ def main():
         if args.encoder_epochs > 0:
             foldin["serving"].append(serving_bench(model, cf, wf, fa, True, rate))
         model.close()
+        if msweep is None and not args.no_m_sweep:
+            # the M comparison (Fig. 7) on the fold-in workload's corpus
+            msweep = m_sweep(cf, wf, args, stream)
+            msweep["workload"] = fa.workload
 
     if rank == 0:
         line = {
