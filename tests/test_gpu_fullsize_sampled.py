@@ -75,3 +75,34 @@ def test_full_size_sampled_phase_parity(name):
     pt = (t[:, None] * M + np.arange(M)).reshape(-1)
     assert np.array_equal(p2[pt], ref.prop[pt]), "word phase: proposals"
     gpu.sync()
+
+
+def test_full_size_foldin_sampled_parity():
+    """Fold-in against a NYTimes-shaped model (99M tokens, K = 1000) of 20,000
+    requests in one call, as the benchmark times it: the word-major phases
+    stage the frozen rows of the Zipf-frequent words in many pieces.  A
+    request's result depends only on its own tokens and stream id, so the
+    oracle's fold-in of a sample of the requests (the longest and random
+    ones) must give the same rows and topics bit for bit."""
+    from paper_1510_08628_gb300.warplda import WarpLDA
+    c, wl = corpus.generate("nytimes", seed=1)
+    gpu = WarpLDA(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, 7)
+    gpu.sweep(5)
+    rq = corpus.requests("nytimes", seed=1, n=20000, doc_offset=c.D + 1000)
+    ids = np.arange(rq.D, dtype=np.int64) * 3 + 11
+    th, zf = gpu.foldin(rq.doc_ptr, rq.doc_word, sweeps=4, seed=23, doc_ids=ids)
+    # the frozen model from the GPU's own state (z in word-major order)
+    z, _, ck, _ = gpu.get_state()
+    wp, _ = gpu.token_order()
+    cw = oracle.word_topic_counts(z, wp, c.V, wl.K)
+    gpu.close()
+    rng = np.random.default_rng(5)
+    pick = _sample(np.diff(rq.doc_ptr), 60, 4, rng)
+    lens = np.diff(rq.doc_ptr)[pick]
+    dp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    dw = np.concatenate([rq.doc_word[rq.doc_ptr[d]: rq.doc_ptr[d + 1]] for d in pick]).astype(np.int32)
+    zo, tho = oracle.foldin(dp, dw, cw, ck, wl.K, wl.M, wl.alpha, wl.beta, c.V, seed=23, sweeps=4,
+                            doc_ids=ids[pick])
+    assert np.array_equal(th[pick], tho)
+    zg = np.concatenate([zf[rq.doc_ptr[d]: rq.doc_ptr[d + 1]] for d in pick])
+    assert np.array_equal(zg, zo)
