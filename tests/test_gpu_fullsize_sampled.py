@@ -77,32 +77,73 @@ def test_full_size_sampled_phase_parity(name):
     gpu.sync()
 
 
-def test_full_size_foldin_sampled_parity():
-    """Fold-in against a NYTimes-shaped model (99M tokens, K = 1000) of 20,000
-    requests in one call, as the benchmark times it: the word-major phases
-    stage the frozen rows of the Zipf-frequent words in many pieces.  A
-    request's result depends only on its own tokens and stream id, so the
-    oracle's fold-in of a sample of the requests (the longest and random
-    ones) must give the same rows and topics bit for bit."""
+@pytest.fixture(scope="module")
+def nytimes_model():
+    """A NYTimes-shaped model (99M tokens, K = 1000) after 5 sweeps, with its
+    frozen C_w and c_k as the oracle sees them."""
     from paper_1510_08628_gb300.warplda import WarpLDA
     c, wl = corpus.generate("nytimes", seed=1)
     gpu = WarpLDA(c.doc_ptr, c.doc_word, c.V, wl.K, wl.alpha, wl.beta, wl.M, 7)
     gpu.sweep(5)
-    rq = corpus.requests("nytimes", seed=1, n=20000, doc_offset=c.D + 1000)
-    ids = np.arange(rq.D, dtype=np.int64) * 3 + 11
-    th, zf = gpu.foldin(rq.doc_ptr, rq.doc_word, sweeps=4, seed=23, doc_ids=ids)
-    # the frozen model from the GPU's own state (z in word-major order)
-    z, _, ck, _ = gpu.get_state()
+    z, _, ck, _ = gpu.get_state()   # z in word-major order
     wp, _ = gpu.token_order()
     cw = oracle.word_topic_counts(z, wp, c.V, wl.K)
+    yield gpu, c, wl, cw, ck
     gpu.close()
-    rng = np.random.default_rng(5)
-    pick = _sample(np.diff(rq.doc_ptr), 60, 4, rng)
+
+
+def _oracle_rows(rq, pick, ids, cw, ck, c, wl, sweeps, seed):
     lens = np.diff(rq.doc_ptr)[pick]
     dp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
     dw = np.concatenate([rq.doc_word[rq.doc_ptr[d]: rq.doc_ptr[d + 1]] for d in pick]).astype(np.int32)
-    zo, tho = oracle.foldin(dp, dw, cw, ck, wl.K, wl.M, wl.alpha, wl.beta, c.V, seed=23, sweeps=4,
-                            doc_ids=ids[pick])
+    return oracle.foldin(dp, dw, cw, ck, wl.K, wl.M, wl.alpha, wl.beta, c.V, seed=seed, sweeps=sweeps,
+                         doc_ids=ids[pick])
+
+
+def test_full_size_foldin_sampled_parity(nytimes_model):
+    """Fold-in of 20,000 requests in one call against the NYTimes-shaped
+    model, as the benchmark times it: the word-major phases stage the frozen
+    rows of the Zipf-frequent words in many pieces.  A request's result
+    depends only on its own tokens and stream id, so the oracle's fold-in of
+    a sample of the requests (the longest and random ones) must give the
+    same rows and topics bit for bit."""
+    gpu, c, wl, cw, ck = nytimes_model
+    rq = corpus.requests("nytimes", seed=1, n=20000, doc_offset=c.D + 1000)
+    ids = np.arange(rq.D, dtype=np.int64) * 3 + 11
+    th, zf = gpu.foldin(rq.doc_ptr, rq.doc_word, sweeps=4, seed=23, doc_ids=ids)
+    rng = np.random.default_rng(5)
+    pick = _sample(np.diff(rq.doc_ptr), 60, 4, rng)
+    zo, tho = _oracle_rows(rq, pick, ids, cw, ck, c, wl, 4, 23)
     assert np.array_equal(th[pick], tho)
     zg = np.concatenate([zf[rq.doc_ptr[d]: rq.doc_ptr[d + 1]] for d in pick])
     assert np.array_equal(zg, zo)
+
+
+def test_full_size_serving_sampled_parity(nytimes_model):
+    """Serving against the NYTimes-shaped model: 2,000 requests of 20 to
+    5,000 tokens (a block each from 512 tokens on) trickling into a server
+    while others run; a sample of the served theta rows, the longest
+    requests included, equals the oracle's fold-in rows."""
+    from paper_1510_08628_gb300.warplda import Server
+    gpu, c, wl, cw, ck = nytimes_model
+    rq = corpus.requests("nytimes", seed=1, n=2000, doc_offset=c.D + 50000)
+    ids = np.arange(rq.D, dtype=np.int64) * 5 + 2
+    srv = Server(gpu, slots=512, pool_tokens=600000, max_doc_tokens=5000, sweeps=6, seed=41)
+    got, nxt = {}, 0
+    for _ in range(100000):
+        for _ in range(37):   # a few dozen arrive before each step
+            if nxt < rq.D and srv.submit(int(ids[nxt]), rq.doc_word[rq.doc_ptr[nxt]: rq.doc_ptr[nxt + 1]]):
+                nxt += 1
+        srv.step()
+        done, th = srv.poll()
+        for i, t in zip(done, th):
+            got[int(i)] = t
+        if len(got) == rq.D:
+            break
+    srv.close()
+    assert len(got) == rq.D
+    rng = np.random.default_rng(7)
+    pick = _sample(np.diff(rq.doc_ptr), 40, 6, rng)
+    _, tho = _oracle_rows(rq, pick, ids, cw, ck, c, wl, 6, 41)
+    for r, d in enumerate(pick):
+        assert np.array_equal(got[int(ids[d])], tho[r]), int(d)
