@@ -1311,6 +1311,12 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     int32_t* vb = odd ? c->prop : reinterpret_cast<int32_t*>(c->sinfo);
     std::vector<int32_t> doc_off(D + 1), word_off(V + 1);
     for (int64_t d = 0; d <= D; ++d) doc_off[d] = (int32_t)doc_ptr[d];
+    // dense rows live in shared memory: a few ranges per block slot, each
+    // long enough that its row load is a small part of it.
+    // Sparse rows live in global memory: ranges of ~4K tokens taken in
+    // order keep the rows that the resident blocks touch at once few enough
+    // to stay in L2.
+    const int ranges_target = c->sparse ? (1 << 30) : kRangesPerSm * c->sms;
     // word-major order (Sec. 5.2): the word ids are checked, then a stable
     // sort of the tokens by word leaves the doc-major positions in prop and
     // the sorted ids in z; each word's first index gives the word offsets
@@ -1336,6 +1342,11 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         if (e == cudaSuccess) e = launch_word_starts(keys, N, (int32_t)V, c->word_off, c->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(wstart.data(), c->word_off, (size_t)V * 4, cudaMemcpyDeviceToHost, c->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(bad, c->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->st);
+        // the document tier needs only the document offsets: the host builds
+        // it while the word ids upload and sort
+        if (e == cudaSuccess)
+            build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->dregion, c->chunk, ranges_target, &c->docs,
+                       c->doc_pipe ? kDocSegs : kSegsMax);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
         if (own_scratch && scratch) cudaFree(scratch);
         if (e != cudaSuccess) return bail(cuda_fail(e, "token order sort"));
@@ -1346,14 +1357,6 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         for (int64_t w = V - 1; w >= 0; --w) c->word_ptr_h[w] = wstart[w] >= 0 ? wstart[w] : c->word_ptr_h[w + 1];
     }
     for (int64_t w = 0; w <= V; ++w) word_off[w] = (int32_t)c->word_ptr_h[w];
-    // dense rows live in shared memory: a few ranges per block slot, each
-    // long enough that its row load is a small part of it.
-    // Sparse rows live in global memory: ranges of ~4K tokens taken in
-    // order keep the rows that the resident blocks touch at once few enough
-    // to stay in L2.
-    const int ranges_target = c->sparse ? (1 << 30) : kRangesPerSm * c->sms;
-    build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->dregion, c->chunk, ranges_target, &c->docs,
-               c->doc_pipe ? kDocSegs : kSegsMax);
     // with tuning cluster_max_tokens, words too long for a block batch but
     // within a cluster's shared memory (or the cap) are sampled on a
     // thread-block cluster (up to 16 blocks where the device allows, else 8).

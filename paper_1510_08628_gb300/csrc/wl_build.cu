@@ -3,8 +3,9 @@
 // batches' lists of their tokens in word-major order.
 //
 //   word_check_kernel     the first token whose word id is outside [0, V).
-//   radix_count_kernel /  one pass of a stable LSD radix sort (8-bit digits)
-//   radix_scatter_kernel  of (word id, doc-major position) pairs: per-tile
+//   radix_count_kernel /  one pass of a stable LSD radix sort (digits of up
+//   radix_scatter_kernel  to 9 bits; two passes for up to 2^18 words) of
+//                         (word id, doc-major position) pairs: per-tile
 //                         digit counts, a device-wide exclusive scan in
 //                         digit-major order, then each tile writes its pairs
 //                         at their digit's offset plus their stable rank.
@@ -26,6 +27,8 @@ namespace wl {
 constexpr int kSortItems = 16;                      // items per thread of a tile
 constexpr int kSortTile = kThreads * kSortItems;    // 4096 pairs per tile
 constexpr int kScanChunk = kThreads * 16;           // entries per block of the scan
+constexpr int kDigitBitsMax = 9;
+constexpr int kBinsMax = 1 << kDigitBitsMax;
 
 // The first position whose word id is outside [0, V) goes to *bad
 // (initialised to INT_MAX by the caller).
@@ -44,20 +47,23 @@ __global__ void word_starts_kernel(const int32_t* __restrict__ keys, int64_t N, 
     }
 }
 
+// tile_cnt[digit * ntiles + tile] = the tile's keys with that digit.
 __global__ void __launch_bounds__(kThreads) radix_count_kernel(const int32_t* __restrict__ keys, int64_t n,
-                                                               int shift, int32_t* __restrict__ tile_cnt,
+                                                               int shift, int bits, int32_t* __restrict__ tile_cnt,
                                                                int64_t ntiles) {
-    __shared__ int h[256];
-    h[threadIdx.x] = 0;
+    __shared__ int h[kBinsMax];
+    const int nbins = 1 << bits;
+    const uint32_t mask = (uint32_t)nbins - 1u;
+    for (int d = threadIdx.x; d < nbins; d += kThreads) h[d] = 0;
     __syncthreads();
     const int64_t t0 = (int64_t)blockIdx.x * kSortTile;
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int64_t i = t0 + r * kThreads + threadIdx.x;
-        if (i < n) atomicAdd(&h[((uint32_t)keys[i] >> shift) & 255u], 1);
+        if (i < n) atomicAdd(&h[((uint32_t)keys[i] >> shift) & mask], 1);
     }
     __syncthreads();
-    tile_cnt[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    for (int d = threadIdx.x; d < nbins; d += kThreads) tile_cnt[(int64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
 // Exclusive scan of int32 data in place, in chunks of kScanChunk: chunk sums,
@@ -131,14 +137,18 @@ static int64_t scan_scratch(int64_t n) {
 // per-warp digit counts become per-warp bases by a scan over the warps, and
 // a per-digit running base carries across rounds.
 __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
-    const int32_t* __restrict__ kin, const int32_t* __restrict__ vin, int64_t n, int shift,
+    const int32_t* __restrict__ kin, const int32_t* __restrict__ vin, int64_t n, int shift, int bits,
     const int32_t* __restrict__ tile_off, int64_t ntiles, int32_t* __restrict__ kout, int32_t* __restrict__ vout) {
-    __shared__ int wc[kWarps][256];
-    __shared__ int wb[kWarps][256];
-    __shared__ int run[256];
+    __shared__ int wc[kWarps][kBinsMax];
+    __shared__ int wb[kWarps][kBinsMax];
+    __shared__ int run[kBinsMax];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int w = 0; w < kWarps; ++w) wc[w][tid] = 0;
-    run[tid] = tile_off[(int64_t)tid * ntiles + blockIdx.x];
+    const int nbins = 1 << bits;
+    const uint32_t mask = (uint32_t)nbins - 1u;
+    for (int d = tid; d < nbins; d += kThreads) {
+        for (int w = 0; w < kWarps; ++w) wc[w][d] = 0;
+        run[d] = tile_off[(int64_t)d * ntiles + blockIdx.x];
+    }
     __syncthreads();
     const int64_t t0 = (int64_t)blockIdx.x * kSortTile;
     const unsigned lt = (1u << lane) - 1u;
@@ -147,21 +157,21 @@ __global__ void __launch_bounds__(kThreads) radix_scatter_kernel(
         const bool ok = i < n;
         const int32_t key = ok ? kin[i] : 0;
         const int32_t val = ok ? (vin ? vin[i] : (int32_t)i) : 0;
-        const int d = ok ? (int)(((uint32_t)key >> shift) & 255u) : 256 + lane;   // padding matches nothing
+        const int d = ok ? (int)(((uint32_t)key >> shift) & mask) : nbins + lane;   // padding matches nothing
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
         const int wrank = __popc(peers & lt);
         if (ok && wrank == 0) wc[warp][d] = __popc(peers);
         __syncthreads();
-        {
-            int acc = run[tid];
+        for (int dd = tid; dd < nbins; dd += kThreads) {
+            int acc = run[dd];
 #pragma unroll
             for (int w = 0; w < kWarps; ++w) {
-                const int c = wc[w][tid];
-                wb[w][tid] = acc;
-                wc[w][tid] = 0;
+                const int c = wc[w][dd];
+                wb[w][dd] = acc;
+                wc[w][dd] = 0;
                 acc += c;
             }
-            run[tid] = acc;
+            run[dd] = acc;
         }
         __syncthreads();
         if (ok) {
@@ -223,7 +233,7 @@ __global__ void __launch_bounds__(kThreads) batch_lists_kernel(
 
 int64_t token_sort_scratch(int64_t N) {
     const int64_t ntiles = std::max<int64_t>(1, (N + kSortTile - 1) / kSortTile);
-    return 256 * ntiles + scan_scratch(256 * ntiles) + 4;
+    return kBinsMax * ntiles + scan_scratch(kBinsMax * ntiles) + 4;
 }
 
 cudaError_t launch_scan_exclusive(int32_t* d, int64_t n, int32_t* tmp, cudaStream_t st) {
@@ -249,11 +259,13 @@ cudaError_t launch_word_starts(const int32_t* keys_sorted, int64_t N, int32_t V,
     return cudaGetLastError();
 }
 
-int token_sort_passes(int64_t V) {
+static int key_bits(int64_t V) {
     int bits = 0;
     while (bits < 31 && ((int64_t)1 << bits) < V) ++bits;
-    return std::max(1, (bits + 7) / 8);
+    return std::max(1, bits);
 }
+
+int token_sort_passes(int64_t V) { return (key_bits(V) + kDigitBitsMax - 1) / kDigitBitsMax; }
 
 cudaError_t launch_token_sort(int32_t* keys_a, int32_t* vals_a, int32_t* keys_b, int32_t* vals_b, int64_t N,
                               int32_t V, int32_t* scratch, int32_t** pos_sorted, int32_t** keys_sorted,
@@ -264,18 +276,21 @@ cudaError_t launch_token_sort(int32_t* keys_a, int32_t* vals_a, int32_t* keys_b,
     if (N <= 0) return cudaSuccess;
     const int64_t ntiles = (N + kSortTile - 1) / kSortTile;
     const int passes = token_sort_passes(V);
+    // the key bits split evenly over the passes (the last takes what is left)
+    const int bits = (key_bits(V) + passes - 1) / passes;
     int32_t* tile = scratch;
-    int32_t* tmp = scratch + 256 * ntiles;
+    int32_t* tmp = scratch + kBinsMax * ntiles;
     const int32_t* kin = keys_a;
     const int32_t* vin = nullptr;   // first pass: values are the positions
     int32_t* kout = keys_b;
     int32_t* vout = vals_b;
     for (int p = 0; p < passes; ++p) {
-        radix_count_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(kin, N, 8 * p, tile, ntiles);
+        const int shift = bits * p, pb = std::min(bits, key_bits(V) - shift);
+        radix_count_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(kin, N, shift, pb, tile, ntiles);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        if ((e = scan_exclusive(tile, 256 * ntiles, tmp, st)) != cudaSuccess) return e;
-        radix_scatter_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(kin, vin, N, 8 * p, tile, ntiles, kout, vout);
+        if ((e = scan_exclusive(tile, ((int64_t)1 << pb) * ntiles, tmp, st)) != cudaSuccess) return e;
+        radix_scatter_kernel<<<(unsigned)ntiles, kThreads, 0, st>>>(kin, vin, N, shift, pb, tile, ntiles, kout, vout);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         *pos_sorted = vout;
         *keys_sorted = kout;

@@ -377,3 +377,26 @@ def test_device_token_order_build(kind, K, tuning):
     es, ei = _expected_batch_lists(c.doc_ptr.astype(np.int64), perm.astype(np.int64), batches.astype(np.int64))
     assert np.array_equal(sperm, es)
     assert np.array_equal(sinfo.astype(np.int64), ei)
+
+
+@pytest.mark.parametrize("V", [512, 513, 5000, 1 << 17, 1 << 18, (1 << 18) + 1, 1_000_000])
+def test_device_word_sort_digit_splits(V):
+    """The device word sort splits the key bits over passes of at most 9
+    bits (one pass up to 512 words, two up to 2^18, three beyond): word
+    offsets and perm equal the stable sort of the tokens by word, with word
+    ids across the whole range and many ties."""
+    rng = np.random.default_rng(V)
+    lens = rng.integers(0, 300, size=2000)
+    lens[::97] = 0
+    N = int(lens.sum())
+    spread = rng.integers(0, V, size=N)
+    heavy = rng.choice(np.array([0, 1, V // 2, V - 2, V - 1]), size=N)
+    doc_word = np.where(rng.random(N) < 0.4, heavy, spread).astype(np.int32)
+    c = corpus.Corpus(np.concatenate([[0], np.cumsum(lens)]).astype(np.int64), doc_word, V)
+    g = _gpu(c, V, 64, 0.3, 0.02, 2, 3)
+    wp, perm = g.token_order()
+    assert np.array_equal(wp, np.concatenate([[0], np.cumsum(np.bincount(c.doc_word, minlength=V))]))
+    want = np.empty(N, np.int64)
+    want[np.argsort(c.doc_word, kind="stable")] = np.arange(N)
+    assert np.array_equal(perm, want)
+    g.close()
