@@ -404,6 +404,9 @@ int warplda_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, const 
  * warplda_get_state and warplda_loglik report the record the same way.
  * Setting WARPLDA_SYNC_CHECK=1 in the environment before warplda_init makes
  * the context read the record after every launch (debugging; slow).
+ * Setting WARPLDA_TRACE_INIT=1 makes warplda_init wait for its stream at each
+ * stage boundary and print every stage's wall time to stderr (diagnostics:
+ * the waits serialise stages that init otherwise overlaps).
  */
 int warplda_sync(warplda_ctx* ctx);
 

@@ -1178,6 +1178,30 @@ int server_admit(warplda_server* s, const std::vector<int32_t>& active, int64_t*
     return WARPLDA_OK;
 }
 
+// WARPLDA_TRACE_INIT=1: warplda_init waits for the stream at each stage
+// boundary and prints the stage's wall time to stderr (diagnostics; the
+// waits serialise what init otherwise overlaps).
+struct InitTrace {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::chrono::steady_clock::time_point t0, last;
+    void start(cudaStream_t s) {
+        const char* v = std::getenv("WARPLDA_TRACE_INIT");
+        on = v && v[0] == '1';
+        st = s;
+        t0 = last = std::chrono::steady_clock::now();
+    }
+    void mark(const char* stage) {
+        if (!on) return;
+        cudaStreamSynchronize(st);
+        const auto now = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "warplda_init %-34s %9.2f ms  (at %9.2f ms)\n", stage,
+                     std::chrono::duration<double, std::milli>(now - last).count(),
+                     std::chrono::duration<double, std::milli>(now - t0).count());
+        last = now;
+    }
+};
+
 }  // namespace
 
 extern "C" {
@@ -1189,6 +1213,8 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
                  uint64_t seed, void* cuda_stream, const warplda_tuning* tuning) {
     if (!out) return fail(WARPLDA_EINVAL, "out is NULL");
     *out = nullptr;
+    InitTrace trace;
+    trace.start((cudaStream_t)cuda_stream);
     if (D < 0 || V < 1) return fail(WARPLDA_EINVAL, "need D >= 0 and V >= 1");
     if (N < 0 || N > (int64_t)0x7FFFFFF0) return fail(WARPLDA_EINVAL, "N must be in [0, 2^31 - 16]");
     if (V > (int64_t)0x7FFFFFF0 || D > (int64_t)0x7FFFFFF0) return fail(WARPLDA_EINVAL, "D, V too large");
@@ -1200,6 +1226,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     if (doc_ptr[0] != 0 || doc_ptr[D] != N) return fail(WARPLDA_EINVAL, "doc_ptr must run from 0 to N");
     for (int64_t d = 0; d < D; ++d)
         if (doc_ptr[d + 1] < doc_ptr[d]) return fail(WARPLDA_EINVAL, "doc_ptr decreases at %lld", (long long)d);
+    trace.mark("argument and CSR checks");
     warplda_ctx* c = new warplda_ctx();
     c->D = D; c->V = V; c->N = N; c->K = K; c->M = M;
     c->alpha = alpha; c->beta = beta;
@@ -1302,6 +1329,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     if ((rc = dalloc(c, &c->doc_off, D + 1, "alloc doc offsets"))) return bail(rc);
     if ((rc = dalloc(c, &c->word_off, V + 1, "alloc word offsets"))) return bail(rc);
     if ((rc = dalloc(c, &c->d_bad, 2, "alloc flag"))) return bail(rc);
+    trace.mark("token array allocation");
     // word ids go where pass 0 of the word sort reads them, so that the last
     // pass leaves the positions in prop (z and prop are rewritten at the end)
     const bool odd = token_sort_passes(V) % 2 == 1;
@@ -1329,6 +1357,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         int32_t* keys = nullptr;
         if (N > 0 && (e = cudaMemcpyAsync(ka, doc_word, (size_t)N * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
             return bail(cuda_fail(e, "upload word ids"));
+        trace.mark("upload of the word ids");
         if ((e = cudaMemcpyAsync(c->d_bad, init_bad, sizeof(init_bad), cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
             return bail(cuda_fail(e, "upload flag"));
         e = launch_word_check(ka, N, (int32_t)V, c->d_bad, c->st);
@@ -1339,6 +1368,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         else if (e == cudaSuccess) e = dev_malloc((void**)&scratch, (size_t)token_sort_scratch(N) * 4);
         if (e == cudaSuccess) e = launch_token_sort(ka, va, kb, vb, N, (int32_t)V, scratch, &pos, &keys, c->st);
         if (e == cudaSuccess && N > 0 && (pos != c->prop || keys != c->z)) e = cudaErrorInvalidValue;   // by the parity above
+        trace.mark("word check and word sort");
         if (e == cudaSuccess) e = launch_word_starts(keys, N, (int32_t)V, c->word_off, c->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(wstart.data(), c->word_off, (size_t)V * 4, cudaMemcpyDeviceToHost, c->st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(bad, c->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->st);
@@ -1347,6 +1377,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         if (e == cudaSuccess)
             build_tier(doc_off, D, K, c->dense, warp_max, c->dbmax, c->dregion, c->chunk, ranges_target, &c->docs,
                        c->doc_pipe ? kDocSegs : kSegsMax);
+        trace.mark("word starts; document tier (host)");
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
         if (own_scratch && scratch) cudaFree(scratch);
         if (e != cudaSuccess) return bail(cuda_fail(e, "token order sort"));
@@ -1387,6 +1418,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     build_tier(word_off, V, K, c->dense, 0, c->bmax, c->region, c->chunk, ranges_target, &c->words, kSegsMax,
                cluster_max, std::max(1, c->cluster_T));
 
+    trace.mark("word tier (host)");
     if ((rc = dalloc(c, &c->ck, K, "alloc c_k"))) return bail(rc);
     if ((rc = dalloc(c, &c->ckb, K, "alloc c_k float"))) return bail(rc);
     if ((rc = dalloc(c, &c->counters, kCounters, "alloc counters"))) return bail(rc);
@@ -1480,6 +1512,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
                 return bail(cuda_fail(e, "upload batch descriptors"));
         }
     }
+    trace.mark("count rows, tier uploads, descriptors");
     if ((e = cudaMemcpyAsync(c->doc_off, doc_off.data(), (D + 1) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
         return bail(cuda_fail(e, "upload doc offsets"));
     if ((e = cudaMemcpyAsync(c->word_off, word_off.data(), (V + 1) * 4, cudaMemcpyHostToDevice, c->st)) != cudaSuccess)
@@ -1489,6 +1522,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     {
         e = launch_perm(pos, N, c->perm, c->st);
         // padding past N is zero, as every array's tail is
+        trace.mark("perm");
         if (e == cudaSuccess) e = cudaMemsetAsync(c->perm + N, 0, 4 * 4, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->sperm, 0, ((size_t)N + 4) * 4, c->st);
         if (e == cudaSuccess) e = cudaMemsetAsync(c->sinfo, 0, ((size_t)N + 4) * 4, c->st);
@@ -1501,6 +1535,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
         if (e != cudaSuccess) return bail(cuda_fail(e, "token order build"));
         if (bad2 != 0x7FFFFFFF) return bail(fail(WARPLDA_EINVAL, "document batch %d malformed", bad2));
+        trace.mark("document batches' word-major lists");
     }
 
     // grids: persistent blocks, as many as fit
@@ -1547,6 +1582,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         return bail(cuda_fail(e, "init z"));
     if ((rc = recount(c))) return bail(rc);
     if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return bail(cuda_fail(e, "init"));
+    trace.mark("grids, initial z and c_k");
     *out = c;
     return WARPLDA_OK;
 }
