@@ -379,6 +379,25 @@ def test_device_token_order_build(kind, K, tuning):
     assert np.array_equal(sinfo.astype(np.int64), ei)
 
 
+def test_init_trace_reports_every_stage(capfd, monkeypatch):
+    """WARPLDA_TRACE_INIT=1: warplda_init prints one timed line per stage to
+    stderr, and the context it builds is the same as without the trace."""
+    c = _edge_corpus("mixed")
+    monkeypatch.setenv("WARPLDA_TRACE_INIT", "1")
+    g = _gpu(c, c.V, 50, 0.3, 0.02, 2, 11)
+    monkeypatch.delenv("WARPLDA_TRACE_INIT")
+    err = capfd.readouterr().err
+    stages = [ln for ln in err.splitlines() if ln.startswith("warplda_init ")]
+    assert len(stages) == 10, err
+    for name in ("word check and word sort", "perm", "grids, initial z and c_k"):
+        assert any(name in ln for ln in stages), (name, err)
+    ref = _gpu(c, c.V, 50, 0.3, 0.02, 2, 11)
+    assert "warplda_init " not in capfd.readouterr().err
+    for x, y in zip(g.get_state(), ref.get_state()):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+    g.close()
+    ref.close()
+
 @pytest.mark.parametrize("V", [512, 513, 5000, 1 << 17, 1 << 18, (1 << 18) + 1, 1_000_000])
 def test_device_word_sort_digit_splits(V):
     """The device word sort splits the key bits over passes of at most 9
