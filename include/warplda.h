@@ -43,6 +43,7 @@ extern "C" {
 #define WARPLDA_ESTATE (-5)    /* call not valid in the context's state */
 #define WARPLDA_EIO (-6)       /* checkpoint file could not be read or written */
 #define WARPLDA_EBUSY (-7)     /* no serving slot or pool memory free now: retry later */
+#define WARPLDA_EINTERNAL (-8) /* unexpected host-side failure (a library bug) */
 
 #define WARPLDA_PHASE_DOC 1
 #define WARPLDA_PHASE_WORD 2

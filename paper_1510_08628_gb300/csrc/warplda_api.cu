@@ -17,6 +17,8 @@
 #include <vector>
 #include <chrono>
 #include <map>
+#include <new>
+#include <stdexcept>
 #include <mutex>
 
 #include "../../include/warplda.h"
@@ -85,6 +87,39 @@ int cuda_fail(cudaError_t e, const char* what) {
         cudaError_t e_ = (call);                            \
         if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
     } while (0)
+
+// Host-side exceptions never cross the C ABI: every int-returning entry
+// point is a function-try-block ending in this handler, so a failed host
+// allocation comes back as ENOMEM (objects being built are freed by their
+// ScopeExit guards as the stack unwinds).
+#define WL_ABI_CATCH                                                        \
+    catch (const std::bad_alloc&) {                                         \
+        return fail(WARPLDA_ENOMEM, "host allocation failed");              \
+    }                                                                       \
+    catch (const std::length_error&) {                                      \
+        return fail(WARPLDA_ENOMEM, "host allocation too large");           \
+    }                                                                       \
+    catch (const std::exception& ex_) {                                     \
+        return fail(WARPLDA_EINTERNAL, "host-side failure: %s", ex_.what()); \
+    }                                                                       \
+    catch (...) {                                                           \
+        return fail(WARPLDA_EINTERNAL, "host-side failure");                \
+    }
+
+// Runs f when the scope ends unless disarmed: frees an object that is being
+// built when its construction is left early, by a return or an exception.
+template <class F>
+struct ScopeExit {
+    F f;
+    bool armed = true;
+    ~ScopeExit() {
+        if (armed) f();
+    }
+};
+template <class F>
+ScopeExit<F> on_exit(F f) {
+    return ScopeExit<F>{f};
+}
 
 enum KernelClass {
     kcDocWarp, kcDocBatch, kcDocHugeHist, kcDocHugeAccept, kcDocHugeDraw,
@@ -1210,7 +1245,7 @@ const char* warplda_last_error(void) { return g_err.c_str(); }
 
 int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64_t* doc_ptr,
                  const int32_t* doc_word, int32_t K, float alpha, float beta, int32_t M,
-                 uint64_t seed, void* cuda_stream, const warplda_tuning* tuning) {
+                 uint64_t seed, void* cuda_stream, const warplda_tuning* tuning) try {
     if (!out) return fail(WARPLDA_EINVAL, "out is NULL");
     *out = nullptr;
     InitTrace trace;
@@ -1228,6 +1263,10 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
         if (doc_ptr[d + 1] < doc_ptr[d]) return fail(WARPLDA_EINVAL, "doc_ptr decreases at %lld", (long long)d);
     trace.mark("argument and CSR checks");
     warplda_ctx* c = new warplda_ctx();
+    auto undo = on_exit([&] {
+        free_all(c);
+        delete c;
+    });
     c->D = D; c->V = V; c->N = N; c->K = K; c->M = M;
     c->alpha = alpha; c->beta = beta;
     c->abar = (float)K * alpha;   // one FP32 product each
@@ -1263,15 +1302,12 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     // the pipelined document kernel takes batches of up to 1021 tokens and
     // 128 documents; their hash tables need at most 4 words per token
     if (tuning && tuning->cluster_max_tokens < -1) {
-        delete c;
         return fail(WARPLDA_EINVAL, "cluster_max_tokens must be -1, 0 or positive");
     }
     if (tuning && (tuning->doc_batch_kernel < 0 || tuning->doc_batch_kernel > 2)) {
-        delete c;
         return fail(WARPLDA_EINVAL, "doc_batch_kernel must be 0, 1 or 2");
     }
     if (tuning && (tuning->foldin_kernel < 0 || tuning->foldin_kernel > 2)) {
-        delete c;
         return fail(WARPLDA_EINVAL, "foldin_kernel must be 0, 1 or 2");
     }
     c->foldin_word_major = !tuning || tuning->foldin_kernel != 1;
@@ -1297,7 +1333,6 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     // hit L2 (Sec. 5.2)
     int warp_max = 0;
     if (tuning && (tuning->word_positioning < 0 || tuning->word_positioning > 1)) {
-        delete c;
         return fail(WARPLDA_EINVAL, "word_positioning must be 0 or 1");
     }
     c->word_storage = (tuning && tuning->word_positioning == 1) ? 1 : 0;
@@ -1309,11 +1344,7 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     if (tuning && tuning->doc_warp_max > 0)
         warp_max = std::min(std::min(32 * c->warp_tpl, bmax), (int)tuning->doc_warp_max);
 
-    auto bail = [&](int rc) {
-        free_all(c);
-        delete c;
-        return rc;
-    };
+    auto bail = [](int rc) { return rc; };   // `undo` frees the context
     cudaError_t e = cudaGetDevice(&c->dev);
     if (e != cudaSuccess) return bail(cuda_fail(e, "cudaGetDevice"));
     e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev);
@@ -1583,11 +1614,12 @@ int warplda_init(warplda_ctx** out, int64_t D, int64_t V, int64_t N, const int64
     if ((rc = recount(c))) return bail(rc);
     if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return bail(cuda_fail(e, "init"));
     trace.mark("grids, initial z and c_k");
+    undo.armed = false;
     *out = c;
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
-int warplda_sweep(warplda_ctx* c, int32_t n) {
+int warplda_sweep(warplda_ctx* c, int32_t n) try {
     if (!c || n < 0) return fail(WARPLDA_EINVAL, "bad context or n");
     if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
@@ -1598,9 +1630,9 @@ int warplda_sweep(warplda_ctx* c, int32_t n) {
         if (rc) return rc;
     }
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
-int warplda_phase(warplda_ctx* c, int32_t phase) {
+int warplda_phase(warplda_ctx* c, int32_t phase) try {
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
     if (phase == WARPLDA_PHASE_DOC) {
@@ -1612,22 +1644,22 @@ int warplda_phase(warplda_ctx* c, int32_t phase) {
         return run_phase(c, false);
     }
     return fail(WARPLDA_EINVAL, "unknown phase %d", phase);
-}
+} WL_ABI_CATCH
 
 static int ensure_scratch(warplda_ctx* c) {
     if (c->scratch) return WARPLDA_OK;
     return dalloc(c, &c->scratch, c->N + 4, "alloc export scratch");
 }
 
-int warplda_counts_dev(warplda_ctx* c, int32_t* z_dev, int32_t* ck_dev) {
+int warplda_counts_dev(warplda_ctx* c, int32_t* z_dev, int32_t* ck_dev) try {
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
     if (z_dev) WL_CU(launch_gather_docmajor(c->z, c->perm, c->N, z_dev, c->st), "gather z");
     if (ck_dev) WL_CU(cudaMemcpyAsync(ck_dev, c->ck, (size_t)c->K * 4, cudaMemcpyDeviceToDevice, c->st), "copy c_k");
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
-int warplda_counts(warplda_ctx* c, int32_t* z_docmajor, int32_t* ck) {
+int warplda_counts(warplda_ctx* c, int32_t* z_docmajor, int32_t* ck) try {
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
     if (z_docmajor && c->N > 0) {
@@ -1652,9 +1684,9 @@ int warplda_counts(warplda_ctx* c, int32_t* z_docmajor, int32_t* ck) {
     if (ck) WL_CU(cudaMemcpyAsync(ck, c->ck, (size_t)c->K * 4, cudaMemcpyDeviceToHost, c->st), "copy c_k");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     return check_record(c, "counts");
-}
+} WL_ABI_CATCH
 
-int warplda_get_state(warplda_ctx* c, int32_t* z, int32_t* prop, int32_t* ck, uint32_t* sweeps) {
+int warplda_get_state(warplda_ctx* c, int32_t* z, int32_t* prop, int32_t* ck, uint32_t* sweeps) try {
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
     if (z && c->N) WL_CU(cudaMemcpyAsync(z, c->z, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->st), "copy z");
@@ -1663,9 +1695,9 @@ int warplda_get_state(warplda_ctx* c, int32_t* z, int32_t* prop, int32_t* ck, ui
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     if (sweeps) *sweeps = c->iter;
     return check_record(c, "state");
-}
+} WL_ABI_CATCH
 
-int warplda_set_state(warplda_ctx* c, const int32_t* z, const int32_t* prop, uint32_t sweeps) {
+int warplda_set_state(warplda_ctx* c, const int32_t* z, const int32_t* prop, uint32_t sweeps) try {
     if (!c || (c->N > 0 && (!z || !prop))) return fail(WARPLDA_EINVAL, "null argument");
     if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
@@ -1693,10 +1725,10 @@ int warplda_set_state(warplda_ctx* c, const int32_t* z, const int32_t* prop, uin
     c->iter = sweeps;
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
 int warplda_doc_batches(warplda_ctx* c, int64_t* n_batches, int32_t* batches, int32_t* sperm,
-                        uint32_t* sinfo) {
+                        uint32_t* sinfo) try {
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
     if (n_batches) *n_batches = (int64_t)(c->docs.batches[0].size() + c->docs.batches[1].size());
@@ -1714,9 +1746,9 @@ int warplda_doc_batches(warplda_ctx* c, int64_t* n_batches, int32_t* batches, in
         WL_CU(cudaMemcpyAsync(sinfo, c->sinfo, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->st), "copy lists");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
-int warplda_token_order(warplda_ctx* c, int64_t* word_ptr, int32_t* perm) {
+int warplda_token_order(warplda_ctx* c, int64_t* word_ptr, int32_t* perm) try {
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
     if (word_ptr) std::memcpy(word_ptr, c->word_ptr_h.data(), (size_t)(c->V + 1) * 8);
@@ -1725,9 +1757,9 @@ int warplda_token_order(warplda_ctx* c, int64_t* word_ptr, int32_t* perm) {
         WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     }
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
-int warplda_loglik(warplda_ctx* c, double* out) {
+int warplda_loglik(warplda_ctx* c, double* out) try {
     if (!c || !out) return fail(WARPLDA_EINVAL, "null argument");
     if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
@@ -1763,7 +1795,7 @@ int warplda_loglik(warplda_ctx* c, double* out) {
     WL_CU(cudaMemcpyAsync(out, c->d_ll, sizeof(double), cudaMemcpyDeviceToHost, c->st), "copy loglik");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     return check_record(c, "loglik");
-}
+} WL_ABI_CATCH
 
 struct CkptHeader {
     char magic[8];
@@ -1774,7 +1806,7 @@ struct CkptHeader {
     uint32_t iter, pad;
 };
 
-int warplda_save(warplda_ctx* c, const char* path) {
+int warplda_save(warplda_ctx* c, const char* path) try {
     if (!c || !path) return fail(WARPLDA_EINVAL, "null argument");
     std::vector<int32_t> z((size_t)c->N), p((size_t)c->N * c->M);
     uint32_t it = 0;
@@ -1791,9 +1823,9 @@ int warplda_save(warplda_ctx* c, const char* path) {
               std::fwrite(p.data(), 4, p.size(), f) == p.size();
     ok = (std::fclose(f) == 0) && ok;
     return ok ? WARPLDA_OK : fail(WARPLDA_EIO, "write to %s failed", path);
-}
+} WL_ABI_CATCH
 
-int warplda_load(warplda_ctx* c, const char* path) {
+int warplda_load(warplda_ctx* c, const char* path) try {
     if (!c || !path) return fail(WARPLDA_EINVAL, "null argument");
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(WARPLDA_EIO, "cannot open %s", path);
@@ -1813,9 +1845,9 @@ int warplda_load(warplda_ctx* c, const char* path) {
     std::fclose(f);
     if (!ok) return fail(WARPLDA_EIO, "%s is truncated", path);
     return warplda_set_state(c, z.data(), p.data(), h.iter);
-}
+} WL_ABI_CATCH
 
-int warplda_get_info(warplda_ctx* c, warplda_info* o) {
+int warplda_get_info(warplda_ctx* c, warplda_info* o) try {
     if (!c || !o) return fail(WARPLDA_EINVAL, "null argument");
     std::memset(o, 0, sizeof(*o));
     o->D = c->D; o->V = c->V; o->N = c->N; o->K = c->K; o->M = c->M;
@@ -1835,9 +1867,9 @@ int warplda_get_info(warplda_ctx* c, warplda_info* o) {
     // class and the warp tier
     o->pipe_doc_tokens = c->doc_pipe ? c->N - c->docs.row_tokens - c->docs.large_tokens - c->docs.warp_tokens : 0;
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
-int warplda_profile(warplda_ctx* c, int32_t enable) {
+int warplda_profile(warplda_ctx* c, int32_t enable) try {
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     for (auto& r : c->recs) {
         cudaEventDestroy(r.a);
@@ -1846,10 +1878,10 @@ int warplda_profile(warplda_ctx* c, int32_t enable) {
     c->recs.clear();
     c->prof = enable != 0;
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
 int warplda_kernel_times(warplda_ctx* c, int32_t cap, const char** names, int64_t* launches,
-                         double* total_ms) {
+                         double* total_ms) try {
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     double ms[kcCount] = {0};
@@ -1871,11 +1903,11 @@ int warplda_kernel_times(warplda_ctx* c, int32_t cap, const char** names, int64_
         ++k;
     }
     return k;
-}
+} WL_ABI_CATCH
 
 int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
                    const int64_t* doc_ids, int32_t sweeps, uint64_t seed, int32_t proposal,
-                   float* theta_out, int32_t* z_out) {
+                   float* theta_out, int32_t* z_out) try {
     if (!c || !doc_ptr || Dn < 0 || sweeps < 0) return fail(WARPLDA_EINVAL, "bad fold-in arguments");
     if (proposal != WARPLDA_PROPOSAL_PLAIN && proposal != WARPLDA_PROPOSAL_LEARNED)
         return fail(WARPLDA_EINVAL, "unknown proposal %d", proposal);
@@ -2053,9 +2085,9 @@ int warplda_foldin(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int
         WL_CU(cudaMemcpyAsync(theta_out, d_theta, (size_t)Dn * K * 4, cudaMemcpyDeviceToHost, c->st), "copy theta");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     return check_record(c, "fold-in");
-}
+} WL_ABI_CATCH
 
-int warplda_word_counts(warplda_ctx* c, int32_t* cw) {
+int warplda_word_counts(warplda_ctx* c, int32_t* cw) try {
     if (!c || !cw) return fail(WARPLDA_EINVAL, "null argument");
     if (c->K > kDenseRowMaxK) return fail(WARPLDA_EINVAL, "dense C_w needs K <= %d", kDenseRowMaxK);
     if (c->doc_done) return fail(WARPLDA_ESTATE, "a word phase is pending");
@@ -2065,7 +2097,7 @@ int warplda_word_counts(warplda_ctx* c, int32_t* cw) {
     WL_CU(cudaMemcpyAsync(cw, c->model_cw, (size_t)c->V * c->K * 4, cudaMemcpyDeviceToHost, c->st), "copy C_w");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     return check_record(c, "word counts");
-}
+} WL_ABI_CATCH
 
 static uint64_t splitmix64(uint64_t* x) {
     uint64_t z = (*x += 0x9E3779B97F4A7C15ull);
@@ -2077,7 +2109,7 @@ static uint64_t splitmix64(uint64_t* x) {
 static float unit_uniform(uint64_t* x) { return (float)((splitmix64(x) >> 40) * (1.0 / 16777216.0)); }
 
 int warplda_encoder_init(warplda_ctx* c, int32_t log2_features, int32_t hidden, int32_t batch_rows,
-                         uint64_t seed) {
+                         uint64_t seed) try {
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     auto& e = c->enc;
     if (e.ready) return fail(WARPLDA_ESTATE, "the encoder is already initialised");
@@ -2133,9 +2165,9 @@ int warplda_encoder_init(warplda_ctx* c, int32_t log2_features, int32_t hidden, 
     e.step = 0;
     e.ready = true;
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
-int warplda_encoder_weights(warplda_ctx* c, int32_t set, float* W1, float* b1, float* W2, float* b2) {
+int warplda_encoder_weights(warplda_ctx* c, int32_t set, float* W1, float* b1, float* W2, float* b2) try {
     if (!c || !W1 || !b1 || !W2 || !b2) return fail(WARPLDA_EINVAL, "null argument");
     auto& e = c->enc;
     if (!e.ready) return fail(WARPLDA_ESTATE, "the encoder is not initialised");
@@ -2163,10 +2195,10 @@ int warplda_encoder_weights(warplda_ctx* c, int32_t set, float* W1, float* b1, f
     for (int64_t j = 0; j < H; ++j)
         for (int64_t k = 0; k < K; ++k) W2[j * K + k] = w2t[k * H + j];
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
 int warplda_encoder_grad(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
-                         const float* theta, double* loss, float* gW1, float* gb1, float* gW2, float* gb2) {
+                         const float* theta, double* loss, float* gW1, float* gb1, float* gW2, float* gb2) try {
     if (!c || !theta || !loss || !gW1 || !gb1 || !gW2 || !gb2) return fail(WARPLDA_EINVAL, "null argument");
     auto& e = c->enc;
     if (!e.ready) return fail(WARPLDA_ESTATE, "the encoder is not initialised");
@@ -2197,9 +2229,9 @@ int warplda_encoder_grad(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, con
     for (int64_t j = 0; j < H; ++j)
         for (int64_t k = 0; k < K; ++k) gW2[j * K + k] = g2[k * H + j];
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
-int warplda_encoder_train(warplda_ctx* c, int32_t epochs, float lr, uint64_t seed, double* epoch_loss) {
+int warplda_encoder_train(warplda_ctx* c, int32_t epochs, float lr, uint64_t seed, double* epoch_loss) try {
     if (!c || epochs < 0 || !(lr > 0.0f)) return fail(WARPLDA_EINVAL, "bad training arguments");
     auto& e = c->enc;
     if (!e.ready) return fail(WARPLDA_ESTATE, "the encoder is not initialised");
@@ -2237,10 +2269,10 @@ int warplda_encoder_train(warplda_ctx* c, int32_t epochs, float lr, uint64_t see
         if (epoch_loss) epoch_loss[ep] = nb ? l / (double)nb : 0.0;
     }
     return check_record(c, "encoder training");
-}
+} WL_ABI_CATCH
 
 int warplda_encoder_proposal(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr, const int32_t* doc_word,
-                             float* q_out) {
+                             float* q_out) try {
     if (!c || !q_out) return fail(WARPLDA_EINVAL, "null argument");
     if (!c->enc.ready) return fail(WARPLDA_ESTATE, "the encoder is not initialised");
     int rc = check_docs(c, Dn, doc_ptr, doc_word);
@@ -2256,10 +2288,10 @@ int warplda_encoder_proposal(warplda_ctx* c, int64_t Dn, const int64_t* doc_ptr,
         WL_CU(cudaMemcpyAsync(q_out, q, (size_t)Dn * c->K * 4, cudaMemcpyDeviceToHost, c->st), "copy proposals");
     WL_CU(cudaStreamSynchronize(c->st), "synchronize");
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
 int warplda_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, const float* bias_dev,
-                      int32_t M, int32_t N, int32_t K, void* cuda_stream) {
+                      int32_t M, int32_t N, int32_t K, void* cuda_stream) try {
     if (!A_dev || !B_dev || !C_dev) return fail(WARPLDA_EINVAL, "null matrix pointer");
     if (M < 0 || N < 0 || K < 0 || M % 128 || N % 128 || K % 64)
         return fail(WARPLDA_EINVAL, "GEMM needs M, N multiples of 128 and K a multiple of 64");
@@ -2288,11 +2320,11 @@ int warplda_gemm_bf16(const void* A_dev, const void* B_dev, float* C_dev, const 
     if (e != cudaSuccess) return cuda_fail(e, "GEMM");
     if (h) return fail(WARPLDA_ETIMEDOUT, "GEMM: a tensor-core wait ran out");
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
 
 int warplda_server_create(warplda_ctx* c, int32_t slots, int64_t pool_tokens, int32_t max_doc_tokens,
-                          int32_t sweeps, uint64_t seed, int32_t proposal, warplda_server** out) {
+                          int32_t sweeps, uint64_t seed, int32_t proposal, warplda_server** out) try {
     if (!c || !out) return fail(WARPLDA_EINVAL, "null argument");
     *out = nullptr;
     if (slots < 1 || slots > (1 << 20) || pool_tokens < 1 || pool_tokens > (int64_t)0x7FFFFFF0 || sweeps < 1 ||
@@ -2310,6 +2342,10 @@ int warplda_server_create(warplda_ctx* c, int32_t slots, int64_t pool_tokens, in
     int rc = ensure_model(c);
     if (rc) return rc;
     auto* s = new warplda_server();
+    auto undo = on_exit([&] {
+        server_free(s);
+        delete s;
+    });
     s->c = c;
     s->nslots = slots;
     s->pool_tokens = pool_tokens;
@@ -2318,11 +2354,7 @@ int warplda_server_create(warplda_ctx* c, int32_t slots, int64_t pool_tokens, in
     s->seed = seed;
     s->proposal = proposal;
     const int K = c->K, M = c->M;
-    auto bail = [&](int code) {
-        server_free(s);
-        delete s;
-        return code;
-    };
+    auto bail = [](int code) { return code; };   // `undo` frees the server
     if ((rc = salloc(s, &s->d_info, slots)) || (rc = salloc(s, &s->d_active, slots)) ||
         (rc = salloc(s, &s->d_z, pool_tokens + 4)) || (rc = salloc(s, &s->d_prop, (pool_tokens + 4) * M)) ||
         (rc = salloc(s, &s->d_words, pool_tokens + 4)) || (rc = salloc(s, &s->d_counter, 8)) ||
@@ -2350,11 +2382,12 @@ int warplda_server_create(warplda_ctx* c, int32_t slots, int64_t pool_tokens, in
     const int per_sm = foldin_blocks_per_sm(K, M, s->tab_words);
     if (per_sm < 1) return bail(fail(WARPLDA_EINVAL, "serving tables do not fit in shared memory"));
     s->grid = per_sm * c->sms;
+    undo.armed = false;
     *out = s;
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
-int warplda_server_submit(warplda_server* s, int64_t id, int32_t L, const int32_t* words) {
+int warplda_server_submit(warplda_server* s, int64_t id, int32_t L, const int32_t* words) try {
     if (!s || L < 0 || (L > 0 && !words)) return fail(WARPLDA_EINVAL, "bad request");
     warplda_ctx* c = s->c;
     if (L > s->max_tokens) return fail(WARPLDA_EINVAL, "request longer than max_doc_tokens");
@@ -2377,9 +2410,9 @@ int warplda_server_submit(warplda_server* s, int64_t id, int32_t L, const int32_
     s->new_ptr.push_back((int64_t)s->new_words.size());
     s->new_req.push_back(make_int4(sl, (int)off, L, (int)(uint32_t)id));
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
-int warplda_server_step(warplda_server* s, int32_t* active_out) {
+int warplda_server_step(warplda_server* s, int32_t* active_out) try {
     if (!s) return fail(WARPLDA_EINVAL, "null server");
     warplda_ctx* c = s->c;
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
@@ -2478,10 +2511,10 @@ int warplda_server_step(warplda_server* s, int32_t* active_out) {
     s->n_fin_staged = nfin;
     WL_CU(cudaEventRecord(s->tick, c->st), "record tick");
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
 int warplda_server_poll(warplda_server* s, int32_t max_results, int64_t* ids, float* theta, int32_t* n_out,
-                        int32_t timeout_ms) {
+                        int32_t timeout_ms) try {
     if (!s || !n_out || max_results < 0 || (max_results > 0 && (!ids || !theta)))
         return fail(WARPLDA_EINVAL, "bad poll arguments");
     *n_out = 0;
@@ -2514,7 +2547,7 @@ int warplda_server_poll(warplda_server* s, int32_t max_results, int64_t* ids, fl
     s->n_fin_staged = 0;
     *n_out = n;
     return WARPLDA_OK;
-}
+} WL_ABI_CATCH
 
 void warplda_server_destroy(warplda_server* s) {
     if (!s) return;
@@ -2524,11 +2557,11 @@ void warplda_server_destroy(warplda_server* s) {
     delete s;
 }
 
-int warplda_sync(warplda_ctx* c) {
+int warplda_sync(warplda_ctx* c) try {
     if (!c) return fail(WARPLDA_EINVAL, "null context");
     WL_CU(cudaSetDevice(c->dev), "cudaSetDevice");
     return check_record(c, "sync");
-}
+} WL_ABI_CATCH
 
 void warplda_destroy(warplda_ctx* c) {
     if (!c) return;

@@ -17,6 +17,7 @@ import numpy as np
 from . import _build
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEDOUT, ESTATE, EIO = 0, -1, -2, -3, -4, -5, -6
+EINTERNAL = -8
 PHASE_DOC, PHASE_WORD = 1, 2
 
 _LOCK = threading.Lock()
