@@ -146,7 +146,7 @@ extern "C" int warplda_loglik_noalloc(int64_t D, int64_t V, int64_t N, int32_t K
                                       float beta, const int64_t* doc_ptr_dev,
                                       const int32_t* z_docmajor_dev, const int64_t* word_ptr_dev,
                                       const int32_t* z_wordmajor_dev, double* out_dev,
-                                      void* cuda_stream) {
+                                      void* cuda_stream) try {
     if (D < 0 || V < 1 || N < 0 || N > (int64_t)0x7FFFFFF0)
         return na_fail(WARPLDA_EINVAL, "need D >= 0, V >= 1 and 0 <= N < 2^31");
     if (K < 1 || K > kNaMaxK)
@@ -177,4 +177,7 @@ extern "C" int warplda_loglik_noalloc(int64_t D, int64_t V, int64_t N, int32_t K
     }
     if (e != cudaSuccess) return na_fail(WARPLDA_ECUDA, std::string("warplda_loglik_noalloc: ") + cudaGetErrorString(e));
     return WARPLDA_OK;
+} catch (...) {
+    // only the error messages allocate on the host; no exception crosses the C ABI
+    return wl::record_error(WARPLDA_ENOMEM, "warplda_loglik_noalloc: host allocation failed");
 }
