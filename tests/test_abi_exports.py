@@ -35,3 +35,15 @@ def test_binding_raises_without_context():
     lib = warplda.load()
     assert lib.warplda_sweep(None, 1) == warplda.EINVAL
     assert b"context" in lib.warplda_last_error()
+
+
+def test_error_codes_match_the_header():
+    """The binding's error constants are the header's WARPLDA_* codes."""
+    from paper_1510_08628_gb300 import warplda
+    src = open(os.path.join(ROOT, "include", "warplda.h")).read()
+    codes = {m.group(1): int(m.group(2))
+             for m in re.finditer(r"#define WARPLDA_(OK|E[A-Z]+) \(?(-?\d+)\)?", src)}
+    assert {"OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEDOUT", "ESTATE", "EIO", "EBUSY", "EINTERNAL"} <= set(codes)
+    for name, value in codes.items():
+        assert getattr(warplda, name) == value, name
+    assert len(set(codes.values())) == len(codes)
